@@ -1,0 +1,286 @@
+"""Seeded synthetic inputs for the extended convolution/correlation workloads.
+
+This module only draws data: images, transformation fields, filter
+coefficients, template images and planted positions/angles.  It holds none of
+the method's arithmetic (no filter decomposition, no steering, no transform of
+a filter by a group element); both the CUDA path and the CPU oracle consume
+what it returns, and each computes everything else on its own.
+
+Seeds follow ``13188 * 10 + workload`` so that every workload is reproducible
+from its number alone.  Workload numbering:
+
+1. SO(2) extended convolution, 256 x 256, analytic filter with |k| <= 4.
+2. SO(2) rotation-independent pattern matching, 2048 x 2048, 20 planted
+   65 x 65 templates, |k| <= 16, 64 sweep angles.
+3. Scale-adaptive smoothing, Voronoi image with block noise, scale field in
+   [1, 8] px (see :func:`scale_smoothing_problem`).
+4. Batched uneven SO(2) correlation (see :func:`batched_descriptors`).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import ndimage
+
+SEED_BASE = 13188 * 10
+
+
+def seed_for(workload: int) -> int:
+    return SEED_BASE + int(workload)
+
+
+# ---------------------------------------------------------------- helpers ---
+
+def periodic_gaussian_blur(img: np.ndarray, sigma: float) -> np.ndarray:
+    """Gaussian blur with wrap-around boundaries (input preparation only)."""
+    return ndimage.gaussian_filter(np.asarray(img, np.float64), sigma, mode="wrap")
+
+
+def smooth_random_template(rng: np.random.Generator, radius: int, blur: float,
+                           taper: float = 4.0) -> np.ndarray:
+    """(2R+1)^2 random smooth template: N(0,1) on a canvas padded by 4*blur,
+    Gaussian blur, centre crop, then a raised-cosine taper to zero on
+    r in [R - taper, R] (zero for r >= R)."""
+    side = 2 * radius + 1
+    pad = int(math.ceil(4 * blur))
+    canvas = rng.standard_normal((side + 2 * pad, side + 2 * pad))
+    canvas = ndimage.gaussian_filter(canvas, blur, mode="reflect")
+    t = canvas[pad:pad + side, pad:pad + side].copy()
+    yy, xx = np.mgrid[-radius:radius + 1, -radius:radius + 1]
+    r = np.hypot(xx, yy)
+    w = np.where(r <= radius - taper, 1.0,
+                 np.where(r >= radius, 0.0,
+                          0.5 * (1 + np.cos(np.pi * (r - (radius - taper)) / taper))))
+    return t * w
+
+
+def _place_centres(rng, h, w, n, min_sep, margin=0):
+    """Seeded rejection sampling of n integer centres whose torus distance is
+    at least ``min_sep``."""
+    centres = []
+    tries = 0
+    while len(centres) < n:
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("could not place centres")
+        cy = int(rng.integers(margin, h - margin)) if h > 2 * margin else int(rng.integers(0, h))
+        cx = int(rng.integers(margin, w - margin)) if w > 2 * margin else int(rng.integers(0, w))
+        ok = True
+        for (py, px) in centres:
+            dy = min(abs(cy - py), h - abs(cy - py))
+            dx = min(abs(cx - px), w - abs(cx - px))
+            if math.hypot(dx, dy) < min_sep:
+                ok = False
+                break
+        if ok:
+            centres.append((cy, cx))
+    return np.array(centres, dtype=np.int64).reshape(-1, 2)
+
+
+def plant_rotated(img: np.ndarray, template: np.ndarray, centre, beta: float) -> None:
+    """Add a copy of ``template`` rotated by ``beta`` (radians, counter-clockwise
+    in (x = column, y = row) coordinates) centred on ``centre`` = (row, col),
+    wrapping periodically.  The copy at offset d is the template sampled at
+    R(-beta) d with scipy's cubic spline; this is data generation, unrelated
+    to the filter model either side builds from the template."""
+    radius = template.shape[0] // 2
+    h, w = img.shape
+    dy, dx = np.mgrid[-radius:radius + 1, -radius:radius + 1].astype(np.float64)
+    c, s = math.cos(beta), math.sin(beta)
+    sx = c * dx + s * dy
+    sy = -s * dx + c * dy
+    vals = ndimage.map_coordinates(template, [sy + radius, sx + radius], order=3,
+                                   mode="constant", cval=0.0)
+    rows = (centre[0] + dy.astype(np.int64)) % h
+    cols = (centre[1] + dx.astype(np.int64)) % w
+    np.add.at(img, (rows, cols), vals)
+
+
+# ------------------------------------------------------------- workload 1 ---
+
+def so2_conv_problem(seed: int | None = None, size: int = 256, K: int = 4,
+                     sigma: float = 6.0, radius: int = 15):
+    """SO(2) extended convolution input.
+
+    * H: size^2 uniform[0,1] noise, periodic Gaussian blur sigma = 2 px, float32.
+    * a_k (k = -K..K, stored at index k+K): a_0 ~ N(0,1) real,
+      a_k = (N + iN)/sqrt(2) for k >= 1, a_{-k} = conj(a_k) (real filter).
+    * alpha: sum of 4 sinusoids sum_i A_i sin(2 pi (u_i x + v_i y)/size + phi_i),
+      integer (u_i, v_i) in [-3,3]^2 minus the origin, A_i ~ U[0, pi],
+      phi_i ~ U[0, 2 pi), reduced mod 2 pi, float32.
+    """
+    rng = np.random.default_rng(seed_for(1) if seed is None else seed)
+    H = periodic_gaussian_blur(rng.uniform(0.0, 1.0, (size, size)), 2.0).astype(np.float32)
+    a = np.zeros(2 * K + 1, np.complex128)
+    a[K] = rng.standard_normal()
+    for k in range(1, K + 1):
+        a[K + k] = (rng.standard_normal() + 1j * rng.standard_normal()) / math.sqrt(2)
+        a[K - k] = np.conj(a[K + k])
+    alpha = _angle_field(rng, size, size)
+    return dict(H=H, alpha=alpha, a=a, sigma=sigma, radius=radius, K=K)
+
+
+def _angle_field(rng, h, w, n_terms=4):
+    yy, xx = np.mgrid[0:h, 0:w].astype(np.float64)
+    field = np.zeros((h, w))
+    for _ in range(n_terms):
+        while True:
+            u, v = rng.integers(-3, 4, size=2)
+            if u != 0 or v != 0:
+                break
+        A = rng.uniform(0, math.pi)
+        phi = rng.uniform(0, 2 * math.pi)
+        field += A * np.sin(2 * math.pi * (u * xx / w + v * yy / h) + phi)
+    return np.mod(field, 2 * math.pi).astype(np.float32)
+
+
+def random_angle_field(seed: int, h: int, w: int) -> np.ndarray:
+    """Low-frequency angle field in [0, 2 pi), float32 (same recipe as workload 1)."""
+    return _angle_field(np.random.default_rng(seed), h, w)
+
+
+def random_gauss_pow_coeffs(seed: int, K: int) -> np.ndarray:
+    """Hermitian-symmetric a_k, k = -K..K at index k+K (real filter)."""
+    rng = np.random.default_rng(seed)
+    a = np.zeros(2 * K + 1, np.complex128)
+    a[K] = rng.standard_normal()
+    for k in range(1, K + 1):
+        a[K + k] = (rng.standard_normal() + 1j * rng.standard_normal()) / math.sqrt(2)
+        a[K - k] = np.conj(a[K + k])
+    return a
+
+
+# ------------------------------------------------------------- workload 2 ---
+
+def so2_match_problem(seed: int | None = None, size: int | tuple = 2048, n_plant: int = 20,
+                      radius: int = 32, K: int = 16, J: int = 64,
+                      noise_sigma: float = 0.1, blur: float = 3.0):
+    """Rotation-independent pattern matching input.
+
+    * template: (2R+1)^2 smooth random template (N(0,1), blur sigma = 3 px,
+      taper to zero on r in [R-4, R]), float64.
+    * H: Gaussian noise sigma = 0.1 plus ``n_plant`` copies of the template
+      rotated by beta ~ U[0, 2 pi) at centres at least 2R+1 apart, float32.
+    * The filter is the template's angular band-limit |k| <= K, polar-sampled
+      at dr = 0.25 px with 128 angles; J sweep angles alpha_j = 2 pi j / J.
+    """
+    rng = np.random.default_rng(seed_for(2) if seed is None else seed)
+    h, w = (size, size) if np.isscalar(size) else size
+    template = smooth_random_template(rng, radius, blur)
+    H = rng.normal(0.0, noise_sigma, (h, w))
+    centres = _place_centres(rng, h, w, n_plant, 2 * radius + 1)
+    betas = rng.uniform(0.0, 2 * math.pi, n_plant)
+    for c, b in zip(centres, betas):
+        plant_rotated(H, template, c, b)
+    return dict(H=H.astype(np.float32), template=template, centres=centres, betas=betas,
+                radius=radius, K=K, J=J, dr=0.25, n_theta=128)
+
+
+# ------------------------------------------------------------- workload 4 ---
+
+def batched_descriptors(seed: int | None = None, n_images: int = 512,
+                        sides=tuple(range(128, 1025, 64)),
+                        template_sizes=tuple(range(33, 98, 2)),
+                        Ks=(4, 8, 16), Js=tuple(range(32, 129, 4))):
+    """Per-image (h, w, template side, K, J, image seed) for the batched
+    uneven workload; images are drawn lazily with :func:`batched_image`."""
+    rng = np.random.default_rng(seed_for(4) if seed is None else seed)
+    out = []
+    for i in range(n_images):
+        h = int(rng.choice(sides))
+        w = int(rng.choice(sides))
+        ts = int(rng.choice(template_sizes))
+        K = int(rng.choice(Ks))
+        J = int(rng.choice(Js))
+        out.append(dict(h=h, w=w, side=ts, radius=(ts - 1) // 2, K=K, J=J,
+                        seed=int(rng.integers(0, 2**31 - 1))))
+    return out
+
+
+def batched_image(desc: dict, noise_sigma: float = 0.1, blur: float = 3.0):
+    """One image of the batched workload: noise + one planted template."""
+    rng = np.random.default_rng(desc["seed"])
+    R = desc["radius"]
+    template = smooth_random_template(rng, R, blur)
+    H = rng.normal(0.0, noise_sigma, (desc["h"], desc["w"]))
+    centre = (int(rng.integers(0, desc["h"])), int(rng.integers(0, desc["w"])))
+    beta = float(rng.uniform(0, 2 * math.pi))
+    plant_rotated(H, template, centre, beta)
+    return dict(H=H.astype(np.float32), template=template, centres=np.array([centre]),
+                betas=np.array([beta]), radius=R, K=desc["K"], J=desc["J"], dr=0.25,
+                n_theta=128)
+
+
+# ------------------------------------------------------------- workload 3 ---
+
+def mellin_gaussian_coeffs(n_h: int = 24, log_period: float = 8.0,
+                           u_lo: float = -math.log(8.0), u_hi: float = math.log(64.0),
+                           ridge: float = 1e-10, n_fit: int = 4001):
+    """Filter design for scale-adaptive smoothing: coefficients c_k,
+    k = 0..n_h-1 (c_{-k} = conj(c_k)), of P(u) = sum_k c_k exp(i w_k u),
+    w_k = 2 pi k / log_period, least-squares fitted (ridge ``ridge``) to the
+    unit Gaussian profile exp(-e^{2u}/2) on u in [u_lo, u_hi].  With
+    u = ln r - ln s this gives exp(-r^2 / (2 s^2)).  Returns complex128 (n_h,)."""
+    u = np.linspace(u_lo, u_hi, n_fit)
+    target = np.exp(-np.exp(2 * u) / 2)
+    w = 2 * math.pi * np.arange(n_h) / log_period
+    cols = [np.ones_like(u)]
+    for k in range(1, n_h):
+        cols += [np.cos(w[k] * u), np.sin(w[k] * u)]
+    A = np.stack(cols, axis=1)
+    coef = np.linalg.solve(A.T @ A + ridge * np.eye(A.shape[1]), A.T @ target)
+    c = np.zeros(n_h, np.complex128)
+    c[0] = coef[0]
+    for k in range(1, n_h):
+        # 2 Re(c_k e^{iwu}) = 2 Re(c_k) cos - 2 Im(c_k) sin
+        c[k] = 0.5 * (coef[2 * k - 1] - 1j * coef[2 * k])
+    return c
+
+
+def voronoi_image(rng, h, w, n_cells=500, block=8, noise=0.05):
+    """Piecewise-constant colour image (3, h, w): torus Voronoi cells with
+    U[0,1]^3 colours plus a per-block, per-channel offset U[-noise, noise]."""
+    from scipy.spatial import cKDTree
+    seeds = rng.uniform(0, 1, (n_cells, 2)) * np.array([h, w])
+    colours = rng.uniform(0, 1, (n_cells, 3))
+    tree = cKDTree(seeds, boxsize=[h, w])
+    img = np.empty((3, h, w), np.float32)
+    rows_per = max(1, (1 << 22) // w)
+    xs = np.arange(w) + 0.5
+    for y0 in range(0, h, rows_per):
+        y1 = min(h, y0 + rows_per)
+        yy, xx = np.meshgrid(np.arange(y0, y1) + 0.5, xs, indexing="ij")
+        _, lab = tree.query(np.stack([yy.ravel(), xx.ravel()], 1), k=1)
+        img[:, y0:y1, :] = colours[lab].T.reshape(3, y1 - y0, w)
+    bh, bw = -(-h // block), -(-w // block)
+    offs = rng.uniform(-noise, noise, (3, bh, bw))
+    img += np.repeat(np.repeat(offs, block, axis=1), block, axis=2)[:, :h, :w]
+    return img
+
+
+def scale_field_from_image(img, s_min=1.0, s_max=8.0, blur=4.0):
+    """s = s_max - (s_max - s_min) * clip(m / p99(m), 0, 1), m = Gaussian
+    blur (sigma 4, wrap) of the central-difference gradient magnitude of the
+    channel mean.  Small scale at strong edges, large in flat regions."""
+    g = np.asarray(img, np.float64).mean(axis=0)
+    gx = 0.5 * (np.roll(g, -1, 1) - np.roll(g, 1, 1))
+    gy = 0.5 * (np.roll(g, -1, 0) - np.roll(g, 1, 0))
+    m = ndimage.gaussian_filter(np.hypot(gx, gy), blur, mode="wrap")
+    p99 = np.percentile(m, 99)
+    t = np.clip(m / p99, 0, 1) if p99 > 0 else np.zeros_like(m)
+    return (s_max - (s_max - s_min) * t).astype(np.float32)
+
+
+def scale_smoothing_problem(seed: int | None = None, size: int | tuple = 4096,
+                            n_cells: int = 500, n_h: int = 24, log_period: float = 8.0,
+                            r_min: float = 1.0, r_max: float = 64.0, centre_tap: float = 1.0):
+    """Scale-adaptive smoothing input: image (3, h, w) float32, scale field
+    s (h, w) float32 in [1, 8], Mellin coefficients of the Gaussian family."""
+    rng = np.random.default_rng(seed_for(3) if seed is None else seed)
+    h, w = (size, size) if np.isscalar(size) else size
+    img = voronoi_image(rng, h, w, n_cells)
+    s = scale_field_from_image(img)
+    c = mellin_gaussian_coeffs(n_h, log_period)
+    return dict(img=img, s=s, c=c, log_period=log_period, r_min=r_min, r_max=r_max,
+                centre_tap=centre_tap)
