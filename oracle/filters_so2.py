@@ -55,7 +55,9 @@ class RadialTable:
     tangents m_i = (v_{i+1} - v_{i-1}) / 2 (in units of one table step),
     with v_{-1} = (-1)^k v_1 (f_k extended to negative radius, since
     f_k(-r) exp(i k (theta + pi)) = f_k(r) exp(i k theta)) and v_n = 0.
-    f_k(r) = 0 for r > (n-1) dr.
+    f_k(r) = 0 for r / dr > (n-1) + 1e-9: the support is closed, and a
+    lattice point on its boundary circle stays inside however the rotated
+    coordinate rounds (the spline need not vanish at the last sample).
     """
 
     def __init__(self, fk, dr: float):
@@ -78,7 +80,7 @@ class RadialTable:
         # v_n = v_{n+1} = 0 already
         u = r / self.dr
         i = np.floor(u).astype(np.int64)
-        inside = (u <= n - 1) & (i >= 0)
+        inside = (u <= n - 1 + 1e-9) & (i >= 0)
         i = np.clip(i, 0, n - 1)
         t = u - i
         vi = ext[i + 1]

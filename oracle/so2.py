@@ -135,3 +135,34 @@ def sweep_so2_fft(H, filt, radius: int, J: int, workers: int = -1):
         arg = np.where(upd, j, arg)
         best = np.where(upd, s, best)
     return best, arg, second
+
+
+def component_correlation(H, filt, k: int, radius: int):
+    """Sec. 4.1 "Standard Correlation": G_k(p) = sum_{d in B} H(p + d) conj(F_k(d)),
+    F_k(d) = f_k(|d|) e^{i k theta(d)} (F_k(0) = 0 for k != 0)."""
+    H = np.asarray(H, np.float64)
+    dx, dy = box_offsets(radius)
+    r = np.hypot(dx, dy).astype(np.float64)
+    th = np.arctan2(dy, dx).astype(np.float64)
+    fk = filt.radial(k, r) * np.exp(1j * k * th)
+    if k != 0:
+        fk = np.where(r == 0, 0.0, fk)
+    out = np.zeros(H.shape, np.complex128)
+    for n in range(dx.size):
+        out += np.roll(H, (-dy[n], -dx[n]), axis=(0, 1)) * np.conj(fk[n])
+    return out
+
+
+def sweep_from_components(G, K: int, J: int):
+    """Sec. 4.1 "Linear Combination" at every alpha_j = 2 pi j / J for a real
+    filter: S(p, j) = sum_{k=-K..K} e^{i k alpha_j} G_k(p) with
+    G_{-k} = conj(G_k).  ``G`` is a list [G_0, ..., G_K]; returns (J, ...)."""
+    S = []
+    for j in range(J):
+        a = 2 * np.pi * j / J
+        s = np.zeros(np.shape(G[0]), np.complex128)
+        for k in range(-K, K + 1):
+            g = G[k] if k >= 0 else np.conj(G[-k])
+            s = s + np.exp(1j * k * a) * g
+        S.append(s)
+    return np.stack(S)

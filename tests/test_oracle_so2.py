@@ -321,3 +321,49 @@ def test_sweep_detects_planted_templates():
         j_true = round(beta * J / (2 * np.pi)) % J
         dj = (arg[cy, cx] - j_true) % J
         assert min(dj, J - dj) <= 1
+
+
+def test_component_steering_matches_bruteforce_sweep():
+    """The Sec. 4.1 algorithm (components, then linear combination) reproduces
+    the definition evaluated with explicitly rotated filters -- pins
+    component_correlation and sweep_from_components against the brute force."""
+    from oracle.so2 import component_correlation, sweep_from_components
+    H, filt, a, _ = small_problem(seed=31, h=12, w=14, K=3)
+    R, J = 3, 10
+    G = [component_correlation(H, filt, k, R) for k in range(0, 4)]
+    S = sweep_from_components(G, 3, J)
+    pix = np.array([[y, x] for y in range(12) for x in range(14)])
+    ref = sweep_so2_at(H, filt, R, J, pix)
+    np.testing.assert_allclose(S.reshape(J, -1).T, ref, atol=1e-10)
+    # and the components alone are standard correlations with F_k (FFT)
+    dx, dy = box_offsets(R)
+    for k in range(4):
+        comp = AnalyticGaussPow(np.where(np.arange(-3, 4) == k, a, 0), 2.0)
+        g = filter_grid(cartesian_gauss_pow(comp.a, 2.0, dx, dy), dx, dy, 12, 14)
+        np.testing.assert_allclose(G[k], fft_corr(H, g), atol=1e-10)
+
+
+def test_fft_sweep_route_matches_bruteforce_on_sampled_template():
+    """The two oracle routes to the sweep (per-pixel brute force and FFT
+    correlation per rotated filter) agree on a planted-template image."""
+    prob = synth.so2_match_problem(seed=832, size=128, n_plant=3, radius=12, K=8, J=32)
+    tab = decompose_sampled(prob["template"], 8, prob["dr"], prob["n_theta"])
+    best, arg, _ = sweep_so2_fft(prob["H"], tab, prob["radius"], 32)
+    pix = np.array([[y, x] for y in range(0, 128, 3) for x in range(0, 128, 5)] + [[127, 127]])
+    S = sweep_so2_at(prob["H"], tab, prob["radius"], 32, pix).real
+    np.testing.assert_allclose(best[pix[:, 0], pix[:, 1]], S.max(axis=1), atol=1e-12)
+
+
+def test_boundary_taps_are_rotation_invariant():
+    """A lattice offset on the support circle |d| = (n-1) dr keeps its value
+    under rotation, whatever the rounding of the rotated coordinate."""
+    rng = np.random.default_rng(4)
+    fk = rng.standard_normal((5, 49)) + 1j * rng.standard_normal((5, 49))
+    fk[0] = np.conj(fk[4]); fk[1] = np.conj(fk[3]); fk[2] = fk[2].real
+    tab = RadialTable(fk, 0.25)               # support r <= 12
+    for (dx, dy) in [(0, -12), (12, 0), (0, 12), (-12, 0)]:
+        base = tab.radial(1, 12.0)
+        for a in np.linspace(0, 2 * np.pi, 97):
+            c, s = np.cos(a), np.sin(a)
+            r = np.hypot(c * dx + s * dy, -s * dx + c * dy)
+            np.testing.assert_allclose(tab.radial(1, r), base, rtol=1e-9, atol=1e-12)
