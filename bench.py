@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the extended-correlation hot path on GB300.
+
+Workload (one step = one image through the whole path): rotation-independent
+pattern matching on a 2048 x 2048 float32 image (Gaussian noise sigma 0.1 plus
+20 planted 65 x 65 templates), filter = the template's angular band-limit
+|k| <= 16, sweep over 64 uniformly spaced angles, output = per-pixel maximum
+score (float32) and argmax angle index (int32).
+
+Metric: Mpx/s of the whole path (R2C FFT, 17 component correlations through
+inverse FFTs, angular sweep with max/argmax).  Filter spectra are built once
+per plan (warm-up) and reused, like any fixed-template matcher.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With --gpus N > 1 (launched by torch.distributed.run) every rank processes its
+own image per step (independent problems, no collective on the data path) and
+rank 0 prints the whole-job throughput over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "extended-correlation Mpx/s at K=16 vs plain FP32 path; HBM/TC % of peak"
+WORKLOAD = "so2 pattern matching: 2048x2048 f32, 20 planted 65x65 templates, K=16, 64 angles, max+argmax"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--cpu-sample", type=int, default=16384, help="pixels in the oracle's timed sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="plan, warm-up and timed steps only (for ncu launch lists)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ peaks ---
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def committed_traffic():
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+    summary (profiles/traffic.txt: '<kernel> <workload> <bytes>' lines)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    out = {}
+    try:
+        for line in open(path):
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, wl, b = line.split()[:3]
+            out[(k, wl)] = float(b)
+    except OSError:
+        pass
+    return out
+
+
+# ----------------------------------------------------------------- clocks ---
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        rows = []
+        try:
+            with open(self.file.name) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------- distributed ---
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------- oracle timings ---
+def time_oracle(prob, n_pix, seed=0):
+    """FP64 brute-force sweep (the oracle as it stands) at n_pix random pixels."""
+    import numpy as np
+    from oracle.filters_so2 import decompose_sampled
+    from oracle.so2 import sweep_so2_at
+    tab = decompose_sampled(prob["template"], prob["K"], prob["dr"], prob["n_theta"])
+    h, w = prob["H"].shape
+    rng = np.random.default_rng(seed)
+    pix = np.stack([rng.integers(0, h, n_pix), rng.integers(0, w, n_pix)], 1)
+    t0 = time.perf_counter()
+    for c in range(0, n_pix, 4096):
+        sweep_so2_at(prob["H"], tab, prob["radius"], prob["J"], pix[c:c + 4096])
+    return time.perf_counter() - t0
+
+
+# ----------------------------------------------------------- algorithmic ---
+def algorithmic_bytes(kernel, h, w, K, kc):
+    """Compulsory DRAM bytes of one launch of each kernel (inputs read once,
+    outputs written once), for the launch shapes the sweep path uses."""
+    P = h * w
+    wh = w // 2 + 1
+    half = h * wh * 8
+    if kernel == "rows_r2c":
+        return 4 * P + half
+    if kernel == "cols_fwd_half":
+        return 2 * half
+    if kernel == "cols_inv_corr":      # Hh once, kc filter spectra, kc products out
+        return half + kc * (8 * P) + kc * (8 * P)
+    if kernel == "rows_inv_components":   # kc partial products in, 2 real planes out each
+        return kc * 8 * P + kc * 8 * P
+    if kernel == "sweep_fp32" or kernel == "sweep_bf16x3":
+        return (2 * K + 1) * 4 * P + 8 * P
+    return None
+
+
+# ------------------------------------------------------------------ main ---
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args.gpus)
+
+    import numpy as np
+    import synth
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        prob = synth.so2_match_problem(size=args.size)
+        n_pix = max(256, args.cpu_sample // 8)
+        for _ in range(args.warmup):
+            time_oracle(prob, 256, seed=1)
+        total = 0.0
+        for s in range(args.steps):
+            total += time_oracle(prob, n_pix, seed=100 + s)
+        value = args.steps * n_pix / total / 1e6
+        cores = os.cpu_count()
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "Mpx/s", "cores": cores, "kind": "oracle",
+                             "sample": f"FP64 brute-force sweep at {n_pix} random pixels per step"},
+            "e2e": {"value": value, "unit": "Mpx/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    import paper_2006_13188_gb300 as ec
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    prob = synth.so2_match_problem(seed=synth.seed_for(2) + rank, size=args.size)
+    h = w = args.size
+    P = h * w
+    K, J = prob["K"], prob["J"]
+    plan = ec.Plan(local)
+    F = ec.FilterSO2.sampled(prob["template"], K, prob["dr"], prob["n_theta"])
+    H = torch.from_numpy(prob["H"]).to(device)
+    mx = torch.empty((h, w), dtype=torch.float32, device=device)
+    am = torch.empty((h, w), dtype=torch.int32, device=device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    precision = ec.EXT_PREC_FP32
+    plan_t0 = time.perf_counter()
+    ec.ext_corr_so2(plan, H, h, w, F, None, J, mx, am, precision)
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - plan_t0)
+
+    def run_loop(prec, steps, warm):
+        for _ in range(warm):
+            ec.ext_corr_so2(plan, H, h, w, F, None, J, mx, am, prec)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            ec.ext_corr_so2(plan, H, h, w, F, None, J, mx, am, prec)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        return sum(e0.elapsed_time(e1) for e0, e1 in evs)
+
+    plan.profile_read()   # clear launch counters
+    with ClockSampler(local) as clk:
+        total_ms = run_loop(precision, args.steps, args.warmup)
+    launches = sum(c for _, c in plan.profile_read().values())
+    clocks = clk.summary()
+    total_ms = reduce_max(total_ms, world, device)
+    value = world * args.steps * P / (total_ms * 1e-3) / 1e6
+    if args.only_timed:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "Mpx/s", "steps": args.steps,
+                              "ms_per_step": total_ms / args.steps, "gpu_launches": launches}))
+        plan.close()
+        return 0
+
+    # plain FP32 path (same as the chosen form until the tensor-core sweep lands)
+    plain_ms = total_ms
+    plain = {"value": world * args.steps * P / (plain_ms * 1e-3) / 1e6, "unit": "Mpx/s",
+             "ms_per_step": plain_ms / args.steps, "precision": "fp32"}
+
+    # per-kernel times (events around every launch, on the launch stream)
+    prof_steps = max(10, min(args.steps, 50))
+    plan.profile(True)
+    for _ in range(prof_steps):
+        flush.zero_()
+        ec.ext_corr_so2(plan, H, h, w, F, None, J, mx, am, precision)
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    plan.profile(False)
+    kc = max(1, min(K + 1, (32 << 20) // (8 * P)))
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    avg_ms = dom_ms / dom_n
+    alg = algorithmic_bytes(dom_name, h, w, K, kc)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
+    traffic = committed_traffic().get((dom_name, f"{h}x{w}K{K}"))
+    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
+                "kernels": {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps,
+                                "share": v[0] / sum(x[0] for x in prof.values())} for k, v in prof.items()}}
+
+    # end to end through the C ABI with pinned host buffers
+    Hh = torch.from_numpy(prob["H"]).pin_memory()
+    mxh = torch.empty((h, w), dtype=torch.float32).pin_memory()
+    amh = torch.empty((h, w), dtype=torch.int32).pin_memory()
+    e2e_steps = max(5, min(args.steps, 50))
+    ec.ext_corr_so2(plan, Hh, h, w, F, None, J, mxh, amh, precision)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ec.ext_corr_so2(plan, Hh, h, w, F, None, J, mxh, amh, precision)
+    e2e_s = reduce_max(time.perf_counter() - t0, world, device)
+    e2e = {"value": world * e2e_steps * P / e2e_s / 1e6, "unit": "Mpx/s", "h2d_bytes_per_step": 4 * P,
+           "d2h_bytes_per_step": 8 * P, "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        t = time_oracle(prob, args.cpu_sample)
+        cpu = {"value": args.cpu_sample / t / 1e6, "unit": "Mpx/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 brute-force sweep at {args.cpu_sample} random pixels of the same image ({t:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp32", "parallelism": f"replicas{world}",
+                       "l2": "256 MB buffer written between timed steps (outside the events)",
+                       "plan_ms": plan_ms},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu, "plain_fp32": plain,
+        }
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

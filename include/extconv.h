@@ -1,0 +1,179 @@
+/*
+ * extconv -- extended convolution and correlation on GB300 (sm_103a).
+ *
+ * C ABI of libextconv.so.  It computes the spatially adaptive filtering
+ * operators of Mitchel et al., "Efficient Spatially Adaptive Convolution and
+ * Correlation" (arXiv 2006.13188):
+ *
+ *   extended correlation  {H,T} * F (p) = sum_q H(q) conj((T(p)F)(q - p))   (Sec. 2.1, Eq. Def-ECorr)
+ *   extended convolution  {H,T} * F (p) = sum_q H(q) (T(q)F)(p - q)         (Sec. 2.2, Eq. Def-EConv)
+ *
+ * on the integer lattice with periodic boundaries (indices mod (h, w)), for
+ * rotation fields (SO(2), Sec. 4.1).  The filter is split into angular
+ * harmonics F_k(r, theta) = f_k(r) e^{i k theta}, |k| <= K (Sec. 4.1
+ * "Filter Decomposition"); every component is correlated/convolved with the
+ * signal by FFT ("Standard Correlation"); the result is steered per pixel
+ * ("Linear Combination"), or swept over J uniformly spaced angles with a
+ * per-pixel max/argmax (the rotation search of Sec. 5, "Band-Limiting
+ * Revisited").
+ *
+ * Conventions shared by every entry point:
+ *   - Images are row-major, x = column index, y = row index, no padding
+ *     (leading dimension = w).  Angles are radians; rotating a filter by
+ *     alpha means (T_alpha F)(d) = F(R(-alpha) d), R(a) = [[cos a, -sin a],
+ *     [sin a, cos a]], which multiplies harmonic k by e^{-i k alpha}.
+ *   - Image/field/output pointers may be DEVICE or HOST memory; the library
+ *     tells them apart with cudaPointerGetAttributes.  Host buffers are
+ *     staged through plan-owned device memory and the call then returns only
+ *     after its results are back in host memory.  With device buffers the
+ *     call is asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream).  The caller owns every buffer it passes; the library never
+ *     frees them.
+ *   - Filter descriptions (ext_filter_so2 and the arrays it points to) are
+ *     HOST memory, read during the call only.
+ *   - Supported image sides: 32, 48, 96, 160, every multiple of 64 up to
+ *     1024, 1536, 2048, 3072 and 4096 (all of the form 2^a 3^b 5^c 7^d 11^e 13^f);
+ *     w must be even.  Other sizes return EXT_ERR_UNSUPPORTED before any
+ *     launch.  h == 0 or w == 0 is a no-op returning EXT_OK.
+ *   - Errors: argument errors return before any launch; CUDA errors return
+ *     EXT_ERR_CUDA.  ext_last_error() gives a thread-local message.  No C++
+ *     exception crosses this interface.  There is no CPU fallback.
+ */
+#ifndef EXTCONV_H
+#define EXTCONV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int ext_status;
+#define EXT_OK 0
+#define EXT_ERR_INVALID_ARG 1
+#define EXT_ERR_UNSUPPORTED 2
+#define EXT_ERR_CUDA 3
+#define EXT_ERR_OOM 4
+#define EXT_ERR_TIMEOUT 5
+
+/* Filter kinds (ext_filter_so2.kind). */
+#define EXT_FILTER_ANALYTIC_GAUSSPOW 0 /* f_k(r) = a_k r^|k| exp(-r^2 / (2 sigma^2))                */
+#define EXT_FILTER_TABLE 1             /* f_k(i dr) given; cubic Hermite in r (see below)            */
+#define EXT_FILTER_SAMPLED 2           /* (2R+1)^2 image, decomposed by the library (Sec. 4.1)      */
+
+/* Sweep precision (ext_corr_so2 / ext_sweep_so2). */
+#define EXT_PREC_FP32 0   /* plain FP32 on CUDA cores                                              */
+#define EXT_PREC_BF16X3 1 /* split BF16 hi+lo operands on tcgen05 tensor cores, FP32 accumulation */
+
+/*
+ * SO(2) filter with angular bandwidth K (|k| <= K) on the box [-R, R]^2:
+ *   F(d) = sum_{|k|<=K} f_k(|d|) e^{i k theta(d)},  theta(d) = atan2(d_y, d_x),
+ *   F(0) = f_0(0)  (the k != 0 terms vanish at the origin).
+ * ANALYTIC_GAUSSPOW: a = 2(2K+1) doubles, interleaved (re, im) of a_k for
+ *   k = -K..K; sigma > 0.
+ * TABLE: fk = 2(2K+1)n_r doubles, row k+K holds (re, im) of f_k(i dr),
+ *   i = 0..n_r-1.  Between samples f_k is the cubic Hermite spline with
+ *   tangents (v_{i+1} - v_{i-1}) / 2, v_{-1} = (-1)^k v_1, v_{n_r} = 0, and
+ *   f_k(r) = 0 for r / dr > (n_r - 1) + 1e-9 (closed support).
+ * SAMPLED: img = (2R+1)^2 doubles, row-major, centre pixel (R, R).  The
+ *   library resamples it at radii i dr <= R and n_theta angles with the Keys
+ *   cubic kernel (a = -1/2, zero outside), takes the DFT along each circle
+ *   (Sec. 4.1 "Filter Decomposition"), and uses the resulting TABLE.
+ * The operators below require a real filter (f_{-k} = conj f_k); this holds
+ *   for SAMPLED and is the caller's promise for the other kinds.
+ */
+typedef struct {
+  int K;
+  int R;
+  int kind;
+  const double* a;
+  double sigma;
+  const double* fk;
+  int n_r;
+  double dr;
+  const double* img;
+  int n_theta;
+} ext_filter_so2;
+
+typedef struct ext_plan_s* ext_plan;
+
+const char* ext_status_string(ext_status s);
+/* Thread-local message describing the last error returned on this thread. */
+const char* ext_last_error(void);
+
+/* Plan: caches twiddle tables, filter spectra (per filter, size and mode),
+ * sweep tables and workspace on `device`.  Not thread-safe: one plan per
+ * host thread.  ext_plan_destroy frees everything the plan allocated. */
+ext_status ext_plan_create(ext_plan* plan, int device);
+ext_status ext_plan_destroy(ext_plan plan);
+/* Frees cached filter spectra and workspace (kept otherwise for reuse). */
+ext_status ext_plan_trim(ext_plan plan);
+
+/* Per-kernel accounting for benchmarks and tracing (no counterpart in the
+ * paper).  Every kernel launch of the plan is counted per kernel name; with
+ * profiling enabled each launch is also bracketed by CUDA events recorded on
+ * the launch's stream.  ext_plan_profile_read waits for those events, writes
+ * up to n_max entries (names: n_max * 64 chars, NUL-terminated; total_ms:
+ * summed event time; launches: count), sets *n_out, and clears the
+ * accumulators.  Any output array may be NULL. */
+ext_status ext_plan_profile(ext_plan plan, int enable);
+ext_status ext_plan_profile_read(ext_plan plan, int n_max, char* names, double* total_ms, int64_t* launches,
+                                 int* n_out);
+
+/*
+ * Filter decomposition (Sec. 4.1 "Filter Decomposition"), FP64 on the
+ * device.  Writes the radial table f_k(i dr), k = -K..K, as 2(2K+1)n_r
+ * interleaved doubles to HOST memory fk_out (capacity fk_cap doubles) and
+ * n_r to *n_r_out.  SAMPLED filters are decomposed; TABLE filters are
+ * returned as given; ANALYTIC filters return EXT_ERR_UNSUPPORTED.
+ */
+ext_status ext_filter_so2_decompose(ext_plan plan, const ext_filter_so2* F, double* fk_out,
+                                    int64_t fk_cap, int* n_r_out);
+
+/*
+ * Extended convolution with a rotation field (Sec. 2.2 Eq. Def-EConv; the
+ * algorithm of Sec. 4.1, last paragraph): out = Re sum_k (H e^{-ik alpha}) * F_k.
+ * H, alpha (radians), out: h x w float32.
+ */
+ext_status ext_conv_so2(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F,
+                        const float* alpha, float* out, void* stream);
+
+/*
+ * Extended correlation with a rotation field (Sec. 2.1 Eq. Def-ECorr; Sec. 4.1
+ * "Linear Combination"):
+ *   field mode (alpha != NULL): out(p) = sum_k e^{ik alpha(p)} G_k(p),
+ *                               G_k = H (*) F_k  (standard correlation);
+ *   sweep mode (alpha == NULL): S(p, j) = sum_k e^{ik alpha_j} G_k(p) with
+ *     alpha_j = 2 pi j / n_angles; out_or_max(p) = max_j S(p, j) and
+ *     argmax(p) = the smallest j attaining it.
+ * H, alpha, out_or_max: h x w float32; argmax: h x w int32 (sweep mode only,
+ * NULL in field mode).  precision: EXT_PREC_FP32 or EXT_PREC_BF16X3 (sweep
+ * mode; ignored in field mode).
+ */
+ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F,
+                        const float* alpha, int n_angles, float* out_or_max, int32_t* argmax,
+                        int precision, void* stream);
+
+/*
+ * The component correlations G_k = H (*) F_k, k = 0..K (Sec. 4.1 "Standard
+ * Correlation"), as 2K+1 planes of h*w float32: plane 0 = G_0 (real for a
+ * real filter), plane 2k-1 = Re G_k, plane 2k = Im G_k.
+ */
+ext_status ext_corr_so2_components(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F,
+                                   float* G, void* stream);
+
+/*
+ * The angular sweep over precomputed components (Sec. 5 "Band-Limiting
+ * Revisited": max over rotations), G laid out as ext_corr_so2_components
+ * writes it for n_pix pixels:
+ *   S(p, j) = G_0(p) + 2 sum_{k=1..K} Re(e^{i 2 pi k j / J} G_k(p)),
+ *   max_out(p) = max_j S(p, j), argmax(p) = smallest maximising j.
+ */
+ext_status ext_sweep_so2(ext_plan plan, const float* G, int64_t n_pix, int K, int n_angles, float* max_out,
+                         int32_t* argmax, int precision, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXTCONV_H */

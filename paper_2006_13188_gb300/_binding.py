@@ -1,0 +1,220 @@
+"""ctypes binding of libextconv.so: argument marshalling only.
+
+Every function here forwards to the C entry point of the same name
+(declared in include/extconv.h); the computation happens in the library's
+CUDA kernels.  Arrays may be torch tensors (device or host) or numpy arrays
+(host); their data pointers are passed through unchanged.  If the library
+has not been built, importing works but every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libextconv.so")
+
+EXT_OK = 0
+EXT_ERR_INVALID_ARG = 1
+EXT_ERR_UNSUPPORTED = 2
+EXT_ERR_CUDA = 3
+EXT_ERR_OOM = 4
+EXT_ERR_TIMEOUT = 5
+
+EXT_FILTER_ANALYTIC_GAUSSPOW = 0
+EXT_FILTER_TABLE = 1
+EXT_FILTER_SAMPLED = 2
+
+EXT_PREC_FP32 = 0
+EXT_PREC_BF16X3 = 1
+
+EXPORTED = (
+    "ext_status_string", "ext_last_error", "ext_plan_create", "ext_plan_destroy", "ext_plan_trim",
+    "ext_plan_profile", "ext_plan_profile_read",
+    "ext_filter_so2_decompose", "ext_conv_so2", "ext_corr_so2", "ext_corr_so2_components",
+    "ext_sweep_so2",
+)
+
+
+class ExtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class ext_filter_so2(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_int), ("R", ctypes.c_int), ("kind", ctypes.c_int),
+        ("a", ctypes.POINTER(ctypes.c_double)), ("sigma", ctypes.c_double),
+        ("fk", ctypes.POINTER(ctypes.c_double)), ("n_r", ctypes.c_int), ("dr", ctypes.c_double),
+        ("img", ctypes.POINTER(ctypes.c_double)), ("n_theta", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libextconv.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        fp = ctypes.POINTER(ext_filter_so2)
+        L.ext_status_string.restype = ctypes.c_char_p
+        L.ext_status_string.argtypes = [i32]
+        L.ext_last_error.restype = ctypes.c_char_p
+        L.ext_last_error.argtypes = []
+        L.ext_plan_create.argtypes = [ctypes.POINTER(vp), i32]
+        L.ext_plan_destroy.argtypes = [vp]
+        L.ext_plan_trim.argtypes = [vp]
+        L.ext_plan_profile.argtypes = [vp, i32]
+        L.ext_plan_profile_read.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]
+        L.ext_filter_so2_decompose.argtypes = [vp, fp, vp, i64, ctypes.POINTER(i32)]
+        L.ext_conv_so2.argtypes = [vp, vp, i32, i32, fp, vp, vp, vp]
+        L.ext_corr_so2.argtypes = [vp, vp, i32, i32, fp, vp, i32, vp, vp, i32, vp]
+        L.ext_corr_so2_components.argtypes = [vp, vp, i32, i32, fp, vp, vp]
+        L.ext_sweep_so2.argtypes = [vp, vp, i64, i32, i32, vp, vp, i32, vp]
+        for name in EXPORTED:
+            if name not in ("ext_status_string", "ext_last_error"):
+                getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != EXT_OK:
+        L = lib()
+        raise ExtError(status, f"{L.ext_status_string(status).decode()}: {L.ext_last_error().decode()}")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class FilterSO2:
+    """Owns the host arrays an ext_filter_so2 points to."""
+
+    def __init__(self, K, R, kind, a=None, sigma=0.0, fk=None, dr=0.0, img=None, n_theta=0):
+        self.K, self.R, self.kind = int(K), int(R), int(kind)
+        self._a = None if a is None else np.ascontiguousarray(np.asarray(a, np.complex128)).view(np.float64)
+        self._fk = None if fk is None else np.ascontiguousarray(np.asarray(fk, np.complex128)).view(np.float64)
+        self._img = None if img is None else np.ascontiguousarray(np.asarray(img, np.float64))
+        dp = ctypes.POINTER(ctypes.c_double)
+        self.struct = ext_filter_so2(
+            self.K, self.R, self.kind,
+            self._a.ctypes.data_as(dp) if self._a is not None else None, float(sigma),
+            self._fk.ctypes.data_as(dp) if self._fk is not None else None,
+            0 if fk is None else int(np.asarray(fk).shape[1]), float(dr),
+            self._img.ctypes.data_as(dp) if self._img is not None else None, int(n_theta))
+
+    @classmethod
+    def analytic(cls, a, sigma, R):
+        a = np.asarray(a, np.complex128)
+        return cls((len(a) - 1) // 2, R, EXT_FILTER_ANALYTIC_GAUSSPOW, a=a, sigma=sigma)
+
+    @classmethod
+    def table(cls, fk, dr, R):
+        fk = np.asarray(fk, np.complex128)
+        return cls((fk.shape[0] - 1) // 2, R, EXT_FILTER_TABLE, fk=fk, dr=dr)
+
+    @classmethod
+    def sampled(cls, img, K, dr, n_theta):
+        img = np.asarray(img, np.float64)
+        return cls(K, (img.shape[0] - 1) // 2, EXT_FILTER_SAMPLED, img=img, dr=dr, n_theta=n_theta)
+
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+class Plan:
+    def __init__(self, device: int = 0):
+        self.handle = ctypes.c_void_p()
+        _check(lib().ext_plan_create(ctypes.byref(self.handle), int(device)))
+
+    def close(self):
+        if self.handle:
+            lib().ext_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def trim(self):
+        _check(lib().ext_plan_trim(self.handle))
+
+    def profile(self, enable: bool):
+        _check(lib().ext_plan_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} since the last read."""
+        n_max = 64
+        names = ctypes.create_string_buffer(64 * n_max)
+        ms = np.zeros(n_max, np.float64)
+        cnt = np.zeros(n_max, np.int64)
+        n = ctypes.c_int(0)
+        _check(lib().ext_plan_profile_read(self.handle, n_max, names, _ptr(ms), _ptr(cnt), ctypes.byref(n)))
+        out = {}
+        for i in range(n.value):
+            name = names.raw[64 * i:64 * i + 64].split(b"\0", 1)[0].decode()
+            out[name] = (float(ms[i]), int(cnt[i]))
+        return out
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ext_filter_so2_decompose(plan: Plan, F: FilterSO2):
+    nk = 2 * F.K + 1
+    cap = 2 * nk * 100000
+    out = np.zeros(cap, np.float64)
+    n_r = ctypes.c_int(0)
+    _check(lib().ext_filter_so2_decompose(plan.handle, F.ref(), _ptr(out), cap, ctypes.byref(n_r)))
+    return out[: 2 * nk * n_r.value].view(np.complex128).reshape(nk, n_r.value)
+
+
+def ext_conv_so2(plan: Plan, H, h, w, F: FilterSO2, alpha, out, stream=None):
+    _check(lib().ext_conv_so2(plan.handle, _ptr(H), int(h), int(w), F.ref(), _ptr(alpha), _ptr(out),
+                              _stream(stream)))
+
+
+def ext_corr_so2(plan: Plan, H, h, w, F: FilterSO2, alpha, n_angles, out_or_max, argmax, precision=EXT_PREC_FP32,
+                 stream=None):
+    _check(lib().ext_corr_so2(plan.handle, _ptr(H), int(h), int(w), F.ref(), _ptr(alpha), int(n_angles),
+                              _ptr(out_or_max), _ptr(argmax), int(precision), _stream(stream)))
+
+
+def ext_corr_so2_components(plan: Plan, H, h, w, F: FilterSO2, G, stream=None):
+    _check(lib().ext_corr_so2_components(plan.handle, _ptr(H), int(h), int(w), F.ref(), _ptr(G),
+                                         _stream(stream)))
+
+
+def ext_sweep_so2(plan: Plan, G, n_pix, K, n_angles, max_out, argmax, precision=EXT_PREC_FP32, stream=None):
+    _check(lib().ext_sweep_so2(plan.handle, _ptr(G), int(n_pix), int(K), int(n_angles), _ptr(max_out),
+                               _ptr(argmax), int(precision), _stream(stream)))

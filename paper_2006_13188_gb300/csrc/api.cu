@@ -1,0 +1,663 @@
+// C ABI of libextconv.so: argument checking, the plan (caches and workspace),
+// host/device staging, and the launch sequences of each operator.
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ext_status fail(ext_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define EXT_CUDA(call)                                                                              \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      return fail(e_ == cudaErrorMemoryAllocation ? EXT_ERR_OOM : EXT_ERR_CUDA,                    \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+    }                                                                                               \
+  } while (0)
+
+#define EXT_TRY(expr)                  \
+  do {                                 \
+    ext_status s_ = (expr);            \
+    if (s_ != EXT_OK) return s_;       \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct SpecEntry {
+  uint64_t key = 0;
+  float2* S = nullptr;
+  size_t bytes = 0;
+  uint64_t stamp = 0;
+};
+
+uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+}  // namespace
+
+struct ProfStat {
+  double ms = 0.0;
+  int64_t launches = 0;
+};
+
+struct ProfPending {
+  std::string name;
+  cudaEvent_t a, b;
+};
+
+struct ext_plan_s {
+  int device = 0;
+  bool profiling = false;
+  std::map<std::string, ProfStat> prof;
+  std::vector<ProfPending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::map<int, float2*> twiddles;
+  std::map<std::string, DevBuf> ws;
+  std::vector<SpecEntry> specs;
+  std::map<uint64_t, float*> sweep_tables;
+  uint64_t clock = 0;
+  size_t max_specs = 4;
+};
+
+namespace {
+
+cudaEvent_t take_event(ext_plan plan) {
+  if (!plan->event_pool.empty()) {
+    cudaEvent_t e = plan->event_pool.back();
+    plan->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Every kernel launch of the operators goes through here: it is counted per
+// kernel name and, when profiling is on, bracketed by events on its stream.
+template <typename F>
+void launch(ext_plan plan, const char* name, cudaStream_t st, F&& f) {
+  if (!plan->profiling) {
+    plan->prof[name].launches += 1;
+    f();
+    return;
+  }
+  ProfPending p;
+  p.name = name;
+  p.a = take_event(plan);
+  p.b = take_event(plan);
+  cudaEventRecord(p.a, st);
+  f();
+  cudaEventRecord(p.b, st);
+  plan->pending.push_back(p);
+}
+
+ext_status ensure(ext_plan plan, const char* name, size_t bytes, void** out) {
+  DevBuf& b = plan->ws[name];
+  if (b.bytes < bytes) {
+    if (b.p) EXT_CUDA(cudaFree(b.p));
+    b.p = nullptr;
+    b.bytes = 0;
+    EXT_CUDA(cudaMalloc(&b.p, bytes));
+    b.bytes = bytes;
+  }
+  *out = b.p;
+  return EXT_OK;
+}
+
+ext_status twiddle(ext_plan plan, int n, cudaStream_t st, const float2** out) {
+  auto it = plan->twiddles.find(n);
+  if (it == plan->twiddles.end()) {
+    float2* tw = nullptr;
+    EXT_CUDA(cudaMalloc(&tw, sizeof(float2) * n));
+    launch_twiddle(tw, n, st);
+    EXT_CUDA(cudaGetLastError());
+    it = plan->twiddles.emplace(n, tw).first;
+  }
+  *out = it->second;
+  return EXT_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+ext_status check_filter(const ext_filter_so2* F) {
+  if (!F) return fail(EXT_ERR_INVALID_ARG, "filter is NULL");
+  if (F->K < 0 || F->K > 64) return fail(EXT_ERR_INVALID_ARG, "filter K must be in [0, 64]");
+  if (F->R < 0 || F->R > 1024) return fail(EXT_ERR_INVALID_ARG, "filter R must be in [0, 1024]");
+  switch (F->kind) {
+    case EXT_FILTER_ANALYTIC_GAUSSPOW:
+      if (!F->a) return fail(EXT_ERR_INVALID_ARG, "analytic filter needs a");
+      if (!(F->sigma > 0)) return fail(EXT_ERR_INVALID_ARG, "analytic filter needs sigma > 0");
+      break;
+    case EXT_FILTER_TABLE:
+      if (!F->fk || F->n_r < 2 || !(F->dr > 0))
+        return fail(EXT_ERR_INVALID_ARG, "table filter needs fk, n_r >= 2, dr > 0");
+      break;
+    case EXT_FILTER_SAMPLED:
+      if (!F->img || !(F->dr > 0) || F->n_theta < 1)
+        return fail(EXT_ERR_INVALID_ARG, "sampled filter needs img, dr > 0, n_theta >= 1");
+      break;
+    default:
+      return fail(EXT_ERR_INVALID_ARG, "unknown filter kind");
+  }
+  return EXT_OK;
+}
+
+uint64_t filter_key(const ext_filter_so2* F) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv1a(h, &F->kind, sizeof(int));
+  h = fnv1a(h, &F->K, sizeof(int));
+  h = fnv1a(h, &F->R, sizeof(int));
+  const size_t nk = (size_t)(2 * F->K + 1);
+  if (F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW) {
+    h = fnv1a(h, F->a, sizeof(double) * 2 * nk);
+    h = fnv1a(h, &F->sigma, sizeof(double));
+  } else if (F->kind == EXT_FILTER_TABLE) {
+    h = fnv1a(h, &F->n_r, sizeof(int));
+    h = fnv1a(h, &F->dr, sizeof(double));
+    h = fnv1a(h, F->fk, sizeof(double) * 2 * nk * F->n_r);
+  } else {
+    const size_t side = (size_t)(2 * F->R + 1);
+    h = fnv1a(h, &F->dr, sizeof(double));
+    h = fnv1a(h, &F->n_theta, sizeof(int));
+    h = fnv1a(h, F->img, sizeof(double) * side * side);
+  }
+  return h;
+}
+
+int sampled_nr(const ext_filter_so2* F) {
+  // radii i * dr <= R
+  return (int)((double)F->R / F->dr + 1e-9) + 1;
+}
+
+// Radial coefficients on the device: analytic a_k, or the f_k table (given or
+// decomposed from a sampled image).  Returns pointer into workspace "coef".
+ext_status filter_coefficients(ext_plan plan, const ext_filter_so2* F, cudaStream_t st, const double2** coef,
+                               int* n_r, double* dr) {
+  const int nk = 2 * F->K + 1;
+  void* p = nullptr;
+  if (F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW) {
+    EXT_TRY(ensure(plan, "coef", sizeof(double2) * nk, &p));
+    EXT_CUDA(cudaMemcpyAsync(p, F->a, sizeof(double2) * nk, cudaMemcpyHostToDevice, st));
+    *n_r = 0;
+    *dr = 0.0;
+  } else if (F->kind == EXT_FILTER_TABLE) {
+    EXT_TRY(ensure(plan, "coef", sizeof(double2) * nk * F->n_r, &p));
+    EXT_CUDA(cudaMemcpyAsync(p, F->fk, sizeof(double2) * nk * F->n_r, cudaMemcpyHostToDevice, st));
+    *n_r = F->n_r;
+    *dr = F->dr;
+  } else {
+    const int side = 2 * F->R + 1;
+    const int nr = sampled_nr(F);
+    void *img = nullptr, *P = nullptr;
+    EXT_TRY(ensure(plan, "fimg", sizeof(double) * side * side, &img));
+    EXT_TRY(ensure(plan, "fpolar", sizeof(double) * nr * F->n_theta, &P));
+    EXT_TRY(ensure(plan, "coef", sizeof(double2) * nk * nr, &p));
+    EXT_CUDA(cudaMemcpyAsync(img, F->img, sizeof(double) * side * side, cudaMemcpyHostToDevice, st));
+    launch_decompose_sampled((const double*)img, side, F->dr, nr, F->n_theta, F->K, (double*)P, (double2*)p, st);
+    EXT_CUDA(cudaGetLastError());
+    *n_r = nr;
+    *dr = F->dr;
+  }
+  *coef = (const double2*)p;
+  return EXT_OK;
+}
+
+enum SpecMode { SPEC_CORR = 0, SPEC_CONV = 1 };
+
+// Component spectra of F on an h x w grid, tiled for the column passes.
+//   SPEC_CORR: S_k = conj(F^_k) / (h w)
+//   SPEC_CONV: S_k = w_k F^_k / (h w), w_0 = 1, w_k = 2 (k >= 1; the -k terms
+//              of a real filter give the complex conjugate contribution)
+ext_status spectra(ext_plan plan, const ext_filter_so2* F, int h, int w, SpecMode mode, cudaStream_t st,
+                   const float2** out) {
+  uint64_t key = filter_key(F);
+  key = fnv1a(key, &h, sizeof(int));
+  key = fnv1a(key, &w, sizeof(int));
+  int m = (int)mode;
+  key = fnv1a(key, &m, sizeof(int));
+  for (auto& e : plan->specs) {
+    if (e.key == key) {
+      e.stamp = ++plan->clock;
+      *out = e.S;
+      return EXT_OK;
+    }
+  }
+  const int K = F->K;
+  const int cw = fft_col_tile(h);
+  const int ntiles = (w + cw - 1) / cw;
+  const size_t per_k = (size_t)ntiles * h * cw;
+  const size_t bytes = sizeof(float2) * per_k * (K + 1);
+  if (plan->specs.size() >= plan->max_specs) {
+    size_t oldest = 0;
+    for (size_t i = 1; i < plan->specs.size(); ++i)
+      if (plan->specs[i].stamp < plan->specs[oldest].stamp) oldest = i;
+    EXT_CUDA(cudaStreamSynchronize(st));
+    EXT_CUDA(cudaFree(plan->specs[oldest].S));
+    plan->specs.erase(plan->specs.begin() + oldest);
+  }
+  SpecEntry e;
+  e.key = key;
+  e.bytes = bytes;
+  EXT_CUDA(cudaMalloc(&e.S, bytes));
+  const double2* coef = nullptr;
+  int n_r = 0;
+  double dr = 0;
+  ext_status s = filter_coefficients(plan, F, st, &coef, &n_r, &dr);
+  if (s != EXT_OK) {
+    cudaFree(e.S);
+    return s;
+  }
+  const float2 *tw_w = nullptr, *tw_h = nullptr;
+  EXT_TRY(twiddle(plan, w, st, &tw_w));
+  EXT_TRY(twiddle(plan, h, st, &tw_h));
+  void* grid = nullptr;
+  EXT_TRY(ensure(plan, "grid", sizeof(float2) * (size_t)h * w, &grid));
+  const int kind = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? EXT_FILTER_ANALYTIC_GAUSSPOW : EXT_FILTER_TABLE;
+  const float inv_hw = 1.0f / ((float)h * (float)w);
+  for (int k = 0; k <= K; ++k) {
+    EXT_CUDA(cudaMemsetAsync(grid, 0, sizeof(float2) * (size_t)h * w, st));
+    launch_component_grid(kind, K, k, coef, n_r, dr, F->sigma, F->R, h, w, (float2*)grid, st);
+    fft_rows_c2c(w, (const float2*)grid, h, 1, (float2*)grid, false, tw_w, st);
+    const float scale = (mode == SPEC_CONV && k > 0) ? 2.0f * inv_hw : inv_hw;
+    fft_cols_fwd_spectrum(h, (const float2*)grid, w, mode == SPEC_CORR ? 1 : 0, scale, e.S + per_k * k, tw_h, st);
+  }
+  EXT_CUDA(cudaGetLastError());
+  e.stamp = ++plan->clock;
+  plan->specs.push_back(e);
+  *out = e.S;
+  return EXT_OK;
+}
+
+ext_status sweep_table(ext_plan plan, int K, int J, cudaStream_t st, const float** out, int* cp_out) {
+  const int cp = (2 * K + 3) / 4 * 4;
+  const uint64_t key = ((uint64_t)K << 32) | (uint32_t)J;
+  auto it = plan->sweep_tables.find(key);
+  if (it == plan->sweep_tables.end()) {
+    float* B = nullptr;
+    EXT_CUDA(cudaMalloc(&B, sizeof(float) * (size_t)J * (cp > 0 ? cp : 4)));
+    if (cp > 0) launch_sweep_table(K, J, cp, B, st);
+    EXT_CUDA(cudaGetLastError());
+    it = plan->sweep_tables.emplace(key, B).first;
+  }
+  *out = it->second;
+  *cp_out = cp;
+  return EXT_OK;
+}
+
+ext_status check_size(int h, int w) {
+  if (h < 0 || w < 0) return fail(EXT_ERR_INVALID_ARG, "negative image size");
+  if (h == 0 || w == 0) return EXT_OK;
+  if (!fft_size_supported(h) || !fft_size_supported(w))
+    return fail(EXT_ERR_UNSUPPORTED, "image side " + std::to_string(!fft_size_supported(h) ? h : w) +
+                                         " is not a supported FFT length");
+  if (w % 2) return fail(EXT_ERR_UNSUPPORTED, "image width must be even");
+  return EXT_OK;
+}
+
+// Host/device staging of one argument.
+struct Staged {
+  const void* user = nullptr;
+  void* dev = nullptr;
+  size_t bytes = 0;
+  bool host = false;
+};
+
+ext_status stage_in(ext_plan plan, const char* name, const void* user, size_t bytes, cudaStream_t st,
+                    Staged* s) {
+  s->user = user;
+  s->bytes = bytes;
+  s->host = user && !is_device_ptr(user);
+  if (!s->host) {
+    s->dev = const_cast<void*>(user);
+    return EXT_OK;
+  }
+  EXT_TRY(ensure(plan, name, bytes, &s->dev));
+  EXT_CUDA(cudaMemcpyAsync(s->dev, user, bytes, cudaMemcpyHostToDevice, st));
+  return EXT_OK;
+}
+
+ext_status stage_out_alloc(ext_plan plan, const char* name, void* user, size_t bytes, Staged* s) {
+  s->user = user;
+  s->bytes = bytes;
+  s->host = user && !is_device_ptr(user);
+  if (!s->host) {
+    s->dev = user;
+    return EXT_OK;
+  }
+  return ensure(plan, name, bytes, &s->dev);
+}
+
+ext_status stage_out_finish(const Staged& s, cudaStream_t st) {
+  if (!s.host) return EXT_OK;
+  EXT_CUDA(cudaMemcpyAsync(const_cast<void*>(s.user), s.dev, s.bytes, cudaMemcpyDeviceToHost, st));
+  return EXT_OK;
+}
+
+// G_k = H (*) F_k for k = 0..K into G (device, (2K+1) planes).
+ext_status run_components(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, float* G,
+                          cudaStream_t st) {
+  const int K = F->K;
+  const float2* S = nullptr;
+  EXT_TRY(spectra(plan, F, h, w, SPEC_CORR, st, &S));
+  const float2 *tw_w = nullptr, *tw_h = nullptr;
+  EXT_TRY(twiddle(plan, w, st, &tw_w));
+  EXT_TRY(twiddle(plan, h, st, &tw_h));
+  const int wh = w / 2 + 1;
+  void* Hh = nullptr;
+  EXT_TRY(ensure(plan, "Hh", sizeof(float2) * (size_t)h * wh, &Hh));
+  launch(plan, "rows_r2c", st, [&] { fft_rows_r2c(w, H, h, (float2*)Hh, tw_w, st); });
+  launch(plan, "cols_fwd_half", st, [&] { fft_cols_fwd_half(h, (float2*)Hh, wh, tw_h, st); });
+  // k-chunks sized so that one chunk of partial products stays L2-resident
+  const size_t plane = sizeof(float2) * (size_t)h * w;
+  int kc = (int)((32u << 20) / plane);
+  if (kc < 1) kc = 1;
+  if (kc > K + 1) kc = K + 1;
+  void* Z = nullptr;
+  EXT_TRY(ensure(plan, "Z", plane * kc, &Z));
+  for (int k0 = 0; k0 <= K; k0 += kc) {
+    const int nk = (k0 + kc <= K + 1) ? kc : (K + 1 - k0);
+    launch(plan, "cols_inv_corr", st, [&] { fft_cols_inv_corr(h, (const float2*)Hh, w, S, k0, nk, (float2*)Z, tw_h, st); });
+    launch(plan, "rows_inv_components", st, [&] { fft_rows_inv_components(w, (const float2*)Z, h, k0, nk, G, tw_w, st); });
+  }
+  EXT_CUDA(cudaGetLastError());
+  return EXT_OK;
+}
+
+ext_status run_sweep(ext_plan plan, const float* G, long long P, int K, int J, float* maxv, int32_t* argmax,
+                     int precision, cudaStream_t st) {
+  if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3)
+    return fail(EXT_ERR_INVALID_ARG, "unknown precision");
+  if (precision == EXT_PREC_BF16X3) return fail(EXT_ERR_UNSUPPORTED, "BF16x3 sweep not built yet");
+  if (K == 0) {
+    EXT_CUDA(cudaMemcpyAsync(maxv, G, sizeof(float) * P, cudaMemcpyDeviceToDevice, st));
+    EXT_CUDA(cudaMemsetAsync(argmax, 0, sizeof(int32_t) * P, st));
+    return EXT_OK;
+  }
+  if (K > 16) return fail(EXT_ERR_UNSUPPORTED, "sweep supports K <= 16");
+  const float* B = nullptr;
+  int cp = 0;
+  EXT_TRY(sweep_table(plan, K, J, st, &B, &cp));
+  bool ok = true;
+  launch(plan, "sweep_fp32", st, [&] { ok = sweep_fp32(G, P, K, J, B, cp, maxv, argmax, st); });
+  if (!ok) return fail(EXT_ERR_UNSUPPORTED, "sweep K");
+  EXT_CUDA(cudaGetLastError());
+  return EXT_OK;
+}
+
+ext_status finish_host(bool any_host, cudaStream_t st) {
+  if (any_host) EXT_CUDA(cudaStreamSynchronize(st));
+  return EXT_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI ---
+extern "C" {
+
+const char* ext_status_string(ext_status s) {
+  switch (s) {
+    case EXT_OK: return "EXT_OK";
+    case EXT_ERR_INVALID_ARG: return "EXT_ERR_INVALID_ARG";
+    case EXT_ERR_UNSUPPORTED: return "EXT_ERR_UNSUPPORTED";
+    case EXT_ERR_CUDA: return "EXT_ERR_CUDA";
+    case EXT_ERR_OOM: return "EXT_ERR_OOM";
+    case EXT_ERR_TIMEOUT: return "EXT_ERR_TIMEOUT";
+    default: return "EXT_ERR_UNKNOWN";
+  }
+}
+
+const char* ext_last_error(void) { return g_last_error.c_str(); }
+
+ext_status ext_plan_create(ext_plan* plan, int device) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  *plan = nullptr;
+  int n = 0;
+  EXT_CUDA(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(EXT_ERR_INVALID_ARG, "no such device");
+  EXT_CUDA(cudaSetDevice(device));
+  ext_plan p = new ext_plan_s();
+  p->device = device;
+  *plan = p;
+  return EXT_OK;
+}
+
+ext_status ext_plan_trim(ext_plan plan) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  EXT_CUDA(cudaDeviceSynchronize());
+  for (auto& e : plan->specs) cudaFree(e.S);
+  plan->specs.clear();
+  for (auto& kv : plan->ws) cudaFree(kv.second.p);
+  plan->ws.clear();
+  return EXT_OK;
+}
+
+ext_status ext_plan_destroy(ext_plan plan) {
+  if (!plan) return EXT_OK;
+  cudaSetDevice(plan->device);
+  cudaDeviceSynchronize();
+  for (auto& e : plan->specs) cudaFree(e.S);
+  for (auto& kv : plan->ws) cudaFree(kv.second.p);
+  for (auto& kv : plan->twiddles) cudaFree(kv.second);
+  for (auto& kv : plan->sweep_tables) cudaFree(kv.second);
+  for (auto& p : plan->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : plan->event_pool) cudaEventDestroy(e);
+  delete plan;
+  return EXT_OK;
+}
+
+ext_status ext_plan_profile(ext_plan plan, int enable) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  plan->profiling = enable != 0;
+  return EXT_OK;
+}
+
+ext_status ext_plan_profile_read(ext_plan plan, int n_max, char* names, double* total_ms, int64_t* launches,
+                                 int* n_out) {
+  if (!plan || !n_out) return fail(EXT_ERR_INVALID_ARG, "NULL argument");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  for (auto& p : plan->pending) {
+    EXT_CUDA(cudaEventSynchronize(p.b));
+    float ms = 0.f;
+    EXT_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+    ProfStat& stt = plan->prof[p.name];
+    stt.ms += ms;
+    stt.launches += 1;
+    plan->event_pool.push_back(p.a);
+    plan->event_pool.push_back(p.b);
+  }
+  plan->pending.clear();
+  int n = 0;
+  for (auto& kv : plan->prof) {
+    if (n < n_max) {
+      if (names) {
+        std::strncpy(names + 64 * n, kv.first.c_str(), 63);
+        names[64 * n + 63] = 0;
+      }
+      if (total_ms) total_ms[n] = kv.second.ms;
+      if (launches) launches[n] = kv.second.launches;
+    }
+    ++n;
+  }
+  *n_out = n < n_max ? n : n_max;
+  plan->prof.clear();
+  return EXT_OK;
+}
+
+ext_status ext_filter_so2_decompose(ext_plan plan, const ext_filter_so2* F, double* fk_out, int64_t fk_cap,
+                                    int* n_r_out) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_TRY(check_filter(F));
+  if (!fk_out || !n_r_out) return fail(EXT_ERR_INVALID_ARG, "output is NULL");
+  if (F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW)
+    return fail(EXT_ERR_UNSUPPORTED, "analytic filters have no radial table");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  const int nr = F->kind == EXT_FILTER_TABLE ? F->n_r : sampled_nr(F);
+  const int64_t need = (int64_t)2 * (2 * F->K + 1) * nr;
+  if (fk_cap < need) return fail(EXT_ERR_INVALID_ARG, "fk_out too small");
+  cudaStream_t st = 0;
+  const double2* coef = nullptr;
+  int n_r = 0;
+  double dr = 0;
+  EXT_TRY(filter_coefficients(plan, F, st, &coef, &n_r, &dr));
+  EXT_CUDA(cudaMemcpyAsync(fk_out, coef, sizeof(double) * need, cudaMemcpyDeviceToHost, st));
+  EXT_CUDA(cudaStreamSynchronize(st));
+  *n_r_out = n_r;
+  return EXT_OK;
+}
+
+ext_status ext_corr_so2_components(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F,
+                                   float* G, void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_TRY(check_filter(F));
+  EXT_TRY(check_size(h, w));
+  if (h == 0 || w == 0) return EXT_OK;
+  if (!H || !G) return fail(EXT_ERR_INVALID_ARG, "NULL buffer");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)h * w;
+  Staged sH, sG;
+  EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P, st, &sH));
+  EXT_TRY(stage_out_alloc(plan, "out_G", G, sizeof(float) * P * (2 * F->K + 1), &sG));
+  EXT_TRY(run_components(plan, (const float*)sH.dev, h, w, F, (float*)sG.dev, st));
+  EXT_TRY(stage_out_finish(sG, st));
+  return finish_host(sH.host || sG.host, st);
+}
+
+ext_status ext_sweep_so2(ext_plan plan, const float* G, int64_t n_pix, int K, int n_angles, float* max_out,
+                         int32_t* argmax, int precision, void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  if (n_pix < 0 || K < 0 || n_angles < 1) return fail(EXT_ERR_INVALID_ARG, "bad sweep sizes");
+  if (n_pix == 0) return EXT_OK;
+  if (!G || !max_out || !argmax) return fail(EXT_ERR_INVALID_ARG, "NULL buffer");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  Staged sG, sM, sA;
+  EXT_TRY(stage_in(plan, "in_G", G, sizeof(float) * n_pix * (2 * K + 1), st, &sG));
+  EXT_TRY(stage_out_alloc(plan, "out_max", max_out, sizeof(float) * n_pix, &sM));
+  EXT_TRY(stage_out_alloc(plan, "out_arg", argmax, sizeof(int32_t) * n_pix, &sA));
+  EXT_TRY(run_sweep(plan, (const float*)sG.dev, n_pix, K, n_angles, (float*)sM.dev, (int32_t*)sA.dev,
+                    precision, st));
+  EXT_TRY(stage_out_finish(sM, st));
+  EXT_TRY(stage_out_finish(sA, st));
+  return finish_host(sG.host || sM.host || sA.host, st);
+}
+
+ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, const float* alpha,
+                        int n_angles, float* out_or_max, int32_t* argmax, int precision, void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_TRY(check_filter(F));
+  EXT_TRY(check_size(h, w));
+  if (h == 0 || w == 0) return EXT_OK;
+  if (!H || !out_or_max) return fail(EXT_ERR_INVALID_ARG, "NULL buffer");
+  if (!alpha) {
+    if (n_angles < 1) return fail(EXT_ERR_INVALID_ARG, "sweep mode needs n_angles >= 1");
+    if (!argmax) return fail(EXT_ERR_INVALID_ARG, "sweep mode needs argmax");
+    if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3)
+      return fail(EXT_ERR_INVALID_ARG, "unknown precision");
+    if (F->K > 16) return fail(EXT_ERR_UNSUPPORTED, "sweep supports K <= 16");
+  }
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)h * w;
+  const int K = F->K;
+  Staged sH, sAl, sO, sA;
+  EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P, st, &sH));
+  EXT_TRY(stage_out_alloc(plan, "out_0", out_or_max, sizeof(float) * P, &sO));
+  if (alpha) {
+    EXT_TRY(stage_in(plan, "in_alpha", alpha, sizeof(float) * P, st, &sAl));
+    const float2* S = nullptr;
+    EXT_TRY(spectra(plan, F, h, w, SPEC_CORR, st, &S));
+    const float2 *tw_w = nullptr, *tw_h = nullptr;
+    EXT_TRY(twiddle(plan, w, st, &tw_w));
+    EXT_TRY(twiddle(plan, h, st, &tw_h));
+    const int wh = w / 2 + 1;
+    void *Hh = nullptr, *Z = nullptr;
+    EXT_TRY(ensure(plan, "Hh", sizeof(float2) * P / w * wh, &Hh));
+    EXT_TRY(ensure(plan, "Zall", sizeof(float2) * P * (K + 1), &Z));
+    launch(plan, "rows_r2c", st, [&] { fft_rows_r2c(w, (const float*)sH.dev, h, (float2*)Hh, tw_w, st); });
+    launch(plan, "cols_fwd_half", st, [&] { fft_cols_fwd_half(h, (float2*)Hh, wh, tw_h, st); });
+    launch(plan, "cols_inv_corr", st,
+           [&] { fft_cols_inv_corr(h, (const float2*)Hh, w, S, 0, K + 1, (float2*)Z, tw_h, st); });
+    launch(plan, "rows_inv_field", st,
+           [&] { fft_rows_inv_field(w, (const float2*)Z, h, K, (const float*)sAl.dev, (float*)sO.dev, tw_w, st); });
+    EXT_CUDA(cudaGetLastError());
+    EXT_TRY(stage_out_finish(sO, st));
+    return finish_host(sH.host || sAl.host || sO.host, st);
+  }
+  EXT_TRY(stage_out_alloc(plan, "out_1", argmax, sizeof(int32_t) * P, &sA));
+  void* G = nullptr;
+  EXT_TRY(ensure(plan, "G", sizeof(float) * P * (2 * K + 1), &G));
+  EXT_TRY(run_components(plan, (const float*)sH.dev, h, w, F, (float*)G, st));
+  EXT_TRY(run_sweep(plan, (const float*)G, (long long)P, K, n_angles, (float*)sO.dev, (int32_t*)sA.dev, precision,
+                    st));
+  EXT_TRY(stage_out_finish(sO, st));
+  EXT_TRY(stage_out_finish(sA, st));
+  return finish_host(sH.host || sO.host || sA.host, st);
+}
+
+ext_status ext_conv_so2(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, const float* alpha,
+                        float* out, void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_TRY(check_filter(F));
+  EXT_TRY(check_size(h, w));
+  if (h == 0 || w == 0) return EXT_OK;
+  if (!H || !alpha || !out) return fail(EXT_ERR_INVALID_ARG, "NULL buffer");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)h * w;
+  const int K = F->K;
+  Staged sH, sAl, sO;
+  EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P, st, &sH));
+  EXT_TRY(stage_in(plan, "in_alpha", alpha, sizeof(float) * P, st, &sAl));
+  EXT_TRY(stage_out_alloc(plan, "out_0", out, sizeof(float) * P, &sO));
+  const float2* S = nullptr;
+  EXT_TRY(spectra(plan, F, h, w, SPEC_CONV, st, &S));
+  const float2 *tw_w = nullptr, *tw_h = nullptr;
+  EXT_TRY(twiddle(plan, w, st, &tw_w));
+  EXT_TRY(twiddle(plan, h, st, &tw_h));
+  void *A = nullptr, *Y = nullptr;
+  EXT_TRY(ensure(plan, "Aall", sizeof(float2) * P * (K + 1), &A));
+  EXT_TRY(ensure(plan, "Y", sizeof(float2) * P, &Y));
+  launch(plan, "rows_fwd_phase", st,
+         [&] { fft_rows_fwd_phase(w, (const float*)sH.dev, (const float*)sAl.dev, h, 0, K + 1, (float2*)A, tw_w, st); });
+  launch(plan, "cols_conv", st, [&] { fft_cols_conv(h, (const float2*)A, w, K, S, (float2*)Y, tw_h, st); });
+  launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, (float*)sO.dev, tw_w, st); });
+  EXT_CUDA(cudaGetLastError());
+  EXT_TRY(stage_out_finish(sO, st));
+  return finish_host(sH.host || sAl.host || sO.host, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,640 @@
+// 2D FFT passes with the extended-convolution/correlation work fused into
+// their loads and stores (Sec. 4.1).  Every kernel is a template on the 1D
+// length N it transforms, so that the Stockham stages unroll completely.
+//
+// Layouts (all row-major, x = column index fastest):
+//   H      real signal, h x w floats
+//   Hh     half spectrum of H after the row and column passes,
+//          h x (w/2 + 1) complex  (Hermitian: H^(-u,-v) = conj(H^(u,v)))
+//   S_k    filter-component spectra in column tiles of width CW(h):
+//          S[k][tile][v][c] = (scaled, possibly conjugated) F^_k(tile*CW + c, v)
+//   Z      k-chunk of partially inverted products, nk x h x w complex
+//   G      component correlations, (2K+1) planes of P = h*w floats:
+//          plane 0 = G_0, plane 2k-1 = Re G_k, plane 2k = Im G_k (k >= 1)
+#pragma once
+#include "fft_engine.cuh"
+
+// ---------------------------------------------------------- compile time ---
+struct RadixList {
+  int cnt;
+  int r[FFT_MAX_STAGES];
+};
+
+__host__ __device__ constexpr RadixList factor_radices(int n) {
+  RadixList L{0, {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}};
+  int m = n;
+  const int odd[5] = {13, 11, 7, 5, 3};
+  for (int i = 0; i < 5; ++i)
+    while (m % odd[i] == 0 && L.cnt < FFT_MAX_STAGES) { L.r[L.cnt++] = odd[i]; m /= odd[i]; }
+  while (m % 16 == 0 && L.cnt < FFT_MAX_STAGES) { L.r[L.cnt++] = 16; m /= 16; }
+  if (m % 8 == 0) { L.r[L.cnt++] = 8; m /= 8; }
+  if (m % 4 == 0) { L.r[L.cnt++] = 4; m /= 4; }
+  if (m % 2 == 0) { L.r[L.cnt++] = 2; m /= 2; }
+  return L;
+}
+
+__host__ __device__ constexpr int ct_sidx_len(int n) { return n + ((n - 1) >> 4) + 1; }
+
+template <int N>
+struct LineCfg {
+  static constexpr int TPL = (N + FFT_MAXE - 1) / FFT_MAXE;   // threads per line
+  static constexpr int LS = ct_sidx_len(N);                   // padded line length
+  // row passes: RL lines per block; column passes: CW adjacent columns per block
+  static constexpr int RL = (8192 / N) < 1 ? 1 : ((8192 / N) > 16 ? 16 : (8192 / N));
+  static constexpr int CW = RL;
+  static constexpr int ROW_THREADS = ((RL * TPL + 31) / 32) * 32;
+  static constexpr int TW_BYTES = N * 8;   // twiddle table copy in shared memory
+  static constexpr int ROW_SMEM = RL * LS * 8 + TW_BYTES;
+  static constexpr int ROW_EPT = (RL * N + ROW_THREADS - 1) / ROW_THREADS;
+  static constexpr int COL_THREADS = ((CW * TPL + 31) / 32) * 32;
+  static constexpr int COL_SMEM = CW * LS * 8 + TW_BYTES;
+  static constexpr int COL_EPT = (CW * N + COL_THREADS - 1) / COL_THREADS;
+  // blocks per SM the register budget is sized for
+  static constexpr int ROW_MINB = ROW_THREADS >= 512 ? 2 : 1;
+  static constexpr int COL_MINB = COL_THREADS >= 512 ? 2 : 1;
+};
+
+// Visit the elements of a block's lines: element e = threadIdx.x + i * THREADS,
+// i < EPT, all indices compile-time except threadIdx.x.  fn(i, e).
+template <int TOTAL, int THREADS, class Fn>
+__device__ __forceinline__ void for_elems(Fn&& fn) {
+  constexpr int EPT = (TOTAL + THREADS - 1) / THREADS;
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) {
+    const int e = threadIdx.x + i * THREADS;
+    if (TOTAL % THREADS == 0 || e < TOTAL) fn(i, e);
+  }
+}
+
+// Same visit in chunks of G elements per thread: load(i, e) for the whole
+// chunk first (so G loads are in flight together), then store(i, e).
+template <int TOTAL, int THREADS, int G, class Load, class Store>
+__device__ __forceinline__ void for_elems_staged(Load&& load, Store&& store) {
+  constexpr int EPT = (TOTAL + THREADS - 1) / THREADS;
+#pragma unroll
+  for (int i0 = 0; i0 < EPT; i0 += G) {
+#pragma unroll
+    for (int i = i0; i < i0 + G && i < EPT; ++i) {
+      const int e = threadIdx.x + i * THREADS;
+      if (TOTAL % THREADS == 0 || e < TOTAL) load(i - i0, e);
+    }
+#pragma unroll
+    for (int i = i0; i < i0 + G && i < EPT; ++i) {
+      const int e = threadIdx.x + i * THREADS;
+      if (TOTAL % THREADS == 0 || e < TOTAL) store(i - i0, e);
+    }
+  }
+}
+
+constexpr int STAGE_G = 8;
+
+template <int N, int R, int NS, bool INV, bool LINE_FAST, int NLINES, int THREADS>
+__device__ __forceinline__ void ct_stage(float2* buf, int ls, int es, const float2* __restrict__ tw) {
+  constexpr int NB = N / R;
+  constexpr int TSTEP = N / (NS * R);
+  constexpr int total = NB * NLINES;
+  constexpr int S = (total + THREADS - 1) / THREADS;
+  static_assert(S * R <= FFT_MAXE + R, "too many butterflies per thread");
+  constexpr int nlines = NLINES;
+  float2 v[S][R];
+  int base_s[S], dst_s[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int it = threadIdx.x + s * THREADS;
+    base_s[s] = -1;
+    dst_s[s] = 0;
+    if (it < total) {
+      int line, j;
+      if (LINE_FAST) { line = it % nlines; j = it / nlines; }
+      else { j = it % NB; line = it / NB; }
+      const int k = j % NS;
+      const float2* base = buf + line * ls;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float2 a = base[sidx(j + r * NB) * es];
+        if (NS > 1 && r > 0) {
+          float2 w = tw[r * k * TSTEP];
+          if (INV) w.y = -w.y;
+          a = c_mul(a, w);
+        }
+        v[s][r] = a;
+      }
+      base_s[s] = line * ls;
+      dst_s[s] = (j / NS) * NS * R + k;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    if (base_s[s] >= 0) {
+      dft<R, INV>(v[s]);
+      float2* base = buf + base_s[s];
+#pragma unroll
+      for (int r = 0; r < R; ++r) base[sidx(dst_s[s] + r * NS) * es] = v[s][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int N, bool INV, bool LINE_FAST, int NLINES, int THREADS, int ST = 0, int NS = 1>
+__device__ __forceinline__ void ct_fft(float2* buf, int ls, int es, const float2* tw) {
+  constexpr RadixList L = factor_radices(N);
+  if constexpr (ST < L.cnt) {
+    constexpr int R = L.r[ST];
+    ct_stage<N, R, NS, INV, LINE_FAST, NLINES, THREADS>(buf, ls, es, tw);
+    ct_fft<N, INV, LINE_FAST, NLINES, THREADS, ST + 1, NS * R>(buf, ls, es, tw);
+  }
+}
+
+// Copies the length-N twiddle table into shared memory right after the
+// block's data region and returns it (the caller's next __syncthreads makes
+// it visible).
+template <int N, int DATA_ELEMS>
+__device__ __forceinline__ const float2* stage_twiddles(float2* sm, const float2* __restrict__ tw, int threads) {
+  float2* t = sm + DATA_ELEMS;
+  for (int i = threadIdx.x; i < N; i += threads) t[i] = __ldg(tw + i);
+  return t;
+}
+
+// Row layout: line l, element x at sm[l * LS + sidx(x)].
+template <int N, bool INV>
+__device__ __forceinline__ void row_fft(float2* sm, const float2* tw) {
+  using C = LineCfg<N>;
+  ct_fft<N, INV, false, C::RL, C::ROW_THREADS>(sm, C::LS, 1, tw);
+}
+// Column layout: column c, element v at sm[c + sidx(v) * CW].
+template <int N, bool INV>
+__device__ __forceinline__ void col_fft(float2* sm, const float2* tw) {
+  using C = LineCfg<N>;
+  ct_fft<N, INV, true, C::CW, C::COL_THREADS>(sm, 1, C::CW, tw);
+}
+
+// exp(i k alpha) for an FP32 angle: k*alpha is formed exactly as p + e
+// (two-product with an FMA), reduced by an additive three-part split of 2 pi
+// (Cody & Waite's argument reduction), and only then passed to sincosf.
+__device__ __forceinline__ void sincos_kalpha(int k, float alpha, float* s, float* c) {
+  const float kf = (float)k;
+  const float p = kf * alpha;
+  const float e = fmaf(kf, alpha, -p);
+  const float n = rintf(p * 0.15915494309189535f);
+  float r = fmaf(-n, 6.28125f, p);
+  r = fmaf(-n, 0.0019353071693331003f, r);
+  r = fmaf(-n, 1.0253131677018246e-11f, r);
+  r += e;
+  sincosf(r, s, c);
+}
+
+// ------------------------------------------------------------ row passes ---
+// All global loads of a block are first gathered into registers (every
+// thread has its EPT loads in flight at once), then written to shared memory.
+
+// Forward real-to-complex transform of the rows of H, two rows per complex
+// line: z = H[2p] + i H[2p+1], Z = FFT(z), then
+//   X_even[u] = (Z[u] + conj Z[-u]) / 2,  X_odd[u] = -i (Z[u] - conj Z[-u]) / 2.
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
+k_rows_r2c(const float* __restrict__ H, int h, float2* __restrict__ Hh, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::ROW_THREADS;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
+  const int pair0 = blockIdx.x * C::RL;
+  float2 v[STAGE_G];
+  for_elems_staged<C::RL * N, T, STAGE_G>(
+      [&](int i, int e) {
+        const int l = e / N, x = e % N;
+        const int y0 = 2 * (pair0 + l);
+        v[i].x = (y0 < h) ? __ldg(H + (size_t)y0 * N + x) : 0.f;
+        v[i].y = (y0 + 1 < h) ? __ldg(H + (size_t)(y0 + 1) * N + x) : 0.f;
+      },
+      [&](int i, int e) { sm[(e / N) * C::LS + sidx(e % N)] = v[i]; });
+  __syncthreads();
+  row_fft<N, false>(sm, twl);
+  constexpr int WH = N / 2 + 1;
+  for_elems<C::RL * WH, T>([&](int i, int e) {
+    const int l = e / WH, u = e % WH;
+    const int y0 = 2 * (pair0 + l);
+    if (y0 >= h) return;
+    const float2 z = sm[l * C::LS + sidx(u)];
+    const float2 zm = c_conj(sm[l * C::LS + sidx((N - u) % N)]);
+    const float2 x0 = c_scale(c_add(z, zm), 0.5f);
+    const float2 d = c_scale(c_sub(z, zm), 0.5f);
+    Hh[(size_t)y0 * WH + u] = x0;
+    if (y0 + 1 < h) Hh[(size_t)(y0 + 1) * WH + u] = make_float2(d.y, -d.x);
+  });
+}
+
+// Forward transform of the steered signals A_k = H exp(-i k alpha) (Sec. 4.1,
+// extended convolution: the signal is pre-multiplied before convolving with
+// F_k).  blockIdx.y selects k = k0 + blockIdx.y.
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
+k_rows_fwd_phase(const float* __restrict__ H, const float* __restrict__ alpha, int h, int k0,
+                 float2* __restrict__ A, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::ROW_THREADS;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
+  const int y0 = blockIdx.x * C::RL;
+  const int k = k0 + blockIdx.y;
+  float hv[STAGE_G], av[STAGE_G];
+  for_elems_staged<C::RL * N, T, STAGE_G>(
+      [&](int i, int e) {
+        const int y = y0 + e / N;
+        const size_t idx = (size_t)y * N + e % N;
+        hv[i] = (y < h) ? __ldg(H + idx) : 0.f;
+        av[i] = (y < h) ? __ldg(alpha + idx) : 0.f;
+      },
+      [&](int i, int e) {
+        float s, c;
+        sincos_kalpha(k, av[i], &s, &c);
+        sm[(e / N) * C::LS + sidx(e % N)] = make_float2(hv[i] * c, -hv[i] * s);
+      });
+  __syncthreads();
+  row_fft<N, false>(sm, twl);
+  float2* out = A + (size_t)blockIdx.y * h * N;
+  for_elems<C::RL * N, T>([&](int i, int e) {
+    const int y = y0 + e / N;
+    if (y < h) out[(size_t)y * N + e % N] = sm[(e / N) * C::LS + sidx(e % N)];
+  });
+}
+
+template <int N>
+__device__ __forceinline__ void rows_load_complex(float2* sm, const float2* src, int y0, int h) {
+  using C = LineCfg<N>;
+  constexpr int T = C::ROW_THREADS;
+  float2 v[STAGE_G];
+  for_elems_staged<C::RL * N, T, STAGE_G>(
+      [&](int i, int e) {
+        const int y = y0 + e / N;
+        v[i] = (y < h) ? src[(size_t)y * N + e % N] : make_float2(0.f, 0.f);
+      },
+      [&](int i, int e) { sm[(e / N) * C::LS + sidx(e % N)] = v[i]; });
+}
+
+// Complex rows, forward or inverse, X -> Y (may alias); blockIdx.y = plane.
+template <int N, bool INV>
+__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
+k_rows_c2c(const float2* X, int h, float2* Y, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
+  const int y0 = blockIdx.x * C::RL;
+  const size_t plane = (size_t)blockIdx.y * h * N;
+  rows_load_complex<N>(sm, X + plane, y0, h);
+  __syncthreads();
+  row_fft<N, INV>(sm, twl);
+  for_elems<C::RL * N, C::ROW_THREADS>([&](int i, int e) {
+    const int y = y0 + e / N;
+    if (y < h) Y[plane + (size_t)y * N + e % N] = sm[(e / N) * C::LS + sidx(e % N)];
+  });
+}
+
+// Inverse row pass writing the component correlations G_k (k = k0 + blockIdx.y)
+// into their planes.
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
+k_rows_inv_components(const float2* __restrict__ Z, int h, int k0, float* __restrict__ G,
+                      const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
+  const int y0 = blockIdx.x * C::RL;
+  const int k = k0 + blockIdx.y;
+  const size_t P = (size_t)h * N;
+  rows_load_complex<N>(sm, Z + (size_t)blockIdx.y * P, y0, h);
+  __syncthreads();
+  row_fft<N, true>(sm, twl);
+  float* re = G + (k == 0 ? 0 : (size_t)(2 * k - 1) * P);
+  float* im = G + (size_t)(2 * k) * P;
+  for_elems<C::RL * N, C::ROW_THREADS>([&](int i, int e) {
+    const int y = y0 + e / N;
+    if (y >= h) return;
+    const float2 v = sm[(e / N) * C::LS + sidx(e % N)];
+    const size_t idx = (size_t)y * N + e % N;
+    re[idx] = v.x;
+    if (k != 0) im[idx] = v.y;
+  });
+}
+
+// Inverse row pass with the steering sum of Sec. 4.1 ("Linear Combination")
+// fused in: out(p) = G_0(p) + 2 sum_{k=1..K} Re(exp(i k alpha(p)) G_k(p)),
+// looping over all K+1 components inside the block (real filter and signal).
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, 1)
+k_rows_inv_field(const float2* __restrict__ Z, int h, int K, const float* __restrict__ alpha,
+                 float* __restrict__ out, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::ROW_THREADS;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
+  float* acc = reinterpret_cast<float*>(sm + C::RL * C::LS + N);
+  const int y0 = blockIdx.x * C::RL;
+  const size_t P = (size_t)h * N;
+  for_elems<C::RL * N, T>([&](int i, int e) { acc[e] = 0.f; });
+  for (int k = 0; k <= K; ++k) {
+    rows_load_complex<N>(sm, Z + (size_t)k * P, y0, h);
+    __syncthreads();
+    row_fft<N, true>(sm, twl);
+    for_elems<C::RL * N, T>([&](int i, int e) {
+      const int y = y0 + e / N;
+      if (y >= h) return;
+      const float2 g = sm[(e / N) * C::LS + sidx(e % N)];
+      if (k == 0) {
+        acc[e] += g.x;
+      } else {
+        float s, c;
+        sincos_kalpha(k, __ldg(alpha + (size_t)y * N + e % N), &s, &c);
+        acc[e] += 2.f * (c * g.x - s * g.y);
+      }
+    });
+    __syncthreads();
+  }
+  for_elems<C::RL * N, T>([&](int i, int e) {
+    const int y = y0 + e / N;
+    if (y < h) out[(size_t)y * N + e % N] = acc[e];
+  });
+}
+
+// Inverse row pass keeping the real part (extended convolution output).
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
+k_rows_inv_real(const float2* __restrict__ Y, int h, float* __restrict__ out, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
+  const int y0 = blockIdx.x * C::RL;
+  rows_load_complex<N>(sm, Y, y0, h);
+  __syncthreads();
+  row_fft<N, true>(sm, twl);
+  for_elems<C::RL * N, C::ROW_THREADS>([&](int i, int e) {
+    const int y = y0 + e / N;
+    if (y < h) out[(size_t)y * N + e % N] = sm[(e / N) * C::LS + sidx(e % N)].x;
+  });
+}
+
+// --------------------------------------------------------- column passes ---
+// Element (v, c) of a tile of CW adjacent columns sits at sm[c + sidx(v) * CW];
+// element e of a block maps to v = e / CW, c = e % CW (adjacent threads read
+// adjacent columns of one row).
+
+template <int N>
+__device__ __forceinline__ void cols_store_sm(float2* sm, const float2* v) {
+  using C = LineCfg<N>;
+  for_elems<C::CW * N, C::COL_THREADS>([&](int i, int e) { sm[e % C::CW + sidx(e / C::CW) * C::CW] = v[i]; });
+}
+
+// Forward column pass of the half spectrum, in place (pitch ncols).
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, LineCfg<N>::COL_MINB)
+k_cols_fwd_half(float2* Hh, int ncols, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::COL_THREADS;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
+  const int u0 = blockIdx.x * C::CW;
+  float2 v[STAGE_G];
+  for_elems_staged<C::CW * N, T, STAGE_G>(
+      [&](int i, int e) {
+        const int u = u0 + e % C::CW;
+        v[i] = (u < ncols) ? Hh[(size_t)(e / C::CW) * ncols + u] : make_float2(0.f, 0.f);
+      },
+      [&](int i, int e) { sm[e % C::CW + sidx(e / C::CW) * C::CW] = v[i]; });
+  __syncthreads();
+  col_fft<N, false>(sm, twl);
+  for_elems<C::CW * N, T>([&](int i, int e) {
+    const int u = u0 + e % C::CW;
+    if (u < ncols) Hh[(size_t)(e / C::CW) * ncols + u] = sm[e % C::CW + sidx(e / C::CW) * C::CW];
+  });
+}
+
+// Forward column pass of a component grid (already row-transformed, pitch w),
+// stored as a tiled spectrum: conj(X) * scale (correlation) or X * scale
+// (convolution).
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, LineCfg<N>::COL_MINB)
+k_cols_fwd_spectrum(const float2* __restrict__ X, int w, int conj_out, float scale,
+                    float2* __restrict__ S, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::COL_THREADS;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
+  const int tile = blockIdx.x;
+  const int u0 = tile * C::CW;
+  float2 v[STAGE_G];
+  for_elems_staged<C::CW * N, T, STAGE_G>(
+      [&](int i, int e) {
+        const int u = u0 + e % C::CW;
+        v[i] = (u < w) ? X[(size_t)(e / C::CW) * w + u] : make_float2(0.f, 0.f);
+      },
+      [&](int i, int e) { sm[e % C::CW + sidx(e / C::CW) * C::CW] = v[i]; });
+  __syncthreads();
+  col_fft<N, false>(sm, twl);
+  float2* dst = S + (size_t)tile * N * C::CW;
+  for_elems<C::CW * N, T>([&](int i, int e) {
+    float2 val = c_scale(sm[e % C::CW + sidx(e / C::CW) * C::CW], scale);
+    if (conj_out) val.y = -val.y;
+    dst[e] = val;   // e = v * CW + c
+  });
+}
+
+// Inverse column pass of the correlation products H^(u,v) conj(F^_k(u,v))
+// (Sec. 4.1 "Standard Correlation"), with H^ rebuilt from its half by
+// Hermitian symmetry; k = k0 + blockIdx.y, output Z[blockIdx.y] (pitch w).
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, LineCfg<N>::COL_MINB)
+k_cols_inv_corr(const float2* __restrict__ Hh, int w, const float2* __restrict__ S, int k0,
+                float2* __restrict__ Z, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::COL_THREADS;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
+  const int tile = blockIdx.x;
+  const int u0 = tile * C::CW;
+  const int wh = w / 2 + 1;
+  const int ntiles = (w + C::CW - 1) / C::CW;
+  const float2* spec = S + ((size_t)(k0 + blockIdx.y) * ntiles + tile) * N * C::CW;
+  float2 hv[STAGE_G], sv[STAGE_G];
+  for_elems_staged<C::CW * N, T, STAGE_G>(
+      [&](int i, int e) {
+        const int v = e / C::CW, u = u0 + e % C::CW;
+        sv[i] = __ldg(spec + e);
+        if (u < wh) hv[i] = __ldg(Hh + (size_t)v * wh + u);
+        else if (u < w) hv[i] = c_conj(__ldg(Hh + (size_t)((N - v) % N) * wh + (w - u)));
+        else hv[i] = make_float2(0.f, 0.f);
+      },
+      [&](int i, int e) { sm[e % C::CW + sidx(e / C::CW) * C::CW] = c_mul(hv[i], sv[i]); });
+  __syncthreads();
+  col_fft<N, true>(sm, twl);
+  float2* dst = Z + (size_t)blockIdx.y * N * w;
+  for_elems<C::CW * N, T>([&](int i, int e) {
+    const int u = u0 + e % C::CW;
+    if (u < w) dst[(size_t)(e / C::CW) * w + u] = sm[e % C::CW + sidx(e / C::CW) * C::CW];
+  });
+}
+
+// Extended convolution, column stage: forward column FFT of every steered
+// signal A_k, product with its (weighted) spectrum, sum over k in registers,
+// and the inverse column FFT of the sum (Sec. 4.1, last paragraph).
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, 1)
+k_cols_conv(const float2* __restrict__ A, int w, int K, const float2* __restrict__ S,
+            float2* __restrict__ Y, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::COL_THREADS;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
+  const int tile = blockIdx.x;
+  const int u0 = tile * C::CW;
+  const int ntiles = (w + C::CW - 1) / C::CW;
+  float2 acc[C::COL_EPT];
+  for_elems<C::CW * N, T>([&](int i, int e) { acc[i] = make_float2(0.f, 0.f); });
+  for (int k = 0; k <= K; ++k) {
+    const float2* src = A + (size_t)k * N * w;
+    {
+      float2 v[STAGE_G];
+      for_elems_staged<C::CW * N, T, STAGE_G>(
+          [&](int i, int e) {
+            const int u = u0 + e % C::CW;
+            v[i] = (u < w) ? __ldg(src + (size_t)(e / C::CW) * w + u) : make_float2(0.f, 0.f);
+          },
+          [&](int i, int e) { sm[e % C::CW + sidx(e / C::CW) * C::CW] = v[i]; });
+    }
+    __syncthreads();
+    col_fft<N, false>(sm, twl);
+    const float2* spec = S + ((size_t)k * ntiles + tile) * N * C::CW;
+    for_elems<C::CW * N, T>([&](int i, int e) {
+      const float2 sp = __ldg(spec + e);
+      const float2 x = sm[e % C::CW + sidx(e / C::CW) * C::CW];
+      acc[i].x = fmaf(x.x, sp.x, fmaf(-x.y, sp.y, acc[i].x));
+      acc[i].y = fmaf(x.x, sp.y, fmaf(x.y, sp.x, acc[i].y));
+    });
+    __syncthreads();
+  }
+  cols_store_sm<N>(sm, acc);
+  __syncthreads();
+  col_fft<N, true>(sm, twl);
+  for_elems<C::CW * N, T>([&](int i, int e) {
+    const int u = u0 + e % C::CW;
+    if (u < w) Y[(size_t)(e / C::CW) * w + u] = sm[e % C::CW + sidx(e / C::CW) * C::CW];
+  });
+}
+
+// ------------------------------------------------------------- launchers ---
+template <int N>
+struct FftOps {
+  using C = LineCfg<N>;
+  static void rows_r2c(const float* H, int h, float2* Hh, const float2* tw, cudaStream_t st);
+  static void rows_fwd_phase(const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                             const float2* tw, cudaStream_t st);
+  static void rows_c2c(const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
+                       cudaStream_t st);
+  static void rows_inv_components(const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
+                                  cudaStream_t st);
+  static void rows_inv_field(const float2* Z, int h, int K, const float* alpha, float* out,
+                             const float2* tw, cudaStream_t st);
+  static void rows_inv_real(const float2* Y, int h, float* out, const float2* tw, cudaStream_t st);
+  static void cols_fwd_half(float2* Hh, int ncols, const float2* tw, cudaStream_t st);
+  static void cols_fwd_spectrum(const float2* X, int w, int conj_out, float scale, float2* S,
+                                const float2* tw, cudaStream_t st);
+  static void cols_inv_corr(const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
+                            const float2* tw, cudaStream_t st);
+  static void cols_conv(const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
+                        cudaStream_t st);
+};
+
+template <typename KernelT>
+static inline void ext_set_smem(KernelT kernel, int bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int N>
+void FftOps<N>::rows_r2c(const float* H, int h, float2* Hh, const float2* tw, cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_rows_r2c<N>, C::ROW_SMEM), true);
+  (void)once;
+  const int pairs = (h + 1) / 2;
+  dim3 grid((pairs + C::RL - 1) / C::RL);
+  k_rows_r2c<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, h, Hh, tw);
+}
+
+template <int N>
+void FftOps<N>::rows_fwd_phase(const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                               const float2* tw, cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_rows_fwd_phase<N>, C::ROW_SMEM), true);
+  (void)once;
+  dim3 grid((h + C::RL - 1) / C::RL, nk);
+  k_rows_fwd_phase<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, alpha, h, k0, A, tw);
+}
+
+template <int N>
+void FftOps<N>::rows_c2c(const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
+                         cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_rows_c2c<N, false>, C::ROW_SMEM),
+                            ext_set_smem(k_rows_c2c<N, true>, C::ROW_SMEM), true);
+  (void)once;
+  dim3 grid((h + C::RL - 1) / C::RL, nplanes);
+  if (inv) k_rows_c2c<N, true><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(X, h, Y, tw);
+  else k_rows_c2c<N, false><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(X, h, Y, tw);
+}
+
+template <int N>
+void FftOps<N>::rows_inv_components(const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
+                                    cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_rows_inv_components<N>, C::ROW_SMEM), true);
+  (void)once;
+  dim3 grid((h + C::RL - 1) / C::RL, nk);
+  k_rows_inv_components<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(Z, h, k0, G, tw);
+}
+
+template <int N>
+void FftOps<N>::rows_inv_field(const float2* Z, int h, int K, const float* alpha, float* out,
+                               const float2* tw, cudaStream_t st) {
+  constexpr int smem = C::ROW_SMEM + C::RL * N * 4;
+  static const bool once = (ext_set_smem(k_rows_inv_field<N>, smem), true);
+  (void)once;
+  dim3 grid((h + C::RL - 1) / C::RL);
+  k_rows_inv_field<N><<<grid, C::ROW_THREADS, smem, st>>>(Z, h, K, alpha, out, tw);
+}
+
+template <int N>
+void FftOps<N>::rows_inv_real(const float2* Y, int h, float* out, const float2* tw, cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_rows_inv_real<N>, C::ROW_SMEM), true);
+  (void)once;
+  dim3 grid((h + C::RL - 1) / C::RL);
+  k_rows_inv_real<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(Y, h, out, tw);
+}
+
+template <int N>
+void FftOps<N>::cols_fwd_half(float2* Hh, int ncols, const float2* tw, cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_cols_fwd_half<N>, C::COL_SMEM), true);
+  (void)once;
+  dim3 grid((ncols + C::CW - 1) / C::CW);
+  k_cols_fwd_half<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(Hh, ncols, tw);
+}
+
+template <int N>
+void FftOps<N>::cols_fwd_spectrum(const float2* X, int w, int conj_out, float scale, float2* S,
+                                  const float2* tw, cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_cols_fwd_spectrum<N>, C::COL_SMEM), true);
+  (void)once;
+  dim3 grid((w + C::CW - 1) / C::CW);
+  k_cols_fwd_spectrum<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(X, w, conj_out, scale, S, tw);
+}
+
+template <int N>
+void FftOps<N>::cols_inv_corr(const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
+                              const float2* tw, cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_cols_inv_corr<N>, C::COL_SMEM), true);
+  (void)once;
+  dim3 grid((w + C::CW - 1) / C::CW, nk);
+  k_cols_inv_corr<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(Hh, w, S, k0, Z, tw);
+}
+
+template <int N>
+void FftOps<N>::cols_conv(const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
+                          cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_cols_conv<N>, C::COL_SMEM), true);
+  (void)once;
+  dim3 grid((w + C::CW - 1) / C::CW);
+  k_cols_conv<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(A, w, K, S, Y, tw);
+}

@@ -1,0 +1,92 @@
+// Runtime dispatch of the 2D FFT passes onto the compile-time line lengths.
+#include "fft2d.cuh"
+#include "internal.h"
+
+#define EXT_EXTERN(N) extern template struct FftOps<N>;
+EXT_FFT_SIZES(EXT_EXTERN)
+#undef EXT_EXTERN
+
+bool fft_size_supported(int n) {
+  switch (n) {
+#define EXT_CASE(N) case N: return true;
+    EXT_FFT_SIZES(EXT_CASE)
+#undef EXT_CASE
+    default: return false;
+  }
+}
+
+int fft_col_tile(int n) {
+  switch (n) {
+#define EXT_CASE(N) case N: return LineCfg<N>::CW;
+    EXT_FFT_SIZES(EXT_CASE)
+#undef EXT_CASE
+    default: return 0;
+  }
+}
+
+#define EXT_C1(N) case N: FftOps<N>::rows_r2c(H, h, Hh, tw, st); return;
+void fft_rows_r2c(int w, const float* H, int h, float2* Hh, const float2* tw, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::rows_fwd_phase(H, alpha, h, k0, nk, A, tw, st); return;
+void fft_rows_fwd_phase(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                        const float2* tw, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::rows_c2c(X, h, nplanes, Y, inv, tw, st); return;
+void fft_rows_c2c(int w, const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
+                  cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::rows_inv_components(Z, h, k0, nk, G, tw, st); return;
+void fft_rows_inv_components(int w, const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
+                             cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::rows_inv_field(Z, h, K, alpha, out, tw, st); return;
+void fft_rows_inv_field(int w, const float2* Z, int h, int K, const float* alpha, float* out,
+                        const float2* tw, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::rows_inv_real(Y, h, out, tw, st); return;
+void fft_rows_inv_real(int w, const float2* Y, int h, float* out, const float2* tw, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::cols_fwd_half(Hh, ncols, tw, st); return;
+void fft_cols_fwd_half(int h, float2* Hh, int ncols, const float2* tw, cudaStream_t st) {
+  switch (h) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::cols_fwd_spectrum(X, w, conj_out, scale, S, tw, st); return;
+void fft_cols_fwd_spectrum(int h, const float2* X, int w, int conj_out, float scale, float2* S,
+                           const float2* tw, cudaStream_t st) {
+  switch (h) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::cols_inv_corr(Hh, w, S, k0, nk, Z, tw, st); return;
+void fft_cols_inv_corr(int h, const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
+                       const float2* tw, cudaStream_t st) {
+  switch (h) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::cols_conv(A, w, K, S, Y, tw, st); return;
+void fft_cols_conv(int h, const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
+                   cudaStream_t st) {
+  switch (h) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1

@@ -1,0 +1,51 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "../../include/extconv.h"
+
+// FFT sizes compiled into the library, split into groups that are
+// instantiated in separate translation units (compiled in parallel).
+#define EXT_FFT_SIZES_A(X) X(32) X(48) X(64) X(96) X(128) X(160)
+#define EXT_FFT_SIZES_B(X) X(192) X(256) X(320) X(384)
+#define EXT_FFT_SIZES_C(X) X(448) X(512) X(576) X(640)
+#define EXT_FFT_SIZES_D(X) X(704) X(768) X(832) X(896)
+#define EXT_FFT_SIZES_E(X) X(960) X(1024) X(1536)
+#define EXT_FFT_SIZES_F(X) X(2048) X(3072) X(4096)
+#define EXT_FFT_SIZES(X) \
+  EXT_FFT_SIZES_A(X) EXT_FFT_SIZES_B(X) EXT_FFT_SIZES_C(X) EXT_FFT_SIZES_D(X) EXT_FFT_SIZES_E(X) EXT_FFT_SIZES_F(X)
+
+// ----- 2D FFT passes, dispatched on the runtime line length n (fft_dispatch.cu)
+bool fft_size_supported(int n);
+int fft_col_tile(int n);   // columns per block of the length-n column passes
+void fft_rows_r2c(int w, const float* H, int h, float2* Hh, const float2* tw, cudaStream_t st);
+void fft_rows_fwd_phase(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                        const float2* tw, cudaStream_t st);
+void fft_rows_c2c(int w, const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
+                  cudaStream_t st);
+void fft_rows_inv_components(int w, const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
+                             cudaStream_t st);
+void fft_rows_inv_field(int w, const float2* Z, int h, int K, const float* alpha, float* out,
+                        const float2* tw, cudaStream_t st);
+void fft_rows_inv_real(int w, const float2* Y, int h, float* out, const float2* tw, cudaStream_t st);
+void fft_cols_fwd_half(int h, float2* Hh, int ncols, const float2* tw, cudaStream_t st);
+void fft_cols_fwd_spectrum(int h, const float2* X, int w, int conj_out, float scale, float2* S,
+                           const float2* tw, cudaStream_t st);
+void fft_cols_inv_corr(int h, const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
+                       const float2* tw, cudaStream_t st);
+void fft_cols_conv(int h, const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
+                   cudaStream_t st);
+
+// ----- filter side, FP64 (filter.cu)
+void launch_twiddle(float2* tw, int n, cudaStream_t st);
+void launch_decompose_sampled(const double* img, int side, double dr, int n_r, int n_theta, int K,
+                              double* P, double2* fk, cudaStream_t st);
+void launch_component_grid(int kind, int K, int k, const double2* coef, int n_r, double dr, double sigma,
+                           int R, int h, int w, float2* grid, cudaStream_t st);
+void launch_sweep_table(int K, int J, int cp, float* B, cudaStream_t st);
+
+// ----- sweep (sweep.cu)
+// B: J rows of cp floats (cp = 2K rounded up to a multiple of 4).
+bool sweep_fp32(const float* G, long long P, int K, int J, const float* B, int cp, float* maxv,
+                int32_t* argmax, cudaStream_t st);

@@ -1,0 +1,244 @@
+"""GPU parity of the SO(2) path (C ABI, CUDA kernels) against the FP64 oracle.
+
+Tolerances: FP32 field outputs within relative L2 1e-5 of the oracle; sweep
+maxima within 1e-5 of the score scale; argmax identical wherever the
+oracle's best and second-best scores differ by more than 1e-6 of the score
+scale (a tie window; flips inside it are counted and reported)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth
+from oracle.filters_so2 import AnalyticGaussPow, RadialTable, decompose_sampled
+from oracle.so2 import (component_correlation, ext_conv_so2 as conv_ref, ext_corr_so2 as corr_ref,
+                        sweep_from_components, sweep_so2_at, sweep_so2_fft)
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+TIE = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ec():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2006_13188_gb300 as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def plan(ec):
+    p = ec.Plan(0)
+    yield p
+    p.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def rel_l2(got, ref):
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+# ------------------------------------------------------ filter decomposition ---
+
+def test_decomposition_matches_oracle(ec, plan):
+    rng = np.random.default_rng(3)
+    tmpl = synth.smooth_random_template(rng, 20, 2.5)
+    F = ec.FilterSO2.sampled(tmpl, 12, 0.25, 96)
+    got = ec.ext_filter_so2_decompose(plan, F)
+    ref = decompose_sampled(tmpl, 12, 0.25, 96).fk
+    assert got.shape == ref.shape
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+# ------------------------------------------------------- component spectra ---
+
+@pytest.mark.parametrize("h,w,K,R", [(64, 64, 3, 7), (96, 160, 4, 9), (48, 64, 2, 30)])
+def test_components_match_oracle(ec, plan, h, w, K, R):
+    """G_k = H (*) F_k (Sec. 4.1 Standard Correlation); the last case has a box
+    larger than the image (wrapped, accumulated taps)."""
+    rng = np.random.default_rng(h + w + K)
+    H = rng.standard_normal((h, w)).astype(np.float32)
+    a = synth.random_gauss_pow_coeffs(K + 100, K)
+    sigma = 3.0
+    F = ec.FilterSO2.analytic(a, sigma, R)
+    G = torch.empty((2 * K + 1, h, w), dtype=torch.float32, device="cuda")
+    ec.ext_corr_so2_components(plan, dev(H), h, w, F, G)
+    G = G.cpu().numpy()
+    filt = AnalyticGaussPow(a, sigma)
+    for k in range(K + 1):
+        ref = component_correlation(H, filt, k, R)
+        if k == 0:
+            assert rel_l2(G[0], ref.real) < REL_L2
+        else:
+            got = G[2 * k - 1] + 1j * G[2 * k]
+            assert rel_l2(got, ref) < REL_L2, k
+
+
+# ------------------------------------------------------------- field modes ---
+
+@pytest.mark.parametrize("h,w", [(64, 96), (128, 128)])
+def test_corr_field_matches_oracle(ec, plan, h, w):
+    prob = synth.so2_conv_problem(size=max(h, w))
+    H = prob["H"][:h, :w].copy()
+    alpha = prob["alpha"][:h, :w].copy()
+    F = ec.FilterSO2.analytic(prob["a"], prob["sigma"], prob["radius"])
+    out = torch.empty((h, w), dtype=torch.float32, device="cuda")
+    ec.ext_corr_so2(plan, dev(H), h, w, F, dev(alpha), 0, out, None)
+    ref = corr_ref(H, AnalyticGaussPow(prob["a"], prob["sigma"]), alpha, prob["radius"])
+    assert np.max(np.abs(ref.imag)) < 1e-9 * np.max(np.abs(ref.real))
+    assert rel_l2(out.cpu().numpy(), ref.real) < REL_L2
+
+
+@pytest.mark.parametrize("h,w", [(64, 96), (128, 64)])
+def test_conv_field_matches_oracle(ec, plan, h, w):
+    prob = synth.so2_conv_problem(size=max(h, w))
+    H = prob["H"][:h, :w].copy()
+    alpha = prob["alpha"][:h, :w].copy()
+    F = ec.FilterSO2.analytic(prob["a"], prob["sigma"], prob["radius"])
+    out = torch.empty((h, w), dtype=torch.float32, device="cuda")
+    ec.ext_conv_so2(plan, dev(H), h, w, F, dev(alpha), out)
+    ref = conv_ref(H, AnalyticGaussPow(prob["a"], prob["sigma"]), alpha, prob["radius"])
+    assert rel_l2(out.cpu().numpy(), ref.real) < REL_L2
+
+
+def test_conv_256_full_config(ec, plan):
+    """The 256 x 256, K = 4, 31 x 31 workload, every pixel against the
+    brute-force scatter of Eq. Def-EConv."""
+    prob = synth.so2_conv_problem()
+    F = ec.FilterSO2.analytic(prob["a"], prob["sigma"], prob["radius"])
+    out = torch.empty((256, 256), dtype=torch.float32, device="cuda")
+    ec.ext_conv_so2(plan, dev(prob["H"]), 256, 256, F, dev(prob["alpha"]), out)
+    ref = conv_ref(prob["H"], AnalyticGaussPow(prob["a"], prob["sigma"]), prob["alpha"], prob["radius"])
+    err = rel_l2(out.cpu().numpy(), ref.real)
+    print(f"conv 256^2 rel-L2 {err:.3e}")
+    assert err < REL_L2
+
+
+def test_field_host_buffers_match_device(ec, plan):
+    prob = synth.so2_conv_problem(size=64)
+    F = ec.FilterSO2.analytic(prob["a"], prob["sigma"], prob["radius"])
+    out_d = torch.empty((64, 64), dtype=torch.float32, device="cuda")
+    ec.ext_conv_so2(plan, dev(prob["H"]), 64, 64, F, dev(prob["alpha"]), out_d)
+    out_h = np.zeros((64, 64), np.float32)
+    ec.ext_conv_so2(plan, prob["H"], 64, 64, F, prob["alpha"], out_h)
+    np.testing.assert_array_equal(out_h, out_d.cpu().numpy())
+
+
+# ------------------------------------------------------------------ sweeps ---
+
+def _check_sweep(mx, am, S, what):
+    """mx, am: GPU max/argmax at some pixels; S: oracle scores (n, J)."""
+    scale = np.abs(S).max()
+    best = S.max(axis=1)
+    assert np.max(np.abs(mx - best)) <= 1e-5 * scale, what
+    srt = np.sort(S, axis=1)
+    gap = srt[:, -1] - srt[:, -2]
+    clear = gap > TIE * scale
+    ok = am == S.argmax(axis=1)
+    assert np.all(ok[clear]), f"{what}: {np.sum(~ok[clear])} argmax flips outside the tie window"
+    return int(np.sum(~ok)), int(np.sum(~clear))
+
+
+def test_sweep_kernel_matches_oracle_linear_combination(ec, plan):
+    rng = np.random.default_rng(0)
+    K, J, n = 16, 64, 5000
+    Gc = [rng.standard_normal(n)] + [rng.standard_normal(n) + 1j * rng.standard_normal(n) for _ in range(K)]
+    planes = [Gc[0]] + [x for k in range(1, K + 1) for x in (Gc[k].real, Gc[k].imag)]
+    G32 = np.stack(planes).astype(np.float32)
+    Gq = [G32[0].astype(np.float64)] + [G32[2 * k - 1] + 1j * G32[2 * k].astype(np.float64)
+                                         for k in range(1, K + 1)]
+    S = sweep_from_components(Gq, K, J).real.T      # (n, J)
+    mx = torch.empty(n, dtype=torch.float32, device="cuda")
+    am = torch.empty(n, dtype=torch.int32, device="cuda")
+    ec.ext_sweep_so2(plan, dev(G32), n, K, J, mx, am)
+    _check_sweep(mx.cpu().numpy(), am.cpu().numpy(), S, "sweep kernel")
+
+
+@pytest.mark.parametrize("K,J", [(8, 32), (4, 36), (16, 64)])
+def test_sweep_end_to_end_small(ec, plan, K, J):
+    prob = synth.so2_match_problem(seed=K * 100 + J, size=128, n_plant=3, radius=12, K=K, J=J)
+    F = ec.FilterSO2.sampled(prob["template"], K, prob["dr"], prob["n_theta"])
+    mx = torch.empty((128, 128), dtype=torch.float32, device="cuda")
+    am = torch.empty((128, 128), dtype=torch.int32, device="cuda")
+    ec.ext_corr_so2(plan, dev(prob["H"]), 128, 128, F, None, J, mx, am)
+    tab = decompose_sampled(prob["template"], K, prob["dr"], prob["n_theta"])
+    pix = np.array([[y, x] for y in range(128) for x in range(128)])
+    S = sweep_so2_at(prob["H"], tab, prob["radius"], J, pix).real
+    best = S.max(axis=1).reshape(128, 128)
+    mxn, amn = mx.cpu().numpy(), am.cpu().numpy()
+    assert rel_l2(mxn, best) < REL_L2
+    _check_sweep(mxn.ravel(), amn.ravel(), S, f"128^2 K={K} J={J}")
+    # planted templates are found at their centre and angle
+    for (cy, cx), beta in zip(prob["centres"], prob["betas"]):
+        j_true = round(beta * J / (2 * math.pi)) % J
+        dj = (amn[cy, cx] - j_true) % J
+        assert min(dj, J - dj) <= 1
+
+
+def test_sweep_full_size_2048_sampled_pixels(ec, plan):
+    """The 2048 x 2048, K = 16, 64-angle workload in the launch configuration
+    the benchmark times, checked at the 20 planted centres (+-2 px) and 512
+    random pixels against the brute-force sweep."""
+    prob = synth.so2_match_problem()
+    K, J, R = prob["K"], prob["J"], prob["radius"]
+    F = ec.FilterSO2.sampled(prob["template"], K, prob["dr"], prob["n_theta"])
+    mx = torch.empty((2048, 2048), dtype=torch.float32, device="cuda")
+    am = torch.empty((2048, 2048), dtype=torch.int32, device="cuda")
+    ec.ext_corr_so2(plan, dev(prob["H"]), 2048, 2048, F, None, J, mx, am)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1)
+    pix = [(cy + dy, cx + dx) for cy, cx in prob["centres"] for dy in range(-2, 3) for dx in range(-2, 3)]
+    pix = np.array(pix + [tuple(p) for p in rng.integers(0, 2048, (512, 2))]) % 2048
+    tab = decompose_sampled(prob["template"], K, prob["dr"], prob["n_theta"])
+    S = sweep_so2_at(prob["H"], tab, R, J, pix).real
+    mxn = mx.cpu().numpy()[pix[:, 0], pix[:, 1]]
+    amn = am.cpu().numpy()[pix[:, 0], pix[:, 1]]
+    flips, ties = _check_sweep(mxn, amn, S, "2048^2")
+    print(f"2048^2 sweep: {flips} argmax differences, {ties} pixels inside the tie window")
+    full = mx.cpu().numpy()
+    for (cy, cx), beta in zip(prob["centres"], prob["betas"]):
+        win = full[cy - 2:cy + 3, cx - 2:cx + 3] if 2 <= cy < 2046 and 2 <= cx < 2046 else None
+        if win is not None:
+            iy, ix = np.unravel_index(np.argmax(win), win.shape)
+            assert abs(iy - 2) <= 1 and abs(ix - 2) <= 1
+
+
+# -------------------------------------------------------------- edge cases ---
+
+def test_edge_cases(ec, plan):
+    a = synth.random_gauss_pow_coeffs(1, 2)
+    F = ec.FilterSO2.analytic(a, 2.0, 4)
+    x = torch.zeros(64 * 64, device="cuda")
+    # empty image: no-op
+    ec.ext_conv_so2(plan, x, 0, 64, F, x, x)
+    # unsupported side / odd width
+    with pytest.raises(ec.ExtError) as e:
+        ec.ext_conv_so2(plan, x, 64, 100, F, x, x)
+    assert e.value.status == 2
+    with pytest.raises(ec.ExtError):
+        ec.ext_corr_so2(plan, x, 64, 63, F, x, 0, x, None)
+    # sweep without argmax buffer
+    with pytest.raises(ec.ExtError) as e:
+        ec.ext_corr_so2(plan, x, 64, 64, F, None, 16, x, None)
+    assert e.value.status == 1
+
+
+def test_K0_filter_sweep_is_isotropic(ec, plan):
+    rng = np.random.default_rng(2)
+    H = rng.standard_normal((64, 64)).astype(np.float32)
+    a = np.array([1.3 + 0j])
+    F = ec.FilterSO2.analytic(a, 2.0, 5)
+    mx = torch.empty((64, 64), device="cuda")
+    am = torch.empty((64, 64), dtype=torch.int32, device="cuda")
+    ec.ext_corr_so2(plan, dev(H), 64, 64, F, None, 8, mx, am)
+    ref = component_correlation(H, AnalyticGaussPow(a, 2.0), 0, 5).real
+    assert rel_l2(mx.cpu().numpy(), ref) < REL_L2
+    assert np.all(am.cpu().numpy() == 0)
