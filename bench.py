@@ -189,9 +189,9 @@ def algorithmic_bytes(kernel, h, w, K, kc):
         return 4 * P + half
     if kernel == "cols_fwd_half":
         return 2 * half
-    if kernel == "cols_inv_corr":      # Hh once, kc filter spectra, kc products out
+    if kernel in ("cols_inv_corr", "cols_inv_corr_pipe"):   # Hh once, kc spectra in, kc products out
         return half + kc * (8 * P) + kc * (8 * P)
-    if kernel == "rows_inv_components":   # kc partial products in, 2 real planes out each
+    if kernel in ("rows_inv_components", "rows_inv_components_pipe"):   # kc products in, 2 planes out each
         return kc * 8 * P + kc * 8 * P
     if kernel == "sweep_fp32" or kernel == "sweep_bf16x3":
         return (2 * K + 1) * 4 * P + 8 * P
@@ -298,7 +298,7 @@ def main():
     torch.cuda.synchronize()
     prof = plan.profile_read()
     plan.profile(False)
-    kc = max(1, min(K + 1, (32 << 20) // (8 * P)))
+    kc = K + 1
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_n) = dom
     avg_ms = dom_ms / dom_n

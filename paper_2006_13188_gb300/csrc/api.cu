@@ -1,6 +1,7 @@
 // C ABI of libextconv.so: argument checking, the plan (caches and workspace),
 // host/device staging, and the launch sequences of each operator.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -77,6 +78,9 @@ struct ext_plan_s {
   std::map<uint64_t, float*> sweep_tables;
   uint64_t clock = 0;
   size_t max_specs = 4;
+  int sms = 0;           // multiprocessors of the device
+  int kchunk = 0;        // components per inverse launch (0 = by L2 budget)
+  bool pipelined = true; // persistent prefetching passes where they fit
 };
 
 namespace {
@@ -376,17 +380,33 @@ ext_status run_components(ext_plan plan, const float* H, int h, int w, const ext
   EXT_TRY(ensure(plan, "Hh", sizeof(float2) * (size_t)h * wh, &Hh));
   launch(plan, "rows_r2c", st, [&] { fft_rows_r2c(w, H, h, (float2*)Hh, tw_w, st); });
   launch(plan, "cols_fwd_half", st, [&] { fft_cols_fwd_half(h, (float2*)Hh, wh, tw_h, st); });
-  // k-chunks sized so that one chunk of partial products stays L2-resident
+  // All components go through each inverse pass in one launch: measured on
+  // 2048^2 x 17 components, one launch beats per-component launches that keep
+  // the partial products L2-resident (tail imbalance dominates), at the cost
+  // of a (K+1)-plane intermediate.
   const size_t plane = sizeof(float2) * (size_t)h * w;
-  int kc = (int)((32u << 20) / plane);
-  if (kc < 1) kc = 1;
-  if (kc > K + 1) kc = K + 1;
+  int kc = K + 1;
+  if (plan->kchunk > 0) kc = plan->kchunk < K + 1 ? plan->kchunk : K + 1;
   void* Z = nullptr;
   EXT_TRY(ensure(plan, "Z", plane * kc, &Z));
   for (int k0 = 0; k0 <= K; k0 += kc) {
     const int nk = (k0 + kc <= K + 1) ? kc : (K + 1 - k0);
-    launch(plan, "cols_inv_corr", st, [&] { fft_cols_inv_corr(h, (const float2*)Hh, w, S, k0, nk, (float2*)Z, tw_h, st); });
-    launch(plan, "rows_inv_components", st, [&] { fft_rows_inv_components(w, (const float2*)Z, h, k0, nk, G, tw_w, st); });
+    bool piped = false;
+    if (plan->pipelined)
+      launch(plan, "cols_inv_corr_pipe", st, [&] {
+        piped = fft_cols_inv_corr_pipe(h, (const float2*)Hh, w, S, k0, nk, (float2*)Z, tw_h, plan->sms, st);
+      });
+    if (!piped)
+      launch(plan, "cols_inv_corr", st,
+             [&] { fft_cols_inv_corr(h, (const float2*)Hh, w, S, k0, nk, (float2*)Z, tw_h, st); });
+    piped = false;
+    if (plan->pipelined)
+      launch(plan, "rows_inv_components_pipe", st, [&] {
+        piped = fft_rows_inv_components_pipe(w, (const float2*)Z, h, k0, nk, G, tw_w, plan->sms, st);
+      });
+    if (!piped)
+      launch(plan, "rows_inv_components", st,
+             [&] { fft_rows_inv_components(w, (const float2*)Z, h, k0, nk, G, tw_w, st); });
   }
   EXT_CUDA(cudaGetLastError());
   return EXT_OK;
@@ -446,6 +466,9 @@ ext_status ext_plan_create(ext_plan* plan, int device) {
   EXT_CUDA(cudaSetDevice(device));
   ext_plan p = new ext_plan_s();
   p->device = device;
+  cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
+  if (const char* e = getenv("EXT_KCHUNK")) p->kchunk = atoi(e);
+  if (const char* e = getenv("EXT_PIPELINED")) p->pipelined = atoi(e) != 0;
   *plan = p;
   return EXT_OK;
 }

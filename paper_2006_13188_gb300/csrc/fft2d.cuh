@@ -146,6 +146,86 @@ __device__ __forceinline__ void ct_fft(float2* buf, int ls, int es, const float2
   }
 }
 
+// Stage with functor I/O: load(line, idx) supplies the inputs (FIRST: from
+// anywhere, e.g. a staging buffer with a product fused in) and
+// store(line, idx, value) consumes the outputs (LAST: e.g. straight to global
+// memory); otherwise both use the padded shared-memory layout of buf.
+template <int N, int R, int NS, bool INV, bool LINE_FAST, int NLINES, int THREADS, bool FIRST, bool LAST,
+          class Load, class Store>
+__device__ __forceinline__ void ct_stage_io(float2* buf, int ls, int es, const float2* __restrict__ tw, Load&& load,
+                                            Store&& store) {
+  constexpr int NB = N / R;
+  constexpr int TSTEP = N / (NS * R);
+  constexpr int total = NB * NLINES;
+  constexpr int S = (total + THREADS - 1) / THREADS;
+  static_assert(S * R <= FFT_MAXE + R, "too many butterflies per thread");
+  float2 v[S][R];
+  int line_s[S], dst_s[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int it = threadIdx.x + s * THREADS;
+    line_s[s] = -1;
+    dst_s[s] = 0;
+    if (total % THREADS == 0 || it < total) {
+      int line, j;
+      if (LINE_FAST) { line = it % NLINES; j = it / NLINES; }
+      else { j = it % NB; line = it / NB; }
+      const int k = j % NS;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float2 a = FIRST ? load(line, j + r * NB) : buf[line * ls + sidx(j + r * NB) * es];
+        if (NS > 1 && r > 0) {
+          float2 w = tw[r * k * TSTEP];
+          if (INV) w.y = -w.y;
+          a = c_mul(a, w);
+        }
+        v[s][r] = a;
+      }
+      line_s[s] = line;
+      dst_s[s] = (j / NS) * NS * R + k;
+    }
+  }
+  if (!FIRST && !LAST) __syncthreads();   // in place: all reads before any write
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    if (line_s[s] >= 0) {
+      dft<R, INV>(v[s]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (LAST) store(line_s[s], dst_s[s] + r * NS, v[s][r]);
+        else buf[line_s[s] * ls + sidx(dst_s[s] + r * NS) * es] = v[s][r];
+      }
+    }
+  }
+  if (!LAST) __syncthreads();
+}
+
+// Whole transform with functor input (first stage) and output (last stage).
+// The caller must __syncthreads() before re-using buf or the load source.
+template <int N, bool INV, bool LINE_FAST, int NLINES, int THREADS, int ST = 0, int NS = 1, class Load, class Store>
+__device__ __forceinline__ void ct_fft_io(float2* buf, int ls, int es, const float2* tw, Load&& load, Store&& store) {
+  constexpr RadixList L = factor_radices(N);
+  if constexpr (ST < L.cnt) {
+    constexpr int R = L.r[ST];
+    ct_stage_io<N, R, NS, INV, LINE_FAST, NLINES, THREADS, ST == 0, ST == L.cnt - 1>(buf, ls, es, tw, load, store);
+    ct_fft_io<N, INV, LINE_FAST, NLINES, THREADS, ST + 1, NS * R>(buf, ls, es, tw, load, store);
+  }
+}
+
+// ------------------------------------------------------------- cp.async ---
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;   // 0 source bytes: the 16 destination bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Copies the length-N twiddle table into shared memory right after the
 // block's data region and returns it (the caller's next __syncthreads makes
 // it visible).
@@ -520,6 +600,143 @@ k_cols_conv(const float2* __restrict__ A, int w, int K, const float2* __restrict
   });
 }
 
+// ------------------------------------------------- pipelined hot passes ---
+// Persistent versions of the two passes that run once per filter component
+// in the correlation path.  Each block owns one SM (grid = min(items, SMs))
+// and walks its tiles; the global data of the next tile is prefetched into
+// shared memory with cp.async while the current tile is transformed.
+
+template <int N>
+struct PipeCfg {
+  using C = LineCfg<N>;
+  // columns: work buffer, spectrum and half-spectrum staging, twiddles
+  static constexpr int COL_SMEM = C::CW * C::LS * 8 + 2 * C::CW * N * 8 + N * 8;
+  // rows: work buffer, staging of the next rows, twiddles
+  static constexpr int ROW_SMEM = C::RL * C::LS * 8 + C::RL * N * 8 + N * 8;
+  static constexpr bool COL_OK = COL_SMEM <= 227 * 1024;
+  static constexpr bool ROW_OK = ROW_SMEM <= 227 * 1024;
+};
+
+// Inverse column pass of H^ conj(F^_k) for k = k0 + (item / ntiles); output
+// Z[item / ntiles] (pitch w).  Half spectrum pitch wh = w/2 + 1.
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, 1)
+k_cols_inv_corr_pipe(const float2* __restrict__ Hh, int w, const float2* __restrict__ S, int k0, int nk,
+                     float2* __restrict__ Z, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::COL_THREADS;
+  constexpr int CW = C::CW;
+  constexpr int TILE = CW * N;
+  extern __shared__ float2 sm[];
+  float2* W = sm;                          // CW * LS
+  float2* SS = sm + CW * C::LS;            // TILE, linear e = v * CW + c
+  float2* HS = SS + TILE;                  // TILE
+  float2* TWs = HS + TILE;                 // N
+  for (int i = threadIdx.x; i < N; i += T) TWs[i] = __ldg(tw + i);
+  const int wh = w / 2 + 1;
+  const int ntiles = (w + CW - 1) / CW;
+  const int nitems = ntiles * nk;
+
+  auto prefetch = [&](int item) {
+    const int kk = item / ntiles, tile = item % ntiles;
+    const float2* spec = S + ((size_t)(k0 + kk) * ntiles + tile) * TILE;
+    for (int q = threadIdx.x; q < TILE / 2; q += T) cp_async16(SS + 2 * q, spec + 2 * q, true);
+    const int u0 = tile * CW;
+    for (int e = threadIdx.x; e < TILE; e += T) {
+      const int v = e / CW, u = u0 + e % CW;
+      const float2* src = Hh;
+      bool valid = u < w;
+      if (u < wh) src = Hh + (size_t)v * wh + u;
+      else if (valid) src = Hh + (size_t)((N - v) % N) * wh + (w - u);
+      cp_async8(HS + e, src, valid);
+    }
+    cp_async_commit();
+  };
+
+  int item = blockIdx.x;
+  if (item < nitems) prefetch(item);
+  for (; item < nitems; item += gridDim.x) {
+    cp_async_wait_all();
+    __syncthreads();
+    const int kk = item / ntiles, tile = item % ntiles;
+    const int u0 = tile * CW;
+    float2* dst = Z + (size_t)kk * N * w;
+    const int next = item + gridDim.x;
+    auto load = [&](int c, int v) -> float2 {
+      const int e = v * CW + c;
+      float2 hv = HS[e];
+      if (u0 + c >= wh) hv.y = -hv.y;
+      return c_mul(hv, SS[e]);
+    };
+    auto store = [&](int c, int v, float2 val) {
+      if (u0 + c < w) dst[(size_t)v * w + u0 + c] = val;
+    };
+    // first stage consumes the staging buffers, then the next tile is prefetched
+    constexpr RadixList L = factor_radices(N);
+    constexpr int R0 = L.r[0];
+    ct_stage_io<N, R0, 1, true, true, CW, T, true, L.cnt == 1>(W, 1, CW, TWs, load, store);
+    if (next < nitems) prefetch(next);
+    if constexpr (L.cnt > 1) ct_fft_io<N, true, true, CW, T, 1, R0>(W, 1, CW, TWs, load, store);
+  }
+  cp_async_wait_all();
+}
+
+// Inverse row pass of Z writing the component planes of G (k = k0 + item / nblk).
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, 1)
+k_rows_inv_components_pipe(const float2* __restrict__ Z, int h, int k0, int nk, float* __restrict__ G,
+                           const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::ROW_THREADS;
+  constexpr int RL = C::RL;
+  extern __shared__ float2 sm[];
+  float2* W = sm;
+  float2* ZS = sm + RL * C::LS;   // RL * N linear
+  float2* TWs = ZS + RL * N;
+  for (int i = threadIdx.x; i < N; i += T) TWs[i] = __ldg(tw + i);
+  const size_t P = (size_t)h * N;
+  const int nblk = (h + RL - 1) / RL;
+  const int nitems = nblk * nk;
+
+  auto prefetch = [&](int item) {
+    const int kk = item / nblk, y0 = (item % nblk) * RL;
+    const float2* src = Z + (size_t)kk * P + (size_t)y0 * N;
+    const int rows = (h - y0) < RL ? (h - y0) : RL;
+    for (int q = threadIdx.x; q < RL * N / 2; q += T) {
+      const bool valid = 2 * q < rows * N;
+      cp_async16(ZS + 2 * q, valid ? src + 2 * q : Z, valid);
+    }
+    cp_async_commit();
+  };
+
+  int item = blockIdx.x;
+  if (item < nitems) prefetch(item);
+  for (; item < nitems; item += gridDim.x) {
+    cp_async_wait_all();
+    __syncthreads();
+    const int kk = item / nblk, y0 = (item % nblk) * RL;
+    const int k = k0 + kk;
+    float* re = G + (k == 0 ? 0 : (size_t)(2 * k - 1) * P);
+    float* im = G + (size_t)(2 * k) * P;
+    const int next = item + gridDim.x;
+    auto load = [&](int l, int x) -> float2 { return ZS[l * N + x]; };
+    auto store = [&](int l, int x, float2 val) {
+      const int y = y0 + l;
+      if (y < h) {
+        const size_t idx = (size_t)y * N + x;
+        re[idx] = val.x;
+        if (k != 0) im[idx] = val.y;
+      }
+    };
+    constexpr RadixList L = factor_radices(N);
+    constexpr int R0 = L.r[0];
+    ct_stage_io<N, R0, 1, true, false, RL, T, true, L.cnt == 1>(W, C::LS, 1, TWs, load, store);
+    if (next < nitems) prefetch(next);
+    if constexpr (L.cnt > 1) ct_fft_io<N, true, false, RL, T, 1, R0>(W, C::LS, 1, TWs, load, store);
+  }
+  cp_async_wait_all();
+}
+
 // ------------------------------------------------------------- launchers ---
 template <int N>
 struct FftOps {
@@ -541,6 +758,11 @@ struct FftOps {
                             const float2* tw, cudaStream_t st);
   static void cols_conv(const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
                         cudaStream_t st);
+  // pipelined persistent variants (false if the shared-memory plan does not fit)
+  static bool cols_inv_corr_pipe(const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
+                                 const float2* tw, int sms, cudaStream_t st);
+  static bool rows_inv_components_pipe(const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
+                                       int sms, cudaStream_t st);
 };
 
 template <typename KernelT>
@@ -637,4 +859,34 @@ void FftOps<N>::cols_conv(const float2* A, int w, int K, const float2* S, float2
   (void)once;
   dim3 grid((w + C::CW - 1) / C::CW);
   k_cols_conv<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(A, w, K, S, Y, tw);
+}
+
+template <int N>
+bool FftOps<N>::cols_inv_corr_pipe(const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
+                                   const float2* tw, int sms, cudaStream_t st) {
+  if constexpr (!PipeCfg<N>::COL_OK) {
+    return false;
+  } else {
+    static const bool once = (ext_set_smem(k_cols_inv_corr_pipe<N>, PipeCfg<N>::COL_SMEM), true);
+    (void)once;
+    const int items = ((w + C::CW - 1) / C::CW) * nk;
+    const int grid = items < sms ? items : sms;
+    k_cols_inv_corr_pipe<N><<<grid, C::COL_THREADS, PipeCfg<N>::COL_SMEM, st>>>(Hh, w, S, k0, nk, Z, tw);
+    return true;
+  }
+}
+
+template <int N>
+bool FftOps<N>::rows_inv_components_pipe(const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
+                                         int sms, cudaStream_t st) {
+  if constexpr (!PipeCfg<N>::ROW_OK) {
+    return false;
+  } else {
+    static const bool once = (ext_set_smem(k_rows_inv_components_pipe<N>, PipeCfg<N>::ROW_SMEM), true);
+    (void)once;
+    const int items = ((h + C::RL - 1) / C::RL) * nk;
+    const int grid = items < sms ? items : sms;
+    k_rows_inv_components_pipe<N><<<grid, C::ROW_THREADS, PipeCfg<N>::ROW_SMEM, st>>>(Z, h, k0, nk, G, tw);
+    return true;
+  }
 }

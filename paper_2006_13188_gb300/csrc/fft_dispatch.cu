@@ -90,3 +90,17 @@ void fft_cols_conv(int h, const float2* A, int w, int K, const float2* S, float2
   switch (h) { EXT_FFT_SIZES(EXT_C1) default: return; }
 }
 #undef EXT_C1
+
+#define EXT_C1(N) case N: return FftOps<N>::cols_inv_corr_pipe(Hh, w, S, k0, nk, Z, tw, sms, st);
+bool fft_cols_inv_corr_pipe(int h, const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
+                            const float2* tw, int sms, cudaStream_t st) {
+  switch (h) { EXT_FFT_SIZES(EXT_C1) default: return false; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: return FftOps<N>::rows_inv_components_pipe(Z, h, k0, nk, G, tw, sms, st);
+bool fft_rows_inv_components_pipe(int w, const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
+                                  int sms, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return false; }
+}
+#undef EXT_C1

@@ -34,6 +34,10 @@ void fft_cols_fwd_spectrum(int h, const float2* X, int w, int conj_out, float sc
                            const float2* tw, cudaStream_t st);
 void fft_cols_inv_corr(int h, const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
                        const float2* tw, cudaStream_t st);
+bool fft_cols_inv_corr_pipe(int h, const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
+                            const float2* tw, int sms, cudaStream_t st);
+bool fft_rows_inv_components_pipe(int w, const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
+                                  int sms, cudaStream_t st);
 void fft_cols_conv(int h, const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
                    cudaStream_t st);
 
