@@ -109,6 +109,13 @@ ext_status ext_plan_destroy(ext_plan plan);
 /* Frees cached filter spectra and workspace (kept otherwise for reuse). */
 ext_status ext_plan_trim(ext_plan plan);
 
+/* Waits for `stream` and reports device-side failures of earlier calls on
+ * this plan: EXT_ERR_TIMEOUT if a bounded wait inside a kernel expired (the
+ * kernel then abandoned its work, freed its tensor memory and returned; the
+ * affected outputs are invalid).  Calls with host buffers do this check
+ * themselves before returning. */
+ext_status ext_plan_sync(ext_plan plan, void* stream);
+
 /* Per-kernel accounting for benchmarks and tracing (no counterpart in the
  * paper).  Every kernel launch of the plan is counted per kernel name; with
  * profiling enabled each launch is also bracketed by CUDA events recorded on

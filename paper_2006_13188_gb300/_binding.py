@@ -32,7 +32,7 @@ EXT_PREC_BF16X3 = 1
 
 EXPORTED = (
     "ext_status_string", "ext_last_error", "ext_plan_create", "ext_plan_destroy", "ext_plan_trim",
-    "ext_plan_profile", "ext_plan_profile_read",
+    "ext_plan_profile", "ext_plan_profile_read", "ext_plan_sync",
     "ext_filter_so2_decompose", "ext_conv_so2", "ext_corr_so2", "ext_corr_so2_components",
     "ext_sweep_so2",
 )
@@ -73,6 +73,7 @@ def lib():
         L.ext_plan_destroy.argtypes = [vp]
         L.ext_plan_trim.argtypes = [vp]
         L.ext_plan_profile.argtypes = [vp, i32]
+        L.ext_plan_sync.argtypes = [vp, vp]
         L.ext_plan_profile_read.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]
         L.ext_filter_so2_decompose.argtypes = [vp, fp, vp, i64, ctypes.POINTER(i32)]
         L.ext_conv_so2.argtypes = [vp, vp, i32, i32, fp, vp, vp, vp]
@@ -165,6 +166,9 @@ class Plan:
 
     def trim(self):
         _check(lib().ext_plan_trim(self.handle))
+
+    def sync(self, stream=None):
+        _check(lib().ext_plan_sync(self.handle, _stream(stream)))
 
     def profile(self, enable: bool):
         _check(lib().ext_plan_profile(self.handle, 1 if enable else 0))

@@ -81,6 +81,7 @@ struct ext_plan_s {
   int sms = 0;           // multiprocessors of the device
   int kchunk = 0;        // components per inverse launch (0 = by L2 budget)
   bool pipelined = true; // persistent prefetching passes where they fit
+  int* dev_err = nullptr; // device-side status word (bounded waits)
 };
 
 namespace {
@@ -416,7 +417,6 @@ ext_status run_sweep(ext_plan plan, const float* G, long long P, int K, int J, f
                      int precision, cudaStream_t st) {
   if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3)
     return fail(EXT_ERR_INVALID_ARG, "unknown precision");
-  if (precision == EXT_PREC_BF16X3) return fail(EXT_ERR_UNSUPPORTED, "BF16x3 sweep not built yet");
   if (K == 0) {
     EXT_CUDA(cudaMemcpyAsync(maxv, G, sizeof(float) * P, cudaMemcpyDeviceToDevice, st));
     EXT_CUDA(cudaMemsetAsync(argmax, 0, sizeof(int32_t) * P, st));
@@ -427,14 +427,33 @@ ext_status run_sweep(ext_plan plan, const float* G, long long P, int K, int J, f
   int cp = 0;
   EXT_TRY(sweep_table(plan, K, J, st, &B, &cp));
   bool ok = true;
-  launch(plan, "sweep_fp32", st, [&] { ok = sweep_fp32(G, P, K, J, B, cp, maxv, argmax, st); });
+  if (precision == EXT_PREC_BF16X3) {
+    if (J > 128) return fail(EXT_ERR_UNSUPPORTED, "BF16x3 sweep supports at most 128 angles");
+    launch(plan, "sweep_bf16x3", st,
+           [&] { ok = sweep_bf16x3(G, P, K, J, B, cp, maxv, argmax, plan->dev_err, plan->sms, st); });
+  } else {
+    launch(plan, "sweep_fp32", st, [&] { ok = sweep_fp32(G, P, K, J, B, cp, maxv, argmax, st); });
+  }
   if (!ok) return fail(EXT_ERR_UNSUPPORTED, "sweep K");
   EXT_CUDA(cudaGetLastError());
   return EXT_OK;
 }
 
-ext_status finish_host(bool any_host, cudaStream_t st) {
-  if (any_host) EXT_CUDA(cudaStreamSynchronize(st));
+ext_status device_status(ext_plan plan) {
+  int e = 0;
+  EXT_CUDA(cudaMemcpy(&e, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    EXT_CUDA(cudaMemset(plan->dev_err, 0, sizeof(int)));
+    return fail(e, "a device-side wait timed out; results of the affected call are invalid");
+  }
+  return EXT_OK;
+}
+
+ext_status finish_host(ext_plan plan, bool any_host, cudaStream_t st) {
+  if (any_host) {
+    EXT_CUDA(cudaStreamSynchronize(st));
+    return device_status(plan);
+  }
   return EXT_OK;
 }
 
@@ -467,6 +486,10 @@ ext_status ext_plan_create(ext_plan* plan, int device) {
   ext_plan p = new ext_plan_s();
   p->device = device;
   cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&p->dev_err, sizeof(int)) != cudaSuccess || cudaMemset(p->dev_err, 0, sizeof(int)) != cudaSuccess) {
+    delete p;
+    return fail(EXT_ERR_CUDA, "cannot allocate the plan status word");
+  }
   if (const char* e = getenv("EXT_KCHUNK")) p->kchunk = atoi(e);
   if (const char* e = getenv("EXT_PIPELINED")) p->pipelined = atoi(e) != 0;
   *plan = p;
@@ -497,8 +520,16 @@ ext_status ext_plan_destroy(ext_plan plan) {
     cudaEventDestroy(p.b);
   }
   for (auto e : plan->event_pool) cudaEventDestroy(e);
+  cudaFree(plan->dev_err);
   delete plan;
   return EXT_OK;
+}
+
+ext_status ext_plan_sync(ext_plan plan, void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  EXT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return device_status(plan);
 }
 
 ext_status ext_plan_profile(ext_plan plan, int enable) {
@@ -576,7 +607,7 @@ ext_status ext_corr_so2_components(ext_plan plan, const float* H, int h, int w, 
   EXT_TRY(stage_out_alloc(plan, "out_G", G, sizeof(float) * P * (2 * F->K + 1), &sG));
   EXT_TRY(run_components(plan, (const float*)sH.dev, h, w, F, (float*)sG.dev, st));
   EXT_TRY(stage_out_finish(sG, st));
-  return finish_host(sH.host || sG.host, st);
+  return finish_host(plan, sH.host || sG.host, st);
 }
 
 ext_status ext_sweep_so2(ext_plan plan, const float* G, int64_t n_pix, int K, int n_angles, float* max_out,
@@ -595,7 +626,7 @@ ext_status ext_sweep_so2(ext_plan plan, const float* G, int64_t n_pix, int K, in
                     precision, st));
   EXT_TRY(stage_out_finish(sM, st));
   EXT_TRY(stage_out_finish(sA, st));
-  return finish_host(sG.host || sM.host || sA.host, st);
+  return finish_host(plan, sG.host || sM.host || sA.host, st);
 }
 
 ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, const float* alpha,
@@ -638,7 +669,7 @@ ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_f
            [&] { fft_rows_inv_field(w, (const float2*)Z, h, K, (const float*)sAl.dev, (float*)sO.dev, tw_w, st); });
     EXT_CUDA(cudaGetLastError());
     EXT_TRY(stage_out_finish(sO, st));
-    return finish_host(sH.host || sAl.host || sO.host, st);
+    return finish_host(plan, sH.host || sAl.host || sO.host, st);
   }
   EXT_TRY(stage_out_alloc(plan, "out_1", argmax, sizeof(int32_t) * P, &sA));
   void* G = nullptr;
@@ -648,7 +679,7 @@ ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_f
                     st));
   EXT_TRY(stage_out_finish(sO, st));
   EXT_TRY(stage_out_finish(sA, st));
-  return finish_host(sH.host || sO.host || sA.host, st);
+  return finish_host(plan, sH.host || sO.host || sA.host, st);
 }
 
 ext_status ext_conv_so2(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, const float* alpha,
@@ -680,7 +711,7 @@ ext_status ext_conv_so2(ext_plan plan, const float* H, int h, int w, const ext_f
   launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, (float*)sO.dev, tw_w, st); });
   EXT_CUDA(cudaGetLastError());
   EXT_TRY(stage_out_finish(sO, st));
-  return finish_host(sH.host || sAl.host || sO.host, st);
+  return finish_host(plan, sH.host || sAl.host || sO.host, st);
 }
 
 }  // extern "C"

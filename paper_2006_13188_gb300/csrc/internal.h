@@ -53,3 +53,6 @@ void launch_sweep_table(int K, int J, int cp, float* B, cudaStream_t st);
 // B: J rows of cp floats (cp = 2K rounded up to a multiple of 4).
 bool sweep_fp32(const float* G, long long P, int K, int J, const float* B, int cp, float* maxv,
                 int32_t* argmax, cudaStream_t st);
+// tcgen05 split-BF16 sweep (sweep_tc.cu); err receives EXT_ERR_TIMEOUT if a bounded wait expires.
+bool sweep_bf16x3(const float* G, long long P, int K, int J, const float* B, int cp, float* maxv, int32_t* argmax,
+                  int* err, int sms, cudaStream_t st);

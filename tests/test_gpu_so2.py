@@ -242,3 +242,69 @@ def test_K0_filter_sweep_is_isotropic(ec, plan):
     ref = component_correlation(H, AnalyticGaussPow(a, 2.0), 0, 5).real
     assert rel_l2(mx.cpu().numpy(), ref) < REL_L2
     assert np.all(am.cpu().numpy() == 0)
+
+
+# ------------------------------------------------- tensor-core (BF16x3) sweep ---
+# Split-BF16 operands with FP32 accumulation: scores within 1e-4 of the score
+# scale, argmax identical wherever the best two scores are more than 2e-4 of
+# the scale apart, and identical on at least 99% of all pixels.
+BF_TOL = 1e-4
+
+
+def _check_bf16x3(mx, am, S, what):
+    scale = np.abs(S).max()
+    best = S.max(axis=1)
+    err = np.max(np.abs(mx - best)) / scale
+    assert err <= BF_TOL, f"{what}: score error {err:.2e}"
+    srt = np.sort(S, axis=1)
+    clear = (srt[:, -1] - srt[:, -2]) > 2 * BF_TOL * scale
+    ok = am == S.argmax(axis=1)
+    assert np.all(ok[clear]), f"{what}: {np.sum(~ok[clear])} argmax flips outside the window"
+    assert ok.mean() >= 0.99, f"{what}: argmax agreement {ok.mean():.4f}"
+    return err, float(ok.mean())
+
+
+@pytest.mark.parametrize("K,J,n", [(16, 64, 5000), (8, 36, 1000), (4, 100, 777), (16, 128, 4096),
+                                   (1, 16, 300), (12, 50, 129)])
+def test_sweep_bf16x3_matches_oracle(ec, plan, K, J, n):
+    rng = np.random.default_rng(K * 1000 + J)
+    Gc = [rng.standard_normal(n)] + [rng.standard_normal(n) + 1j * rng.standard_normal(n) for _ in range(K)]
+    planes = [Gc[0]] + [x for k in range(1, K + 1) for x in (Gc[k].real, Gc[k].imag)]
+    G32 = np.stack(planes).astype(np.float32)
+    Gq = [G32[0].astype(np.float64)] + [G32[2 * k - 1] + 1j * G32[2 * k].astype(np.float64)
+                                         for k in range(1, K + 1)]
+    S = sweep_from_components(Gq, K, J).real.T
+    mx = torch.empty(n, dtype=torch.float32, device="cuda")
+    am = torch.empty(n, dtype=torch.int32, device="cuda")
+    ec.ext_sweep_so2(plan, dev(G32), n, K, J, mx, am, ec.EXT_PREC_BF16X3)
+    plan.sync()
+    err, agree = _check_bf16x3(mx.cpu().numpy(), am.cpu().numpy(), S, f"K={K} J={J}")
+    print(f"bf16x3 K={K} J={J} n={n}: score error {err:.2e}, argmax agreement {agree:.4f}")
+
+
+def test_sweep_bf16x3_full_size_2048(ec, plan):
+    """The benchmarked configuration with the tensor-core sweep: sampled
+    pixels against the oracle, and the whole image against the FP32 path."""
+    prob = synth.so2_match_problem()
+    K, J, R = prob["K"], prob["J"], prob["radius"]
+    F = ec.FilterSO2.sampled(prob["template"], K, prob["dr"], prob["n_theta"])
+    H = dev(prob["H"])
+    mx = torch.empty((2048, 2048), dtype=torch.float32, device="cuda")
+    am = torch.empty((2048, 2048), dtype=torch.int32, device="cuda")
+    ec.ext_corr_so2(plan, H, 2048, 2048, F, None, J, mx, am, ec.EXT_PREC_BF16X3)
+    mx32 = torch.empty_like(mx)
+    am32 = torch.empty_like(am)
+    ec.ext_corr_so2(plan, H, 2048, 2048, F, None, J, mx32, am32, ec.EXT_PREC_FP32)
+    plan.sync()
+    rng = np.random.default_rng(7)
+    pix = [(cy + dy, cx + dx) for cy, cx in prob["centres"] for dy in range(-2, 3) for dx in range(-2, 3)]
+    pix = np.array(pix + [tuple(p) for p in rng.integers(0, 2048, (512, 2))]) % 2048
+    tab = decompose_sampled(prob["template"], K, prob["dr"], prob["n_theta"])
+    S = sweep_so2_at(prob["H"], tab, R, J, pix).real
+    _check_bf16x3(mx.cpu().numpy()[pix[:, 0], pix[:, 1]], am.cpu().numpy()[pix[:, 0], pix[:, 1]], S, "2048^2")
+    a, b = am.cpu().numpy(), am32.cpu().numpy()
+    agree = float((a == b).mean())
+    scale = float(mx32.abs().max())
+    err = float((mx - mx32).abs().max()) / scale
+    print(f"2048^2 bf16x3 vs fp32: score error {err:.2e}, argmax agreement {agree:.5f}")
+    assert err <= BF_TOL and agree >= 0.99
