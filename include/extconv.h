@@ -179,6 +179,27 @@ ext_status ext_corr_so2_components(ext_plan plan, const float* H, int h, int w, 
 ext_status ext_sweep_so2(ext_plan plan, const float* G, int64_t n_pix, int K, int n_angles, float* max_out,
                          int32_t* argmax, int precision, void* stream);
 
+/*
+ * Allocation-free variant of the FP32 angular sweep (the paper has no
+ * counterpart: this entry point exists for callers that cannot let a library
+ * allocate device memory -- an application whose device memory is all owned
+ * by its own allocator, a latency-critical loop that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree imply, or a process under a
+ * fixed device-memory reservation).  Same arithmetic and outputs as
+ * ext_sweep_so2 with EXT_PREC_FP32, but no plan and no allocation of any
+ * kind: its only scratch, the steering-weight table, lives in a fixed 16 KB
+ * device array inside the library (every GPU that loads the library keeps it
+ * until the process exits).  Limits: 1 <= K <= 16, 1 <= n_angles <= 128;
+ * larger sizes return EXT_ERR_UNSUPPORTED.  G, max_out and argmax must be
+ * DEVICE buffers (EXT_ERR_INVALID_ARG otherwise).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one table and each call rewrites it in full on `stream`: calls that
+ * overlap on the GPU (different streams, or different threads) race on it.
+ */
+ext_status ext_sweep_so2_noalloc(const float* G, int64_t n_pix, int K, int n_angles, float* max_out,
+                                 int32_t* argmax, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

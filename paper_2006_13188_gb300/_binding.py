@@ -34,7 +34,7 @@ EXPORTED = (
     "ext_status_string", "ext_last_error", "ext_plan_create", "ext_plan_destroy", "ext_plan_trim",
     "ext_plan_profile", "ext_plan_profile_read", "ext_plan_sync",
     "ext_filter_so2_decompose", "ext_conv_so2", "ext_corr_so2", "ext_corr_so2_components",
-    "ext_sweep_so2",
+    "ext_sweep_so2", "ext_sweep_so2_noalloc",
 )
 
 
@@ -80,6 +80,7 @@ def lib():
         L.ext_corr_so2.argtypes = [vp, vp, i32, i32, fp, vp, i32, vp, vp, i32, vp]
         L.ext_corr_so2_components.argtypes = [vp, vp, i32, i32, fp, vp, vp]
         L.ext_sweep_so2.argtypes = [vp, vp, i64, i32, i32, vp, vp, i32, vp]
+        L.ext_sweep_so2_noalloc.argtypes = [vp, i64, i32, i32, vp, vp, vp]
         for name in EXPORTED:
             if name not in ("ext_status_string", "ext_last_error"):
                 getattr(L, name).restype = i32
@@ -222,3 +223,9 @@ def ext_corr_so2_components(plan: Plan, H, h, w, F: FilterSO2, G, stream=None):
 def ext_sweep_so2(plan: Plan, G, n_pix, K, n_angles, max_out, argmax, precision=EXT_PREC_FP32, stream=None):
     _check(lib().ext_sweep_so2(plan.handle, _ptr(G), int(n_pix), int(K), int(n_angles), _ptr(max_out),
                                _ptr(argmax), int(precision), _stream(stream)))
+
+
+def ext_sweep_so2_noalloc(G, n_pix, K, n_angles, max_out, argmax, stream=None):
+    """Allocation-free FP32 sweep (device buffers only; see include/extconv.h)."""
+    _check(lib().ext_sweep_so2_noalloc(_ptr(G), int(n_pix), int(K), int(n_angles), _ptr(max_out), _ptr(argmax),
+                                       _stream(stream)))

@@ -56,6 +56,8 @@ uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
 
 }  // namespace
 
+void ext_set_error(const char* msg) { g_last_error = msg; }
+
 struct ProfStat {
   double ms = 0.0;
   int64_t launches = 0;

@@ -16,6 +16,9 @@
 #define EXT_FFT_SIZES(X) \
   EXT_FFT_SIZES_A(X) EXT_FFT_SIZES_B(X) EXT_FFT_SIZES_C(X) EXT_FFT_SIZES_D(X) EXT_FFT_SIZES_E(X) EXT_FFT_SIZES_F(X)
 
+// Sets the thread-local message returned by ext_last_error (api.cu).
+void ext_set_error(const char* msg);
+
 // ----- 2D FFT passes, dispatched on the runtime line length n (fft_dispatch.cu)
 bool fft_size_supported(int n);
 int fft_col_tile(int n);   // columns per block of the length-n column passes

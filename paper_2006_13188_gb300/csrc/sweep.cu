@@ -10,6 +10,7 @@
 #include "internal.h"
 
 #include <cfloat>
+#include <mutex>
 
 // Each thread handles two adjacent pixels so that every B value read from
 // shared memory feeds two FMAs.  B rows are padded to CP floats (multiple of 4).
@@ -98,4 +99,88 @@ bool sweep_fp32(const float* G, long long P, int K, int J, const float* B, int c
 #undef EXT_SWEEP_CASE
     default: return false;
   }
+}
+
+// ------------------------------------------------- allocation-free variant ---
+// Some callers cannot let a library allocate device memory: an application
+// whose device memory is all handed out by its own allocator (a framework's
+// caching pool sized to the whole budget), a latency-critical loop where the
+// implicit device synchronisation of cudaMalloc/cudaFree is not acceptable,
+// or a process running under a fixed device-memory reservation.  For them,
+// ext_sweep_so2_noalloc keeps its only scratch -- the steering-weight table
+// B[j][c] of the sweep -- in this file-scope device array.  Every GPU that
+// loads the library holds these 16 KB until the process exits.
+#define EXT_NOALLOC_MAX_ANGLES 128
+#define EXT_NOALLOC_ROW 32   // 2K <= 32 channels per angle
+static __device__ __align__(256) float g_noalloc_table[EXT_NOALLOC_MAX_ANGLES * EXT_NOALLOC_ROW];
+
+namespace {
+std::mutex g_noalloc_mutex;
+float* g_noalloc_ptr[256] = {};   // device address of the table, per device ordinal
+
+// The array's name is only a host-side stand-in in host code; its device
+// address is looked up once per device, with that device current.
+ext_status noalloc_table(float** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256) {
+    ext_set_error("ext_sweep_so2_noalloc: no usable current device");
+    return EXT_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_table);
+    if (e != cudaSuccess || !p) {
+      ext_set_error("ext_sweep_so2_noalloc: cudaGetSymbolAddress of the scratch table failed");
+      return EXT_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return EXT_OK;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" ext_status ext_sweep_so2_noalloc(const float* G, int64_t n_pix, int K, int n_angles, float* max_out,
+                                            int32_t* argmax, void* stream) {
+  if (n_pix < 0 || K < 1 || n_angles < 1) {
+    ext_set_error("ext_sweep_so2_noalloc: need n_pix >= 0, K >= 1, n_angles >= 1");
+    return EXT_ERR_INVALID_ARG;
+  }
+  if (K > EXT_NOALLOC_ROW / 2 || n_angles > EXT_NOALLOC_MAX_ANGLES) {
+    ext_set_error("ext_sweep_so2_noalloc: K must be <= 16 and n_angles <= 128 (fixed scratch table)");
+    return EXT_ERR_UNSUPPORTED;
+  }
+  if (n_pix == 0) return EXT_OK;
+  if (!G || !max_out || !argmax || !on_device(G) || !on_device(max_out) || !on_device(argmax)) {
+    ext_set_error("ext_sweep_so2_noalloc: G, max_out and argmax must be device buffers");
+    return EXT_ERR_INVALID_ARG;
+  }
+  float* table = nullptr;
+  ext_status s = noalloc_table(&table);
+  if (s != EXT_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int cp = (2 * K + 3) / 4 * 4;
+  // the table is rewritten in full on every call (rows of cp floats, zero padded)
+  launch_sweep_table(K, n_angles, cp, table, st);
+  if (!sweep_fp32(G, n_pix, K, n_angles, table, cp, max_out, argmax, st)) {
+    ext_set_error("ext_sweep_so2_noalloc: unsupported K");
+    return EXT_ERR_UNSUPPORTED;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ext_set_error(cudaGetErrorString(e));
+    return EXT_ERR_CUDA;
+  }
+  return EXT_OK;
 }
