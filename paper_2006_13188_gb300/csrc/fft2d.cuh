@@ -113,7 +113,7 @@ __device__ __forceinline__ void ct_stage(float2* buf, int ls, int es, const floa
       for (int r = 0; r < R; ++r) {
         float2 a = base[sidx(j + r * NB) * es];
         if (NS > 1 && r > 0) {
-          float2 w = tw[r * k * TSTEP];
+          float2 w = tw[r * NS - 1 + k];   // stage table, see stage_twiddles
           if (INV) w.y = -w.y;
           a = c_mul(a, w);
         }
@@ -175,7 +175,7 @@ __device__ __forceinline__ void ct_stage_io(float2* buf, int ls, int es, const f
       for (int r = 0; r < R; ++r) {
         float2 a = FIRST ? load(line, j + r * NB) : buf[line * ls + sidx(j + r * NB) * es];
         if (NS > 1 && r > 0) {
-          float2 w = tw[r * k * TSTEP];
+          float2 w = tw[r * NS - 1 + k];   // stage table, see stage_twiddles
           if (INV) w.y = -w.y;
           a = c_mul(a, w);
         }
@@ -226,13 +226,24 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool val
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Copies the length-N twiddle table into shared memory right after the
-// block's data region and returns it (the caller's next __syncthreads makes
-// it visible).
+// Builds the per-stage twiddle tables in shared memory right after the
+// block's data region and returns them (the caller's next __syncthreads makes
+// them visible).  The stage with span NS and radix R needs
+// W_N^(r k N / (NS R)) for r = 1..R-1, k = 0..NS-1; it is stored at
+// r * NS - 1 + k, contiguous in k so that adjacent butterflies read adjacent
+// words.  The stage blocks telescope to N - 1 entries in total.  Values are
+// copied from the FP64-derived table W_N^m = exp(-2 pi i m / N).
 template <int N, int DATA_ELEMS>
 __device__ __forceinline__ const float2* stage_twiddles(float2* sm, const float2* __restrict__ tw, int threads) {
   float2* t = sm + DATA_ELEMS;
-  for (int i = threadIdx.x; i < N; i += threads) t[i] = __ldg(tw + i);
+  constexpr RadixList L = factor_radices(N);
+  for (int i = threadIdx.x; i < N - 1; i += threads) {
+    int ns = 1, s = 0;
+    while (s + 1 < L.cnt && ns * L.r[s] <= i + 1) { ns *= L.r[s]; ++s; }
+    const int rel = i + 1 - ns;
+    const int r = rel / ns + 1, k = rel % ns;
+    t[i] = __ldg(tw + r * k * (N / (ns * L.r[s])));
+  }
   return t;
 }
 
@@ -631,8 +642,7 @@ k_cols_inv_corr_pipe(const float2* __restrict__ Hh, int w, const float2* __restr
   float2* W = sm;                          // CW * LS
   float2* SS = sm + CW * C::LS;            // TILE, linear e = v * CW + c
   float2* HS = SS + TILE;                  // TILE
-  float2* TWs = HS + TILE;                 // N
-  for (int i = threadIdx.x; i < N; i += T) TWs[i] = __ldg(tw + i);
+  const float2* TWs = stage_twiddles<N, CW * C::LS + 2 * TILE>(sm, tw, T);   // N - 1 entries
   const int wh = w / 2 + 1;
   const int ntiles = (w + CW - 1) / CW;
   const int nitems = ntiles * nk;
@@ -692,8 +702,7 @@ k_rows_inv_components_pipe(const float2* __restrict__ Z, int h, int k0, int nk, 
   extern __shared__ float2 sm[];
   float2* W = sm;
   float2* ZS = sm + RL * C::LS;   // RL * N linear
-  float2* TWs = ZS + RL * N;
-  for (int i = threadIdx.x; i < N; i += T) TWs[i] = __ldg(tw + i);
+  const float2* TWs = stage_twiddles<N, RL * C::LS + RL * N>(sm, tw, T);
   const size_t P = (size_t)h * N;
   const int nblk = (h + RL - 1) / RL;
   const int nitems = nblk * nk;

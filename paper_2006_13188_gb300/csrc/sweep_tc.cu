@@ -91,7 +91,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
 
 // KC: channels per split part (2K padded to 16); JP: angles padded to 16.
 template <int KC, int JP>
-__global__ void __launch_bounds__(THREADS) k_sweep_tc(const float* __restrict__ G, long long P, int C2, int J,
+__global__ void __launch_bounds__(THREADS, 4) k_sweep_tc(const float* __restrict__ G, long long P, int C2, int J,
                                                       const float* __restrict__ B, int cp, float* __restrict__ maxv,
                                                       int32_t* __restrict__ argmax, int* __restrict__ err,
                                                       unsigned long long limit_ns) {
@@ -150,14 +150,21 @@ __global__ void __launch_bounds__(THREADS) k_sweep_tc(const float* __restrict__ 
   uint32_t phase = 0;
 
   const long long ntiles = (P + TILE_M - 1) / TILE_M;
+  // this thread's pixel row of the tile, prefetched one tile ahead
+  float a[KC];
+  float g0 = 0.f;
+  auto load_tile = [&](long long t, float (&dst)[KC], float& g) {
+    const long long p = t * TILE_M + tid;
+    const bool live = t < ntiles && p < P;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) dst[c] = (live && c < C2) ? __ldg(G + (size_t)(c + 1) * P + p) : 0.f;
+    g = live ? __ldg(G + p) : 0.f;
+  };
+  load_tile(blockIdx.x, a, g0);
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long p = tile * TILE_M + tid;
     const bool live = p < P;
     // A' row of this pixel: [A_hi | A_hi | A_lo]
-    float a[KC];
-#pragma unroll
-    for (int c = 0; c < KC; ++c) a[c] = (live && c < C2) ? __ldg(G + (size_t)(c + 1) * P + p) : 0.f;
-    const float g0 = live ? __ldg(G + p) : 0.f;
     unsigned char* arow = As + (tid / 8) * SBO + (tid % 8) * 16;
 #pragma unroll
     for (int kb = 0; kb < KC / 8; ++kb) {
@@ -174,6 +181,7 @@ __global__ void __launch_bounds__(THREADS) k_sweep_tc(const float* __restrict__ 
       *reinterpret_cast<uint4*>(arow + (kb + KC / 8) * 128) = vh;
       *reinterpret_cast<uint4*>(arow + (kb + 2 * KC / 8) * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
+    const float g0_cur = g0;
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -191,6 +199,8 @@ __global__ void __launch_bounds__(THREADS) k_sweep_tc(const float* __restrict__ 
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar_addr)
                    : "memory");
     }
+    // the next tile's loads are in flight while the MMA and the epilogue run
+    load_tile(tile + gridDim.x, a, g0);
     if (!mbar_wait_bounded(mbar_addr, phase, limit_ns, err)) abort_flag = 1;
     phase ^= 1u;
     __syncthreads();
@@ -213,7 +223,7 @@ __global__ void __launch_bounds__(THREADS) k_sweep_tc(const float* __restrict__ 
       }
     }
     if (live) {
-      maxv[p] = g0 + best;
+      maxv[p] = g0_cur + best;
       argmax[p] = bj;
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -232,13 +242,17 @@ bool launch_tc(const float* G, long long P, int K, int J, const float* B, int cp
   constexpr int KB = 3 * KC / 8;
   constexpr int SBO = KB * 128;
   constexpr int bytes = (TILE_M / 8) * SBO + (JP / 8) * SBO;
-  // request enough shared memory that at most 4 blocks share an SM (4 x TMEM columns <= 512)
-  constexpr int request = bytes < 50 * 1024 ? 50 * 1024 : bytes;
+  // at most 512 / TCOLS blocks may share an SM's tensor memory (and at most 6):
+  // request enough shared memory that no more fit
+  constexpr int TCOLS = JP <= 32 ? 32 : (JP <= 64 ? 64 : (JP <= 128 ? 128 : 256));
+  constexpr int per_sm = (512 / TCOLS) < 6 ? (512 / TCOLS) : 6;
+  constexpr int floor_bytes = (220 * 1024) / per_sm;
+  constexpr int request = bytes < floor_bytes ? floor_bytes : bytes;
   static const bool once =
       (cudaFuncSetAttribute(k_sweep_tc<KC, JP>, cudaFuncAttributeMaxDynamicSharedMemorySize, request), true);
   (void)once;
   const long long ntiles = (P + TILE_M - 1) / TILE_M;
-  long long grid = (long long)sms * 4;
+  long long grid = (long long)sms * per_sm;
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
   k_sweep_tc<KC, JP><<<(unsigned)grid, THREADS, request, st>>>(G, P, 2 * K, J, B, cp, maxv, argmax, err,
