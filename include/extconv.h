@@ -180,6 +180,25 @@ ext_status ext_sweep_so2(ext_plan plan, const float* G, int64_t n_pix, int K, in
                          int32_t* argmax, int precision, void* stream);
 
 /*
+ * Scale-adaptive extended convolution and smoothing (Sec. 8).  The filter is
+ * a radially symmetric function written in log-radial (Mellin) harmonics,
+ *   F(d) = P(ln|d|) for r_min <= |d| <= r_max,  F(0) = centre_tap, else 0,
+ *   P(u) = sum_{k=-(n_h-1)}^{n_h-1} c_k e^{i w_k u},  w_k = 2 pi k / log_period,
+ *   c_{-k} = conj(c_k)  (mellin_c: n_h complex c_0..c_{n_h-1}, interleaved
+ *   doubles, HOST memory).
+ * Scaling the filter by s(q) multiplies harmonic k by e^{-i w_k ln s(q)} on the
+ * same support (the centre tap is scale invariant).  With A * B denoting the
+ * extended convolution of Eq. Def-EConv under this scale field,
+ *   mode 0: out_c = {H_c, s} * F
+ *   mode 1: out_c = {H_c, s} * F / {1, s} * F                 (Eq. normalization)
+ *   mode 2: out_c = {H_c / s^2, s} * F / {1 / s^2, s} * F     (unit-integral signal)
+ * H, out: channels planes of h x w float32; s: h x w float32 scale field, > 0.
+ */
+ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, int w, const double* mellin_c, int n_h,
+                          double log_period, double r_min, double r_max, double centre_tap, const float* s, int mode,
+                          float* out, void* stream);
+
+/*
  * Allocation-free variant of the FP32 angular sweep (the paper has no
  * counterpart: this entry point exists for callers that cannot let a library
  * allocate device memory -- an application whose device memory is all owned

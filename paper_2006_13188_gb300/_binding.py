@@ -34,7 +34,7 @@ EXPORTED = (
     "ext_status_string", "ext_last_error", "ext_plan_create", "ext_plan_destroy", "ext_plan_trim",
     "ext_plan_profile", "ext_plan_profile_read", "ext_plan_sync",
     "ext_filter_so2_decompose", "ext_conv_so2", "ext_corr_so2", "ext_corr_so2_components",
-    "ext_sweep_so2", "ext_sweep_so2_noalloc",
+    "ext_sweep_so2", "ext_sweep_so2_noalloc", "ext_conv_scale",
 )
 
 
@@ -81,6 +81,8 @@ def lib():
         L.ext_corr_so2_components.argtypes = [vp, vp, i32, i32, fp, vp, vp]
         L.ext_sweep_so2.argtypes = [vp, vp, i64, i32, i32, vp, vp, i32, vp]
         L.ext_sweep_so2_noalloc.argtypes = [vp, i64, i32, i32, vp, vp, vp]
+        dbl = ctypes.c_double
+        L.ext_conv_scale.argtypes = [vp, vp, i32, i32, i32, vp, i32, dbl, dbl, dbl, dbl, vp, i32, vp, vp]
         for name in EXPORTED:
             if name not in ("ext_status_string", "ext_last_error"):
                 getattr(L, name).restype = i32
@@ -229,3 +231,12 @@ def ext_sweep_so2_noalloc(G, n_pix, K, n_angles, max_out, argmax, stream=None):
     """Allocation-free FP32 sweep (device buffers only; see include/extconv.h)."""
     _check(lib().ext_sweep_so2_noalloc(_ptr(G), int(n_pix), int(K), int(n_angles), _ptr(max_out), _ptr(argmax),
                                        _stream(stream)))
+
+
+def ext_conv_scale(plan: Plan, H, channels, h, w, mellin_c, log_period, r_min, r_max, centre_tap, s, mode, out,
+                   stream=None):
+    """Scale-adaptive extended convolution / smoothing (see include/extconv.h)."""
+    c = np.ascontiguousarray(np.asarray(mellin_c, np.complex128)).view(np.float64)
+    _check(lib().ext_conv_scale(plan.handle, _ptr(H), int(channels), int(h), int(w), _ptr(c), int(len(c) // 2),
+                                float(log_period), float(r_min), float(r_max), float(centre_tap), _ptr(s), int(mode),
+                                _ptr(out), _stream(stream)))

@@ -240,13 +240,14 @@ ext_status filter_coefficients(ext_plan plan, const ext_filter_so2* F, cudaStrea
 
 enum SpecMode { SPEC_CORR = 0, SPEC_CONV = 1 };
 
-// Component spectra of F on an h x w grid, tiled for the column passes.
+// Spectra of `ncomp` filter components on an h x w grid, tiled for the column
+// passes; sample(k, grid) writes component k into a zeroed h x w grid.
 //   SPEC_CORR: S_k = conj(F^_k) / (h w)
 //   SPEC_CONV: S_k = w_k F^_k / (h w), w_0 = 1, w_k = 2 (k >= 1; the -k terms
 //              of a real filter give the complex conjugate contribution)
-ext_status spectra(ext_plan plan, const ext_filter_so2* F, int h, int w, SpecMode mode, cudaStream_t st,
-                   const float2** out) {
-  uint64_t key = filter_key(F);
+template <class Sampler>
+ext_status spectra_generic(ext_plan plan, uint64_t key, int h, int w, int ncomp, SpecMode mode, cudaStream_t st,
+                           Sampler&& sample, const float2** out) {
   key = fnv1a(key, &h, sizeof(int));
   key = fnv1a(key, &w, sizeof(int));
   int m = (int)mode;
@@ -258,11 +259,10 @@ ext_status spectra(ext_plan plan, const ext_filter_so2* F, int h, int w, SpecMod
       return EXT_OK;
     }
   }
-  const int K = F->K;
   const int cw = fft_col_tile(h);
   const int ntiles = (w + cw - 1) / cw;
   const size_t per_k = (size_t)ntiles * h * cw;
-  const size_t bytes = sizeof(float2) * per_k * (K + 1);
+  const size_t bytes = sizeof(float2) * per_k * ncomp;
   if (plan->specs.size() >= plan->max_specs) {
     size_t oldest = 0;
     for (size_t i = 1; i < plan->specs.size(); ++i)
@@ -275,24 +275,15 @@ ext_status spectra(ext_plan plan, const ext_filter_so2* F, int h, int w, SpecMod
   e.key = key;
   e.bytes = bytes;
   EXT_CUDA(cudaMalloc(&e.S, bytes));
-  const double2* coef = nullptr;
-  int n_r = 0;
-  double dr = 0;
-  ext_status s = filter_coefficients(plan, F, st, &coef, &n_r, &dr);
-  if (s != EXT_OK) {
-    cudaFree(e.S);
-    return s;
-  }
   const float2 *tw_w = nullptr, *tw_h = nullptr;
   EXT_TRY(twiddle(plan, w, st, &tw_w));
   EXT_TRY(twiddle(plan, h, st, &tw_h));
   void* grid = nullptr;
   EXT_TRY(ensure(plan, "grid", sizeof(float2) * (size_t)h * w, &grid));
-  const int kind = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? EXT_FILTER_ANALYTIC_GAUSSPOW : EXT_FILTER_TABLE;
   const float inv_hw = 1.0f / ((float)h * (float)w);
-  for (int k = 0; k <= K; ++k) {
+  for (int k = 0; k < ncomp; ++k) {
     EXT_CUDA(cudaMemsetAsync(grid, 0, sizeof(float2) * (size_t)h * w, st));
-    launch_component_grid(kind, K, k, coef, n_r, dr, F->sigma, F->R, h, w, (float2*)grid, st);
+    sample(k, (float2*)grid);
     fft_rows_c2c(w, (const float2*)grid, h, 1, (float2*)grid, false, tw_w, st);
     const float scale = (mode == SPEC_CONV && k > 0) ? 2.0f * inv_hw : inv_hw;
     fft_cols_fwd_spectrum(h, (const float2*)grid, w, mode == SPEC_CORR ? 1 : 0, scale, e.S + per_k * k, tw_h, st);
@@ -302,6 +293,28 @@ ext_status spectra(ext_plan plan, const ext_filter_so2* F, int h, int w, SpecMod
   plan->specs.push_back(e);
   *out = e.S;
   return EXT_OK;
+}
+
+// Component spectra of an SO(2) filter F_k = f_k(r) e^{ik theta}, k = 0..K.
+ext_status spectra(ext_plan plan, const ext_filter_so2* F, int h, int w, SpecMode mode, cudaStream_t st,
+                   const float2** out) {
+  const uint64_t key = filter_key(F);
+  // the radial coefficients are only needed on a cache miss; compute them lazily
+  const double2* coef = nullptr;
+  int n_r = 0;
+  double dr = 0;
+  ext_status cs = EXT_OK;
+  bool have = false;
+  const int kind = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? EXT_FILTER_ANALYTIC_GAUSSPOW : EXT_FILTER_TABLE;
+  auto sample = [&](int k, float2* grid) {
+    if (!have) {
+      cs = filter_coefficients(plan, F, st, &coef, &n_r, &dr);
+      have = true;
+    }
+    if (cs == EXT_OK) launch_component_grid(kind, F->K, k, coef, n_r, dr, F->sigma, F->R, h, w, grid, st);
+  };
+  EXT_TRY(spectra_generic(plan, key, h, w, F->K + 1, mode, st, sample, out));
+  return cs;
 }
 
 ext_status sweep_table(ext_plan plan, int K, int J, cudaStream_t st, const float** out, int* cp_out) {
@@ -714,6 +727,69 @@ ext_status ext_conv_so2(ext_plan plan, const float* H, int h, int w, const ext_f
   EXT_CUDA(cudaGetLastError());
   EXT_TRY(stage_out_finish(sO, st));
   return finish_host(plan, sH.host || sAl.host || sO.host, st);
+}
+
+ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, int w, const double* mellin_c, int n_h,
+                          double log_period, double r_min, double r_max, double centre_tap, const float* s, int mode,
+                          float* out, void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_TRY(check_size(h, w));
+  if (h == 0 || w == 0) return EXT_OK;
+  if (!H || !s || !out || !mellin_c) return fail(EXT_ERR_INVALID_ARG, "NULL buffer");
+  if (channels < 1 || channels > 64) return fail(EXT_ERR_INVALID_ARG, "channels must be in [1, 64]");
+  if (n_h < 1 || n_h > 256) return fail(EXT_ERR_INVALID_ARG, "n_h must be in [1, 256]");
+  if (!(log_period > 0)) return fail(EXT_ERR_INVALID_ARG, "log_period must be > 0");
+  if (!(r_min > 0) || !(r_max >= r_min) || r_max > 1024) return fail(EXT_ERR_INVALID_ARG, "need 0 < r_min <= r_max <= 1024");
+  if (mode < 0 || mode > 2) return fail(EXT_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)h * w;
+  Staged sH, sS, sO;
+  EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P * channels, st, &sH));
+  EXT_TRY(stage_in(plan, "in_s", s, sizeof(float) * P, st, &sS));
+  EXT_TRY(stage_out_alloc(plan, "out_0", out, sizeof(float) * P * channels, &sO));
+  // spectra of the Mellin components (Sec. 8), cached per filter and size
+  uint64_t key = 0x5ca1e5ca1e5ca1eull;
+  key = fnv1a(key, mellin_c, sizeof(double) * 2 * n_h);
+  key = fnv1a(key, &n_h, sizeof(int));
+  key = fnv1a(key, &log_period, sizeof(double));
+  key = fnv1a(key, &r_min, sizeof(double));
+  key = fnv1a(key, &r_max, sizeof(double));
+  const int R = (int)r_max;
+  const double two_pi = 6.283185307179586476925286766559;
+  auto sample = [&](int k, float2* grid) {
+    launch_component_grid_mellin(make_double2(mellin_c[2 * k], mellin_c[2 * k + 1]), two_pi * k / log_period, r_min,
+                                 r_max, R, h, w, grid, st);
+  };
+  const float2* S = nullptr;
+  EXT_TRY(spectra_generic(plan, key, h, w, n_h, SPEC_CONV, st, sample, &S));
+  const float2 *tw_w = nullptr, *tw_h = nullptr;
+  EXT_TRY(twiddle(plan, w, st, &tw_w));
+  EXT_TRY(twiddle(plan, h, st, &tw_h));
+  void *A = nullptr, *Y = nullptr, *Nb = nullptr, *Db = nullptr;
+  EXT_TRY(ensure(plan, "Aall", sizeof(float2) * P * n_h, &A));
+  EXT_TRY(ensure(plan, "Y", sizeof(float2) * P, &Y));
+  EXT_TRY(ensure(plan, "Nscale", sizeof(float) * P * channels, &Nb));
+  EXT_TRY(ensure(plan, "Dscale", sizeof(float) * P, &Db));
+  const float omega_step = (float)(two_pi / log_period);
+  const int unit = mode == 2 ? 1 : 0;
+  const int nsig = channels + (mode == 0 ? 0 : 1);
+  for (int sig = 0; sig < nsig; ++sig) {
+    const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
+    float* dst = sig < channels ? (float*)Nb + P * sig : (float*)Db;
+    launch(plan, "rows_fwd_scale", st, [&] {
+      fft_rows_fwd_scale(w, src, (const float*)sS.dev, h, 0, n_h, omega_step, unit, (float2*)A, tw_w, st);
+    });
+    launch(plan, "cols_conv", st, [&] { fft_cols_conv(h, (const float2*)A, w, n_h - 1, S, (float2*)Y, tw_h, st); });
+    launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, dst, tw_w, st); });
+  }
+  launch(plan, "scale_finalize", st, [&] {
+    launch_scale_finalize((const float*)sH.dev, (const float*)sS.dev, (const float*)Nb, (const float*)Db, channels,
+                          (long long)P, mode, (float)centre_tap, (float*)sO.dev, plan->sms, st);
+  });
+  EXT_CUDA(cudaGetLastError());
+  EXT_TRY(stage_out_finish(sO, st));
+  return finish_host(plan, sH.host || sS.host || sO.host, st);
 }
 
 }  // extern "C"

@@ -275,6 +275,19 @@ __device__ __forceinline__ void sincos_kalpha(int k, float alpha, float* s, floa
   sincosf(r, s, c);
 }
 
+// exp(i w x) for FP32 w, x: the product is formed exactly as p + e and
+// reduced like sincos_kalpha.
+__device__ __forceinline__ void sincos_wx(float wk, float x, float* s, float* c) {
+  const float p = wk * x;
+  const float e = fmaf(wk, x, -p);
+  const float n = rintf(p * 0.15915494309189535f);
+  float r = fmaf(-n, 6.28125f, p);
+  r = fmaf(-n, 0.0019353071693331003f, r);
+  r = fmaf(-n, 1.0253131677018246e-11f, r);
+  r += e;
+  sincosf(r, s, c);
+}
+
 // ------------------------------------------------------------ row passes ---
 // All global loads of a block are first gathered into registers (every
 // thread has its EPT loads in flight at once), then written to shared memory.
@@ -340,6 +353,44 @@ k_rows_fwd_phase(const float* __restrict__ H, const float* __restrict__ alpha, i
         float s, c;
         sincos_kalpha(k, av[i], &s, &c);
         sm[(e / N) * C::LS + sidx(e % N)] = make_float2(hv[i] * c, -hv[i] * s);
+      });
+  __syncthreads();
+  row_fft<N, false>(sm, twl);
+  float2* out = A + (size_t)blockIdx.y * h * N;
+  for_elems<C::RL * N, T>([&](int i, int e) {
+    const int y = y0 + e / N;
+    if (y < h) out[(size_t)y * N + e % N] = sm[(e / N) * C::LS + sidx(e % N)];
+  });
+}
+
+// Forward transform of the scale-steered signals of Sec. 8:
+//   A_k = H wgt exp(-i w_k ln s),  w_k = omega_step * (k0 + blockIdx.y),
+// wgt = 1/s^2 when unit_integral (the normalised signal H~ = H/|T|^2), else 1;
+// H == nullptr stands for the constant signal 1 (the denominator of
+// Eq. normalization).
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
+k_rows_fwd_scale(const float* __restrict__ H, const float* __restrict__ sfield, int h, int k0, float omega_step,
+                 int unit_integral, float2* __restrict__ A, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::ROW_THREADS;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::RL * C::LS>(sm, tw, C::ROW_THREADS);
+  const int y0 = blockIdx.x * C::RL;
+  const float wk = omega_step * (float)(k0 + (int)blockIdx.y);
+  float hv[STAGE_G], sv[STAGE_G];
+  for_elems_staged<C::RL * N, T, STAGE_G>(
+      [&](int i, int e) {
+        const int y = y0 + e / N;
+        const size_t idx = (size_t)y * N + e % N;
+        hv[i] = (y < h) ? (H ? __ldg(H + idx) : 1.0f) : 0.f;
+        sv[i] = (y < h) ? __ldg(sfield + idx) : 1.0f;
+      },
+      [&](int i, int e) {
+        float sn, cs;
+        sincos_wx(wk, logf(sv[i]), &sn, &cs);
+        const float a = unit_integral ? hv[i] / (sv[i] * sv[i]) : hv[i];
+        sm[(e / N) * C::LS + sidx(e % N)] = make_float2(a * cs, -a * sn);
       });
   __syncthreads();
   row_fft<N, false>(sm, twl);
@@ -755,6 +806,8 @@ struct FftOps {
                              const float2* tw, cudaStream_t st);
   static void rows_c2c(const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
                        cudaStream_t st);
+  static void rows_fwd_scale(const float* H, const float* s, int h, int k0, int nk, float omega_step,
+                             int unit_integral, float2* A, const float2* tw, cudaStream_t st);
   static void rows_inv_components(const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
                                   cudaStream_t st);
   static void rows_inv_field(const float2* Z, int h, int K, const float* alpha, float* out,
@@ -898,4 +951,13 @@ bool FftOps<N>::rows_inv_components_pipe(const float2* Z, int h, int k0, int nk,
     k_rows_inv_components_pipe<N><<<grid, C::ROW_THREADS, PipeCfg<N>::ROW_SMEM, st>>>(Z, h, k0, nk, G, tw);
     return true;
   }
+}
+
+template <int N>
+void FftOps<N>::rows_fwd_scale(const float* H, const float* s, int h, int k0, int nk, float omega_step,
+                               int unit_integral, float2* A, const float2* tw, cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_rows_fwd_scale<N>, C::ROW_SMEM), true);
+  (void)once;
+  dim3 grid((h + C::RL - 1) / C::RL, nk);
+  k_rows_fwd_scale<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, s, h, k0, omega_step, unit_integral, A, tw);
 }

@@ -189,3 +189,66 @@ __global__ void k_sweep_table(int K, int J, int cp, float* __restrict__ B) {
 void launch_sweep_table(int K, int J, int cp, float* B, cudaStream_t st) {
   k_sweep_table<<<J, 64, 0, st>>>(K, J, cp, B);
 }
+
+// ------------------------------------------------------ Mellin components ---
+// Scale harmonics of Sec. 8, F_k(r) = e^{i w_k ln r} (times the constant f_k of
+// a radially symmetric filter): M_k(d) = c_k exp(i w_k ln|d|) on the annulus
+// r_min <= |d| <= r_max, w_k = 2 pi k / L.  The centre tap is applied by the
+// normalisation epilogue, not here.
+__global__ void k_component_grid_mellin(double2 ck, double omega, double r_min, double r_max, int R, int h, int w,
+                                        int wrap, float2* __restrict__ grid) {
+  const int side = 2 * R + 1;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)side * side) return;
+  const int dy = (int)(idx / side) - R, dx = (int)(idx % side) - R;
+  const double r = hypot((double)dx, (double)dy);
+  if (r < r_min || r > r_max || r == 0.0) return;
+  double s, c;
+  sincos(omega * log(r), &s, &c);
+  const double2 val = make_double2(ck.x * c - ck.y * s, ck.x * s + ck.y * c);
+  const int gy = ((dy % h) + h) % h, gx = ((dx % w) + w) % w;
+  float2* cell = grid + (size_t)gy * w + gx;
+  if (wrap) {
+    atomicAdd(&cell->x, (float)val.x);
+    atomicAdd(&cell->y, (float)val.y);
+  } else {
+    *cell = make_float2((float)val.x, (float)val.y);
+  }
+}
+
+void launch_component_grid_mellin(double2 ck, double omega, double r_min, double r_max, int R, int h, int w,
+                                  float2* grid, cudaStream_t st) {
+  const int side = 2 * R + 1;
+  const long long n = (long long)side * side;
+  const int wrap = (side > h || side > w) ? 1 : 0;
+  k_component_grid_mellin<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ck, omega, r_min, r_max, R, h, w, wrap, grid);
+}
+
+// ------------------------------------------------ smoothing epilogue ---
+// Adds the centre tap c_delta A(p) to every accumulated convolution and, for
+// modes 1 and 2, divides each channel by the denominator (Eq. normalization):
+//   mode 0: out_c = N_c + c_delta H_c
+//   mode 1: out_c = (N_c + c_delta H_c) / (D + c_delta)
+//   mode 2: out_c = (N_c + c_delta H_c / s^2) / (D + c_delta / s^2)
+__global__ void k_scale_finalize(const float* __restrict__ H, const float* __restrict__ s, const float* __restrict__ N,
+                                 const float* __restrict__ D, int channels, long long P, int mode, float cd,
+                                 float* __restrict__ out) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    const float sv = __ldg(s + p);
+    const float wgt = mode == 2 ? 1.0f / (sv * sv) : 1.0f;
+    const float den = mode == 0 ? 1.0f : (__ldg(D + p) + cd * wgt);
+    for (int c = 0; c < channels; ++c) {
+      const size_t i = (size_t)c * P + p;
+      const float num = __ldg(N + i) + cd * wgt * __ldg(H + i);
+      out[i] = mode == 0 ? num : num / den;
+    }
+  }
+}
+
+void launch_scale_finalize(const float* H, const float* s, const float* N, const float* D, int channels, long long P,
+                           int mode, float cd, float* out, int sms, cudaStream_t st) {
+  long long blocks = (P + 255) / 256;
+  if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+  if (blocks < 1) blocks = 1;
+  k_scale_finalize<<<(unsigned)blocks, 256, 0, st>>>(H, s, N, D, channels, P, mode, cd, out);
+}

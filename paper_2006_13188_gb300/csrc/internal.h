@@ -25,6 +25,8 @@ int fft_col_tile(int n);   // columns per block of the length-n column passes
 void fft_rows_r2c(int w, const float* H, int h, float2* Hh, const float2* tw, cudaStream_t st);
 void fft_rows_fwd_phase(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
                         const float2* tw, cudaStream_t st);
+void fft_rows_fwd_scale(int w, const float* H, const float* s, int h, int k0, int nk, float omega_step,
+                        int unit_integral, float2* A, const float2* tw, cudaStream_t st);
 void fft_rows_c2c(int w, const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
                   cudaStream_t st);
 void fft_rows_inv_components(int w, const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
@@ -51,6 +53,10 @@ void launch_decompose_sampled(const double* img, int side, double dr, int n_r, i
 void launch_component_grid(int kind, int K, int k, const double2* coef, int n_r, double dr, double sigma,
                            int R, int h, int w, float2* grid, cudaStream_t st);
 void launch_sweep_table(int K, int J, int cp, float* B, cudaStream_t st);
+void launch_component_grid_mellin(double2 ck, double omega, double r_min, double r_max, int R, int h, int w,
+                                  float2* grid, cudaStream_t st);
+void launch_scale_finalize(const float* H, const float* s, const float* N, const float* D, int channels, long long P,
+                           int mode, float cd, float* out, int sms, cudaStream_t st);
 
 // ----- sweep (sweep.cu)
 // B: J rows of cp floats (cp = 2K rounded up to a multiple of 4).
