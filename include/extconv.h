@@ -180,6 +180,26 @@ ext_status ext_sweep_so2(ext_plan plan, const float* G, int64_t n_pix, int K, in
                          int32_t* argmax, int precision, void* stream);
 
 /*
+ * Batched correlation sweep over many images of uneven sizes, bandwidths and
+ * angle counts (each image as ext_corr_so2 in sweep mode with its own
+ * filter).  All image and output buffers must be DEVICE memory; filter
+ * descriptions are HOST memory read during the call.  The whole batch is
+ * recorded once as a CUDA graph (per-image filter decomposition, component
+ * spectra, forward FFT, inverse passes and sweep) and replayed while the
+ * descriptor list, the filters and the plan's workspace stay the same; the
+ * call is asynchronous on `stream`.
+ */
+typedef struct {
+  const float* H;          /* h x w image, device */
+  int h, w;
+  const ext_filter_so2* F; /* its filter, host */
+  int n_angles;            /* sweep angles J */
+  float* max_out;          /* h x w, device */
+  int32_t* argmax;         /* h x w, device */
+} ext_image_desc;
+ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, int precision, void* stream);
+
+/*
  * Scale-adaptive extended convolution and smoothing (Sec. 8).  The filter is
  * a radially symmetric function written in log-radial (Mellin) harmonics,
  *   F(d) = P(ln|d|) for r_min <= |d| <= r_max,  F(0) = centre_tap, else 0,

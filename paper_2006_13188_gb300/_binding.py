@@ -34,7 +34,7 @@ EXPORTED = (
     "ext_status_string", "ext_last_error", "ext_plan_create", "ext_plan_destroy", "ext_plan_trim",
     "ext_plan_profile", "ext_plan_profile_read", "ext_plan_sync",
     "ext_filter_so2_decompose", "ext_conv_so2", "ext_corr_so2", "ext_corr_so2_components",
-    "ext_sweep_so2", "ext_sweep_so2_noalloc", "ext_conv_scale",
+    "ext_sweep_so2", "ext_sweep_so2_noalloc", "ext_conv_scale", "ext_batch_corr_so2",
 )
 
 
@@ -42,6 +42,10 @@ class ExtError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{msg} (status {status})")
         self.status = status
+
+
+class ext_image_desc(ctypes.Structure):
+    pass
 
 
 class ext_filter_so2(ctypes.Structure):
@@ -52,6 +56,11 @@ class ext_filter_so2(ctypes.Structure):
         ("img", ctypes.POINTER(ctypes.c_double)), ("n_theta", ctypes.c_int),
     ]
 
+
+ext_image_desc._fields_ = [
+    ("H", ctypes.c_void_p), ("h", ctypes.c_int), ("w", ctypes.c_int), ("F", ctypes.POINTER(ext_filter_so2)),
+    ("n_angles", ctypes.c_int), ("max_out", ctypes.c_void_p), ("argmax", ctypes.c_void_p),
+]
 
 _lib = None
 
@@ -81,6 +90,7 @@ def lib():
         L.ext_corr_so2_components.argtypes = [vp, vp, i32, i32, fp, vp, vp]
         L.ext_sweep_so2.argtypes = [vp, vp, i64, i32, i32, vp, vp, i32, vp]
         L.ext_sweep_so2_noalloc.argtypes = [vp, i64, i32, i32, vp, vp, vp]
+        L.ext_batch_corr_so2.argtypes = [vp, ctypes.POINTER(ext_image_desc), i32, i32, vp]
         dbl = ctypes.c_double
         L.ext_conv_scale.argtypes = [vp, vp, i32, i32, i32, vp, i32, dbl, dbl, dbl, dbl, vp, i32, vp, vp]
         for name in EXPORTED:
@@ -240,3 +250,13 @@ def ext_conv_scale(plan: Plan, H, channels, h, w, mellin_c, log_period, r_min, r
     _check(lib().ext_conv_scale(plan.handle, _ptr(H), int(channels), int(h), int(w), _ptr(c), int(len(c) // 2),
                                 float(log_period), float(r_min), float(r_max), float(centre_tap), _ptr(s), int(mode),
                                 _ptr(out), _stream(stream)))
+
+
+def ext_batch_corr_so2(plan: Plan, items, precision=EXT_PREC_BF16X3, stream=None):
+    """items: sequence of (H, h, w, FilterSO2, n_angles, max_out, argmax) with device tensors."""
+    arr = (ext_image_desc * len(items))()
+    keep = []
+    for i, (H, h, w, F, J, mx, am) in enumerate(items):
+        arr[i] = ext_image_desc(_ptr(H), int(h), int(w), ctypes.pointer(F.struct), int(J), _ptr(mx), _ptr(am))
+        keep.append(F)
+    _check(lib().ext_batch_corr_so2(plan.handle, arr, len(items), int(precision), _stream(stream)))

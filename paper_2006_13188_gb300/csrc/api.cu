@@ -2,6 +2,7 @@
 // host/device staging, and the launch sequences of each operator.
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <string>
@@ -84,6 +85,10 @@ struct ext_plan_s {
   int kchunk = 0;        // components per inverse launch (0 = by L2 budget)
   bool pipelined = true; // persistent prefetching passes where they fit
   int* dev_err = nullptr; // device-side status word (bounded waits)
+  // batched correlation: captured CUDA graph of the last batch and its key
+  cudaGraphExec_t batch_exec = nullptr;
+  uint64_t batch_key = 0;
+  std::vector<unsigned char> batch_host;   // packed filter data (host staging)
 };
 
 namespace {
@@ -245,6 +250,37 @@ enum SpecMode { SPEC_CORR = 0, SPEC_CONV = 1 };
 //   SPEC_CORR: S_k = conj(F^_k) / (h w)
 //   SPEC_CONV: S_k = w_k F^_k / (h w), w_0 = 1, w_k = 2 (k >= 1; the -k terms
 //              of a real filter give the complex conjugate contribution)
+// Writes the spectra of `ncomp` components into S (tiled layout, see below).
+// sample(k0, nk, grid) writes components k0..k0+nk-1 into consecutive zeroed
+// h x w planes of grid; components are processed in chunks bounded by memory.
+template <class Sampler>
+ext_status build_spectra(ext_plan plan, int h, int w, int ncomp, int mode, cudaStream_t st, Sampler&& sample,
+                         float2* S) {
+  const int cw = fft_col_tile(h);
+  const size_t per_k = (size_t)((w + cw - 1) / cw) * h * cw;
+  const size_t plane = sizeof(float2) * (size_t)h * w;
+  int chunk = (int)((512ull << 20) / plane);
+  if (chunk < 1) chunk = 1;
+  if (chunk > ncomp) chunk = ncomp;
+  const float2 *tw_w = nullptr, *tw_h = nullptr;
+  EXT_TRY(twiddle(plan, w, st, &tw_w));
+  EXT_TRY(twiddle(plan, h, st, &tw_h));
+  void* grid = nullptr;
+  EXT_TRY(ensure(plan, "grid", plane * chunk, &grid));
+  const float inv_hw = 1.0f / ((float)h * (float)w);
+  for (int k0 = 0; k0 < ncomp; k0 += chunk) {
+    const int nk = k0 + chunk <= ncomp ? chunk : ncomp - k0;
+    EXT_CUDA(cudaMemsetAsync(grid, 0, plane * nk, st));
+    sample(k0, nk, (float2*)grid);
+    fft_rows_c2c(w, (const float2*)grid, h, nk, (float2*)grid, false, tw_w, st);
+    const float s_rest = mode == 1 ? 2.0f * inv_hw : inv_hw;   // SPEC_CONV weights k >= 1 by 2
+    const float s0 = k0 == 0 ? inv_hw : s_rest;
+    fft_cols_fwd_spectrum(h, (const float2*)grid, w, mode == 0 ? 1 : 0, s0, S + per_k * k0, tw_h, st, nk, s_rest);
+  }
+  EXT_CUDA(cudaGetLastError());
+  return EXT_OK;
+}
+
 template <class Sampler>
 ext_status spectra_generic(ext_plan plan, uint64_t key, int h, int w, int ncomp, SpecMode mode, cudaStream_t st,
                            Sampler&& sample, const float2** out) {
@@ -278,17 +314,7 @@ ext_status spectra_generic(ext_plan plan, uint64_t key, int h, int w, int ncomp,
   const float2 *tw_w = nullptr, *tw_h = nullptr;
   EXT_TRY(twiddle(plan, w, st, &tw_w));
   EXT_TRY(twiddle(plan, h, st, &tw_h));
-  void* grid = nullptr;
-  EXT_TRY(ensure(plan, "grid", sizeof(float2) * (size_t)h * w, &grid));
-  const float inv_hw = 1.0f / ((float)h * (float)w);
-  for (int k = 0; k < ncomp; ++k) {
-    EXT_CUDA(cudaMemsetAsync(grid, 0, sizeof(float2) * (size_t)h * w, st));
-    sample(k, (float2*)grid);
-    fft_rows_c2c(w, (const float2*)grid, h, 1, (float2*)grid, false, tw_w, st);
-    const float scale = (mode == SPEC_CONV && k > 0) ? 2.0f * inv_hw : inv_hw;
-    fft_cols_fwd_spectrum(h, (const float2*)grid, w, mode == SPEC_CORR ? 1 : 0, scale, e.S + per_k * k, tw_h, st);
-  }
-  EXT_CUDA(cudaGetLastError());
+  EXT_TRY(build_spectra(plan, h, w, ncomp, mode, st, sample, e.S));
   e.stamp = ++plan->clock;
   plan->specs.push_back(e);
   *out = e.S;
@@ -306,12 +332,12 @@ ext_status spectra(ext_plan plan, const ext_filter_so2* F, int h, int w, SpecMod
   ext_status cs = EXT_OK;
   bool have = false;
   const int kind = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? EXT_FILTER_ANALYTIC_GAUSSPOW : EXT_FILTER_TABLE;
-  auto sample = [&](int k, float2* grid) {
+  auto sample = [&](int k0, int nk, float2* grid) {
     if (!have) {
       cs = filter_coefficients(plan, F, st, &coef, &n_r, &dr);
       have = true;
     }
-    if (cs == EXT_OK) launch_component_grid(kind, F->K, k, coef, n_r, dr, F->sigma, F->R, h, w, grid, st);
+    if (cs == EXT_OK) launch_component_grid(kind, F->K, k0, coef, n_r, dr, F->sigma, F->R, h, w, grid, st, nk);
   };
   EXT_TRY(spectra_generic(plan, key, h, w, F->K + 1, mode, st, sample, out));
   return cs;
@@ -535,6 +561,7 @@ ext_status ext_plan_destroy(ext_plan plan) {
     cudaEventDestroy(p.b);
   }
   for (auto e : plan->event_pool) cudaEventDestroy(e);
+  if (plan->batch_exec) cudaGraphExecDestroy(plan->batch_exec);
   cudaFree(plan->dev_err);
   delete plan;
   return EXT_OK;
@@ -757,9 +784,10 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
   key = fnv1a(key, &r_max, sizeof(double));
   const int R = (int)r_max;
   const double two_pi = 6.283185307179586476925286766559;
-  auto sample = [&](int k, float2* grid) {
-    launch_component_grid_mellin(make_double2(mellin_c[2 * k], mellin_c[2 * k + 1]), two_pi * k / log_period, r_min,
-                                 r_max, R, h, w, grid, st);
+  auto sample = [&](int k0, int nk, float2* grid) {
+    for (int k = k0; k < k0 + nk; ++k)
+      launch_component_grid_mellin(make_double2(mellin_c[2 * k], mellin_c[2 * k + 1]), two_pi * k / log_period,
+                                   r_min, r_max, R, h, w, grid + (size_t)(k - k0) * h * w, st);
   };
   const float2* S = nullptr;
   EXT_TRY(spectra_generic(plan, key, h, w, n_h, SPEC_CONV, st, sample, &S));
@@ -790,6 +818,155 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
   EXT_CUDA(cudaGetLastError());
   EXT_TRY(stage_out_finish(sO, st));
   return finish_host(plan, sH.host || sS.host || sO.host, st);
+}
+
+ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, int precision, void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  if (n < 0 || (n > 0 && !imgs)) return fail(EXT_ERR_INVALID_ARG, "bad image list");
+  if (n == 0) return EXT_OK;
+  if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3) return fail(EXT_ERR_INVALID_ARG, "unknown precision");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  // ---- validate, size the workspaces, pack the filter data
+  size_t max_S = 0, max_grid = 0, max_Hh = 0, max_Z = 0, max_G = 0, max_polar = 0;
+  std::vector<size_t> off_in(n), off_coef(n);
+  std::vector<int> nr(n);
+  size_t host_bytes = 0, coef_bytes = 0;
+  uint64_t key = 0xba7c4ba7c4ull;
+  for (int i = 0; i < n; ++i) {
+    const ext_image_desc& d = imgs[i];
+    EXT_TRY(check_filter(d.F));
+    EXT_TRY(check_size(d.h, d.w));
+    if (d.h == 0 || d.w == 0) return fail(EXT_ERR_INVALID_ARG, "empty image in a batch");
+    if (!d.H || !d.max_out || !d.argmax) return fail(EXT_ERR_INVALID_ARG, "NULL buffer in a batch");
+    if (!is_device_ptr(d.H) || !is_device_ptr(d.max_out) || !is_device_ptr(d.argmax))
+      return fail(EXT_ERR_INVALID_ARG, "batched images and outputs must be device buffers");
+    const int K = d.F->K;
+    if (d.n_angles < 1 || K > 16 || (precision == EXT_PREC_BF16X3 && d.n_angles > 128))
+      return fail(EXT_ERR_UNSUPPORTED, "batched sweep supports K <= 16 and 1..128 angles (BF16x3)");
+    const size_t P = (size_t)d.h * d.w;
+    const int cw = fft_col_tile(d.h);
+    max_S = std::max(max_S, sizeof(float2) * (size_t)(K + 1) * ((d.w + cw - 1) / cw) * d.h * cw);
+    max_grid = std::max(max_grid, sizeof(float2) * P * std::min<size_t>(K + 1, std::max<size_t>(1, (512ull << 20) / (8 * P))));
+    max_Hh = std::max(max_Hh, sizeof(float2) * (size_t)d.h * (d.w / 2 + 1));
+    max_Z = std::max(max_Z, sizeof(float2) * P * (K + 1));
+    max_G = std::max(max_G, sizeof(float) * P * (2 * K + 1));
+    const size_t nk = (size_t)(2 * K + 1);
+    size_t in_bytes = 0;
+    if (d.F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW) { in_bytes = sizeof(double2) * nk; nr[i] = 0; }
+    else if (d.F->kind == EXT_FILTER_TABLE) { in_bytes = sizeof(double2) * nk * d.F->n_r; nr[i] = d.F->n_r; }
+    else {
+      const size_t side = 2 * d.F->R + 1;
+      in_bytes = sizeof(double) * side * side;
+      nr[i] = sampled_nr(d.F);
+      max_polar = std::max(max_polar, sizeof(double) * nr[i] * d.F->n_theta);
+    }
+    off_in[i] = host_bytes;
+    host_bytes += (in_bytes + 255) / 256 * 256;
+    off_coef[i] = coef_bytes;
+    coef_bytes += (sizeof(double2) * nk * std::max(nr[i], 1) + 255) / 256 * 256;
+    const uint64_t fk = filter_key(d.F);
+    key = fnv1a(key, &fk, sizeof(fk));
+    key = fnv1a(key, &d, sizeof(d));
+  }
+  key = fnv1a(key, &precision, sizeof(int));
+  void *dS, *dgrid, *dHh, *dZ, *dG, *dpolar, *din, *dcoef;
+  EXT_TRY(ensure(plan, "Sbatch", max_S, &dS));
+  EXT_TRY(ensure(plan, "grid", max_grid, &dgrid));
+  EXT_TRY(ensure(plan, "Hh", max_Hh, &dHh));
+  EXT_TRY(ensure(plan, "Z", max_Z, &dZ));
+  EXT_TRY(ensure(plan, "G", max_G, &dG));
+  EXT_TRY(ensure(plan, "fpolar", std::max<size_t>(max_polar, 8), &dpolar));
+  EXT_TRY(ensure(plan, "batch_in", host_bytes, &din));
+  EXT_TRY(ensure(plan, "batch_coef", coef_bytes, &dcoef));
+  for (void* q : {dS, dgrid, dHh, dZ, dG, dpolar, din, dcoef}) key = fnv1a(key, &q, sizeof(q));
+  // tables used inside the graph are created beforehand
+  for (int i = 0; i < n; ++i) {
+    const float2* t;
+    EXT_TRY(twiddle(plan, imgs[i].w, st, &t));
+    EXT_TRY(twiddle(plan, imgs[i].h, st, &t));
+    if (imgs[i].F->K > 0) {
+      const float* B;
+      int cp;
+      EXT_TRY(sweep_table(plan, imgs[i].F->K, imgs[i].n_angles, st, &B, &cp));
+    }
+  }
+  // ---- upload the filter data (every call; the graph reads it from batch_in)
+  plan->batch_host.resize(std::max<size_t>(host_bytes, 1));
+  for (int i = 0; i < n; ++i) {
+    const ext_filter_so2* F = imgs[i].F;
+    const size_t nk = (size_t)(2 * F->K + 1);
+    unsigned char* dst = plan->batch_host.data() + off_in[i];
+    if (F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW) std::memcpy(dst, F->a, sizeof(double2) * nk);
+    else if (F->kind == EXT_FILTER_TABLE) std::memcpy(dst, F->fk, sizeof(double2) * nk * F->n_r);
+    else std::memcpy(dst, F->img, sizeof(double) * (2 * F->R + 1) * (2 * F->R + 1));
+  }
+  EXT_CUDA(cudaMemcpyAsync(din, plan->batch_host.data(), host_bytes, cudaMemcpyHostToDevice, st));
+  EXT_CUDA(cudaStreamSynchronize(st));   // the host staging buffer is reused by the next call
+  // ---- capture the per-image launch sequences once, then replay
+  if (plan->batch_exec == nullptr || plan->batch_key != key) {
+    if (plan->batch_exec) {
+      EXT_CUDA(cudaGraphExecDestroy(plan->batch_exec));
+      plan->batch_exec = nullptr;
+    }
+    const bool profiling = plan->profiling;
+    plan->profiling = false;   // no event records inside the graph
+    cudaStream_t cs = nullptr;
+    EXT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    EXT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    ext_status ss = EXT_OK;
+    for (int i = 0; i < n && ss == EXT_OK; ++i) {
+      const ext_image_desc& d = imgs[i];
+      const ext_filter_so2* F = d.F;
+      const int K = F->K, h = d.h, w = d.w;
+      const size_t P = (size_t)h * w;
+      const double2* coef = (const double2*)((unsigned char*)din + off_in[i]);
+      if (F->kind == EXT_FILTER_SAMPLED) {
+        double2* table = (double2*)((unsigned char*)dcoef + off_coef[i]);
+        launch_decompose_sampled((const double*)coef, 2 * F->R + 1, F->dr, nr[i], F->n_theta, K, (double*)dpolar, table,
+                                 cs);
+        coef = table;
+      }
+      const int kind = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? EXT_FILTER_ANALYTIC_GAUSSPOW : EXT_FILTER_TABLE;
+      const double dr = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? 0.0 : F->dr;
+      auto sample = [&](int k0, int nk, float2* grid) {
+        launch_component_grid(kind, K, k0, coef, nr[i], dr, F->sigma, F->R, h, w, grid, cs, nk);
+      };
+      ss = build_spectra(plan, h, w, K + 1, SPEC_CORR, cs, sample, (float2*)dS);
+      if (ss != EXT_OK) break;
+      const float2 *tw_w = nullptr, *tw_h = nullptr;
+      twiddle(plan, w, cs, &tw_w);
+      twiddle(plan, h, cs, &tw_h);
+      const int wh = w / 2 + 1;
+      fft_rows_r2c(w, d.H, h, (float2*)dHh, tw_w, cs);
+      fft_cols_fwd_half(h, (float2*)dHh, wh, tw_h, cs);
+      if (!fft_cols_inv_corr_pipe(h, (const float2*)dHh, w, (const float2*)dS, 0, K + 1, (float2*)dZ, tw_h, plan->sms, cs))
+        fft_cols_inv_corr(h, (const float2*)dHh, w, (const float2*)dS, 0, K + 1, (float2*)dZ, tw_h, cs);
+      if (!fft_rows_inv_components_pipe(w, (const float2*)dZ, h, 0, K + 1, (float*)dG, tw_w, plan->sms, cs))
+        fft_rows_inv_components(w, (const float2*)dZ, h, 0, K + 1, (float*)dG, tw_w, cs);
+      ss = run_sweep(plan, (const float*)dG, (long long)P, K, d.n_angles, d.max_out, d.argmax, precision, cs);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    plan->profiling = profiling;
+    if (ss != EXT_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cs);
+      return ss;
+    }
+    if (ce != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      return fail(EXT_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(ce));
+    }
+    ce = cudaGraphInstantiate(&plan->batch_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (ce != cudaSuccess) return fail(EXT_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(ce));
+    plan->batch_key = key;
+  }
+  plan->prof["batch_graph"].launches += 1;
+  EXT_CUDA(cudaGraphLaunch(plan->batch_exec, st));
+  return EXT_OK;
 }
 
 }  // extern "C"

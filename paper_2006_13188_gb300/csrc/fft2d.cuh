@@ -555,11 +555,15 @@ k_cols_fwd_half(float2* Hh, int ncols, const float2* __restrict__ tw) {
 // (convolution).
 template <int N>
 __global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, LineCfg<N>::COL_MINB)
-k_cols_fwd_spectrum(const float2* __restrict__ X, int w, int conj_out, float scale,
+k_cols_fwd_spectrum(const float2* __restrict__ X, int w, int conj_out, float scale, float scale_rest,
                     float2* __restrict__ S, const float2* __restrict__ tw) {
   using C = LineCfg<N>;
   constexpr int T = C::COL_THREADS;
   extern __shared__ float2 sm[];
+  // blockIdx.y = plane: plane 0 is scaled by `scale`, the others by `scale_rest`
+  X += (size_t)blockIdx.y * N * w;
+  S += (size_t)blockIdx.y * ((w + C::CW - 1) / C::CW) * N * C::CW;
+  if (blockIdx.y > 0) scale = scale_rest;
   const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
   const int tile = blockIdx.x;
   const int u0 = tile * C::CW;
@@ -815,7 +819,7 @@ struct FftOps {
   static void rows_inv_real(const float2* Y, int h, float* out, const float2* tw, cudaStream_t st);
   static void cols_fwd_half(float2* Hh, int ncols, const float2* tw, cudaStream_t st);
   static void cols_fwd_spectrum(const float2* X, int w, int conj_out, float scale, float2* S,
-                                const float2* tw, cudaStream_t st);
+                                const float2* tw, cudaStream_t st, int nplanes, float scale_rest);
   static void cols_inv_corr(const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
                             const float2* tw, cudaStream_t st);
   static void cols_conv(const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
@@ -898,11 +902,11 @@ void FftOps<N>::cols_fwd_half(float2* Hh, int ncols, const float2* tw, cudaStrea
 
 template <int N>
 void FftOps<N>::cols_fwd_spectrum(const float2* X, int w, int conj_out, float scale, float2* S,
-                                  const float2* tw, cudaStream_t st) {
+                                  const float2* tw, cudaStream_t st, int nplanes, float scale_rest) {
   static const bool once = (ext_set_smem(k_cols_fwd_spectrum<N>, C::COL_SMEM), true);
   (void)once;
-  dim3 grid((w + C::CW - 1) / C::CW);
-  k_cols_fwd_spectrum<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(X, w, conj_out, scale, S, tw);
+  dim3 grid((w + C::CW - 1) / C::CW, nplanes);
+  k_cols_fwd_spectrum<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(X, w, conj_out, scale, scale_rest, S, tw);
 }
 
 template <int N>

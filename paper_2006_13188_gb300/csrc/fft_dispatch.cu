@@ -70,9 +70,9 @@ void fft_cols_fwd_half(int h, float2* Hh, int ncols, const float2* tw, cudaStrea
 }
 #undef EXT_C1
 
-#define EXT_C1(N) case N: FftOps<N>::cols_fwd_spectrum(X, w, conj_out, scale, S, tw, st); return;
+#define EXT_C1(N) case N: FftOps<N>::cols_fwd_spectrum(X, w, conj_out, scale, S, tw, st, nplanes, scale_rest); return;
 void fft_cols_fwd_spectrum(int h, const float2* X, int w, int conj_out, float scale, float2* S,
-                           const float2* tw, cudaStream_t st) {
+                           const float2* tw, cudaStream_t st, int nplanes, float scale_rest) {
   switch (h) { EXT_FFT_SIZES(EXT_C1) default: return; }
 }
 #undef EXT_C1

@@ -127,6 +127,9 @@ __device__ double2 radial_table(const double2* __restrict__ v, int n, double dr,
 __global__ void k_component_grid(int kind, int K, int k, const double2* __restrict__ coef, int n_r,
                                  double dr, double sigma, int R, int h, int w, int wrap,
                                  float2* __restrict__ grid) {
+  // blockIdx.y selects component k + blockIdx.y, written to plane blockIdx.y
+  k += blockIdx.y;
+  grid += (size_t)blockIdx.y * h * w;
   const int side = 2 * R + 1;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)side * side) return;
@@ -159,12 +162,12 @@ __global__ void k_component_grid(int kind, int K, int k, const double2* __restri
 }
 
 void launch_component_grid(int kind, int K, int k, const double2* coef, int n_r, double dr, double sigma,
-                           int R, int h, int w, float2* grid, cudaStream_t st) {
+                           int R, int h, int w, float2* grid, cudaStream_t st, int ncomp) {
   const int side = 2 * R + 1;
   const long long n = (long long)side * side;
   const int wrap = (side > h || side > w) ? 1 : 0;
-  k_component_grid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kind, K, k, coef, n_r, dr, sigma, R, h, w,
-                                                                wrap, grid);
+  dim3 grid_dim((unsigned)((n + 255) / 256), ncomp);
+  k_component_grid<<<grid_dim, 256, 0, st>>>(kind, K, k, coef, n_r, dr, sigma, R, h, w, wrap, grid);
 }
 
 // -------------------------------------------------------- sweep weights ---

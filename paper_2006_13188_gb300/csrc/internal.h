@@ -36,7 +36,7 @@ void fft_rows_inv_field(int w, const float2* Z, int h, int K, const float* alpha
 void fft_rows_inv_real(int w, const float2* Y, int h, float* out, const float2* tw, cudaStream_t st);
 void fft_cols_fwd_half(int h, float2* Hh, int ncols, const float2* tw, cudaStream_t st);
 void fft_cols_fwd_spectrum(int h, const float2* X, int w, int conj_out, float scale, float2* S,
-                           const float2* tw, cudaStream_t st);
+                           const float2* tw, cudaStream_t st, int nplanes = 1, float scale_rest = 0.f);
 void fft_cols_inv_corr(int h, const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
                        const float2* tw, cudaStream_t st);
 bool fft_cols_inv_corr_pipe(int h, const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
@@ -50,8 +50,9 @@ void fft_cols_conv(int h, const float2* A, int w, int K, const float2* S, float2
 void launch_twiddle(float2* tw, int n, cudaStream_t st);
 void launch_decompose_sampled(const double* img, int side, double dr, int n_r, int n_theta, int K,
                               double* P, double2* fk, cudaStream_t st);
+// ncomp consecutive components k .. k+ncomp-1 into consecutive h x w planes of grid
 void launch_component_grid(int kind, int K, int k, const double2* coef, int n_r, double dr, double sigma,
-                           int R, int h, int w, float2* grid, cudaStream_t st);
+                           int R, int h, int w, float2* grid, cudaStream_t st, int ncomp = 1);
 void launch_sweep_table(int K, int J, int cp, float* B, cudaStream_t st);
 void launch_component_grid_mellin(double2 ck, double omega, double r_min, double r_max, int R, int h, int w,
                                   float2* grid, cudaStream_t st);
