@@ -255,7 +255,7 @@ enum SpecMode { SPEC_CORR = 0, SPEC_CONV = 1 };
 // h x w planes of grid; components are processed in chunks bounded by memory.
 template <class Sampler>
 ext_status build_spectra(ext_plan plan, int h, int w, int ncomp, int mode, cudaStream_t st, Sampler&& sample,
-                         float2* S) {
+                         float2* S, const char* grid_name = "grid") {
   const int cw = fft_col_tile(h);
   const size_t per_k = (size_t)((w + cw - 1) / cw) * h * cw;
   const size_t plane = sizeof(float2) * (size_t)h * w;
@@ -266,7 +266,7 @@ ext_status build_spectra(ext_plan plan, int h, int w, int ncomp, int mode, cudaS
   EXT_TRY(twiddle(plan, w, st, &tw_w));
   EXT_TRY(twiddle(plan, h, st, &tw_h));
   void* grid = nullptr;
-  EXT_TRY(ensure(plan, "grid", plane * chunk, &grid));
+  EXT_TRY(ensure(plan, grid_name, plane * chunk, &grid));
   const float inv_hw = 1.0f / ((float)h * (float)w);
   for (int k0 = 0; k0 < ncomp; k0 += chunk) {
     const int nk = k0 + chunk <= ncomp ? chunk : ncomp - k0;
@@ -870,16 +870,27 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
     key = fnv1a(key, &d, sizeof(d));
   }
   key = fnv1a(key, &precision, sizeof(int));
-  void *dS, *dgrid, *dHh, *dZ, *dG, *dpolar, *din, *dcoef;
-  EXT_TRY(ensure(plan, "Sbatch", max_S, &dS));
-  EXT_TRY(ensure(plan, "grid", max_grid, &dgrid));
-  EXT_TRY(ensure(plan, "Hh", max_Hh, &dHh));
-  EXT_TRY(ensure(plan, "Z", max_Z, &dZ));
-  EXT_TRY(ensure(plan, "G", max_G, &dG));
-  EXT_TRY(ensure(plan, "fpolar", std::max<size_t>(max_polar, 8), &dpolar));
+  // independent images run on NB parallel branches of the graph, each with its own workspace set
+  const int NB = n < 4 ? n : 4;
+  static const char* kS[4] = {"Sbatch0", "Sbatch1", "Sbatch2", "Sbatch3"};
+  static const char* kGrid[4] = {"grid0", "grid1", "grid2", "grid3"};
+  static const char* kHh[4] = {"Hh0", "Hh1", "Hh2", "Hh3"};
+  static const char* kZ[4] = {"Z0", "Z1", "Z2", "Z3"};
+  static const char* kG[4] = {"G0", "G1", "G2", "G3"};
+  static const char* kP[4] = {"fpolar0", "fpolar1", "fpolar2", "fpolar3"};
+  void *dS[4], *dgrid[4], *dHh[4], *dZ[4], *dG[4], *dpolar[4], *din, *dcoef;
+  for (int b = 0; b < NB; ++b) {
+    EXT_TRY(ensure(plan, kS[b], max_S, &dS[b]));
+    EXT_TRY(ensure(plan, kGrid[b], max_grid, &dgrid[b]));
+    EXT_TRY(ensure(plan, kHh[b], max_Hh, &dHh[b]));
+    EXT_TRY(ensure(plan, kZ[b], max_Z, &dZ[b]));
+    EXT_TRY(ensure(plan, kG[b], max_G, &dG[b]));
+    EXT_TRY(ensure(plan, kP[b], std::max<size_t>(max_polar, 8), &dpolar[b]));
+    for (void* q : {dS[b], dgrid[b], dHh[b], dZ[b], dG[b], dpolar[b]}) key = fnv1a(key, &q, sizeof(q));
+  }
   EXT_TRY(ensure(plan, "batch_in", host_bytes, &din));
   EXT_TRY(ensure(plan, "batch_coef", coef_bytes, &dcoef));
-  for (void* q : {dS, dgrid, dHh, dZ, dG, dpolar, din, dcoef}) key = fnv1a(key, &q, sizeof(q));
+  for (void* q : {din, dcoef}) key = fnv1a(key, &q, sizeof(q));
   // tables used inside the graph are created beforehand
   for (int i = 0; i < n; ++i) {
     const float2* t;
@@ -911,11 +922,21 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
     }
     const bool profiling = plan->profiling;
     plan->profiling = false;   // no event records inside the graph
-    cudaStream_t cs = nullptr;
+    cudaStream_t cs = nullptr, br[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
     EXT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    for (int b = 0; b < NB; ++b) {
+      EXT_CUDA(cudaStreamCreateWithFlags(&br[b], cudaStreamNonBlocking));
+      EXT_CUDA(cudaEventCreateWithFlags(&join[b], cudaEventDisableTiming));
+    }
+    EXT_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     EXT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    EXT_CUDA(cudaEventRecord(fork, cs));
+    for (int b = 0; b < NB; ++b) EXT_CUDA(cudaStreamWaitEvent(br[b], fork, 0));
     ext_status ss = EXT_OK;
     for (int i = 0; i < n && ss == EXT_OK; ++i) {
+      const int b = i % NB;
+      cudaStream_t bs = br[b];
       const ext_image_desc& d = imgs[i];
       const ext_filter_so2* F = d.F;
       const int K = F->K, h = d.h, w = d.w;
@@ -923,44 +944,57 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
       const double2* coef = (const double2*)((unsigned char*)din + off_in[i]);
       if (F->kind == EXT_FILTER_SAMPLED) {
         double2* table = (double2*)((unsigned char*)dcoef + off_coef[i]);
-        launch_decompose_sampled((const double*)coef, 2 * F->R + 1, F->dr, nr[i], F->n_theta, K, (double*)dpolar, table,
-                                 cs);
+        launch_decompose_sampled((const double*)coef, 2 * F->R + 1, F->dr, nr[i], F->n_theta, K, (double*)dpolar[b], table,
+                                 bs);
         coef = table;
       }
       const int kind = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? EXT_FILTER_ANALYTIC_GAUSSPOW : EXT_FILTER_TABLE;
       const double dr = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? 0.0 : F->dr;
       auto sample = [&](int k0, int nk, float2* grid) {
-        launch_component_grid(kind, K, k0, coef, nr[i], dr, F->sigma, F->R, h, w, grid, cs, nk);
+        launch_component_grid(kind, K, k0, coef, nr[i], dr, F->sigma, F->R, h, w, grid, bs, nk);
       };
-      ss = build_spectra(plan, h, w, K + 1, SPEC_CORR, cs, sample, (float2*)dS);
+      ss = build_spectra(plan, h, w, K + 1, SPEC_CORR, bs, sample, (float2*)dS[b], kGrid[b]);
       if (ss != EXT_OK) break;
       const float2 *tw_w = nullptr, *tw_h = nullptr;
-      twiddle(plan, w, cs, &tw_w);
-      twiddle(plan, h, cs, &tw_h);
+      twiddle(plan, w, bs, &tw_w);
+      twiddle(plan, h, bs, &tw_h);
       const int wh = w / 2 + 1;
-      fft_rows_r2c(w, d.H, h, (float2*)dHh, tw_w, cs);
-      fft_cols_fwd_half(h, (float2*)dHh, wh, tw_h, cs);
-      if (!fft_cols_inv_corr_pipe(h, (const float2*)dHh, w, (const float2*)dS, 0, K + 1, (float2*)dZ, tw_h, plan->sms, cs))
-        fft_cols_inv_corr(h, (const float2*)dHh, w, (const float2*)dS, 0, K + 1, (float2*)dZ, tw_h, cs);
-      if (!fft_rows_inv_components_pipe(w, (const float2*)dZ, h, 0, K + 1, (float*)dG, tw_w, plan->sms, cs))
-        fft_rows_inv_components(w, (const float2*)dZ, h, 0, K + 1, (float*)dG, tw_w, cs);
-      ss = run_sweep(plan, (const float*)dG, (long long)P, K, d.n_angles, d.max_out, d.argmax, precision, cs);
+      fft_rows_r2c(w, d.H, h, (float2*)dHh[b], tw_w, bs);
+      fft_cols_fwd_half(h, (float2*)dHh[b], wh, tw_h, bs);
+      if (!fft_cols_inv_corr_pipe(h, (const float2*)dHh[b], w, (const float2*)dS[b], 0, K + 1, (float2*)dZ[b], tw_h,
+                                  plan->sms, bs))
+        fft_cols_inv_corr(h, (const float2*)dHh[b], w, (const float2*)dS[b], 0, K + 1, (float2*)dZ[b], tw_h, bs);
+      if (!fft_rows_inv_components_pipe(w, (const float2*)dZ[b], h, 0, K + 1, (float*)dG[b], tw_w, plan->sms, bs))
+        fft_rows_inv_components(w, (const float2*)dZ[b], h, 0, K + 1, (float*)dG[b], tw_w, bs);
+      ss = run_sweep(plan, (const float*)dG[b], (long long)P, K, d.n_angles, d.max_out, d.argmax, precision, bs);
+    }
+    for (int b = 0; b < NB; ++b) {
+      cudaEventRecord(join[b], br[b]);
+      cudaStreamWaitEvent(cs, join[b], 0);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     plan->profiling = profiling;
+    auto cleanup = [&] {
+      cudaStreamDestroy(cs);
+      for (int b = 0; b < NB; ++b) {
+        cudaStreamDestroy(br[b]);
+        cudaEventDestroy(join[b]);
+      }
+      cudaEventDestroy(fork);
+    };
     if (ss != EXT_OK) {
       if (graph) cudaGraphDestroy(graph);
-      cudaStreamDestroy(cs);
+      cleanup();
       return ss;
     }
     if (ce != cudaSuccess) {
-      cudaStreamDestroy(cs);
+      cleanup();
       return fail(EXT_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(ce));
     }
     ce = cudaGraphInstantiate(&plan->batch_exec, graph, 0);
     cudaGraphDestroy(graph);
-    cudaStreamDestroy(cs);
+    cleanup();
     if (ce != cudaSuccess) return fail(EXT_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(ce));
     plan->batch_key = key;
   }
