@@ -71,27 +71,33 @@ class RadialTable:
         return (self.n - 1) * self.dr
 
     def radial(self, k: int, r):
-        r = np.asarray(r, np.float64)
-        v = self.fk[k + self.K]
-        n = self.n
-        ext = np.zeros(n + 3, np.complex128)      # ext[j + 1] = v_j, j = -1..n+1
-        ext[1:n + 1] = v
-        ext[0] = ((-1) ** abs(k)) * v[1] if n > 1 else 0.0
-        # v_n = v_{n+1} = 0 already
-        u = r / self.dr
-        i = np.floor(u).astype(np.int64)
-        inside = (u <= n - 1 + 1e-9) & (i >= 0)
-        i = np.clip(i, 0, n - 1)
-        t = u - i
-        vi = ext[i + 1]
-        vi1 = ext[i + 2]
-        mi = 0.5 * (ext[i + 2] - ext[i])
-        mi1 = 0.5 * (ext[i + 3] - ext[i + 1])
-        t2 = t * t
-        t3 = t2 * t
-        val = ((2 * t3 - 3 * t2 + 1) * vi + (t3 - 2 * t2 + t) * mi
-               + (-2 * t3 + 3 * t2) * vi1 + (t3 - t2) * mi1)
-        return np.where(inside, val, 0.0)
+        return hermite_eval(self.fk[k + self.K], self.dr, k, r)
+
+
+def hermite_eval(v, dr: float, parity: int, r):
+    """Cubic Hermite interpolant of samples v_i = f(i dr) (see RadialTable),
+    with f extended to negative radius as f(-r) = (-1)^parity f(r), v_n = 0,
+    and f = 0 for r / dr > n - 1 + 1e-9."""
+    r = np.asarray(r, np.float64)
+    v = np.asarray(v, np.complex128)
+    n = len(v)
+    ext = np.zeros(n + 3, np.complex128)      # ext[j + 1] = v_j, j = -1..n+1
+    ext[1:n + 1] = v
+    ext[0] = ((-1) ** abs(parity)) * v[1] if n > 1 else 0.0
+    u = r / dr
+    i = np.floor(u).astype(np.int64)
+    inside = (u <= n - 1 + 1e-9) & (i >= 0)
+    i = np.clip(i, 0, n - 1)
+    t = u - i
+    vi = ext[i + 1]
+    vi1 = ext[i + 2]
+    mi = 0.5 * (ext[i + 2] - ext[i])
+    mi1 = 0.5 * (ext[i + 3] - ext[i + 1])
+    t2 = t * t
+    t3 = t2 * t
+    val = ((2 * t3 - 3 * t2 + 1) * vi + (t3 - 2 * t2 + t) * mi
+           + (-2 * t3 + 3 * t2) * vi1 + (t3 - t2) * mi1)
+    return np.where(inside, val, 0.0)
 
 
 def filter_eval(filt, x, y):

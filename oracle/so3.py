@@ -1,0 +1,179 @@
+"""FP64 oracle for SO(3) extended correlation (Sec. 9; test infrastructure only).
+
+Spherical harmonics are the orthonormal complex Y_l^m with the Condon-Shortley
+phase (the associated Legendre functions come from scipy.special.lpmv, a
+library step); theta is the polar angle from +z, phi = atan2(y, x); voxel
+offsets d = (dx, dy, dz) with x = column, y = row, z = slice.
+
+Filter (Sec. 9 "Filter Decomposition"):
+    F(x) = sum_{l <= L} sum_{|a| <= l} f_l^a(|x|) Y_l^a(x^),
+f_l^a given as radial tables with the cubic Hermite interpolant of
+oracle.filters_so2.RadialTable; at x = 0 only l = 0 contributes.
+
+Rotations act by (T_R F)(x) = F(R^-1 x).  The matrix C^l(R) is defined by
+    T_R Y_l^a = sum_b C^l_ab(R) Y_l^b
+and computed here straight from that definition, by projecting Y_l^a(R^-1 x)
+onto Y_l^b with a quadrature that is exact for band-limited products.
+(Sec. 9 calls these the Wigner-D functions; its index roles are fixed by this
+definition.)
+
+Extended correlation (Eq. Def-ECorr) with a rotation R at every voxel, or
+swept over a list of rotations:
+    S(p, R) = sum_{d in B} V(p + d) conj(F(R^-1 d)),   B = [-Rb, Rb]^3,
+periodic mod the volume shape.  The component form of Sec. 9,
+    S(p, R) = sum_{l,a,b} conj(C^l_ab(R)) G_l^{ab}(p),
+    G_l^{ab} = V (*) (f_l^a Y_l^b),
+is provided separately (component_correlation, sweep_from_components) and is
+pinned against the brute force.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import lpmv, roots_legendre
+
+from .filters_so2 import hermite_eval
+
+
+def sph_harm(l: int, m: int, theta, phi):
+    """Orthonormal Y_l^m(theta, phi) with the Condon-Shortley phase."""
+    theta = np.asarray(theta, np.float64)
+    phi = np.asarray(phi, np.float64)
+    am = abs(m)
+    norm = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - am) / math.factorial(l + am))
+    y = norm * lpmv(am, l, np.cos(theta)) * np.exp(1j * am * phi)
+    if m < 0:
+        y = ((-1) ** am) * np.conj(y)
+    return y
+
+
+def to_spherical(x, y, z):
+    r = np.sqrt(x * x + y * y + z * z)
+    theta = np.arccos(np.clip(np.where(r > 0, z / np.where(r > 0, r, 1.0), 1.0), -1.0, 1.0))
+    phi = np.arctan2(y, x)
+    return r, theta, phi
+
+
+class SHFilter:
+    """F(x) = sum_{l,a} f_l^a(|x|) Y_l^a(x^); tables[l] has shape (2l+1, n_r),
+    row a + l holding f_l^a(i dr).  The radial profiles of degree l have
+    parity (-1)^l (f_l^a ~ r^l near the origin for a smooth F)."""
+
+    def __init__(self, tables, dr: float):
+        self.tables = [np.asarray(t, np.complex128) for t in tables]
+        self.L = len(self.tables) - 1
+        self.dr = float(dr)
+
+    def radial(self, l, a, r):
+        return hermite_eval(self.tables[l][a + l], self.dr, l, r)
+
+
+def filter_eval(F: SHFilter, x, y, z):
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    z = np.asarray(z, np.float64)
+    r, th, ph = to_spherical(x, y, z)
+    out = np.zeros(np.broadcast(x, y, z).shape, np.complex128)
+    at0 = r == 0
+    for l in range(F.L + 1):
+        for a in range(-l, l + 1):
+            term = F.radial(l, a, r) * sph_harm(l, a, th, ph)
+            if l > 0:
+                term = np.where(at0, 0.0, term)
+            out += term
+    return out
+
+
+def rotated_filter_eval(F: SHFilter, Rm, dx, dy, dz):
+    """(T_R F)(d) = F(R^-1 d) with the rotated coordinate formed explicitly."""
+    Ri = np.asarray(Rm, np.float64).T
+    x = Ri[0, 0] * dx + Ri[0, 1] * dy + Ri[0, 2] * dz
+    y = Ri[1, 0] * dx + Ri[1, 1] * dy + Ri[1, 2] * dz
+    z = Ri[2, 0] * dx + Ri[2, 1] * dy + Ri[2, 2] * dz
+    return filter_eval(F, x, y, z)
+
+
+# ------------------------------------------------------------- rotations ---
+
+def quat_to_matrix(q):
+    """Unit quaternion (w, x, y, z) -> rotation matrix."""
+    w, x, y, z = (float(v) for v in q)
+    n = math.sqrt(w * w + x * x + y * y + z * z)
+    w, x, y, z = w / n, x / n, y / n, z / n
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def _sphere_quadrature(L):
+    n_t = L + 2
+    n_p = 2 * L + 3
+    xs, ws = roots_legendre(n_t)
+    th = np.arccos(xs)
+    ph = 2 * math.pi * np.arange(n_p) / n_p
+    T, Pp = np.meshgrid(th, ph, indexing="ij")
+    W = np.repeat(ws[:, None], n_p, axis=1) * (2 * math.pi / n_p)
+    return T.ravel(), Pp.ravel(), W.ravel()
+
+
+def wigner_by_projection(l: int, Rm):
+    """C^l(R) from its definition: C_ab = < Y_l^a(R^-1 x), Y_l^b(x) > on S^2,
+    by a Gauss-Legendre x uniform quadrature exact for degree <= 2l."""
+    th, ph, wq = _sphere_quadrature(2 * l + 1)
+    x, y, z = np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)
+    Ri = np.asarray(Rm, np.float64).T
+    xr = Ri[0, 0] * x + Ri[0, 1] * y + Ri[0, 2] * z
+    yr = Ri[1, 0] * x + Ri[1, 1] * y + Ri[1, 2] * z
+    zr = Ri[2, 0] * x + Ri[2, 1] * y + Ri[2, 2] * z
+    _, thr, phr = to_spherical(xr, yr, zr)
+    C = np.zeros((2 * l + 1, 2 * l + 1), np.complex128)
+    Yb = np.stack([sph_harm(l, b, th, ph) for b in range(-l, l + 1)])        # (2l+1, nq)
+    for a in range(-l, l + 1):
+        Ya_rot = sph_harm(l, a, thr, phr)
+        C[a + l] = (Ya_rot[None, :] * np.conj(Yb) * wq[None, :]).sum(axis=1)
+    return C
+
+
+# ------------------------------------------------------------- operators ---
+
+def box_offsets3(radius: int):
+    dz, dy, dx = np.mgrid[-radius:radius + 1, -radius:radius + 1, -radius:radius + 1]
+    return dx.ravel(), dy.ravel(), dz.ravel()
+
+
+def corr_so3_at(V, F: SHFilter, radius: int, rotations, voxels):
+    """S(p, R) for every p in `voxels` (rows (z, y, x)) and every rotation
+    matrix in `rotations`; returns (n_vox, n_rot) complex."""
+    V = np.asarray(V, np.float64)
+    nz, ny, nx = V.shape
+    dx, dy, dz = box_offsets3(radius)
+    vox = np.asarray(voxels, np.int64).reshape(-1, 3)
+    patches = V[(vox[:, 0:1] + dz[None]) % nz, (vox[:, 1:2] + dy[None]) % ny, (vox[:, 2:3] + dx[None]) % nx]
+    bank = np.stack([rotated_filter_eval(F, Rm, dx.astype(np.float64), dy.astype(np.float64),
+                                         dz.astype(np.float64)) for Rm in rotations])
+    return patches @ np.conj(bank).T
+
+
+def component_correlation(V, F: SHFilter, l: int, a: int, b: int, radius: int):
+    """G_l^{ab}(p) = sum_d V(p + d) conj(f_l^a(|d|) Y_l^b(d^)) over the box."""
+    V = np.asarray(V, np.float64)
+    dx, dy, dz = box_offsets3(radius)
+    r, th, ph = to_spherical(dx.astype(np.float64), dy.astype(np.float64), dz.astype(np.float64))
+    phi_c = F.radial(l, a, r) * sph_harm(l, b, th, ph)
+    if l > 0:
+        phi_c = np.where(r == 0, 0.0, phi_c)
+    out = np.zeros(V.shape, np.complex128)
+    for n in range(dx.size):
+        if phi_c[n] != 0:
+            out += np.roll(V, (-dz[n], -dy[n], -dx[n]), axis=(0, 1, 2)) * np.conj(phi_c[n])
+    return out
+
+
+def sweep_from_components(G, Cs):
+    """S = sum_{l,a,b} conj(C^l_ab) G_l^{ab}; G[l] has shape (2l+1, 2l+1, ...),
+    Cs[l] the (2l+1, 2l+1) matrix of one rotation."""
+    S = 0
+    for l in range(len(G)):
+        S = S + np.tensordot(np.conj(Cs[l]), G[l], axes=([0, 1], [0, 1]))
+    return S

@@ -284,3 +284,136 @@ def scale_smoothing_problem(seed: int | None = None, size: int | tuple = 4096,
     c = mellin_gaussian_coeffs(n_h, log_period)
     return dict(img=img, s=s, c=c, log_period=log_period, r_min=r_min, r_max=r_max,
                 centre_tap=centre_tap)
+
+
+# ------------------------------------------------------------- workload 5 ---
+
+def so3_filter_tables(seed: int, L: int = 6, r_max: float = 8.0, dr: float = 0.125):
+    """Random smooth radial profiles f_l^a(r), l <= L, |a| <= l, sampled at
+    i*dr <= r_max: three Gaussian bumps (centres U[1.5, 6], width 0.8) with
+    complex N(0,1) weights, times r^l exp(-r^2/32) near the origin and a
+    raised-cosine taper to zero on [r_max - 1.5, r_max].  Real-function
+    symmetry f_l^{-a} = (-1)^a conj(f_l^a).  Returns a list over l of
+    (2l+1, n_r) complex arrays."""
+    rng = np.random.default_rng(seed)
+    n_r = int(round(r_max / dr)) + 1
+    r = np.arange(n_r) * dr
+    taper = np.where(r <= r_max - 1.5, 1.0,
+                     0.5 * (1 + np.cos(np.pi * np.clip(r - (r_max - 1.5), 0, 1.5) / 1.5)))
+    taper[r >= r_max] = 0.0
+    tables = []
+    for l in range(L + 1):
+        t = np.zeros((2 * l + 1, n_r), np.complex128)
+        g = (r ** l) * np.exp(-r * r / 32.0) * taper
+        g /= max(np.max(np.abs(g)), 1e-12)
+        for a in range(0, l + 1):
+            prof = np.zeros(n_r, np.complex128)
+            for _ in range(3):
+                mu = rng.uniform(1.5, 6.0)
+                wgt = rng.standard_normal() + 1j * rng.standard_normal()
+                prof += wgt * np.exp(-(r - mu) ** 2 / (2 * 0.8 ** 2))
+            prof *= g
+            if a == 0:
+                prof = prof.real.astype(np.complex128)
+            t[a + l] = prof
+            t[-a + l] = ((-1) ** a) * np.conj(prof)
+        tables.append(t)
+    return tables
+
+
+def haar_quaternion(rng):
+    q = rng.standard_normal(4)
+    return q / np.linalg.norm(q)
+
+
+def _quat_matrix(q):
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def _quat_from_zyz(alpha, beta, gamma):
+    # q = q_z(alpha) q_y(beta) q_z(gamma)
+    def qz(t):
+        return np.array([math.cos(t / 2), 0.0, 0.0, math.sin(t / 2)])
+
+    def qy(t):
+        return np.array([math.cos(t / 2), 0.0, math.sin(t / 2), 0.0])
+
+    def mul(p, q):
+        w1, x1, y1, z1 = p
+        w2, x2, y2, z2 = q
+        return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                         w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+    return mul(mul(qz(alpha), qy(beta)), qz(gamma))
+
+
+def so3_rotation_grid(n_dirs: int = 192, n_psi: int = 24):
+    """n_dirs * n_psi rotations R = R_z(phi) R_y(theta) R_z(psi): (theta, phi)
+    on a Fibonacci sphere of n_dirs near-uniform directions (the base of a
+    Hopf-fibration grid), psi = 2 pi j / n_psi.  Quaternions (w, x, y, z),
+    shape (n_dirs * n_psi, 4)."""
+    golden = math.pi * (3.0 - math.sqrt(5.0))
+    out = []
+    for i in range(n_dirs):
+        zc = 1.0 - (2.0 * i + 1.0) / n_dirs
+        theta = math.acos(zc)
+        phi = (golden * i) % (2 * math.pi)
+        for j in range(n_psi):
+            out.append(_quat_from_zyz(phi, theta, 2 * math.pi * j / n_psi))
+    return np.array(out)
+
+
+def _sample_template(tables, dr, radius, Rm=None):
+    """Samples sum_{l,a} f_l^a(|x|) Y_l^a(x^) at x = R^-1 d on the (2R+1)^3 box
+    (data generation for planting; linear interpolation of the radial
+    profiles, scipy's associated Legendre functions)."""
+    from scipy.special import lpmv
+    dz, dy, dx = np.mgrid[-radius:radius + 1, -radius:radius + 1, -radius:radius + 1].astype(np.float64)
+    pts = np.stack([dx.ravel(), dy.ravel(), dz.ravel()])
+    if Rm is not None:
+        pts = Rm.T @ pts
+    x, y, z = pts
+    r = np.sqrt(x * x + y * y + z * z)
+    ct = np.where(r > 0, z / np.where(r > 0, r, 1), 1.0)
+    ph = np.arctan2(y, x)
+    n_r = tables[0].shape[1]
+    rr = np.arange(n_r) * dr
+    out = np.zeros(r.shape, np.complex128)
+    for l, t in enumerate(tables):
+        for a in range(-l, l + 1):
+            am = abs(a)
+            norm = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - am) / math.factorial(l + am))
+            yv = norm * lpmv(am, l, np.clip(ct, -1, 1)) * np.exp(1j * am * ph)
+            if a < 0:
+                yv = ((-1) ** am) * np.conj(yv)
+            prof = np.interp(r, rr, t[a + l].real, right=0.0) + 1j * np.interp(r, rr, t[a + l].imag, right=0.0)
+            out += prof * yv
+    return out.real.reshape(2 * radius + 1, 2 * radius + 1, 2 * radius + 1)
+
+
+def so3_match_problem(seed: int | None = None, size: int = 128, n_plant: int = 16, L: int = 6,
+                      radius: int = 8, dr: float = 0.125, noise_sigma: float = 0.1):
+    """3D matching input: Gaussian noise sigma 0.1 plus n_plant copies of the
+    band-limited template (profiles from so3_filter_tables) rotated by
+    Haar-random rotations at centres >= 2R+1 apart (torus distance).
+    Volume float32 (z, y, x)."""
+    rng = np.random.default_rng(seed_for(5) if seed is None else seed)
+    tables = so3_filter_tables(int(rng.integers(0, 2**31 - 1)), L, float(radius), dr)
+    V = rng.normal(0.0, noise_sigma, (size, size, size))
+    centres = []
+    while len(centres) < n_plant:
+        c = rng.integers(0, size, 3)
+        if all(np.linalg.norm(np.minimum(np.abs(c - p), size - np.abs(c - p))) >= 2 * radius + 1 for p in centres):
+            centres.append(c)
+    quats = np.array([haar_quaternion(rng) for _ in range(n_plant)])
+    d = np.arange(-radius, radius + 1)
+    for c, q in zip(centres, quats):
+        block = _sample_template(tables, dr, radius, _quat_matrix(q))
+        zi = (c[0] + d) % size
+        yi = (c[1] + d) % size
+        xi = (c[2] + d) % size
+        V[np.ix_(zi, yi, xi)] += block
+    return dict(V=V.astype(np.float32), tables=tables, dr=dr, radius=radius, L=L,
+                centres=np.array(centres), quats=quats)
