@@ -219,6 +219,43 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
                           float* out, void* stream);
 
 /*
+ * SO(3) extended correlation (Sec. 9).  Volume V: nz x ny x nx float32
+ * (z slowest; x = column, y = row, z = slice), periodic.  Filter
+ *   F(x) = sum_{l<=L} sum_{|a|<=l} f_l^a(|x|) Y_l^a(x^)
+ * with orthonormal Condon-Shortley spherical harmonics (theta from +z,
+ * phi = atan2(y, x)); `tables` (HOST) holds f_l^a(i dr), i < n_r, as complex
+ * doubles, row l^2 + l + a; cubic Hermite in r with parity (-1)^l and closed
+ * support as for ext_filter_so2 tables; at x = 0 only l = 0 contributes; the
+ * box is [-R, R]^3.  A real filter (f_l^{-a} = (-1)^a conj f_l^a) is assumed.
+ * Rotations act as (T_R F)(x) = F(R^-1 x); C^l_ab(R) is the coefficient of
+ * Y_l^b in T_R Y_l^a; the score of rotation R at voxel p is
+ *   S(p, R) = sum_d V(p+d) conj((T_R F)(d)) = sum_{l,a,b} conj(C^l_ab(R)) G_l^{ab}(p),
+ * G_l^{ab} = V (*) (f_l^a Y_l^b).  Rotations are unit quaternions (w, x, y, z),
+ * HOST memory.  L <= 6.
+ *
+ * Real channel layout of G (ext_so3_channels(L) channels, one plane each):
+ * for l = 0..L: the self pair (a, b) = (0, 0) (one channel, Re G), then the
+ * pairs (0, b > 0) and (a > 0, any b) in order of a then b (two channels,
+ * Re G and Im G); (-a, -b) is implied by G_l^{-a,-b} = (-1)^{a+b} conj G_l^{ab}.
+ */
+int ext_so3_channels(int L);
+/* C^l(R) for every rotation, l = 0..L, row-major (2l+1)^2 blocks per l, as
+ * complex doubles into HOST out (n_rot * sum_l (2l+1)^2 complex values). */
+ext_status ext_so3_wigner(ext_plan plan, const double* quats, int n_rot, int L, double* out);
+/* The component correlations in the real channel layout (Sec. 9 "Standard
+ * Correlation"): G = ext_so3_channels(L) planes of nz*ny*nx floats. */
+ext_status ext_corr_so3_components(ext_plan plan, const float* V, int nz, int ny, int nx, const double* tables, int L,
+                                   int n_r, double dr, int R, float* G, void* stream);
+/* Sweep over n_rot rotations (Sec. 9 "Linear Combination" at every rotation):
+ * per voxel max_R S and the first maximising rotation index. */
+ext_status ext_sweep_so3(ext_plan plan, const float* G, int64_t n_vox, int L, const double* quats, int n_rot,
+                         float* max_out, int32_t* argmax, int precision, void* stream);
+/* Components then sweep. */
+ext_status ext_corr_so3(ext_plan plan, const float* V, int nz, int ny, int nx, const double* tables, int L, int n_r,
+                        double dr, int R, const double* quats, int n_rot, float* max_out, int32_t* argmax,
+                        int precision, void* stream);
+
+/*
  * Allocation-free variant of the FP32 angular sweep (the paper has no
  * counterpart: this entry point exists for callers that cannot let a library
  * allocate device memory -- an application whose device memory is all owned

@@ -177,3 +177,34 @@ def sweep_from_components(G, Cs):
     for l in range(len(G)):
         S = S + np.tensordot(np.conj(Cs[l]), G[l], axes=([0, 1], [0, 1]))
     return S
+
+
+def component_correlation_at(V, F: SHFilter, l: int, a: int, b: int, radius: int, voxels):
+    """G_l^{ab} at the given voxels (rows (z, y, x)), summed directly."""
+    V = np.asarray(V, np.float64)
+    nz, ny, nx = V.shape
+    dx, dy, dz = box_offsets3(radius)
+    r, th, ph = to_spherical(dx.astype(np.float64), dy.astype(np.float64), dz.astype(np.float64))
+    phi_c = F.radial(l, a, r) * sph_harm(l, b, th, ph)
+    if l > 0:
+        phi_c = np.where(r == 0, 0.0, phi_c)
+    vox = np.asarray(voxels, np.int64).reshape(-1, 3)
+    patches = V[(vox[:, 0:1] + dz[None]) % nz, (vox[:, 1:2] + dy[None]) % ny, (vox[:, 2:3] + dx[None]) % nx]
+    return patches @ np.conj(phi_c)
+
+
+def channel_layout(L: int):
+    """Unique (l, a, b) up to the pairing (a, b) <-> (-a, -b): per l the self
+    pair (0, 0), then (0, b > 0), then (a > 0, b = -l..l); with their first
+    real channel (self: 1 channel, others: Re and Im)."""
+    out, ch = [], 0
+    for l in range(L + 1):
+        out.append((l, 0, 0, ch))
+        ch += 1
+        for a in range(0, l + 1):
+            for b in range(-l, l + 1):
+                if a == 0 and b <= 0:
+                    continue
+                out.append((l, a, b, ch))
+                ch += 2
+    return out, ch

@@ -6,5 +6,6 @@ in include/extconv.h); this package is its thin Python binding.
 from ._binding import (  # noqa: F401
     EXT_FILTER_ANALYTIC_GAUSSPOW, EXT_FILTER_SAMPLED, EXT_FILTER_TABLE, EXT_PREC_BF16X3, EXT_PREC_FP32,
     EXPORTED, ExtError, FilterSO2, LIB_PATH, Plan, ext_conv_so2, ext_corr_so2, ext_corr_so2_components,
-    ext_filter_so2_decompose, ext_sweep_so2, ext_sweep_so2_noalloc, ext_conv_scale, ext_batch_corr_so2, lib,
+    ext_filter_so2_decompose, ext_sweep_so2, ext_sweep_so2_noalloc, ext_conv_scale, ext_batch_corr_so2,
+    ext_so3_channels, ext_so3_wigner, ext_corr_so3_components, ext_sweep_so3, ext_corr_so3, so3_pack_tables, lib,
 )

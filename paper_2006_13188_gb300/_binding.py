@@ -35,6 +35,7 @@ EXPORTED = (
     "ext_plan_profile", "ext_plan_profile_read", "ext_plan_sync",
     "ext_filter_so2_decompose", "ext_conv_so2", "ext_corr_so2", "ext_corr_so2_components",
     "ext_sweep_so2", "ext_sweep_so2_noalloc", "ext_conv_scale", "ext_batch_corr_so2",
+    "ext_so3_channels", "ext_so3_wigner", "ext_corr_so3_components", "ext_sweep_so3", "ext_corr_so3",
 )
 
 
@@ -91,10 +92,15 @@ def lib():
         L.ext_sweep_so2.argtypes = [vp, vp, i64, i32, i32, vp, vp, i32, vp]
         L.ext_sweep_so2_noalloc.argtypes = [vp, i64, i32, i32, vp, vp, vp]
         L.ext_batch_corr_so2.argtypes = [vp, ctypes.POINTER(ext_image_desc), i32, i32, vp]
+        L.ext_so3_channels.argtypes = [i32]
+        L.ext_so3_wigner.argtypes = [vp, vp, i32, i32, vp]
+        L.ext_corr_so3_components.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, vp]
+        L.ext_sweep_so3.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp, i32, vp]
+        L.ext_corr_so3.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, i32, vp, vp, i32, vp]
         dbl = ctypes.c_double
         L.ext_conv_scale.argtypes = [vp, vp, i32, i32, i32, vp, i32, dbl, dbl, dbl, dbl, vp, i32, vp, vp]
         for name in EXPORTED:
-            if name not in ("ext_status_string", "ext_last_error"):
+            if name not in ("ext_status_string", "ext_last_error", "ext_so3_channels"):
                 getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -260,3 +266,43 @@ def ext_batch_corr_so2(plan: Plan, items, precision=EXT_PREC_BF16X3, stream=None
         arr[i] = ext_image_desc(_ptr(H), int(h), int(w), ctypes.pointer(F.struct), int(J), _ptr(mx), _ptr(am))
         keep.append(F)
     _check(lib().ext_batch_corr_so2(plan.handle, arr, len(items), int(precision), _stream(stream)))
+
+
+def so3_pack_tables(tables):
+    """List over l of (2l+1, n_r) complex arrays -> contiguous (L+1)^2 x n_r complex128."""
+    return np.ascontiguousarray(np.concatenate([np.asarray(t, np.complex128) for t in tables], axis=0))
+
+
+def ext_so3_channels(L):
+    return int(lib().ext_so3_channels(int(L)))
+
+
+def ext_so3_wigner(plan: Plan, quats, L):
+    q = np.ascontiguousarray(np.asarray(quats, np.float64).reshape(-1, 4))
+    per = (L + 1) * (2 * L + 1) * (2 * L + 3) // 3
+    out = np.zeros((q.shape[0], per), np.complex128)
+    _check(lib().ext_so3_wigner(plan.handle, _ptr(q), q.shape[0], int(L), _ptr(out.view(np.float64))))
+    return out
+
+
+def ext_corr_so3_components(plan: Plan, V, nz, ny, nx, tables, dr, R, G, stream=None):
+    t = so3_pack_tables(tables)
+    L = len(tables) - 1
+    _check(lib().ext_corr_so3_components(plan.handle, _ptr(V), int(nz), int(ny), int(nx), _ptr(t.view(np.float64)),
+                                         L, t.shape[1], float(dr), int(R), _ptr(G), _stream(stream)))
+
+
+def ext_sweep_so3(plan: Plan, G, n_vox, L, quats, max_out, argmax, precision=EXT_PREC_BF16X3, stream=None):
+    q = np.ascontiguousarray(np.asarray(quats, np.float64).reshape(-1, 4))
+    _check(lib().ext_sweep_so3(plan.handle, _ptr(G), int(n_vox), int(L), _ptr(q), q.shape[0], _ptr(max_out),
+                               _ptr(argmax), int(precision), _stream(stream)))
+
+
+def ext_corr_so3(plan: Plan, V, nz, ny, nx, tables, dr, R, quats, max_out, argmax, precision=EXT_PREC_BF16X3,
+                 stream=None):
+    t = so3_pack_tables(tables)
+    L = len(tables) - 1
+    q = np.ascontiguousarray(np.asarray(quats, np.float64).reshape(-1, 4))
+    _check(lib().ext_corr_so3(plan.handle, _ptr(V), int(nz), int(ny), int(nx), _ptr(t.view(np.float64)), L, t.shape[1],
+                              float(dr), int(R), _ptr(q), q.shape[0], _ptr(max_out), _ptr(argmax), int(precision),
+                              _stream(stream)))

@@ -666,6 +666,61 @@ k_cols_conv(const float2* __restrict__ A, int w, int K, const float2* __restrict
   });
 }
 
+// In-place complex column pass over `planes` planes of N x w (plane stride N w):
+// the y-pass of a 3D transform (planes = z slices) or the z-pass (planes = 1,
+// w = ny * nx).
+template <int N, bool INV>
+__global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, LineCfg<N>::COL_MINB)
+k_cols_c2c(float2* X, int w, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::COL_THREADS;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, T);
+  float2* P = X + (size_t)blockIdx.y * N * w;
+  const int u0 = blockIdx.x * C::CW;
+  float2 v[STAGE_G];
+  for_elems_staged<C::CW * N, T, STAGE_G>(
+      [&](int i, int e) {
+        const int u = u0 + e % C::CW;
+        v[i] = (u < w) ? P[(size_t)(e / C::CW) * w + u] : make_float2(0.f, 0.f);
+      },
+      [&](int i, int e) { sm[e % C::CW + sidx(e / C::CW) * C::CW] = v[i]; });
+  __syncthreads();
+  col_fft<N, INV>(sm, twl);
+  for_elems<C::CW * N, T>([&](int i, int e) {
+    const int u = u0 + e % C::CW;
+    if (u < w) P[(size_t)(e / C::CW) * w + u] = sm[e % C::CW + sidx(e / C::CW) * C::CW];
+  });
+}
+
+// Inverse row pass of component planes (each `rows` rows of N) writing the
+// real and imaginary parts of component k0 + blockIdx.y into the channel
+// planes chan[k].x and chan[k].y of G (chan[k].y < 0: imaginary part dropped).
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
+k_rows_inv_channels(const float2* __restrict__ Z, int rows, int k0, const int2* __restrict__ chan,
+                    float* __restrict__ G, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::RL * C::LS>(sm, tw, C::ROW_THREADS);
+  const int y0 = blockIdx.x * C::RL;
+  const size_t P = (size_t)rows * N;
+  rows_load_complex<N>(sm, Z + (size_t)blockIdx.y * P, y0, rows);
+  __syncthreads();
+  row_fft<N, true>(sm, twl);
+  const int2 ch = chan[k0 + blockIdx.y];
+  float* re = G + (size_t)ch.x * P;
+  float* im = G + (size_t)(ch.y < 0 ? 0 : ch.y) * P;
+  for_elems<C::RL * N, C::ROW_THREADS>([&](int i, int e) {
+    const int y = y0 + e / N;
+    if (y >= rows) return;
+    const float2 v = sm[(e / N) * C::LS + sidx(e % N)];
+    const size_t idx = (size_t)y * N + e % N;
+    re[idx] = v.x;
+    if (ch.y >= 0) im[idx] = v.y;
+  });
+}
+
 // ------------------------------------------------- pipelined hot passes ---
 // Persistent versions of the two passes that run once per filter component
 // in the correlation path.  Each block owns one SM (grid = min(items, SMs))
@@ -685,7 +740,10 @@ struct PipeCfg {
 
 // Inverse column pass of H^ conj(F^_k) for k = k0 + (item / ntiles); output
 // Z[item / ntiles] (pitch w).  Half spectrum pitch wh = w/2 + 1.
-template <int N>
+// HERM: Hh is the half spectrum (pitch w/2+1) of a real signal and the other
+// half is rebuilt by Hermitian symmetry; otherwise Hh is the full spectrum
+// (pitch w).
+template <int N, bool HERM>
 __global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, 1)
 k_cols_inv_corr_pipe(const float2* __restrict__ Hh, int w, const float2* __restrict__ S, int k0, int nk,
                      float2* __restrict__ Z, const float2* __restrict__ tw) {
@@ -711,7 +769,8 @@ k_cols_inv_corr_pipe(const float2* __restrict__ Hh, int w, const float2* __restr
       const int v = e / CW, u = u0 + e % CW;
       const float2* src = Hh;
       bool valid = u < w;
-      if (u < wh) src = Hh + (size_t)v * wh + u;
+      if (!HERM) src = valid ? Hh + (size_t)v * w + u : Hh;
+      else if (u < wh) src = Hh + (size_t)v * wh + u;
       else if (valid) src = Hh + (size_t)((N - v) % N) * wh + (w - u);
       cp_async8(HS + e, src, valid);
     }
@@ -730,7 +789,7 @@ k_cols_inv_corr_pipe(const float2* __restrict__ Hh, int w, const float2* __restr
     auto load = [&](int c, int v) -> float2 {
       const int e = v * CW + c;
       float2 hv = HS[e];
-      if (u0 + c >= wh) hv.y = -hv.y;
+      if (HERM && u0 + c >= wh) hv.y = -hv.y;
       return c_mul(hv, SS[e]);
     };
     auto store = [&](int c, int v, float2 val) {
@@ -824,6 +883,11 @@ struct FftOps {
                             const float2* tw, cudaStream_t st);
   static void cols_conv(const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
                         cudaStream_t st);
+  static void cols_c2c(float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st);
+  static void rows_inv_channels(const float2* Z, int rows, int k0, int nk, const int2* chan, float* G,
+                                const float2* tw, cudaStream_t st);
+  static bool cols_inv_full_pipe(const float2* H, int w, const float2* S, int k0, int nk, float2* Z,
+                                 const float2* tw, int sms, cudaStream_t st);
   // pipelined persistent variants (false if the shared-memory plan does not fit)
   static bool cols_inv_corr_pipe(const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
                                  const float2* tw, int sms, cudaStream_t st);
@@ -928,18 +992,63 @@ void FftOps<N>::cols_conv(const float2* A, int w, int K, const float2* S, float2
 }
 
 template <int N>
+static inline int pipe_grid(int items, int sms, int smem, int threads) {
+  int bps = (227 * 1024) / (smem + 1024);
+  const int by_threads = 2048 / threads;
+  if (bps > by_threads) bps = by_threads;
+  if (bps > 16) bps = 16;
+  if (bps < 1) bps = 1;
+  const long long cap = (long long)sms * bps;
+  return items < cap ? items : (int)cap;
+}
+
+template <int N>
 bool FftOps<N>::cols_inv_corr_pipe(const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
                                    const float2* tw, int sms, cudaStream_t st) {
   if constexpr (!PipeCfg<N>::COL_OK) {
     return false;
   } else {
-    static const bool once = (ext_set_smem(k_cols_inv_corr_pipe<N>, PipeCfg<N>::COL_SMEM), true);
+    static const bool once = (ext_set_smem(k_cols_inv_corr_pipe<N, true>, PipeCfg<N>::COL_SMEM), true);
     (void)once;
     const int items = ((w + C::CW - 1) / C::CW) * nk;
-    const int grid = items < sms ? items : sms;
-    k_cols_inv_corr_pipe<N><<<grid, C::COL_THREADS, PipeCfg<N>::COL_SMEM, st>>>(Hh, w, S, k0, nk, Z, tw);
+    const int grid = pipe_grid<N>(items, sms, PipeCfg<N>::COL_SMEM, C::COL_THREADS);
+    k_cols_inv_corr_pipe<N, true><<<grid, C::COL_THREADS, PipeCfg<N>::COL_SMEM, st>>>(Hh, w, S, k0, nk, Z, tw);
     return true;
   }
+}
+
+template <int N>
+bool FftOps<N>::cols_inv_full_pipe(const float2* H, int w, const float2* S, int k0, int nk, float2* Z,
+                                   const float2* tw, int sms, cudaStream_t st) {
+  if constexpr (!PipeCfg<N>::COL_OK) {
+    return false;
+  } else {
+    static const bool once = (ext_set_smem(k_cols_inv_corr_pipe<N, false>, PipeCfg<N>::COL_SMEM), true);
+    (void)once;
+    const int items = ((w + C::CW - 1) / C::CW) * nk;
+    const int grid = pipe_grid<N>(items, sms, PipeCfg<N>::COL_SMEM, C::COL_THREADS);
+    k_cols_inv_corr_pipe<N, false><<<grid, C::COL_THREADS, PipeCfg<N>::COL_SMEM, st>>>(H, w, S, k0, nk, Z, tw);
+    return true;
+  }
+}
+
+template <int N>
+void FftOps<N>::cols_c2c(float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_cols_c2c<N, false>, C::COL_SMEM),
+                            ext_set_smem(k_cols_c2c<N, true>, C::COL_SMEM), true);
+  (void)once;
+  dim3 grid((w + C::CW - 1) / C::CW, planes);
+  if (inv) k_cols_c2c<N, true><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(X, w, tw);
+  else k_cols_c2c<N, false><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(X, w, tw);
+}
+
+template <int N>
+void FftOps<N>::rows_inv_channels(const float2* Z, int rows, int k0, int nk, const int2* chan, float* G,
+                                  const float2* tw, cudaStream_t st) {
+  static const bool once = (ext_set_smem(k_rows_inv_channels<N>, C::ROW_SMEM), true);
+  (void)once;
+  dim3 grid((rows + C::RL - 1) / C::RL, nk);
+  k_rows_inv_channels<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(Z, rows, k0, chan, G, tw);
 }
 
 template <int N>
@@ -951,7 +1060,7 @@ bool FftOps<N>::rows_inv_components_pipe(const float2* Z, int h, int k0, int nk,
     static const bool once = (ext_set_smem(k_rows_inv_components_pipe<N>, PipeCfg<N>::ROW_SMEM), true);
     (void)once;
     const int items = ((h + C::RL - 1) / C::RL) * nk;
-    const int grid = items < sms ? items : sms;
+    const int grid = pipe_grid<N>(items, sms, PipeCfg<N>::ROW_SMEM, C::ROW_THREADS);
     k_rows_inv_components_pipe<N><<<grid, C::ROW_THREADS, PipeCfg<N>::ROW_SMEM, st>>>(Z, h, k0, nk, G, tw);
     return true;
   }

@@ -111,3 +111,23 @@ void fft_rows_fwd_scale(int w, const float* H, const float* s, int h, int k0, in
   switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
 }
 #undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::cols_c2c(X, w, planes, inv, tw, st); return;
+void fft_cols_c2c(int h, float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st) {
+  switch (h) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::rows_inv_channels(Z, rows, k0, nk, chan, G, tw, st); return;
+void fft_rows_inv_channels(int w, const float2* Z, int rows, int k0, int nk, const int2* chan, float* G,
+                           const float2* tw, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: return FftOps<N>::cols_inv_full_pipe(H, w, S, k0, nk, Z, tw, sms, st);
+bool fft_cols_inv_full_pipe(int h, const float2* H, int w, const float2* S, int k0, int nk, float2* Z,
+                            const float2* tw, int sms, cudaStream_t st) {
+  switch (h) { EXT_FFT_SIZES(EXT_C1) default: return false; }
+}
+#undef EXT_C1

@@ -43,6 +43,13 @@ bool fft_cols_inv_corr_pipe(int h, const float2* Hh, int w, const float2* S, int
                             const float2* tw, int sms, cudaStream_t st);
 bool fft_rows_inv_components_pipe(int w, const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
                                   int sms, cudaStream_t st);
+// 3D building blocks: in-place complex column pass over planes; inverse row
+// pass into real channel planes; full-spectrum product column pass.
+void fft_cols_c2c(int h, float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st);
+void fft_rows_inv_channels(int w, const float2* Z, int rows, int k0, int nk, const int2* chan, float* G,
+                           const float2* tw, cudaStream_t st);
+bool fft_cols_inv_full_pipe(int h, const float2* H, int w, const float2* S, int k0, int nk, float2* Z,
+                            const float2* tw, int sms, cudaStream_t st);
 void fft_cols_conv(int h, const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
                    cudaStream_t st);
 
@@ -66,3 +73,16 @@ bool sweep_fp32(const float* G, long long P, int K, int J, const float* B, int c
 // tcgen05 split-BF16 sweep (sweep_tc.cu); err receives EXT_ERR_TIMEOUT if a bounded wait expires.
 bool sweep_bf16x3(const float* G, long long P, int K, int J, const float* B, int cp, float* maxv, int32_t* argmax,
                   int* err, int sms, cudaStream_t st);
+
+// ----- SO(3) (so3.cu, sweep_so3.cu)
+void launch_so3_component_grid(const int4* comp, int k0, int nk, const double2* tables, int n_r, double dr, int L,
+                               int R, int nz, int ny, int nx, float2* grid, cudaStream_t st);
+void launch_so3_wigner(const double* quats, int n, int L, double2* C, const int4* chans, int nchan, int cpad,
+                       float* Brow, cudaStream_t st);
+void launch_real_to_complex(const float* V, long long n, float2* X, int sms, cudaStream_t st);
+void sweep_so3_fp32(const float* G, long long P, int C, const float* B, int cpad, int J, float* maxv,
+                    int32_t* argmax, cudaStream_t st);
+size_t so3_btc_bytes(int J, int cpad);
+void so3_build_btc(const float* B, int cpad, int J, unsigned char* Bt, cudaStream_t st);
+void sweep_so3_tc(const float* G, long long P, int C, int cpad, const unsigned char* Bt, int J, float* maxv,
+                  int32_t* argmax, int* err, int sms, cudaStream_t st);

@@ -1,0 +1,256 @@
+// Sweep over a grid of rotations for SO(3) (Sec. 9 "Linear Combination" at
+// every grid rotation), with per-voxel max and first argmax:
+//   S(p, j) = sum_c A(p, c) B[j][c],
+// A = the real channels of the component correlations G_l^{ab} (planar, one
+// plane per channel), B[j] = the steering row of rotation j (C^l_00 for a
+// self channel, 2 Re C^l_ab and 2 Im C^l_ab for a pair of channels).
+#include "internal.h"
+#include "tc_common.cuh"
+
+#include <cfloat>
+
+// ------------------------------------------------------------ plain FP32 ---
+// Block: 64 voxels x 64 rotations per tile, 256 threads with 4 x 4 outputs
+// each, channels streamed through shared memory 32 at a time; the running
+// per-voxel max over rotation tiles stays in shared memory.
+namespace {
+constexpr int FM = 64, FN = 64, FK = 32;
+}
+
+__global__ void __launch_bounds__(256) k_sweep_so3_fp32(const float* __restrict__ G, long long P, int C,
+                                                        const float* __restrict__ B, int cpad, int J,
+                                                        float* __restrict__ maxv, int32_t* __restrict__ argmax) {
+  __shared__ float As[FK][FM];
+  __shared__ float Bs[FK][FN + 1];
+  __shared__ float best_v[FM][16];
+  __shared__ int best_j[FM][16];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;   // tx: rotation group, ty: voxel group
+  const long long p0 = (long long)blockIdx.x * FM;
+  float vbest[4];
+  int jbest[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { vbest[i] = -FLT_MAX; jbest[i] = 0; }
+  for (int n0 = 0; n0 < J; n0 += FN) {
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+    for (int c0 = 0; c0 < C; c0 += FK) {
+      for (int e = tid; e < FK * FM; e += 256) {
+        const int c = e / FM, m = e % FM;
+        const long long p = p0 + m;
+        As[c][m] = (c0 + c < C && p < P) ? __ldg(G + (size_t)(c0 + c) * P + p) : 0.f;
+      }
+      for (int e = tid; e < FK * FN; e += 256) {
+        const int n = e / FK, c = e % FK;
+        Bs[c][n] = (n0 + n < J && c0 + c < cpad) ? __ldg(B + (size_t)(n0 + n) * cpad + c0 + c) : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int c = 0; c < FK; ++c) {
+        float a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[c][ty * 4 + i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) b[k] = Bs[c][tx * 4 + k];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(a[i], b[k], acc[i][k]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int j = n0 + tx * 4 + k;
+        if (j < J && acc[i][k] > vbest[i]) { vbest[i] = acc[i][k]; jbest[i] = j; }
+      }
+  }
+  // reduce over the 16 rotation groups; ties keep the smallest j
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { best_v[ty * 4 + i][tx] = vbest[i]; best_j[ty * 4 + i][tx] = jbest[i]; }
+  __syncthreads();
+  if (tid < FM) {
+    float v = -FLT_MAX;
+    int jj = 0;
+    bool first = true;
+    for (int g = 0; g < 16; ++g) {
+      const float x = best_v[tid][g];
+      const int xj = best_j[tid][g];
+      if (first || x > v || (x == v && xj < jj)) { v = x; jj = xj; first = false; }
+    }
+    const long long p = p0 + tid;
+    if (p < P) { maxv[p] = v; argmax[p] = jj; }
+  }
+}
+
+void sweep_so3_fp32(const float* G, long long P, int C, const float* B, int cpad, int J, float* maxv,
+                    int32_t* argmax, cudaStream_t st) {
+  const long long blocks = (P + FM - 1) / FM;
+  k_sweep_so3_fp32<<<(unsigned)blocks, 256, 0, st>>>(G, P, C, B, cpad, J, maxv, argmax);
+}
+
+// ------------------------------------------------------------ tcgen05 -----
+// M = 128 voxels per tile (one TMEM lane per voxel), N = 256 rotations per
+// N tile (256 TMEM columns), K streamed in chunks of 32 channels; each chunk
+// is split [A_hi | A_hi | A_lo] x [B_hi ; B_lo ; B_hi] (96 bf16) and issued as
+// six K = 16 MMAs.  B' is prepared once per rotation set in the exact
+// shared-memory image of each (N tile, K chunk) block.
+namespace {
+constexpr int TM = 128, TN = 256, TKC = 32, TKT = 3 * TKC, TKB = TKT / 8;
+constexpr int T_SBO = TKB * 128;                   // 1536 B between 8-row groups
+constexpr int TA_BYTES = (TM / 8) * T_SBO;          // 24 KB
+constexpr int TB_BYTES = (TN / 8) * T_SBO;          // 48 KB
+}
+
+// B' blocks: [n_tile][k_chunk][TB_BYTES] in core-matrix order from B[j][cpad]
+__global__ void k_so3_btc(const float* __restrict__ B, int cpad, int J, int ntn, int nkc, unsigned char* __restrict__ Bt) {
+  const long long total = (long long)ntn * nkc * TN * TKB;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    const int kb = (int)(q % TKB);
+    const int n = (int)((q / TKB) % TN);
+    const int kc = (int)((q / ((long long)TKB * TN)) % nkc);
+    const int nt = (int)(q / ((long long)TKB * TN * nkc));
+    const int part = kb / (TKC / 8);   // 0 hi, 1 lo, 2 hi
+    const int c0 = kc * TKC + (kb % (TKC / 8)) * 8;
+    const int j = nt * TN + n;
+    uint32_t w[4];
+    for (int t = 0; t < 4; ++t) {
+      float e[2];
+      for (int u = 0; u < 2; ++u) {
+        const int c = c0 + 2 * t + u;
+        const float b = (j < J && c < cpad) ? B[(size_t)j * cpad + c] : 0.f;
+        const float hi = tc::bf16_round(b);
+        e[u] = part == 1 ? b - hi : hi;
+      }
+      w[t] = tc::pack_bf16(e[0], e[1]);
+    }
+    unsigned char* blk = Bt + ((size_t)nt * nkc + kc) * TB_BYTES;
+    *reinterpret_cast<uint4*>(blk + (n / 8) * T_SBO + kb * 128 + (n % 8) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_sweep_so3_tc(const float* __restrict__ G, long long P, int C, int nkc,
+                                                      const unsigned char* __restrict__ Bt, int ntn, int J,
+                                                      float* __restrict__ maxv, int32_t* __restrict__ argmax,
+                                                      int* __restrict__ err, unsigned long long limit_ns) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* As = smem;
+  unsigned char* Bs = smem + TA_BYTES;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    abort_flag = 0;
+    tc::mbar_init(tc::smem_u32(&mbar), 1);
+  }
+  if (warp == 0) tc::tmem_alloc<TN>(tc::smem_u32(&tmem_slot));
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_slot, mbar_addr = tc::smem_u32(&mbar);
+  const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
+  constexpr uint32_t IDESC = tc::make_idesc(TM, TN);
+  uint32_t phase = 0;
+  const long long ntm = (P + TM - 1) / TM;
+  for (long long mt = blockIdx.x; mt < ntm && !abort_flag; mt += gridDim.x) {
+    const long long p = mt * TM + tid;
+    const bool live = p < P;
+    float best = -FLT_MAX;
+    int bj = 0;
+    for (int nt = 0; nt < ntn && !abort_flag; ++nt) {
+      for (int kc = 0; kc < nkc; ++kc) {
+        // B' block: straight copy of its shared-memory image
+        const uint4* src = reinterpret_cast<const uint4*>(Bt + ((size_t)nt * nkc + kc) * TB_BYTES);
+        uint4* dst = reinterpret_cast<uint4*>(Bs);
+        for (int q = tid; q < TB_BYTES / 16; q += 128) dst[q] = __ldg(src + q);
+        // A' row of this voxel for channels kc*32 .. kc*32+31
+        float a[TKC];
+#pragma unroll
+        for (int c = 0; c < TKC; ++c) {
+          const int ch = kc * TKC + c;
+          a[c] = (live && ch < C) ? __ldg(G + (size_t)ch * P + p) : 0.f;
+        }
+        unsigned char* arow = As + (tid / 8) * T_SBO + (tid % 8) * 16;
+#pragma unroll
+        for (int kb = 0; kb < TKC / 8; ++kb) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const float x0 = a[kb * 8 + 2 * t], x1 = a[kb * 8 + 2 * t + 1];
+            hi[t] = tc::pack_bf16(x0, x1);
+            lo[t] = tc::pack_bf16(x0 - tc::bf16_round(x0), x1 - tc::bf16_round(x1));
+          }
+          const uint4 vh = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(arow + kb * 128) = vh;
+          *reinterpret_cast<uint4*>(arow + (kb + TKC / 8) * 128) = vh;
+          *reinterpret_cast<uint4*>(arow + (kb + 2 * TKC / 8) * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after();
+#pragma unroll
+          for (int s = 0; s < TKT / 16; ++s)
+            tc::mma_bf16(tmem, tc::make_desc(a_base + s * 256, 128, T_SBO), tc::make_desc(b_base + s * 256, 128, T_SBO),
+                         IDESC, (kc > 0 || s > 0) ? 1u : 0u);
+          tc::mma_commit(mbar_addr);
+        }
+        if (!tc::mbar_wait_bounded(mbar_addr, phase, limit_ns, err, EXT_ERR_TIMEOUT)) abort_flag = 1;
+        phase ^= 1u;
+        __syncthreads();
+        if (abort_flag) break;
+      }
+      if (abort_flag) break;
+      tc::fence_after();
+#pragma unroll 1
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int j = nt * TN + c0 + i;
+          if (j < J && (v[i] > best || (j == 0))) { best = v[i]; bj = j; }
+        }
+      }
+      tc::fence_before();
+      __syncthreads();
+    }
+    if (live && !abort_flag) { maxv[p] = best; argmax[p] = bj; }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc<TN>(tmem);
+  }
+}
+
+size_t so3_btc_bytes(int J, int cpad) {
+  const int ntn = (J + TN - 1) / TN, nkc = (cpad + TKC - 1) / TKC;
+  return (size_t)ntn * nkc * TB_BYTES;
+}
+
+void so3_build_btc(const float* B, int cpad, int J, unsigned char* Bt, cudaStream_t st) {
+  const int ntn = (J + TN - 1) / TN, nkc = (cpad + TKC - 1) / TKC;
+  k_so3_btc<<<1024, 256, 0, st>>>(B, cpad, J, ntn, nkc, Bt);
+}
+
+void sweep_so3_tc(const float* G, long long P, int C, int cpad, const unsigned char* Bt, int J, float* maxv,
+                  int32_t* argmax, int* err, int sms, cudaStream_t st) {
+  const int ntn = (J + TN - 1) / TN, nkc = (cpad + TKC - 1) / TKC;
+  // two blocks per SM share the 512 TMEM columns: request shared memory accordingly
+  constexpr int request = 100 * 1024;
+  static const bool once =
+      (cudaFuncSetAttribute(k_sweep_so3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, request), true);
+  (void)once;
+  const long long ntm = (P + TM - 1) / TM;
+  long long grid = (long long)sms * 2;
+  if (grid > ntm) grid = ntm;
+  k_sweep_so3_tc<<<(unsigned)grid, 128, request, st>>>(G, P, C, nkc, Bt, ntn, J, maxv, argmax, err,
+                                                       2000000000ull);
+}

@@ -1,0 +1,197 @@
+"""GPU parity of the SO(3) path (Sec. 9) against the FP64 oracle: rotation
+matrices (FP64 on the device, 1e-12), component correlations and the FP32
+sweep (1e-5 of the scale), the split-BF16 tensor-core sweep (1e-4 of the
+scale, >= 99% argmax agreement), and planted-template detection on the
+128^3, L = 6, 4608-rotation workload."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth
+from oracle.so3 import (SHFilter, channel_layout, component_correlation_at, corr_so3_at, quat_to_matrix,
+                        wigner_by_projection)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ec():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2006_13188_gb300 as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def plan(ec):
+    p = ec.Plan(0)
+    yield p
+    p.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_wigner_matrices_match_definition(ec, plan):
+    rng = np.random.default_rng(0)
+    q = [synth.haar_quaternion(rng) for _ in range(12)]
+    q += [np.array([1.0, 0, 0, 0]), np.array([math.cos(0.35), 0, 0, math.sin(0.35)]),
+          np.array([0.0, 1.0, 0, 0]), np.array([0.0, 0, 1.0, 0])]           # identity, z-rotation, beta = pi
+    L = 6
+    got = ec.ext_so3_wigner(plan, np.array(q), L)
+    for n, qq in enumerate(q):
+        R = quat_to_matrix(qq)
+        off = 0
+        for l in range(L + 1):
+            d = 2 * l + 1
+            ref = wigner_by_projection(l, R)
+            np.testing.assert_allclose(got[n, off:off + d * d].reshape(d, d), ref, atol=1e-12)
+            off += d * d
+
+
+def _full_G(channels, L, lay):
+    """Per-l (2l+1, 2l+1, n) complex components from the real channels."""
+    n = channels.shape[1]
+    G = [np.zeros((2 * l + 1, 2 * l + 1, n), np.complex128) for l in range(L + 1)]
+    for (l, a, b, ch) in lay:
+        if a == 0 and b == 0:
+            g = channels[ch].astype(np.float64) + 0j
+        else:
+            g = channels[ch].astype(np.float64) + 1j * channels[ch + 1].astype(np.float64)
+            G[l][-a + l, -b + l] = (-1) ** (a + b) * np.conj(g)
+        G[l][a + l, b + l] = g
+    return G
+
+
+def _scores_from_channels(channels, L, rots):
+    lay, _ = channel_layout(L)
+    G = _full_G(channels, L, lay)
+    S = np.zeros((channels.shape[1], len(rots)))
+    for j, R in enumerate(rots):
+        s = 0
+        for l in range(L + 1):
+            C = wigner_by_projection(l, R)
+            s = s + np.tensordot(np.conj(C), G[l], axes=([0, 1], [0, 1]))
+        S[:, j] = s.real
+    return S
+
+
+def test_components_match_oracle(ec, plan):
+    prob = synth.so3_match_problem(seed=3, size=32, n_plant=2, L=3, radius=4, dr=0.25)
+    V = prob["V"]
+    L = 3
+    nch = ec.ext_so3_channels(L)
+    G = torch.empty((nch, 32, 32, 32), dtype=torch.float32, device="cuda")
+    ec.ext_corr_so3_components(plan, dev(V), 32, 32, 32, prob["tables"], prob["dr"], prob["radius"], G)
+    plan.sync()
+    Gn = G.cpu().numpy().reshape(nch, -1)
+    F = SHFilter(prob["tables"], prob["dr"])
+    rng = np.random.default_rng(1)
+    vox = np.vstack([prob["centres"], rng.integers(0, 32, (40, 3))])
+    flat = (vox[:, 0] * 32 + vox[:, 1]) * 32 + vox[:, 2]
+    lay, _ = channel_layout(L)
+    scale = max(np.abs(Gn).max(), 1e-30)
+    for (l, a, b, ch) in lay:
+        ref = component_correlation_at(V, F, l, a, b, prob["radius"], vox)
+        assert np.max(np.abs(Gn[ch, flat] - ref.real)) <= 1e-5 * scale, (l, a, b)
+        if not (a == 0 and b == 0):
+            assert np.max(np.abs(Gn[ch + 1, flat] - ref.imag)) <= 1e-5 * scale, (l, a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_sweep_matches_oracle_linear_combination(ec, plan, prec):
+    L, n, nrot = 6, 600, 300
+    rng = np.random.default_rng(7)
+    nch = ec.ext_so3_channels(L)
+    channels = rng.standard_normal((nch, n)).astype(np.float32)
+    quats = np.array([synth.haar_quaternion(rng) for _ in range(nrot)])
+    precision = ec.EXT_PREC_FP32 if prec == "fp32" else ec.EXT_PREC_BF16X3
+    mx = torch.empty(n, dtype=torch.float32, device="cuda")
+    am = torch.empty(n, dtype=torch.int32, device="cuda")
+    ec.ext_sweep_so3(plan, dev(channels), n, L, quats, mx, am, precision)
+    plan.sync()
+    S = _scores_from_channels(channels, L, [quat_to_matrix(q) for q in quats])
+    scale = np.abs(S).max()
+    err = np.max(np.abs(mx.cpu().numpy() - S.max(axis=1))) / scale
+    srt = np.sort(S, axis=1)
+    gap = (srt[:, -1] - srt[:, -2]) / scale
+    ok = am.cpu().numpy() == S.argmax(axis=1)
+    tol, window = (1e-5, 1e-6) if prec == "fp32" else (1e-4, 2e-4)
+    print(f"so3 sweep {prec}: score error {err:.2e}, argmax agreement {ok.mean():.4f}")
+    assert err <= tol
+    assert np.all(ok[gap > window])
+    assert ok.mean() >= 0.99
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_end_to_end_small_volume(ec, plan, prec):
+    prob = synth.so3_match_problem(seed=5, size=32, n_plant=1, L=3, radius=4, dr=0.25)
+    rng = np.random.default_rng(2)
+    quats = np.vstack([prob["quats"], [synth.haar_quaternion(rng) for _ in range(63)]])
+    precision = ec.EXT_PREC_FP32 if prec == "fp32" else ec.EXT_PREC_BF16X3
+    mx = torch.empty((32, 32, 32), dtype=torch.float32, device="cuda")
+    am = torch.empty((32, 32, 32), dtype=torch.int32, device="cuda")
+    ec.ext_corr_so3(plan, dev(prob["V"]), 32, 32, 32, prob["tables"], prob["dr"], prob["radius"], quats, mx, am,
+                    precision)
+    plan.sync()
+    F = SHFilter(prob["tables"], prob["dr"])
+    c = prob["centres"][0]
+    vox = np.vstack([c, (c + np.array([1, 0, -1])) % 32, rng.integers(0, 32, (24, 3))])
+    S = corr_so3_at(prob["V"], F, prob["radius"], [quat_to_matrix(q) for q in quats], vox).real
+    got = mx.cpu().numpy()[vox[:, 0], vox[:, 1], vox[:, 2]]
+    arg = am.cpu().numpy()[vox[:, 0], vox[:, 1], vox[:, 2]]
+    scale = np.abs(S).max()
+    tol = 1e-5 if prec == "fp32" else 1e-4
+    assert np.max(np.abs(got - S.max(axis=1))) <= tol * scale
+    assert arg[0] == 0   # the planted rotation is the first of the set
+
+
+def _angle(q1, q2):
+    d = abs(float(np.dot(q1 / np.linalg.norm(q1), q2 / np.linalg.norm(q2))))
+    return 2 * math.degrees(math.acos(min(1.0, d)))
+
+
+def test_full_size_planted_detection(ec, plan):
+    """128^3, L = 6 (455 channels), 4608-rotation grid, split-BF16 sweep:
+    every planted template peaks at its centre with a grid rotation close to
+    its true rotation; sampled component channels match the oracle."""
+    prob = synth.so3_match_problem()
+    n = prob["V"].shape[0]
+    grid = synth.so3_rotation_grid()
+    mx = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    am = torch.empty((n, n, n), dtype=torch.int32, device="cuda")
+    ec.ext_corr_so3(plan, dev(prob["V"]), n, n, n, prob["tables"], prob["dr"], prob["radius"], grid, mx, am,
+                    ec.EXT_PREC_BF16X3)
+    plan.sync()
+    mxn, amn = mx.cpu().numpy(), am.cpu().numpy()
+    nearest = [min(_angle(q, g) for g in grid) for q in prob["quats"]]
+    for c, q, near in zip(prob["centres"], prob["quats"], nearest):
+        win = np.roll(mxn, (1 - c[0], 1 - c[1], 1 - c[2]), axis=(0, 1, 2))[:3, :3, :3]
+        assert np.unravel_index(np.argmax(win), win.shape) == (1, 1, 1)
+        found = grid[amn[c[0], c[1], c[2]]]
+        assert _angle(found, q) <= near + 15.0, (_angle(found, q), near)
+    # component channels at a few voxels
+    L = prob["L"]
+    nch = ec.ext_so3_channels(L)
+    G = torch.empty((nch, n, n, n), dtype=torch.float32, device="cuda")
+    ec.ext_corr_so3_components(plan, dev(prob["V"]), n, n, n, prob["tables"], prob["dr"], prob["radius"], G)
+    plan.sync()
+    F = SHFilter(prob["tables"], prob["dr"])
+    vox = np.vstack([prob["centres"][:3], [[0, 0, 0], [127, 64, 3]]])
+    flat = (vox[:, 0] * n + vox[:, 1]) * n + vox[:, 2]
+    Gn = G.reshape(nch, -1)[:, torch.from_numpy(flat).cuda()].cpu().numpy()
+    lay, _ = channel_layout(L)
+    ref = np.zeros((nch, len(vox)))
+    for (l, a, b, ch) in lay:
+        g = component_correlation_at(prob["V"], F, l, a, b, prob["radius"], vox)
+        ref[ch] = g.real
+        if not (a == 0 and b == 0):
+            ref[ch + 1] = g.imag
+    err = np.linalg.norm(Gn - ref) / np.linalg.norm(ref)
+    print(f"so3 128^3 sampled channels rel-L2 {err:.2e}")
+    assert err < 1e-5

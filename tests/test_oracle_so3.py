@@ -146,3 +146,30 @@ def test_planted_template_peaks_at_its_rotation():
     S = corr_so3_at(prob["V"], F, prob["radius"], Rs, vox).real
     assert np.argmax(S[0]) == 0
     assert S[0, 0] > S[1:, 0].max()
+
+
+def test_component_correlation_at_voxels_matches_full():
+    from oracle.so3 import component_correlation_at
+    rng = np.random.default_rng(9)
+    V = rng.standard_normal((6, 7, 8))
+    F = small_filter(seed=2, L=2, radius=2.0)
+    vox = np.array([[0, 0, 0], [5, 6, 7], [2, 3, 4]])
+    for (l, a, b) in [(0, 0, 0), (1, 1, -1), (2, -2, 1)]:
+        full = component_correlation(V, F, l, a, b, 2)
+        np.testing.assert_allclose(component_correlation_at(V, F, l, a, b, 2, vox),
+                                   full[vox[:, 0], vox[:, 1], vox[:, 2]], atol=1e-12)
+
+
+def test_channel_layout_counts_and_pairing():
+    """(2l+1)^2 real channels per degree; G_l^{-a,-b} = (-1)^{a+b} conj G_l^{ab}
+    for a real filter and signal (the pairing the layout relies on)."""
+    from oracle.so3 import channel_layout
+    lay, n = channel_layout(6)
+    assert n == 455 and len(lay) == 231
+    rng = np.random.default_rng(10)
+    V = rng.standard_normal((6, 6, 6))
+    F = small_filter(seed=3, L=2, radius=2.0)
+    for (l, a, b) in [(1, 1, 0), (2, 1, -2), (2, 0, 1)]:
+        g = component_correlation(V, F, l, a, b, 2)
+        gm = component_correlation(V, F, l, -a, -b, 2)
+        np.testing.assert_allclose(gm, (-1) ** (a + b) * np.conj(g), atol=1e-12)
