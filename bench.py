@@ -47,10 +47,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",
                     help="plan, warm-up and timed steps only (for ncu launch lists)")
-    ap.add_argument("--workload", default="so2", choices=["so2", "scale", "batched"],
+    ap.add_argument("--workload", default="so2", choices=["so2", "scale", "batched", "so3"],
                     help="so2: the pattern-matching sweep (default, the headline metric); "
                          "scale: scale-adaptive smoothing of a 4096x4096x3 image; "
-                         "batched: 512 uneven images in one captured graph")
+                         "batched: 512 uneven images in one captured graph; "
+                         "so3: 128^3 volume, L=6, 4608-rotation sweep")
     ap.add_argument("--n-images", type=int, default=512)
     return ap.parse_args()
 
@@ -370,6 +371,97 @@ def bench_batched(args, world, rank, local):
     return 0
 
 
+# --------------------------------------------------------- SO(3) workload ---
+SO3_WORKLOAD = ("SO(3) matching: 128^3 f32 volume (noise 0.1 + 16 planted 17^3 templates), SH degree L=6 "
+                "(455 real channels, 231 complex correlations), 4608-rotation grid sweep with max/argmax")
+
+
+def measured_bf16():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured"
+    except Exception:
+        return 1900.0, 1700.0, "fallback"
+
+
+def bench_so3(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_2006_13188_gb300 as ec
+    import synth
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    prob = synth.so3_match_problem(seed=synth.seed_for(5) + rank)
+    grid = synth.so3_rotation_grid()
+    n = prob["V"].shape[0]
+    P = n ** 3
+    L = prob["L"]
+    plan = ec.Plan(local)
+    V = torch.from_numpy(prob["V"]).to(device)
+    mx = torch.empty((n, n, n), dtype=torch.float32, device=device)
+    am = torch.empty((n, n, n), dtype=torch.int32, device=device)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    def call(prec):
+        ec.ext_corr_so3(plan, V, n, n, n, prob["tables"], prob["dr"], prob["radius"], grid, mx, am, prec)
+    t0 = time.perf_counter()
+    call(ec.EXT_PREC_BF16X3)
+    plan.sync()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+
+    def timed(prec, steps):
+        for _ in range(args.warmup):
+            call(prec)
+        plan.sync()
+        barrier(world)
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call(prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return reduce_max(tot, world, device)
+    with ClockSampler(local) as clk:
+        total = timed(ec.EXT_PREC_BF16X3, args.steps)
+    plain = timed(ec.EXT_PREC_FP32, max(1, min(args.steps, 3)))
+    plain_steps = max(1, min(args.steps, 3))
+    value = world * args.steps * P / (total * 1e-3) / 1e6
+    plan.profile_read()
+    plan.profile(True)
+    call(ec.EXT_PREC_BF16X3)
+    plan.sync()
+    prof = {k: v for k, v in plan.profile_read().items() if v[1] > 0}
+    plan.profile(False)
+    nch = ec.ext_so3_channels(L)
+    sweep_ms = prof.get("so3_sweep_bf16x3", (None, 1))[0]
+    flops = 3 * 2.0 * P * nch * len(grid)          # three split-BF16 products
+    burst, sustained, kind = measured_bf16()
+    ach = flops / (sweep_ms * 1e-3) / 1e12 if sweep_ms else None
+    if rank == 0:
+        print(json.dumps({
+            "metric": "SO(3) extended-correlation Mvox/s (4608-rotation sweep)", "value": value, "unit": "Mvox/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 FFT + bf16x3 sweep (f32 accumulate)", "data": "synthetic",
+            "config": {"workload": SO3_WORKLOAD, "plan_ms": plan_ms, "l2": "256 MB written between steps"},
+            "clocks": clk.summary(),
+            "plain_fp32": {"value": world * plain_steps * P / (plain * 1e-3) / 1e6, "unit": "Mvox/s",
+                           "ms_per_step": plain / plain_steps},
+            "roofline": {"kernel": "so3_sweep_bf16x3", "bound": "tensor", "achieved": ach, "peak": sustained,
+                         "peak_kind": kind + " bf16 sustained", "unit": "TFLOP/s",
+                         "frac": ach / sustained if ach else None, "traffic": None,
+                         "algorithmic_flops": flops,
+                         "kernels": {k: {"ms_per_call": v[0], "launches": v[1]} for k, v in prof.items()}}}))
+    plan.close()
+    return 0
+
+
 # ------------------------------------------------------------------ main ---
 def main():
     args = parse_args()
@@ -378,6 +470,8 @@ def main():
         return bench_scale(args, world, rank, local)
     if args.workload == "batched" and args.impl == "ours":
         return bench_batched(args, world, rank, local)
+    if args.workload == "so3" and args.impl == "ours":
+        return bench_so3(args, world, rank, local)
 
     import numpy as np
     import synth
