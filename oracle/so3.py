@@ -208,3 +208,83 @@ def channel_layout(L: int):
                 out.append((l, a, b, ch))
                 ch += 2
     return out, ch
+
+
+# ------------------------------------------------------- proposal support ---
+
+def full_components(chan, L: int):
+    """Per-l (2l+1, 2l+1) complex G_l^{ab} at one voxel from its real channels."""
+    lay, _ = channel_layout(L)
+    G = [np.zeros((2 * l + 1, 2 * l + 1), np.complex128) for l in range(L + 1)]
+    for (l, a, b, ch) in lay:
+        if a == 0 and b == 0:
+            G[l][l, l] = chan[ch]
+        else:
+            g = chan[ch] + 1j * chan[ch + 1]
+            G[l][a + l, b + l] = g
+            G[l][-a + l, -b + l] = (-1) ** (a + b) * np.conj(g)
+    return G
+
+
+def score_from_channels(chan, L: int, Rm):
+    """S(p, R) = sum_{l,a,b} conj(C^l_ab(R)) G_l^{ab}(p) (real for a real filter)."""
+    G = full_components(np.asarray(chan, np.float64), L)
+    return float(sum(np.sum(np.conj(wigner_by_projection(l, Rm)) * G[l]) for l in range(L + 1)).real)
+
+
+def upper_bound(chan, L: int):
+    """sum_l sqrt(2l+1) |G_l|_F >= |S(p, R)| for every R (Cauchy-Schwarz with
+    the unitary C^l, |C^l|_F = sqrt(2l+1))."""
+    G = full_components(np.asarray(chan, np.float64), L)
+    return float(sum(np.sqrt(2 * l + 1) * np.linalg.norm(G[l]) for l in range(L + 1)))
+
+
+def quat_mul(p, q):
+    w1, x1, y1, z1 = p
+    w2, x2, y2, z2 = q
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+
+
+def quat_exp(v):
+    """Unit quaternion of the rotation vector v (angle |v| about v/|v|)."""
+    v = np.asarray(v, np.float64)
+    t = np.linalg.norm(v)
+    if t == 0:
+        return np.array([1.0, 0.0, 0.0, 0.0])
+    return np.concatenate([[np.cos(t / 2)], np.sin(t / 2) * v / t])
+
+
+def refine(chan, L: int, q0, steps: int = 5, h: float = 1e-3, theta0: float = 0.25, tries: int = 6):
+    """Gradient ascent on the exact score over SO(3): the gradient in the body
+    frame by central differences along R exp(+-h e_i); each step moves by an
+    angle theta along it, halving theta until the score increases (at most
+    `tries` times, stopping if none does); an accepted step keeps theta.
+    Returns (quaternion, score)."""
+    q = np.asarray(q0, np.float64) / np.linalg.norm(q0)
+    s = score_from_channels(chan, L, quat_to_matrix(q))
+    theta = theta0
+    for _ in range(steps):
+        g = np.zeros(3)
+        for i in range(3):
+            e = np.zeros(3)
+            e[i] = h
+            sp = score_from_channels(chan, L, quat_to_matrix(quat_mul(q, quat_exp(e))))
+            sm = score_from_channels(chan, L, quat_to_matrix(quat_mul(q, quat_exp(-e))))
+            g[i] = (sp - sm) / (2 * h)
+        gn = np.linalg.norm(g)
+        if gn == 0:
+            break
+        u = g / gn
+        moved = False
+        t = theta
+        for _ in range(tries):
+            qn = quat_mul(q, quat_exp(t * u))
+            sn = score_from_channels(chan, L, quat_to_matrix(qn))
+            if sn > s:
+                q, s, theta, moved = qn / np.linalg.norm(qn), sn, t, True
+                break
+            t *= 0.5
+        if not moved:
+            break
+    return q, s
