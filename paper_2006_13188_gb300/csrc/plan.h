@@ -1,0 +1,220 @@
+// The plan object behind the C ABI and the helpers every operator uses:
+// workspace, per-kernel launch accounting, host/device staging of arguments
+// and the device status word.
+#pragma once
+#include <cstdio>
+#include <cstdlib>
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+inline ext_status fail(ext_status s, const std::string& msg) {
+  ext_set_error(msg.c_str());
+  return s;
+}
+
+#define EXT_CUDA(call)                                                                              \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      return fail(e_ == cudaErrorMemoryAllocation ? EXT_ERR_OOM : EXT_ERR_CUDA,                    \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+    }                                                                                               \
+  } while (0)
+
+#define EXT_TRY(expr)                  \
+  do {                                 \
+    ext_status s_ = (expr);            \
+    if (s_ != EXT_OK) return s_;       \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct SpecEntry {
+  uint64_t key = 0;
+  float2* S = nullptr;
+  size_t bytes = 0;
+  uint64_t stamp = 0;
+};
+
+uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+}  // namespace
+struct ProfStat {
+  double ms = 0.0;
+  int64_t launches = 0;
+};
+
+struct ProfPending {
+  std::string name;
+  cudaEvent_t a, b;
+};
+
+struct ext_plan_s {
+  int device = 0;
+  bool profiling = false;
+  std::map<std::string, ProfStat> prof;
+  std::vector<ProfPending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::map<int, float2*> twiddles;
+  std::map<std::string, DevBuf> ws;
+  std::vector<SpecEntry> specs;
+  std::map<uint64_t, float*> sweep_tables;
+  uint64_t clock = 0;
+  size_t max_specs = 4;
+  int sms = 0;           // multiprocessors of the device
+  int kchunk = 0;        // components per inverse launch (0 = by L2 budget)
+  bool pipelined = true; // persistent prefetching passes where they fit
+  int* dev_err = nullptr; // device-side status word (bounded waits)
+  // batched correlation: captured CUDA graph of the last batch and its key
+  cudaGraphExec_t batch_exec = nullptr;
+  uint64_t batch_key = 0;
+  std::vector<unsigned char> batch_host;   // packed filter data (host staging)
+  // SO(3): steering tables of the last rotation set
+  uint64_t so3_rot_key = 0;
+  int so3_rot_n = 0, so3_rot_L = -1;
+};
+
+namespace {
+
+cudaEvent_t take_event(ext_plan plan) {
+  if (!plan->event_pool.empty()) {
+    cudaEvent_t e = plan->event_pool.back();
+    plan->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Every kernel launch of the operators goes through here: it is counted per
+// kernel name and, when profiling is on, bracketed by events on its stream.
+template <typename F>
+void launch(ext_plan plan, const char* name, cudaStream_t st, F&& f) {
+  if (!plan->profiling) {
+    plan->prof[name].launches += 1;
+    f();
+    return;
+  }
+  ProfPending p;
+  p.name = name;
+  p.a = take_event(plan);
+  p.b = take_event(plan);
+  cudaEventRecord(p.a, st);
+  f();
+  cudaEventRecord(p.b, st);
+  plan->pending.push_back(p);
+}
+
+ext_status ensure(ext_plan plan, const char* name, size_t bytes, void** out) {
+  DevBuf& b = plan->ws[name];
+  if (b.bytes < bytes) {
+    if (b.p) EXT_CUDA(cudaFree(b.p));
+    b.p = nullptr;
+    b.bytes = 0;
+    EXT_CUDA(cudaMalloc(&b.p, bytes));
+    b.bytes = bytes;
+  }
+  *out = b.p;
+  return EXT_OK;
+}
+
+ext_status twiddle(ext_plan plan, int n, cudaStream_t st, const float2** out) {
+  auto it = plan->twiddles.find(n);
+  if (it == plan->twiddles.end()) {
+    float2* tw = nullptr;
+    EXT_CUDA(cudaMalloc(&tw, sizeof(float2) * n));
+    launch_twiddle(tw, n, st);
+    EXT_CUDA(cudaGetLastError());
+    it = plan->twiddles.emplace(n, tw).first;
+  }
+  *out = it->second;
+  return EXT_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct Staged {
+  const void* user = nullptr;
+  void* dev = nullptr;
+  size_t bytes = 0;
+  bool host = false;
+};
+
+ext_status stage_in(ext_plan plan, const char* name, const void* user, size_t bytes, cudaStream_t st,
+                    Staged* s) {
+  s->user = user;
+  s->bytes = bytes;
+  s->host = user && !is_device_ptr(user);
+  if (!s->host) {
+    s->dev = const_cast<void*>(user);
+    return EXT_OK;
+  }
+  EXT_TRY(ensure(plan, name, bytes, &s->dev));
+  EXT_CUDA(cudaMemcpyAsync(s->dev, user, bytes, cudaMemcpyHostToDevice, st));
+  return EXT_OK;
+}
+
+ext_status stage_out_alloc(ext_plan plan, const char* name, void* user, size_t bytes, Staged* s) {
+  s->user = user;
+  s->bytes = bytes;
+  s->host = user && !is_device_ptr(user);
+  if (!s->host) {
+    s->dev = user;
+    return EXT_OK;
+  }
+  return ensure(plan, name, bytes, &s->dev);
+}
+
+ext_status stage_out_finish(const Staged& s, cudaStream_t st) {
+  if (!s.host) return EXT_OK;
+  EXT_CUDA(cudaMemcpyAsync(const_cast<void*>(s.user), s.dev, s.bytes, cudaMemcpyDeviceToHost, st));
+  return EXT_OK;
+}
+
+// G_k = H (*) F_k for k = 0..K into G (device, (2K+1) planes).
+ext_status device_status(ext_plan plan) {
+  int e = 0;
+  EXT_CUDA(cudaMemcpy(&e, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    EXT_CUDA(cudaMemset(plan->dev_err, 0, sizeof(int)));
+    return fail(e, "a device-side wait timed out; results of the affected call are invalid");
+  }
+  return EXT_OK;
+}
+
+ext_status finish_host(ext_plan plan, bool any_host, cudaStream_t st) {
+  if (any_host) {
+    EXT_CUDA(cudaStreamSynchronize(st));
+    return device_status(plan);
+  }
+  return EXT_OK;
+}
+
+}  // namespace
