@@ -256,6 +256,105 @@ ext_status ext_corr_so3(ext_plan plan, const float* V, int nz, int ny, int nx, c
                         int precision, void* stream);
 
 /*
+ * Learned SO(3) proposal (Sec. 9 matching, with a network proposing the
+ * rotation instead of sweeping a grid everywhere).
+ *
+ * Score bounds.  For every rotation R, |S(p, R)| <= UB(p) = sum_l sqrt(2l+1)
+ * |G_l(p)|_F (Cauchy-Schwarz; C^l(R) is unitary with |C^l|_F^2 = 2l+1), and
+ * also <= sum_l |G_l(p)|_* (nuclear norm: Re tr(U^H G) <= |G|_* for every
+ * unitary U).  The proposal evaluates UB at every voxel; where UB >= B it
+ * bounds the nuclear norms from above without an SVD (two orthonormal
+ * directions from one block power step, the rest by sqrt(rank) times the
+ * Frobenius norm) and keeps the smaller bound per degree.  Voxels whose bound
+ * is below the detection threshold B cannot reach it and are not evaluated
+ * further.
+ *
+ * Proposal.  For the other voxels (the candidates) the network maps the
+ * unit-normalised channel vector x = G(p)/|G(p)| to a unit quaternion, which
+ * `refine` improves by gradient ascent on the exact score S(p, R) (5 steps;
+ * the gradient in the body frame, d/dxi_i S(R exp(xi e_i)), exactly from the
+ * rotation generators acting on C^l(R); a step moves by an angle t along it,
+ * t = 0.25 at first, halved up to 6 times until S increases, none: stop; an
+ * accepted step keeps t).  The refinement runs in FP32.
+ *
+ * Fallback.  Every candidate whose refined score is below B is swept over the
+ * rotation grid as in ext_sweep_so3; the higher of the two results is kept.
+ * So every voxel with max_R S(p, R) >= B on the grid ends with a score >= B.
+ *
+ * Quaternions are (w, x, y, z) with the rotation matrix of a unit quaternion;
+ * q and -q are the same rotation.
+ */
+typedef struct ext_mlp_s* ext_mlp;
+
+/* A network n_in -> hidden -> hidden -> 4 with ReLU; x = row / |row| on input,
+ * output o normalised to q = o / |o|; loss mean_i (1 - <q_i, q*_i>^2).  BF16
+ * weights and activations on the tensor cores, FP32 accumulation, FP32 master
+ * weights for Adam (Kingma & Ba: beta1 0.9, beta2 0.999, eps 1e-8).  hidden a
+ * multiple of 16 in [16, 1024]; 1 <= n_in <= 4096.  Weights start at zero:
+ * set them with ext_mlp_set_params.  The network runs on its plan's device
+ * and workspace: every call but ext_mlp_destroy needs the plan alive. */
+ext_status ext_mlp_create(ext_plan plan, int n_in, int hidden, ext_mlp* out);
+ext_status ext_mlp_destroy(ext_mlp net);
+/* Row-major FP32 W1 [hidden][n_in], b1 [hidden], W2 [hidden][hidden], b2
+ * [hidden], W3 [4][hidden], b3 [4]; host or device pointers.  Resets Adam. */
+ext_status ext_mlp_set_params(ext_mlp net, const float* W1, const float* b1, const float* W2, const float* b2,
+                              const float* W3, const float* b3);
+ext_status ext_mlp_get_params(ext_mlp net, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3);
+/* q [n][4] = the network's unit quaternion of each row of X [n][n_in]. */
+ext_status ext_mlp_forward(ext_mlp net, const float* X, int n, float* q, void* stream);
+/* Mean loss of rows X [n][n_in] against targets qt [n][4] into *loss (host or
+ * device float) and its gradients, concatenated in the parameter order and
+ * shapes of ext_mlp_set_params, into grads (host or device; NULL: none). */
+ext_status ext_mlp_grads(ext_mlp net, const float* X, const float* qt, int n, float* loss, float* grads,
+                         void* stream);
+/* `steps` Adam steps of learning rate lr on batches of `batch` rows of the
+ * training set X [n_train][n_in], targets qt [n_train][4]: step s uses rows
+ * rows[s*batch .. s*batch+batch-1] (int32, in [0, n_train)).  If Q (float
+ * [steps*batch][4] unit quaternions) is given, row i of step s is first
+ * rotated by Q[s*batch+i] as in ext_so3_augment (then n_in must equal
+ * ext_so3_channels(L)).  losses [steps] (host or device, or NULL) receives
+ * each step's mean loss.  All arrays host or device. */
+ext_status ext_mlp_train(ext_mlp net, const float* X, const float* qt, int n_train, int L, const int32_t* rows,
+                         const float* Q, int steps, int batch, float lr, float* losses, void* stream);
+
+/* UB(p) for every voxel of G (channel layout of ext_corr_so3_components). */
+ext_status ext_so3_upper_bound(ext_plan plan, const float* G, int64_t n_vox, int L, float* ub, void* stream);
+/* The refined bound of each row of X [n][ext_so3_channels(L)] (channel
+ * vectors): sum_l min(sqrt(2l+1) |G_l|_F, an upper bound of |G_l|_*) into
+ * out [n]; it is >= sum_l |G_l|_* >= max_R |S(R)|. */
+ext_status ext_so3_refined_bound(ext_plan plan, const float* X, int n, int L, float* out, void* stream);
+/* X [n][ext_so3_channels(L)] = the channel vectors G(:, vox[i]) (raw, not
+ * normalised); vox int32 in [0, n_vox). */
+ext_status ext_so3_gather(ext_plan plan, const float* G, int64_t n_vox, int L, const int32_t* vox, int n, float* X,
+                          void* stream);
+/* Rotation augmentation: the score function S'(R) = S(Q^-1 R) of row X[i]
+ * has the channels X_out[i] (G'_l = G_l C^l(Q)), and its maximiser is Q R*:
+ * q_out[i] = Q[i] q_in[i] (float quaternions [n][4]). */
+ext_status ext_so3_augment(ext_plan plan, const float* X, int n, int L, const float* Q, const float* q_in,
+                           float* X_out, float* q_out, void* stream);
+/* The refinement alone: from q0 [n][4] on the channel rows X [n][C], C =
+ * ext_so3_channels(L): refined unit quaternions q_out [n][4] and scores
+ * s_out [n]. */
+ext_status ext_so3_refine(ext_plan plan, const float* X, int n, int L, const float* q0, float* q_out, float* s_out,
+                          void* stream);
+/* The whole proposal on component channels G (n_vox voxels).  net may be NULL:
+ * then every candidate goes to the grid sweep.  Outputs per voxel: score
+ * (-infinity where UB < B), quat [n_vox][4] (the rotation found; identity
+ * where UB < B; may be NULL) and grid_idx (-2: not a candidate, -1: refined
+ * rotation kept, j >= 0: swept, j the grid argmax; may be NULL).  counts
+ * (host int64[3], may be NULL): voxels with UB >= B, candidates (refined
+ * bound >= B), swept candidates.  The call synchronises `stream` up to three
+ * times to size its launches. */
+ext_status ext_so3_propose(ext_plan plan, const float* G, int64_t n_vox, int L, ext_mlp net, const double* quats,
+                           int n_rot, float bound, float* score, float* quat, int32_t* grid_idx, int precision,
+                           int64_t* counts, void* stream);
+/* Components (ext_corr_so3_components) then ext_so3_propose. */
+ext_status ext_corr_so3_propose(ext_plan plan, const float* V, int nz, int ny, int nx, const double* tables, int L,
+                                int n_r, double dr, int R, ext_mlp net, const double* quats, int n_rot, float bound,
+                                float* score, float* quat, int32_t* grid_idx, int precision, int64_t* counts,
+                                void* stream);
+
+/*
  * Allocation-free variant of the FP32 angular sweep (the paper has no
  * counterpart: this entry point exists for callers that cannot let a library
  * allocate device memory -- an application whose device memory is all owned

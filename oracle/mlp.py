@@ -62,3 +62,19 @@ def init_params(rng, n_in, hidden=256):
         return rng.standard_normal((o, i)) * np.sqrt(2.0 / i)
     return dict(W1=he(hidden, n_in), b1=np.zeros(hidden), W2=he(hidden, hidden), b2=np.zeros(hidden),
                 W3=he(4, hidden) * 0.5, b3=np.zeros(4))
+
+
+def adam_step(p, g, state, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) of every parameter;
+    state holds the moments m, v and the step count t (start: {})."""
+    t = state.get("t", 0) + 1
+    state["t"] = t
+    out = {}
+    for k, w in p.items():
+        m = b1 * state.get("m_" + k, np.zeros_like(w)) + (1 - b1) * g[k]
+        v = b2 * state.get("v_" + k, np.zeros_like(w)) + (1 - b2) * g[k] ** 2
+        state["m_" + k], state["v_" + k] = m, v
+        mhat = m / (1 - b1 ** t)
+        vhat = v / (1 - b2 ** t)
+        out[k] = w - lr * mhat / (np.sqrt(vhat) + eps)
+    return out

@@ -239,6 +239,14 @@ def upper_bound(chan, L: int):
     return float(sum(np.sqrt(2 * l + 1) * np.linalg.norm(G[l]) for l in range(L + 1)))
 
 
+def nuclear_bound(chan, L: int):
+    """sum_l |G_l|_* (nuclear norm, by numpy's SVD) >= |S(p, R)| for every R:
+    Re tr(U^H G) <= |G|_* for every unitary U, C^l(R) among them.  Never
+    above upper_bound (|G|_* <= sqrt(rank) |G|_F)."""
+    G = full_components(np.asarray(chan, np.float64), L)
+    return float(sum(np.linalg.svd(G[l], compute_uv=False).sum() for l in range(L + 1)))
+
+
 def quat_mul(p, q):
     w1, x1, y1, z1 = p
     w2, x2, y2, z2 = q
@@ -255,23 +263,45 @@ def quat_exp(v):
     return np.concatenate([[np.cos(t / 2)], np.sin(t / 2) * v / t])
 
 
-def refine(chan, L: int, q0, steps: int = 5, h: float = 1e-3, theta0: float = 0.25, tries: int = 6):
-    """Gradient ascent on the exact score over SO(3): the gradient in the body
-    frame by central differences along R exp(+-h e_i); each step moves by an
-    angle theta along it, halving theta until the score increases (at most
-    `tries` times, stopping if none does); an accepted step keeps theta.
+def rotation_generators(l: int):
+    """A_i = d/dt C^l(exp(t e_i)) at t = 0 for i = x, y, z.  With
+    (T_R F)(x) = F(R^-1 x), d/dt Y(exp(-t e_i) x) = -(e_i x x).grad Y = -i L_i Y
+    (L = -i x x grad), so (A_i)_ab = -i <Y_l^b, L_i Y_l^a>, from the textbook
+    relations L_z Y_l^m = m Y_l^m, L_+- Y_l^m = sqrt(l(l+1) - m(m+-1)) Y_l^{m+-1},
+    L_x = (L_+ + L_-)/2, L_y = (L_+ - L_-)/(2i)."""
+    d = 2 * l + 1
+    Lp = np.zeros((d, d), np.complex128)       # <Y^b, L_+ Y^a> at [b, a]
+    for a in range(-l, l):
+        Lp[a + 1 + l, a + l] = math.sqrt(l * (l + 1) - a * (a + 1))
+    Lm = Lp.conj().T
+    Lz = np.diag(np.arange(-l, l + 1)).astype(np.complex128)
+    Lx, Ly = (Lp + Lm) / 2, (Lp - Lm) / 2j
+    return [(-1j * Li).T for Li in (Lx, Ly, Lz)]   # [a, b] = -i <Y^b, L_i Y^a>
+
+
+def score_gradient(chan, L: int, Rm):
+    """Body-frame gradient of the score: d/dxi_i S(R exp(xi e_i)) at 0 =
+    Re sum_l tr((A_i C^l(R))^H G_l), since C(R exp(xi)) = C(exp(xi)) C(R)."""
+    G = full_components(np.asarray(chan, np.float64), L)
+    g = np.zeros(3)
+    for l in range(L + 1):
+        C = wigner_by_projection(l, Rm)
+        for i, A in enumerate(rotation_generators(l)):
+            g[i] += float(np.sum(np.conj(A @ C) * G[l]).real)
+    return g
+
+
+def refine(chan, L: int, q0, steps: int = 5, theta0: float = 0.25, tries: int = 6):
+    """Gradient ascent on the exact score over SO(3), in the body frame: the
+    gradient g from the rotation generators (score_gradient); each step moves
+    q -> q exp(t g/|g|), t halved until the score increases (at most `tries`
+    times, stopping if none does); an accepted step keeps t for the next one.
     Returns (quaternion, score)."""
     q = np.asarray(q0, np.float64) / np.linalg.norm(q0)
     s = score_from_channels(chan, L, quat_to_matrix(q))
     theta = theta0
     for _ in range(steps):
-        g = np.zeros(3)
-        for i in range(3):
-            e = np.zeros(3)
-            e[i] = h
-            sp = score_from_channels(chan, L, quat_to_matrix(quat_mul(q, quat_exp(e))))
-            sm = score_from_channels(chan, L, quat_to_matrix(quat_mul(q, quat_exp(-e))))
-            g[i] = (sp - sm) / (2 * h)
+        g = score_gradient(chan, L, quat_to_matrix(q))
         gn = np.linalg.norm(g)
         if gn == 0:
             break

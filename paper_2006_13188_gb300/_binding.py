@@ -36,6 +36,9 @@ EXPORTED = (
     "ext_filter_so2_decompose", "ext_conv_so2", "ext_corr_so2", "ext_corr_so2_components",
     "ext_sweep_so2", "ext_sweep_so2_noalloc", "ext_conv_scale", "ext_batch_corr_so2",
     "ext_so3_channels", "ext_so3_wigner", "ext_corr_so3_components", "ext_sweep_so3", "ext_corr_so3",
+    "ext_mlp_create", "ext_mlp_destroy", "ext_mlp_set_params", "ext_mlp_get_params", "ext_mlp_forward",
+    "ext_mlp_grads", "ext_mlp_train", "ext_so3_upper_bound", "ext_so3_refined_bound", "ext_so3_gather", "ext_so3_augment", "ext_so3_refine",
+    "ext_so3_propose", "ext_corr_so3_propose",
 )
 
 
@@ -97,7 +100,22 @@ def lib():
         L.ext_corr_so3_components.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, vp]
         L.ext_sweep_so3.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp, i32, vp]
         L.ext_corr_so3.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, i32, vp, vp, i32, vp]
-        dbl = ctypes.c_double
+        dbl, f32 = ctypes.c_double, ctypes.c_float
+        L.ext_mlp_create.argtypes = [vp, i32, i32, ctypes.POINTER(vp)]
+        L.ext_mlp_destroy.argtypes = [vp]
+        L.ext_mlp_set_params.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.ext_mlp_get_params.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.ext_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
+        L.ext_mlp_grads.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+        L.ext_mlp_train.argtypes = [vp, vp, vp, i32, i32, vp, vp, i32, i32, f32, vp, vp]
+        L.ext_so3_upper_bound.argtypes = [vp, vp, i64, i32, vp, vp]
+        L.ext_so3_refined_bound.argtypes = [vp, vp, i32, i32, vp, vp]
+        L.ext_so3_gather.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp]
+        L.ext_so3_augment.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp]
+        L.ext_so3_refine.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
+        L.ext_so3_propose.argtypes = [vp, vp, i64, i32, vp, vp, i32, f32, vp, vp, vp, i32, vp, vp]
+        L.ext_corr_so3_propose.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, dbl, i32, vp, vp, i32, f32, vp, vp,
+                                           vp, i32, vp, vp]
         L.ext_conv_scale.argtypes = [vp, vp, i32, i32, i32, vp, i32, dbl, dbl, dbl, dbl, vp, i32, vp, vp]
         for name in EXPORTED:
             if name not in ("ext_status_string", "ext_last_error", "ext_so3_channels"):
@@ -175,11 +193,15 @@ class FilterSO2:
 
 class Plan:
     def __init__(self, device: int = 0):
+        import weakref
         self.handle = ctypes.c_void_p()
+        self._nets = weakref.WeakSet()
         _check(lib().ext_plan_create(ctypes.byref(self.handle), int(device)))
 
     def close(self):
         if self.handle:
+            for net in list(self._nets):      # networks use the plan: close them first
+                net.close()
             lib().ext_plan_destroy(self.handle)
             self.handle = ctypes.c_void_p()
 
@@ -306,3 +328,103 @@ def ext_corr_so3(plan: Plan, V, nz, ny, nx, tables, dr, R, quats, max_out, argma
     _check(lib().ext_corr_so3(plan.handle, _ptr(V), int(nz), int(ny), int(nx), _ptr(t.view(np.float64)), L, t.shape[1],
                               float(dr), int(R), _ptr(q), q.shape[0], _ptr(max_out), _ptr(argmax), int(precision),
                               _stream(stream)))
+
+
+class MLP:
+    """The proposal network (ext_mlp): n_in -> hidden -> hidden -> 4, owned by a plan."""
+
+    def __init__(self, plan: Plan, n_in: int, hidden: int = 256):
+        self.plan = plan
+        self.n_in, self.hidden = int(n_in), int(hidden)
+        self.handle = ctypes.c_void_p()
+        _check(lib().ext_mlp_create(plan.handle, self.n_in, self.hidden, ctypes.byref(self.handle)))
+        plan._nets.add(self)
+
+    def close(self):
+        if self.handle:
+            lib().ext_mlp_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        """p: dict W1, b1, W2, b2, W3, b3 (arrays or tensors, FP32 on host or device)."""
+        arrs = [p[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+        arrs = [np.ascontiguousarray(np.asarray(a, np.float32)) if not hasattr(a, "data_ptr") else a for a in arrs]
+        _check(lib().ext_mlp_set_params(self.handle, *[_ptr(a) for a in arrs]))
+
+    def get_params(self):
+        H, n = self.hidden, self.n_in
+        out = dict(W1=np.zeros((H, n), np.float32), b1=np.zeros(H, np.float32), W2=np.zeros((H, H), np.float32),
+                   b2=np.zeros(H, np.float32), W3=np.zeros((4, H), np.float32), b3=np.zeros(4, np.float32))
+        _check(lib().ext_mlp_get_params(self.handle, *[_ptr(out[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]))
+        return out
+
+    def n_params(self):
+        H, n = self.hidden, self.n_in
+        return H * n + H + H * H + H + 4 * H + 4
+
+
+def ext_mlp_forward(net: MLP, X, n, q, stream=None):
+    _check(lib().ext_mlp_forward(net.handle, _ptr(X), int(n), _ptr(q), _stream(stream)))
+
+
+def ext_mlp_grads(net: MLP, X, qt, n, loss, grads, stream=None):
+    _check(lib().ext_mlp_grads(net.handle, _ptr(X), _ptr(qt), int(n), _ptr(loss), _ptr(grads), _stream(stream)))
+
+
+def ext_mlp_train(net: MLP, X, qt, n_train, L, rows, Q, steps, batch, lr, losses, stream=None):
+    _check(lib().ext_mlp_train(net.handle, _ptr(X), _ptr(qt), int(n_train), int(L), _ptr(rows), _ptr(Q), int(steps),
+                               int(batch), float(lr), _ptr(losses), _stream(stream)))
+
+
+def ext_so3_upper_bound(plan: Plan, G, n_vox, L, ub, stream=None):
+    _check(lib().ext_so3_upper_bound(plan.handle, _ptr(G), int(n_vox), int(L), _ptr(ub), _stream(stream)))
+
+
+def ext_so3_refined_bound(plan: Plan, X, n, L, out, stream=None):
+    _check(lib().ext_so3_refined_bound(plan.handle, _ptr(X), int(n), int(L), _ptr(out), _stream(stream)))
+
+
+def ext_so3_gather(plan: Plan, G, n_vox, L, vox, n, X, stream=None):
+    _check(lib().ext_so3_gather(plan.handle, _ptr(G), int(n_vox), int(L), _ptr(vox), int(n), _ptr(X),
+                                _stream(stream)))
+
+
+def ext_so3_augment(plan: Plan, X, n, L, Q, q_in, X_out, q_out, stream=None):
+    _check(lib().ext_so3_augment(plan.handle, _ptr(X), int(n), int(L), _ptr(Q), _ptr(q_in), _ptr(X_out), _ptr(q_out),
+                                 _stream(stream)))
+
+
+def ext_so3_refine(plan: Plan, X, n, L, q0, q_out, s_out, stream=None):
+    _check(lib().ext_so3_refine(plan.handle, _ptr(X), int(n), int(L), _ptr(q0), _ptr(q_out), _ptr(s_out),
+                                _stream(stream)))
+
+
+def ext_so3_propose(plan: Plan, G, n_vox, L, net, quats, bound, score, quat=None, grid_idx=None,
+                    precision=EXT_PREC_BF16X3, stream=None):
+    """Returns (voxels with UB >= bound, candidates, swept candidates)."""
+    q = np.ascontiguousarray(np.asarray(quats, np.float64).reshape(-1, 4))
+    counts = np.zeros(3, np.int64)
+    _check(lib().ext_so3_propose(plan.handle, _ptr(G), int(n_vox), int(L), net.handle if net is not None else None,
+                                 _ptr(q), q.shape[0], float(bound), _ptr(score), _ptr(quat), _ptr(grid_idx),
+                                 int(precision), _ptr(counts), _stream(stream)))
+    return int(counts[0]), int(counts[1]), int(counts[2])
+
+
+def ext_corr_so3_propose(plan: Plan, V, nz, ny, nx, tables, dr, R, net, quats, bound, score, quat=None, grid_idx=None,
+                         precision=EXT_PREC_BF16X3, stream=None):
+    """Returns (voxels with UB >= bound, candidates, swept candidates)."""
+    t = so3_pack_tables(tables)
+    L = len(tables) - 1
+    q = np.ascontiguousarray(np.asarray(quats, np.float64).reshape(-1, 4))
+    counts = np.zeros(3, np.int64)
+    _check(lib().ext_corr_so3_propose(plan.handle, _ptr(V), int(nz), int(ny), int(nx), _ptr(t.view(np.float64)), L,
+                                      t.shape[1], float(dr), int(R), net.handle if net is not None else None, _ptr(q),
+                                      q.shape[0], float(bound), _ptr(score), _ptr(quat), _ptr(grid_idx),
+                                      int(precision), _ptr(counts), _stream(stream)))
+    return int(counts[0]), int(counts[1]), int(counts[2])

@@ -338,6 +338,13 @@ ext_status ext_plan_trim(ext_plan plan) {
   plan->specs.clear();
   for (auto& kv : plan->ws) cudaFree(kv.second.p);
   plan->ws.clear();
+  // everything cached in the workspace is gone: the captured batch graph and
+  // the SO(3) tables point into it
+  if (plan->batch_exec) cudaGraphExecDestroy(plan->batch_exec);
+  plan->batch_exec = nullptr;
+  plan->batch_key = 0;
+  plan->so3_rot_key = 0;
+  plan->so3_steer_L = -1;
   return EXT_OK;
 }
 
@@ -355,6 +362,7 @@ ext_status ext_plan_destroy(ext_plan plan) {
   }
   for (auto e : plan->event_pool) cudaEventDestroy(e);
   if (plan->batch_exec) cudaGraphExecDestroy(plan->batch_exec);
+  if (plan->pinned) cudaFreeHost(plan->pinned);
   cudaFree(plan->dev_err);
   delete plan;
   return EXT_OK;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 
 #include "../../include/extconv.h"
@@ -84,5 +85,74 @@ void sweep_so3_fp32(const float* G, long long P, int C, const float* B, int cpad
                     int32_t* argmax, cudaStream_t st);
 size_t so3_btc_bytes(int J, int cpad);
 void so3_build_btc(const float* B, int cpad, int J, unsigned char* Bt, cudaStream_t st);
+// keys (P entries of scratch, or NULL): lets small voxel counts split the
+// rotation tiles over more blocks (sweep_so3_tc_split(P, J, sms) > 1)
+int sweep_so3_tc_split(long long P, int J, int sms);
 void sweep_so3_tc(const float* G, long long P, int C, int cpad, const unsigned char* Bt, int J, float* maxv,
-                  int32_t* argmax, int* err, int sms, cudaStream_t st);
+                  int32_t* argmax, unsigned long long* keys, int* err, int sms, cudaStream_t st);
+
+// ----- learned SO(3) proposal: tensor-core GEMM and network kernels (mlp.cu)
+// Epilogue of C = A B^T: optional bias[n], ReLU, zeroing where mask[m][n] <= 0,
+// FP32 and/or BF16 stores, row-major or transposed (out[n][m]).
+struct GemmEpilogue {
+  const float* bias = nullptr;
+  int relu = 0;
+  const __nv_bfloat16* mask = nullptr;
+  int ldm = 0;
+  float* out_f32 = nullptr;
+  int ldo = 0;
+  __nv_bfloat16* out_bf16 = nullptr;
+  int ldo16 = 0;
+  int trans = 0;
+};
+// A [M][lda], B [N][ldb], BF16, K-major; K, lda, ldb multiples of 8; 16-byte aligned rows.
+void gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
+               const GemmEpilogue& ep, int* err, cudaStream_t st);
+// rows (optionally selected by idx) of X [.][ldx] (first C entries) -> unit-norm BF16 rows of pitch dp
+void launch_rows_normalize_bf16(const float* X, int ldx, const int32_t* idx, int n, int C, int dp,
+                                __nv_bfloat16* Y, cudaStream_t st);
+void launch_gather_quats(const float* q, const int32_t* idx, int n, float* out, cudaStream_t st);
+void launch_quat_loss(const float* o, int ldo, const float* qt, int n, float* loss, __nv_bfloat16* dout,
+                      float* dout_f, cudaStream_t st);
+void launch_colsum(const float* X, int rows, int cols, int ld, float* out, cudaStream_t st);
+void launch_transpose_bf16(const __nv_bfloat16* X, int rows, int cols, int ldx, __nv_bfloat16* Y, int yrows,
+                           int ycols, int ldy, cudaStream_t st);
+void launch_adam(float* w, float* m, float* v, const float* g, long long n, float lr, int step, __nv_bfloat16* w16,
+                 cudaStream_t st);
+void launch_normalize_quat(const float* o, int ldo, int n, float* q, cudaStream_t st);
+void launch_f32_to_bf16(const float* x, long long n, __nv_bfloat16* y, cudaStream_t st);
+
+// ----- SO(3) proposal support (so3_proposal.cu)
+// Unique entries (l, a, b) of the rotation matrices, C^l_ab(R) = d^l_ba(beta) e^{-i((a+b) sigma + (b-a) delta)}
+// with sigma = (alpha + gamma) / 2, delta = (alpha - gamma) / 2 (zyz Euler angles); d from Wigner's sum
+// formula as sum_j coef[j] cos(beta/2)^(pc0 - 2j) sin(beta/2)^(ps0 + 2j).
+struct So3Steer {
+  int n;                 // entries (231 for L = 6)
+  uint32_t meta[256];    // ch | self << 10 | (ks + 12) << 11 | (kd + 12) << 16 | ns << 21 | pc0 << 24 | ps0 << 28
+  unsigned char l[256];  // degree of each entry (entries are ordered by degree)
+  float coef[7][256];
+};
+void launch_so3_upper_bound(const float* G, long long P, const So3Steer* tab, float* ub, int sms, cudaStream_t st);
+// ordered compaction: idx[k] = the k-th i with (below ? v[i] < thr : v[i] >= thr); *count = their number
+size_t compact_scratch_bytes(long long n);
+void compact(const float* v, long long n, float thr, int below, int32_t* idx, int* count, void* scratch,
+             cudaStream_t st);
+void launch_gather_rows(const float* G, long long P, int C, const int32_t* vox, int n, float* X, int ldx,
+                        cudaStream_t st);
+void launch_gather_channels(const float* G, long long P, int C, const int32_t* vox, const int32_t* sel, int n,
+                            float* out, cudaStream_t st);
+void launch_so3_refine(const float* X, int ldx, int n, const float* q0, const So3Steer* tab, int steps, float theta0,
+                       int tries, float* q_out, float* s_out, int sms, cudaStream_t st);
+void launch_so3_augment(const float* X, int ldx, const int32_t* rows, int n, const float* Q, const float* q_in,
+                        const So3Steer* tab, int C, float* X_out, int ldo, float* q_out, cudaStream_t st);
+void launch_so3_fill(long long P, float* score, float* quat, int32_t* grid_idx, cudaStream_t st);
+void launch_so3_scatter(const int32_t* cand, int n, const float* s, const float* q, float* score, float* quat,
+                        int32_t* grid_idx, cudaStream_t st);
+void launch_so3_merge(const int32_t* cand, const int32_t* fb, int n_fb, const float* m, const int32_t* j,
+                      const double* grid, float* score, float* quat, int32_t* grid_idx, cudaStream_t st);
+void launch_check_index(const int32_t* idx, long long n, long long upper, int* bad, cudaStream_t st);
+// per row of X (channel layout of degree L): sum_l min(sqrt(2l+1) |G_l|_F, deflated bound of |G_l|_*)
+void launch_so3_refined_bound(const float* X, int ldx, int n, const So3Steer* tab, int L, float* out, int sms,
+                              cudaStream_t st);
+void launch_gather_row_copies(const float* X, int ld, const int32_t* sel, int n, float* Y, cudaStream_t st);
+void launch_gather_int(const int32_t* x, const int32_t* sel, int n, int32_t* y, cudaStream_t st);

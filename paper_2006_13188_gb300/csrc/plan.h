@@ -89,6 +89,8 @@ struct ext_plan_s {
   // SO(3): steering tables of the last rotation set
   uint64_t so3_rot_key = 0;
   int so3_rot_n = 0, so3_rot_L = -1;
+  int so3_steer_L = -1;            // degree of the steering-entry table in workspace "so3_steer"
+  int* pinned = nullptr;           // small pinned host buffer for counts read back mid-call
 };
 
 namespace {

@@ -134,9 +134,20 @@ __global__ void k_so3_btc(const float* __restrict__ B, int cpad, int J, int ntn,
   }
 }
 
+// With gridDim.y > 1 the rotation tiles are split over blockIdx.y and every
+// block folds its (max, first argmax) into keys[p] (ordered score bits above
+// the complemented index: atomicMax keeps the larger score, then the smaller
+// index); k_sweep_keys_finish decodes them.
+__device__ __forceinline__ unsigned long long sweep_key(float v, int j) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t o = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+  return ((unsigned long long)o << 32) | (uint32_t)(0xFFFFFFFFu - (uint32_t)j);
+}
+
 __global__ void __launch_bounds__(128) k_sweep_so3_tc(const float* __restrict__ G, long long P, int C, int nkc,
                                                       const unsigned char* __restrict__ Bt, int ntn, int J,
                                                       float* __restrict__ maxv, int32_t* __restrict__ argmax,
+                                                      unsigned long long* __restrict__ keys,
                                                       int* __restrict__ err, unsigned long long limit_ns) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* As = smem;
@@ -158,12 +169,14 @@ __global__ void __launch_bounds__(128) k_sweep_so3_tc(const float* __restrict__ 
   constexpr uint32_t IDESC = tc::make_idesc(TM, TN);
   uint32_t phase = 0;
   const long long ntm = (P + TM - 1) / TM;
+  const int nsplit = gridDim.y;
+  const int nt0 = (int)((long long)ntn * blockIdx.y / nsplit), nt1 = (int)((long long)ntn * (blockIdx.y + 1) / nsplit);
   for (long long mt = blockIdx.x; mt < ntm && !abort_flag; mt += gridDim.x) {
     const long long p = mt * TM + tid;
     const bool live = p < P;
     float best = -FLT_MAX;
-    int bj = 0;
-    for (int nt = 0; nt < ntn && !abort_flag; ++nt) {
+    int bj = nt0 * TN;
+    for (int nt = nt0; nt < nt1 && !abort_flag; ++nt) {
       for (int kc = 0; kc < nkc; ++kc) {
         // B' block: straight copy of its shared-memory image
         const uint4* src = reinterpret_cast<const uint4*>(Bt + ((size_t)nt * nkc + kc) * TB_BYTES);
@@ -215,13 +228,20 @@ __global__ void __launch_bounds__(128) k_sweep_so3_tc(const float* __restrict__ 
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int j = nt * TN + c0 + i;
-          if (j < J && (v[i] > best || (j == 0))) { best = v[i]; bj = j; }
+          if (j < J && (v[i] > best || (j == nt0 * TN))) { best = v[i]; bj = j; }
         }
       }
       tc::fence_before();
       __syncthreads();
     }
-    if (live && !abort_flag) { maxv[p] = best; argmax[p] = bj; }
+    if (live && !abort_flag) {
+      if (nsplit == 1) {
+        maxv[p] = best;
+        argmax[p] = bj;
+      } else {
+        atomicMax(keys + p, sweep_key(best, bj));
+      }
+    }
   }
   __syncthreads();
   if (warp == 0) {
@@ -240,8 +260,28 @@ void so3_build_btc(const float* B, int cpad, int J, unsigned char* Bt, cudaStrea
   k_so3_btc<<<1024, 256, 0, st>>>(B, cpad, J, ntn, nkc, Bt);
 }
 
+__global__ void k_sweep_keys_finish(const unsigned long long* __restrict__ keys, long long P, float* __restrict__ maxv,
+                                    int32_t* __restrict__ argmax) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long k = keys[p];
+    const uint32_t o = (uint32_t)(k >> 32);
+    const uint32_t b = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+    maxv[p] = __uint_as_float(b);
+    argmax[p] = (int32_t)(0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu));
+  }
+}
+
+int sweep_so3_tc_split(long long P, int J, int sms) {
+  const int ntn = (J + TN - 1) / TN;
+  const long long ntm = (P + TM - 1) / TM;
+  long long s = (2LL * sms) / (ntm > 0 ? ntm : 1);
+  if (s < 1) s = 1;
+  if (s > ntn) s = ntn;
+  return (int)s;
+}
+
 void sweep_so3_tc(const float* G, long long P, int C, int cpad, const unsigned char* Bt, int J, float* maxv,
-                  int32_t* argmax, int* err, int sms, cudaStream_t st) {
+                  int32_t* argmax, unsigned long long* keys, int* err, int sms, cudaStream_t st) {
   const int ntn = (J + TN - 1) / TN, nkc = (cpad + TKC - 1) / TKC;
   // two blocks per SM share the 512 TMEM columns: request shared memory accordingly
   constexpr int request = 100 * 1024;
@@ -249,8 +289,15 @@ void sweep_so3_tc(const float* G, long long P, int C, int cpad, const unsigned c
       (cudaFuncSetAttribute(k_sweep_so3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, request), true);
   (void)once;
   const long long ntm = (P + TM - 1) / TM;
-  long long grid = (long long)sms * 2;
+  const int nsplit = keys ? sweep_so3_tc_split(P, J, sms) : 1;
+  long long grid = ((long long)sms * 2 + nsplit - 1) / nsplit;
   if (grid > ntm) grid = ntm;
-  k_sweep_so3_tc<<<(unsigned)grid, 128, request, st>>>(G, P, C, nkc, Bt, ntn, J, maxv, argmax, err,
-                                                       2000000000ull);
+  if (nsplit > 1) cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * P, st);
+  k_sweep_so3_tc<<<dim3((unsigned)grid, nsplit), 128, request, st>>>(G, P, C, nkc, Bt, ntn, J, maxv, argmax, keys,
+                                                                     err, 2000000000ull);
+  if (nsplit > 1) {
+    long long b = (P + 255) / 256;
+    if (b > 4096) b = 4096;
+    k_sweep_keys_finish<<<(unsigned)b, 256, 0, st>>>(keys, P, maxv, argmax);
+  }
 }

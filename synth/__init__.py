@@ -394,13 +394,15 @@ def _sample_template(tables, dr, radius, Rm=None):
 
 
 def so3_match_problem(seed: int | None = None, size: int = 128, n_plant: int = 16, L: int = 6,
-                      radius: int = 8, dr: float = 0.125, noise_sigma: float = 0.1):
+                      radius: int = 8, dr: float = 0.125, noise_sigma: float = 0.1, tables=None):
     """3D matching input: Gaussian noise sigma 0.1 plus n_plant copies of the
-    band-limited template (profiles from so3_filter_tables) rotated by
-    Haar-random rotations at centres >= 2R+1 apart (torus distance).
-    Volume float32 (z, y, x)."""
+    band-limited template (profiles from so3_filter_tables, or the given
+    `tables`) rotated by Haar-random rotations at centres >= 2R+1 apart
+    (torus distance).  Volume float32 (z, y, x)."""
     rng = np.random.default_rng(seed_for(5) if seed is None else seed)
-    tables = so3_filter_tables(int(rng.integers(0, 2**31 - 1)), L, float(radius), dr)
+    filter_seed = int(rng.integers(0, 2**31 - 1))
+    if tables is None:
+        tables = so3_filter_tables(filter_seed, L, float(radius), dr)
     V = rng.normal(0.0, noise_sigma, (size, size, size))
     centres = []
     while len(centres) < n_plant:
@@ -417,3 +419,27 @@ def so3_match_problem(seed: int | None = None, size: int = 128, n_plant: int = 1
         V[np.ix_(zi, yi, xi)] += block
     return dict(V=V.astype(np.float32), tables=tables, dr=dr, radius=radius, L=L,
                 centres=np.array(centres), quats=quats)
+
+
+def mlp_init(seed: int, n_in: int, hidden: int = 256):
+    """Initial weights of the proposal network (He-normal, zero biases; the
+    output layer scaled by 0.5), FP32, shapes W1 [hidden][n_in], b1 [hidden],
+    W2 [hidden][hidden], b2 [hidden], W3 [4][hidden], b3 [4]."""
+    rng = np.random.default_rng(seed)
+
+    def he(o, i):
+        return (rng.standard_normal((o, i)) * np.sqrt(2.0 / i)).astype(np.float32)
+    return dict(W1=he(hidden, n_in), b1=np.zeros(hidden, np.float32), W2=he(hidden, hidden),
+                b2=np.zeros(hidden, np.float32), W3=(he(4, hidden) * 0.5).astype(np.float32),
+                b3=np.zeros(4, np.float32))
+
+
+def training_draws(seed: int, n_train: int, steps: int, batch: int):
+    """Minibatch row indices (int32 [steps*batch]) and Haar-random
+    augmentation rotations (float32 [steps*batch][4]) for training the
+    proposal network."""
+    rng = np.random.default_rng(seed)
+    rows = rng.integers(0, n_train, steps * batch).astype(np.int32)
+    q = rng.standard_normal((steps * batch, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return rows, q.astype(np.float32)

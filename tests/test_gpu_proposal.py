@@ -1,0 +1,417 @@
+"""GPU parity of the learned SO(3) proposal against the FP64 oracles: the
+network's forward pass and gradients (BF16 operands, FP32 accumulation:
+rel-L2 <= 1e-2 per tensor, cosine >= 0.999), the first Adam step, the score
+upper bound, gathering, rotation augmentation (S'(R) = S(Q^-1 R)), the FP32
+refinement against the FP64 refinement, and the whole proposal on a planted
+128^3 volume against the exhaustive grid sweep, with the ablation without the
+network."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth
+from oracle import mlp as omlp
+from oracle.so3 import (SHFilter, channel_layout, component_correlation_at, nuclear_bound, quat_mul, quat_to_matrix,
+                        refine, score_from_channels, upper_bound, wigner_by_projection)
+
+pytestmark = pytest.mark.gpu
+
+L6 = 6
+NCH = 455
+
+
+@pytest.fixture(scope="module")
+def ec():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2006_13188_gb300 as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def plan(ec):
+    p = ec.Plan(0)
+    yield p
+    p.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def bf16(x):
+    """Round to bfloat16 (nearest even), returned as float64."""
+    a = np.ascontiguousarray(np.asarray(x, np.float32)).view(np.uint32).astype(np.uint64)
+    r = ((a + 0x7FFF + ((a >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def oracle_params(p):
+    """The GPU's arithmetic operands: BF16 weights, FP32 biases."""
+    return {k: (bf16(v) if k.startswith("W") else np.asarray(v, np.float64)) for k, v in p.items()}
+
+
+def unit_rows(X):
+    X = np.asarray(X, np.float64)
+    return X / np.linalg.norm(X, axis=1, keepdims=True)
+
+
+def haar(rng, n):
+    return np.array([synth.haar_quaternion(rng) for _ in range(n)])
+
+
+def angle(q1, q2):
+    d = abs(float(np.dot(q1 / np.linalg.norm(q1), q2 / np.linalg.norm(q2))))
+    return 2 * math.acos(min(1.0, d))
+
+
+def test_mlp_forward_matches_oracle(ec, plan):
+    rng = np.random.default_rng(20)
+    n, H = 300, 256                          # 3 row tiles with a ragged tail
+    p = synth.mlp_init(7, NCH, H)
+    p["b1"] = (0.1 * rng.standard_normal(H)).astype(np.float32)
+    p["b2"] = (0.1 * rng.standard_normal(H)).astype(np.float32)
+    p["b3"] = (0.1 * rng.standard_normal(4)).astype(np.float32)
+    net = ec.MLP(plan, NCH, H)
+    net.set_params(p)
+    X = rng.standard_normal((n, NCH)).astype(np.float32)
+    q = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ec.ext_mlp_forward(net, dev(X), n, q)
+    plan.sync()
+    qo = omlp.quaternion(omlp.forward(oracle_params(p), bf16(unit_rows(X)))["o"])
+    err = np.linalg.norm(q.cpu().numpy() - qo) / np.linalg.norm(qo)
+    print(f"mlp forward rel-L2 {err:.2e}")
+    assert err < 1e-2
+    back = net.get_params()
+    for k in p:
+        np.testing.assert_array_equal(back[k], p[k])
+
+
+@pytest.mark.parametrize("case", ["all_active", "he_init"])
+def test_mlp_gradients_match_oracle(ec, plan, case):
+    """all_active: biases that keep every ReLU unit on (no derivative can
+    switch), the BF16 bar rel-L2 <= 1e-2.  he_init: zero biases, half the
+    units off; a unit whose pre-activation lies within the BF16 rounding of
+    the activations from zero switches its ReLU derivative, adding a
+    full-size entry to the difference (about 20 of 51,200 here; measured
+    rel-L2 2.4e-2, reproduced by a NumPy model of the BF16 arithmetic), so
+    the bar there is rel-L2 <= 5e-2 with cosine >= 0.999."""
+    rng = np.random.default_rng(21)
+    n, H = 200, 256
+    p = synth.mlp_init(8, NCH, H)
+    if case == "all_active":
+        p["b1"] = np.full(H, 1.0, np.float32)
+        p["b2"] = np.full(H, 10.0, np.float32)
+    rel_bar = 1e-2 if case == "all_active" else 5e-2
+    net = ec.MLP(plan, NCH, H)
+    net.set_params(p)
+    X = rng.standard_normal((n, NCH)).astype(np.float32)
+    qt = haar(rng, n).astype(np.float32)
+    grads = torch.empty(net.n_params(), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    ec.ext_mlp_grads(net, dev(X), dev(qt), n, loss, grads)
+    plan.sync()
+    po = oracle_params(p)
+    cache = omlp.forward(po, bf16(unit_rows(X)))
+    go = omlp.backward(po, cache, qt.astype(np.float64))
+    lo = omlp.loss(cache["o"], qt.astype(np.float64))
+    assert abs(float(loss.item()) - lo) <= 1e-2 * lo
+    g = grads.cpu().numpy().astype(np.float64)
+    off = 0
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        ref = go[k].ravel()
+        got = g[off:off + ref.size]
+        off += ref.size
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        cos = float(np.dot(got, ref) / (np.linalg.norm(got) * np.linalg.norm(ref)))
+        print(f"grad {k}: rel-L2 {rel:.2e} cosine {cos:.6f}")
+        assert rel <= rel_bar and cos >= 0.999, k
+    assert off == g.size
+
+
+def test_adam_first_step(ec, plan):
+    """One training step on a fixed batch equals the oracle's Adam step
+    (Kingma & Ba, Algorithm 1) applied to the GPU's own gradients."""
+    rng = np.random.default_rng(22)
+    n, H = 96, 64
+    p = synth.mlp_init(9, NCH, H)
+    net = ec.MLP(plan, NCH, H)
+    net.set_params(p)
+    X = rng.standard_normal((n, NCH)).astype(np.float32)
+    qt = haar(rng, n).astype(np.float32)
+    grads = torch.empty(net.n_params(), dtype=torch.float32, device="cuda")
+    ec.ext_mlp_grads(net, dev(X), dev(qt), n, None, grads)
+    plan.sync()
+    g = grads.cpu().numpy().astype(np.float64)
+    gd, off = {}, 0
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        gd[k] = g[off:off + p[k].size].reshape(p[k].shape)
+        off += p[k].size
+    losses = np.zeros(1, np.float32)
+    ec.ext_mlp_train(net, dev(X), dev(qt), n, -1, dev(np.arange(n, dtype=np.int32)), None, 1, n, 1e-3, losses)
+    expect = omlp.adam_step({k: v.astype(np.float64) for k, v in p.items()}, gd, {}, lr=1e-3)
+    got = net.get_params()
+    for k in p:
+        np.testing.assert_allclose(got[k], expect[k], atol=3e-7, rtol=0, err_msg=k)
+    assert losses[0] > 0
+
+
+def test_upper_bound_matches_oracle_and_bounds_the_sweep(ec, plan):
+    rng = np.random.default_rng(23)
+    n = 3000
+    G = rng.standard_normal((NCH, n)).astype(np.float32)
+    ub = torch.empty(n, dtype=torch.float32, device="cuda")
+    ec.ext_so3_upper_bound(plan, dev(G), n, L6, ub)
+    plan.sync()
+    ubn = ub.cpu().numpy()
+    for p in range(0, n, 97):
+        ref = upper_bound(G[:, p].astype(np.float64), L6)
+        assert abs(ubn[p] - ref) <= 1e-5 * ref
+    quats = haar(rng, 384)
+    mx = torch.empty(n, dtype=torch.float32, device="cuda")
+    am = torch.empty(n, dtype=torch.int32, device="cuda")
+    ec.ext_sweep_so3(plan, dev(G), n, L6, quats, mx, am, ec.EXT_PREC_FP32)
+    plan.sync()
+    assert np.all(mx.cpu().numpy() <= ubn * (1 + 1e-5))
+
+
+def _real_pair_vector(rng, l):
+    """v_{-a} = (-1)^a conj(v_a): the symmetry of a real filter and signal."""
+    v = np.zeros(2 * l + 1, complex)
+    v[l] = rng.standard_normal()
+    for a in range(1, l + 1):
+        z = rng.standard_normal() + 1j * rng.standard_normal()
+        v[a + l] = z
+        v[-a + l] = (-1) ** a * np.conj(z)
+    return v
+
+
+def test_refined_bound_matches_oracle(ec, plan):
+    """Rows with the structure of a template match (G_l = M_l C^l(R), M_l a
+    rank-2 PSD matrix with the real-pair symmetry, plus 1% noise) and plain
+    Gaussian rows: the GPU bound is never below the exact sum of nuclear
+    norms (numpy SVD), never above the Frobenius bound, and within 1% of the
+    nuclear sum on the template rows."""
+    rng = np.random.default_rng(28)
+    lay, _ = channel_layout(L6)
+    rows = []
+    for t in range(24):
+        R = quat_to_matrix(synth.haar_quaternion(rng))
+        full = []
+        for l in range(L6 + 1):
+            B = np.stack([_real_pair_vector(rng, l), _real_pair_vector(rng, l)], axis=1)
+            full.append(B @ B.conj().T @ wigner_by_projection(l, R))
+        x = np.zeros(NCH)
+        for (l, a, b, ch) in lay:
+            g = full[l][a + l, b + l]
+            x[ch] = g.real
+            if not (a == 0 and b == 0):
+                x[ch + 1] = g.imag
+        rows.append(x + 0.01 * np.abs(x).mean() * rng.standard_normal(NCH))
+    X = np.vstack([np.array(rows), rng.standard_normal((24, NCH))]).astype(np.float32)
+    n = X.shape[0]
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ec.ext_so3_refined_bound(plan, dev(X), n, L6, out)
+    plan.sync()
+    got = out.cpu().numpy().astype(np.float64)
+    for i in range(n):
+        x = X[i].astype(np.float64)
+        nuc, fro = nuclear_bound(x, L6), upper_bound(x, L6)
+        assert got[i] >= nuc * (1 - 1e-6), (i, got[i], nuc)
+        assert got[i] <= fro * (1 + 1e-4), (i, got[i], fro)
+        if i < 24:
+            assert got[i] <= 1.01 * nuc, (i, got[i], nuc)
+
+
+def test_gather_is_exact(ec, plan):
+    rng = np.random.default_rng(24)
+    P = 5000
+    G = rng.standard_normal((NCH, P)).astype(np.float32)
+    vox = rng.integers(0, P, 333).astype(np.int32)
+    X = torch.empty((333, NCH), dtype=torch.float32, device="cuda")
+    ec.ext_so3_gather(plan, dev(G), P, L6, dev(vox), 333, X)
+    plan.sync()
+    np.testing.assert_array_equal(X.cpu().numpy(), G[:, vox].T)
+    with pytest.raises(ec.ExtError):
+        ec.ext_so3_gather(plan, dev(G), P, L6, dev(np.array([0, P], np.int32)), 2, X)
+
+
+def test_augmentation_rotates_the_score_function(ec, plan):
+    rng = np.random.default_rng(25)
+    n = 5
+    X = rng.standard_normal((n, NCH)).astype(np.float32)
+    Q = haar(rng, n).astype(np.float32)
+    qi = haar(rng, n).astype(np.float32)
+    Xo = torch.empty((n, NCH), dtype=torch.float32, device="cuda")
+    qo = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ec.ext_so3_augment(plan, dev(X), n, L6, dev(Q), dev(qi), Xo, qo)
+    plan.sync()
+    Xo, qo = Xo.cpu().numpy().astype(np.float64), qo.cpu().numpy()
+    for i in range(n):
+        scale = upper_bound(X[i].astype(np.float64), L6)
+        Qm = quat_to_matrix(Q[i])
+        for R in [quat_to_matrix(q) for q in haar(rng, 2)]:
+            s_new = score_from_channels(Xo[i], L6, R)
+            s_old = score_from_channels(X[i].astype(np.float64), L6, Qm.T @ R)
+            assert abs(s_new - s_old) <= 2e-6 * scale
+        assert angle(qo[i], quat_mul(Q[i].astype(np.float64), qi[i].astype(np.float64))) < 1e-3
+
+
+def _oracle_channels(V, tables, dr, radius, vox, L):
+    """Component channels at voxels by the oracle's direct correlation."""
+    F = SHFilter(tables, dr)
+    lay, nch = channel_layout(L)
+    out = np.zeros((len(vox), nch))
+    for (l, a, b, ch) in lay:
+        g = component_correlation_at(V, F, l, a, b, radius, vox)
+        out[:, ch] = g.real
+        if not (a == 0 and b == 0):
+            out[:, ch + 1] = g.imag
+    return out
+
+
+def test_refinement_matches_oracle(ec, plan):
+    """FP32 refinement on the GPU vs the FP64 oracle from the same starts, on
+    channels of a planted template computed by the oracle."""
+    prob = synth.so3_match_problem(seed=31, size=24, n_plant=1, L=L6, radius=5, dr=0.25)
+    c = prob["centres"][0]
+    vox = np.array([c] + [(c + np.array(o)) % 24 for o in [(1, 0, 0), (0, -1, 1), (1, 1, 0)]])
+    chan = _oracle_channels(prob["V"], prob["tables"], prob["dr"], prob["radius"], vox, L6)
+    rng = np.random.default_rng(26)
+    starts, rows = [], []
+    for i in range(len(vox)):
+        for t in (0.2, 0.45):                       # perturbed planted rotation
+            axis = rng.standard_normal(3)
+            axis /= np.linalg.norm(axis)
+            starts.append(quat_mul(prob["quats"][0], np.concatenate([[math.cos(t / 2)], math.sin(t / 2) * axis])))
+            rows.append(i)
+        starts.append(synth.haar_quaternion(rng))   # random start
+        rows.append(i)
+    X = chan[rows].astype(np.float32)
+    q0 = np.array(starts, np.float32)
+    n = len(rows)
+    qg = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    sg = torch.empty(n, dtype=torch.float32, device="cuda")
+    ec.ext_so3_refine(plan, dev(X), n, L6, dev(q0), qg, sg)
+    plan.sync()
+    qg, sg = qg.cpu().numpy().astype(np.float64), sg.cpu().numpy().astype(np.float64)
+    agree = 0
+    for i in range(n):
+        x = X[i].astype(np.float64)
+        scale = upper_bound(x, L6)
+        s_self = score_from_channels(x, L6, quat_to_matrix(qg[i]))
+        s_start = score_from_channels(x, L6, quat_to_matrix(q0[i].astype(np.float64)))
+        qo, so = refine(x, L6, q0[i].astype(np.float64))
+        print(f"refine {i}: gpu {sg[i]:.6f} (exact {s_self:.6f}) oracle {so:.6f} start {s_start:.6f} "
+              f"angle {math.degrees(angle(qg[i], qo)):.3f} deg")
+        assert abs(sg[i] - s_self) <= 1e-5 * scale        # the reported score is the score of the reported rotation
+        assert s_self >= s_start - 1e-5 * scale            # ascent
+        if abs(sg[i] - so) <= 1e-4 * scale:
+            agree += 1
+    assert agree >= n - 1
+
+
+# ------------------------------------------------------------ whole pipeline ---
+
+@pytest.fixture(scope="module")
+def trained(ec, plan):
+    """A network trained on two planted 64^3 volumes (same filter as the test
+    volume, other centres and rotations): rows = channels at the planted
+    centres and their 5^3 neighbourhoods; labels = the grid argmax refined
+    on the GPU; rotation augmentation on every step."""
+    from paper_2006_13188_gb300 import proposal
+    tables = synth.so3_filter_tables(1306, L6, 8.0, 0.125)
+    grid = synth.so3_rotation_grid()
+    rows, labels, peaks = [], [], []
+    for seed in (401, 402):
+        prob = synth.so3_match_problem(seed=seed, size=64, n_plant=6, L=L6, tables=tables)
+        vox = proposal.neighbourhood_voxels(prob["centres"], (64, 64, 64), reach=2)
+        X, q, mx = proposal.training_rows(plan, dev(prob["V"]), (64, 64, 64), tables, prob["dr"], prob["radius"],
+                                          grid, vox)
+        rows.append(X)
+        labels.append(q)
+        peaks.extend(mx.cpu().numpy()[62::125].tolist())      # the centre is voxel 62 of each 5^3 block
+    X, qt = torch.cat(rows), torch.cat(labels)
+    net = ec.MLP(plan, NCH, 256)
+    net.set_params(synth.mlp_init(11, NCH, 256))
+    steps, batch = 6000, 512
+    r, Q = synth.training_draws(12, X.shape[0], steps, batch)
+    losses = proposal.train(net, X, qt, L6, dev(r), dev(Q), steps, batch)
+    bound = 0.5 * float(np.median(peaks))
+    print(f"training: {X.shape[0]} rows, loss {losses[:50].mean():.4f} -> {losses[-50:].mean():.4f}, B = {bound:.4f}")
+    return dict(net=net, bound=bound, tables=tables, grid=grid, losses=losses)
+
+
+def test_training_reduces_the_loss(trained):
+    ls = trained["losses"]
+    assert np.all(np.isfinite(ls))
+    assert ls[-100:].mean() < 0.5 * ls[:100].mean()
+
+
+def test_proposal_matches_exhaustive_sweep(ec, plan, trained):
+    """128^3, 16 planted templates, 4608-rotation grid.  Over the candidate
+    voxels (UB >= B): score error (S_grid - S_prop) / max|S| <= 1e-4 one-sided
+    (an off-grid optimum may beat the grid) at >= 99% of them; every voxel
+    whose grid maximum reaches B is found with a score >= its grid maximum -
+    1e-4 max|S|; the planted templates are detected at their centres with
+    rotations closer than the grid's; sampled (score, rotation) pairs are the
+    oracle's exact score of that rotation.  Without the network every
+    candidate is swept and the scores are the grid sweep's."""
+    prob = synth.so3_match_problem(seed=403, tables=trained["tables"])
+    n = 128
+    P = n ** 3
+    grid, bound = trained["grid"], trained["bound"]
+    V = dev(prob["V"])
+    mx = torch.empty(P, dtype=torch.float32, device="cuda")
+    am = torch.empty(P, dtype=torch.int32, device="cuda")
+    ec.ext_corr_so3(plan, V, n, n, n, prob["tables"], prob["dr"], prob["radius"], grid, mx, am, ec.EXT_PREC_BF16X3)
+    sc = torch.empty(P, dtype=torch.float32, device="cuda")
+    qq = torch.empty((P, 4), dtype=torch.float32, device="cuda")
+    gi = torch.empty(P, dtype=torch.int32, device="cuda")
+    nub, nc, nf = ec.ext_corr_so3_propose(plan, V, n, n, n, prob["tables"], prob["dr"], prob["radius"],
+                                          trained["net"], grid, bound, sc, qq, gi, ec.EXT_PREC_BF16X3)
+    plan.sync()
+    mxn, scn, qqn, gin = mx.cpu().numpy(), sc.cpu().numpy(), qq.cpu().numpy(), gi.cpu().numpy()
+    cand = np.isfinite(scn)
+    assert cand.sum() == nc and (gin >= 0).sum() == nf
+    scale = float(np.abs(mxn).max())
+    err = (mxn[cand] - scn[cand]) / scale
+    agree = np.mean(err <= 1e-4)
+    strong = mxn >= bound
+    print(f"proposal: {nub} voxels with UB >= B, {nc} candidates of {P}, {nf} swept, {strong.sum()} with grid max "
+          f">= B; agreement {agree:.4f}, worst {err.max():.2e}")
+    assert agree >= 0.99
+    assert np.all(cand[strong])
+    assert np.all(scn[strong] >= bound)          # detection is never lost
+    # planted templates: peak at the centre, rotation at least as good as the grid's
+    for c, qtrue in zip(prob["centres"], prob["quats"]):
+        p = (c[0] * n + c[1]) * n + c[2]
+        win = np.roll(scn.reshape(n, n, n), (1 - c[0], 1 - c[1], 1 - c[2]), axis=(0, 1, 2))[:3, :3, :3]
+        assert np.unravel_index(np.argmax(win), win.shape) == (1, 1, 1)
+        assert scn[p] >= mxn[p] - 1e-4 * scale
+    # exact score of the returned rotation at sampled candidates (oracle channels)
+    rng = np.random.default_rng(27)
+    cidx = np.flatnonzero(cand)
+    pick = np.concatenate([[(c[0] * n + c[1]) * n + c[2] for c in prob["centres"][:3]],
+                           rng.choice(cidx, size=min(5, len(cidx)), replace=False)])
+    vox = np.stack([pick // (n * n), (pick // n) % n, pick % n], axis=1)
+    chan = _oracle_channels(prob["V"], prob["tables"], prob["dr"], prob["radius"], vox, L6)
+    for k, p in enumerate(pick):
+        s_exact = score_from_channels(chan[k], L6, quat_to_matrix(qqn[p].astype(np.float64)))
+        assert abs(s_exact - scn[p]) <= 1e-4 * scale, (p, s_exact, scn[p])
+    # ablation: no network -> every candidate is swept, scores equal the grid sweep's
+    sc0 = torch.empty(P, dtype=torch.float32, device="cuda")
+    gi0 = torch.empty(P, dtype=torch.int32, device="cuda")
+    nub0, nc0, nf0 = ec.ext_corr_so3_propose(plan, V, n, n, n, prob["tables"], prob["dr"], prob["radius"], None,
+                                             grid, bound, sc0, None, gi0, ec.EXT_PREC_BF16X3)
+    plan.sync()
+    assert nub0 == nub and nc0 == nc and nf0 == nc
+    sc0n = sc0.cpu().numpy()
+    np.testing.assert_array_equal(sc0n[cand], mxn[cand])
+    np.testing.assert_array_equal(gi0.cpu().numpy()[cand], am.cpu().numpy()[cand])
+    print(f"ablation: {nf0} swept without the network vs {nf} with it")
+    assert nf <= nc - 0.5 * strong.sum()

@@ -3,6 +3,7 @@ antipodal invariance, the score upper bound, and refinement behaviour."""
 import math
 
 import numpy as np
+import pytest
 
 import synth
 from oracle import mlp
@@ -75,3 +76,51 @@ def test_refinement_is_monotone_and_approaches_the_planted_rotation():
     def ang(a, b):
         return 2 * math.acos(min(1.0, abs(float(np.dot(a, b)))))
     assert ang(q1, qtrue) < ang(q0, qtrue)
+
+
+def test_adam_first_step_is_signed_learning_rate():
+    """Algorithm 1 of Kingma & Ba: after bias correction the first step is
+    -lr * g / (|g| + eps), i.e. -lr * sign(g) for |g| >> eps; without the
+    corrections it would be lr * 0.1 / sqrt(0.001) = 3.16 lr."""
+    rng = np.random.default_rng(5)
+    p = {"W": rng.standard_normal((3, 4)), "b": rng.standard_normal(4)}
+    g = {"W": rng.standard_normal((3, 4)), "b": np.array([0.5, -2.0, 1e-3, 0.0])}
+    st = {}
+    out = mlp.adam_step(p, g, st, lr=0.01)
+    np.testing.assert_allclose(out["W"] - p["W"], -0.01 * np.sign(g["W"]), rtol=1e-6)
+    np.testing.assert_allclose(out["b"][:3] - p["b"][:3], -0.01 * np.sign(g["b"][:3]), rtol=1e-4)
+    assert out["b"][3] == p["b"][3]                      # zero gradient: no move
+    assert st["t"] == 1
+
+
+def test_adam_minimises_a_quadratic():
+    p = {"w": np.array([0.0, 10.0])}
+    st = {}
+    for _ in range(3000):
+        g = {"w": 2.0 * (p["w"] - np.array([3.0, -1.0]))}
+        p = mlp.adam_step(p, g, st, lr=0.02)
+    np.testing.assert_allclose(p["w"], [3.0, -1.0], atol=1e-2)
+
+
+def test_nuclear_bound_dominates_and_is_tight_for_a_pure_rotation():
+    """|S(R)| <= sum_l |G_l|_* <= upper_bound; if G_l = C^l(R0) for every l
+    the bound is reached at R0 (S(R0) = sum_l tr(C^H C) = sum_l (2l+1))."""
+    from oracle.so3 import nuclear_bound, wigner_by_projection
+    chan, _ = _template_channels()
+    nb, ub = nuclear_bound(chan, 3), upper_bound(chan, 3)
+    assert nb <= ub * (1 + 1e-12)
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        R = quat_to_matrix(synth.haar_quaternion(rng))
+        assert abs(score_from_channels(chan, 3, R)) <= nb * (1 + 1e-12)
+    R0 = quat_to_matrix(synth.haar_quaternion(rng))
+    lay, n = channel_layout(3)
+    pure = np.zeros(n)
+    for (l, a, b, ch) in lay:
+        c = wigner_by_projection(l, R0)[a + l, b + l]
+        pure[ch] = c.real
+        if not (a == 0 and b == 0):
+            pure[ch + 1] = c.imag
+    assert abs(nuclear_bound(pure, 3) - 16.0) < 1e-9
+    assert abs(score_from_channels(pure, 3, R0) - 16.0) < 1e-9
+    assert upper_bound(pure, 3) == pytest.approx(16.0)

@@ -173,3 +173,33 @@ def test_channel_layout_counts_and_pairing():
         g = component_correlation(V, F, l, a, b, 2)
         gm = component_correlation(V, F, l, -a, -b, 2)
         np.testing.assert_allclose(gm, (-1) ** (a + b) * np.conj(g), atol=1e-12)
+
+
+@pytest.mark.parametrize("l", [1, 3, 6])
+def test_rotation_generators_are_the_derivative_of_the_definition(l):
+    """A_i from the ladder relations equals the central difference of C^l
+    computed from its definition (projection) about e_i."""
+    from oracle.so3 import quat_exp, rotation_generators
+    h = 1e-5
+    for i, A in enumerate(rotation_generators(l)):
+        e = np.zeros(3)
+        e[i] = h
+        Cp = wigner_by_projection(l, quat_to_matrix(quat_exp(e)))
+        Cm = wigner_by_projection(l, quat_to_matrix(quat_exp(-e)))
+        np.testing.assert_allclose(A, (Cp - Cm) / (2 * h), atol=1e-8)
+
+
+def test_score_gradient_matches_finite_differences():
+    from oracle.so3 import channel_layout, quat_exp, quat_mul, score_from_channels, score_gradient
+    rng = np.random.default_rng(12)
+    _, n = channel_layout(4)
+    chan = rng.standard_normal(n)
+    q = synth.haar_quaternion(rng)
+    g = score_gradient(chan, 4, quat_to_matrix(q))
+    h = 1e-5
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = h
+        fd = (score_from_channels(chan, 4, quat_to_matrix(quat_mul(q, quat_exp(e))))
+              - score_from_channels(chan, 4, quat_to_matrix(quat_mul(q, quat_exp(-e))))) / (2 * h)
+        assert abs(g[i] - fd) <= 1e-6 * max(1.0, abs(fd))
