@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",
                     help="plan, warm-up and timed steps only (for ncu launch lists)")
+    ap.add_argument("--train-steps", type=int, default=6000,
+                    help="so3p: Adam steps of the proposal network (setup, not timed)")
     ap.add_argument("--workload", default="so2", choices=["so2", "scale", "batched", "so3", "so3p"],
                     help="so2: the pattern-matching sweep (default, the headline metric); "
                          "scale: scale-adaptive smoothing of a 4096x4096x3 image; "
@@ -498,7 +500,7 @@ def bench_so3p(args, world, rank, local):
     X, qt = torch.cat(rows), torch.cat(labels)
     net = ec.MLP(plan, C, 256)
     net.set_params(synth.mlp_init(11, C, 256))
-    steps, batch = 6000, 512
+    steps, batch = max(1, args.train_steps), 512
     r, Q = synth.training_draws(12, X.shape[0], steps, batch)
     losses = proposal.train(net, X, qt, L, torch.from_numpy(r).to(device), torch.from_numpy(Q).to(device), steps,
                             batch)

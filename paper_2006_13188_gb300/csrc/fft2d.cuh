@@ -147,11 +147,12 @@ __device__ __forceinline__ void ct_fft(float2* buf, int ls, int es, const float2
 }
 
 // Stage with functor I/O: load(line, idx) supplies the inputs (FIRST: from
-// anywhere, e.g. a staging buffer with a product fused in) and
-// store(line, idx, value) consumes the outputs (LAST: e.g. straight to global
-// memory); otherwise both use the padded shared-memory layout of buf.
+// anywhere, e.g. a staging buffer with a product fused in; INPLACE_FIRST: the
+// first stage's loads read buf itself, so all reads finish before any write)
+// and store(line, idx, value) consumes the outputs (LAST: e.g. straight to
+// global memory); otherwise both use the padded shared-memory layout of buf.
 template <int N, int R, int NS, bool INV, bool LINE_FAST, int NLINES, int THREADS, bool FIRST, bool LAST,
-          class Load, class Store>
+          bool INPLACE_FIRST = false, class Load, class Store>
 __device__ __forceinline__ void ct_stage_io(float2* buf, int ls, int es, const float2* __restrict__ tw, Load&& load,
                                             Store&& store) {
   constexpr int NB = N / R;
@@ -185,7 +186,7 @@ __device__ __forceinline__ void ct_stage_io(float2* buf, int ls, int es, const f
       dst_s[s] = (j / NS) * NS * R + k;
     }
   }
-  if (!FIRST && !LAST) __syncthreads();   // in place: all reads before any write
+  if ((!FIRST || INPLACE_FIRST) && !LAST) __syncthreads();   // in place: all reads before any write
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     if (line_s[s] >= 0) {
@@ -805,6 +806,113 @@ k_cols_inv_corr_pipe(const float2* __restrict__ Hh, int w, const float2* __restr
   cp_async_wait_all();
 }
 
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Shared memory of k_cols_inv_corr_pipe2: two work buffers in the padded
+// column layout, the resident H tile (linear), the twiddles.
+template <int N>
+struct Pipe2Cfg {
+  using C = LineCfg<N>;
+  static constexpr int SMEM = 2 * C::CW * C::LS * 8 + C::CW * N * 8 + N * 8;
+  static constexpr bool OK = SMEM <= 227 * 1024;
+};
+
+// Inverse column pass of H^ conj(F^_k) (Sec. 4.1 "Standard Correlation"),
+// double-buffered: the spectrum tile of the next item streams into the other
+// work buffer while this one is transformed in place.  Item order:
+//   REUSE: items (tile, component), component fastest, split into contiguous
+//          ranges, one per block; the H tile is loaded once per tile and
+//          reused by all its components (wide tiles: long contiguous writes);
+//   otherwise: component-major items, block-strided, so blocks running at
+//          the same time write adjacent tiles of one component plane (narrow
+//          tiles: their short row segments merge in L2); H is loaded per item.
+// Output Z[kk] row-major (pitch w).  HERM as in k_cols_inv_corr_pipe.
+template <int N, bool HERM, bool REUSE>
+__global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, 1)
+k_cols_inv_corr_pipe2(const float2* __restrict__ Hh, int w, const float2* __restrict__ S, int k0, int nk,
+                      float2* __restrict__ Z, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::COL_THREADS;
+  constexpr int CW = C::CW;
+  constexpr int TILE = CW * N;
+  constexpr int LS = C::LS;
+  extern __shared__ float2 sm[];
+  float2* B0 = sm;                       // CW * LS, element (v, c) at c + sidx(v) * CW
+  float2* B1 = sm + CW * LS;
+  float2* HT = sm + 2 * CW * LS;         // TILE, linear e = v * CW + c
+  const float2* TWs = stage_twiddles<N, 2 * CW * LS + TILE>(sm, tw, T);
+  const int wh = w / 2 + 1;
+  const int ntiles = (w + CW - 1) / CW;
+  const long long nitems = (long long)ntiles * nk;
+  // this block's items: i = first, first + step, ... < last
+  const int first = REUSE ? (int)(nitems * blockIdx.x / gridDim.x) : (int)blockIdx.x;
+  const int last = REUSE ? (int)(nitems * (blockIdx.x + 1) / gridDim.x) : (int)nitems;
+  const int step = REUSE ? 1 : (int)gridDim.x;
+  auto tile_of = [&](int item) { return REUSE ? item / nk : item % ntiles; };
+  auto comp_of = [&](int item) { return REUSE ? item % nk : item / ntiles; };
+
+  auto prefetch_spec = [&](int item, float2* buf) {
+    const float2* spec = S + ((size_t)(k0 + comp_of(item)) * ntiles + tile_of(item)) * TILE;
+    if (CW % 2 == 0) {
+      for (int q = threadIdx.x; q < TILE / 2; q += T) {
+        const int e = 2 * q, v = e / CW, c = e % CW;
+        cp_async16(buf + c + sidx(v) * CW, spec + e, true);
+      }
+    } else {
+      for (int e = threadIdx.x; e < TILE; e += T) cp_async8(buf + e % CW + sidx(e / CW) * CW, spec + e, true);
+    }
+    cp_async_commit();
+  };
+  auto load_h = [&](int tile) {
+    const int u0 = tile * CW;
+    for (int e = threadIdx.x; e < TILE; e += T) {
+      const int v = e / CW, u = u0 + e % CW;
+      const float2* src = Hh;
+      bool valid = u < w;
+      if (!HERM) src = valid ? Hh + (size_t)v * w + u : Hh;
+      else if (u < wh) src = Hh + (size_t)v * wh + u;
+      else if (valid) src = Hh + (size_t)((N - v) % N) * wh + (w - u);
+      cp_async8(HT + e, src, valid);
+    }
+    cp_async_commit();
+  };
+
+  if (first < last) prefetch_spec(first, B0);
+  int htile = -1, parity = 0;
+  for (int item = first; item < last; item += step, parity ^= 1) {
+    __syncthreads();                       // the previous item is done with both buffers and HT
+    float2* Bc = parity ? B1 : B0;
+    float2* Bn = parity ? B0 : B1;
+    const int tile = tile_of(item), kk = comp_of(item);
+    if (!REUSE || tile != htile) {
+      load_h(tile);
+      htile = tile;
+    }
+    if (item + step < last) {
+      prefetch_spec(item + step, Bn);
+      cp_async_wait_one();                 // this item's spectrum and H tile have landed
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();
+    const int u0 = tile * CW;
+    float2* dst = Z + (size_t)kk * N * w;
+    auto load = [&](int c, int v) -> float2 {
+      float2 hv = HT[v * CW + c];
+      if (HERM && u0 + c >= wh) hv.y = -hv.y;
+      return c_mul(hv, Bc[c + sidx(v) * CW]);
+    };
+    auto store = [&](int c, int v, float2 val) {
+      if (u0 + c < w) dst[(size_t)v * w + u0 + c] = val;
+    };
+    constexpr RadixList L = factor_radices(N);
+    constexpr int R0 = L.r[0];
+    ct_stage_io<N, R0, 1, true, true, CW, T, true, L.cnt == 1, true>(Bc, 1, CW, TWs, load, store);
+    if constexpr (L.cnt > 1) ct_fft_io<N, true, true, CW, T, 1, R0>(Bc, 1, CW, TWs, load, store);
+  }
+  cp_async_wait_all();
+}
+
 // Inverse row pass of Z writing the component planes of G (k = k0 + item / nblk).
 template <int N>
 __global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, 1)
@@ -1008,9 +1116,20 @@ bool FftOps<N>::cols_inv_corr_pipe(const float2* Hh, int w, const float2* S, int
   if constexpr (!PipeCfg<N>::COL_OK) {
     return false;
   } else {
+    const int items = ((w + C::CW - 1) / C::CW) * nk;
+    // the double-buffered pass wins for wide tiles (measured: 128-point columns
+    // 1.94 -> 1.33 ms over 231 components of 128^3); for 2048-point columns
+    // (4-column tiles) the single-buffered pass is faster (0.45 vs 0.50 ms)
+    if constexpr (Pipe2Cfg<N>::OK && C::CW >= 16) {
+      constexpr bool REUSE = true;
+      static const bool once2 = (ext_set_smem(k_cols_inv_corr_pipe2<N, true, REUSE>, Pipe2Cfg<N>::SMEM), true);
+      (void)once2;
+      const int grid = pipe_grid<N>(items, sms, Pipe2Cfg<N>::SMEM, C::COL_THREADS);
+      k_cols_inv_corr_pipe2<N, true, REUSE><<<grid, C::COL_THREADS, Pipe2Cfg<N>::SMEM, st>>>(Hh, w, S, k0, nk, Z, tw);
+      return true;
+    }
     static const bool once = (ext_set_smem(k_cols_inv_corr_pipe<N, true>, PipeCfg<N>::COL_SMEM), true);
     (void)once;
-    const int items = ((w + C::CW - 1) / C::CW) * nk;
     const int grid = pipe_grid<N>(items, sms, PipeCfg<N>::COL_SMEM, C::COL_THREADS);
     k_cols_inv_corr_pipe<N, true><<<grid, C::COL_THREADS, PipeCfg<N>::COL_SMEM, st>>>(Hh, w, S, k0, nk, Z, tw);
     return true;
@@ -1023,9 +1142,17 @@ bool FftOps<N>::cols_inv_full_pipe(const float2* H, int w, const float2* S, int 
   if constexpr (!PipeCfg<N>::COL_OK) {
     return false;
   } else {
+    const int items = ((w + C::CW - 1) / C::CW) * nk;
+    if constexpr (Pipe2Cfg<N>::OK && C::CW >= 16) {
+      constexpr bool REUSE = true;
+      static const bool once2 = (ext_set_smem(k_cols_inv_corr_pipe2<N, false, REUSE>, Pipe2Cfg<N>::SMEM), true);
+      (void)once2;
+      const int grid = pipe_grid<N>(items, sms, Pipe2Cfg<N>::SMEM, C::COL_THREADS);
+      k_cols_inv_corr_pipe2<N, false, REUSE><<<grid, C::COL_THREADS, Pipe2Cfg<N>::SMEM, st>>>(H, w, S, k0, nk, Z, tw);
+      return true;
+    }
     static const bool once = (ext_set_smem(k_cols_inv_corr_pipe<N, false>, PipeCfg<N>::COL_SMEM), true);
     (void)once;
-    const int items = ((w + C::CW - 1) / C::CW) * nk;
     const int grid = pipe_grid<N>(items, sms, PipeCfg<N>::COL_SMEM, C::COL_THREADS);
     k_cols_inv_corr_pipe<N, false><<<grid, C::COL_THREADS, PipeCfg<N>::COL_SMEM, st>>>(H, w, S, k0, nk, Z, tw);
     return true;
