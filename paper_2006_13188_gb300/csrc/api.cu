@@ -219,7 +219,47 @@ ext_status check_size(int h, int w) {
   return EXT_OK;
 }
 
-// Host/device staging of one argument.
+// ----- tensor maps (driver entry point, no link against libcuda)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    cudaGetLastError();
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Rows per tensor copy of the H tile: a divisor of h, at most 256, whose box
+// (br rows x cw complex) is a multiple of 128 bytes; 0 if none.
+int tma_rows(int h, int cw) {
+  for (int br = 256; br >= 1; --br)
+    if (h % br == 0 && (br * cw * 8) % 128 == 0) return br;
+  return 0;
+}
+
+// Tensor map of the full h x w complex spectrum as h rows of 2w floats, box
+// 2 cw floats x br rows.
+bool spectrum_tmap(const float2* Hf, int h, int w, int cw, int br, CUtensorMap* out) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * w, (cuuint64_t)h};
+  const cuuint64_t strides[1] = {(cuuint64_t)2 * w * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * cw), (cuuint32_t)br};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(Hf), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// G_k = H (*) F_k for k = 0..K into G (device, planes G_0, Re G_1, Im G_1, ...).
 ext_status run_components(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, float* G,
                           cudaStream_t st) {
   const int K = F->K;
@@ -242,10 +282,27 @@ ext_status run_components(ext_plan plan, const float* H, int h, int w, const ext
   if (plan->kchunk > 0) kc = plan->kchunk < K + 1 ? plan->kchunk : K + 1;
   void* Z = nullptr;
   EXT_TRY(ensure(plan, "Z", plane * kc, &Z));
+  // TMA-staged column pass on the full spectrum where the tile shape allows it
+  CUtensorMap tmH;
+  const int cw = fft_col_tile(h);
+  const int br = plan->tma && fft_cols_tma_ok(h) ? tma_rows(h, cw) : 0;
+  bool use_tma = false;
+  if (br > 0) {
+    void* Hf = nullptr;
+    EXT_TRY(ensure(plan, "Hf", sizeof(float2) * (size_t)h * w, &Hf));
+    use_tma = spectrum_tmap((const float2*)Hf, h, w, cw, br, &tmH);
+    if (use_tma)
+      launch(plan, "expand_hermitian", st,
+             [&] { launch_expand_hermitian((const float2*)Hh, h, w, (float2*)Hf, plan->sms, st); });
+  }
   for (int k0 = 0; k0 <= K; k0 += kc) {
     const int nk = (k0 + kc <= K + 1) ? kc : (K + 1 - k0);
     bool piped = false;
-    if (plan->pipelined)
+    if (use_tma)
+      launch(plan, "cols_inv_corr_tma", st, [&] {
+        piped = fft_cols_inv_corr_tma(h, tmH, w, br, S, k0, nk, (float2*)Z, tw_h, plan->dev_err, plan->sms, st);
+      });
+    if (!piped && plan->pipelined)
       launch(plan, "cols_inv_corr_pipe", st, [&] {
         piped = fft_cols_inv_corr_pipe(h, (const float2*)Hh, w, S, k0, nk, (float2*)Z, tw_h, plan->sms, st);
       });
@@ -326,6 +383,7 @@ ext_status ext_plan_create(ext_plan* plan, int device) {
   }
   if (const char* e = getenv("EXT_KCHUNK")) p->kchunk = atoi(e);
   if (const char* e = getenv("EXT_PIPELINED")) p->pipelined = atoi(e) != 0;
+  if (const char* e = getenv("EXT_TMA")) p->tma = atoi(e) != 0;
   *plan = p;
   return EXT_OK;
 }

@@ -13,6 +13,10 @@
 //          plane 0 = G_0, plane 2k-1 = Re G_k, plane 2k = Im G_k (k >= 1)
 #pragma once
 #include "fft_engine.cuh"
+#include "tc_common.cuh"
+#include "../../include/extconv.h"
+
+#include <cuda.h>
 
 // ---------------------------------------------------------- compile time ---
 struct RadixList {
@@ -913,6 +917,97 @@ k_cols_inv_corr_pipe2(const float2* __restrict__ Hh, int w, const float2* __rest
   cp_async_wait_all();
 }
 
+// Inverse column pass of H^ conj(F^_k) staged by the tensor memory
+// accelerator: per item one 1D bulk copy brings the spectrum tile (TILE
+// contiguous elements) and N / br 2D tensor copies bring the H tile (CW
+// columns of the FULL spectrum, rows y .. y+br-1 each) into shared memory,
+// both completing on one mbarrier; thread 0 issues them, so the other
+// threads spend no instructions on loading.  Items are component-major and
+// block-strided (blocks running together write adjacent tiles of one
+// component plane).  The next item's copies are issued as soon as the first
+// butterfly stage has consumed the staging buffers.  Every wait is bounded:
+// on expiry err = EXT_ERR_TIMEOUT and the block stops.  Output Z[kk]
+// row-major (pitch w).
+template <int N>
+struct TmaColCfg {
+  using C = LineCfg<N>;
+  static constexpr int TILE = C::CW * N;
+  // work buffer, then the two staging tiles at 128-byte aligned offsets, then twiddles
+  static constexpr int OFF_S = ((C::CW * C::LS + 15) / 16) * 16;
+  static constexpr int OFF_H = OFF_S + ((TILE + 15) / 16) * 16;
+  static constexpr int OFF_TW = OFF_H + ((TILE + 15) / 16) * 16;
+  static constexpr int SMEM = (OFF_TW + N) * 8 + 128;   // + slack to align the base to 128 bytes
+  static constexpr bool OK = SMEM <= 227 * 1024 && C::CW % 2 == 0;
+};
+
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, 1)
+k_cols_inv_corr_tma(const __grid_constant__ CUtensorMap tmH, int w, int br, const float2* __restrict__ S, int k0,
+                    int nk, float2* __restrict__ Z, const float2* __restrict__ tw, int* __restrict__ err) {
+  using C = LineCfg<N>;
+  using TC = TmaColCfg<N>;
+  constexpr int T = C::COL_THREADS;
+  constexpr int CW = C::CW;
+  constexpr int TILE = TC::TILE;
+  extern __shared__ float2 sm_raw[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int abort_flag;
+  // 128-byte aligned base for the tensor copies
+  float2* sm = reinterpret_cast<float2*>(sm_raw) + ((128 - (tc::smem_u32(sm_raw) & 127)) & 127) / 8;
+  float2* W = sm;
+  float2* SS = sm + TC::OFF_S;
+  float2* HS = sm + TC::OFF_H;
+  const float2* TWs = stage_twiddles<N, TC::OFF_TW>(sm, tw, T);
+  const int ntiles = (w + CW - 1) / CW;
+  const int nitems = ntiles * nk;
+  const uint32_t mb = tc::smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    tc::mbar_init(mb, 1);
+  }
+  __syncthreads();
+  auto issue = [&](int item) {   // thread 0
+    const int kk = item / ntiles, tile = item % ntiles;
+    tc::fence_proxy_async();      // earlier generic-proxy reads of the staging tiles come first
+    tc::mbar_expect_tx(mb, 2u * TILE * 8u);
+    tc::bulk_load(tc::smem_u32(SS), S + ((size_t)(k0 + kk) * ntiles + tile) * TILE, TILE * 8u, mb);
+    for (int y = 0; y < N; y += br) tc::tma_load_2d(tc::smem_u32(HS + y * CW), &tmH, 2 * tile * CW, y, mb);
+  };
+  uint32_t phase = 0;
+  int item = blockIdx.x;
+  bool pending = false;
+  if (item < nitems && threadIdx.x == 0) issue(item);
+  pending = item < nitems;
+  for (; item < nitems; item += gridDim.x) {
+    if (!tc::mbar_wait_bounded(mb, phase, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    phase ^= 1u;
+    pending = false;
+    const int kk = item / ntiles, tile = item % ntiles;
+    const int u0 = tile * CW;
+    float2* dst = Z + (size_t)kk * N * w;
+    const int next = item + gridDim.x;
+    auto load = [&](int c, int v) -> float2 {
+      const int e = v * CW + c;
+      return c_mul(HS[e], SS[e]);
+    };
+    auto store = [&](int c, int v, float2 val) {
+      if (u0 + c < w) dst[(size_t)v * w + u0 + c] = val;
+    };
+    constexpr RadixList L = factor_radices(N);
+    constexpr int R0 = L.r[0];
+    ct_stage_io<N, R0, 1, true, true, CW, T, true, L.cnt == 1>(W, 1, CW, TWs, load, store);
+    if (next < nitems) {
+      if (threadIdx.x == 0) issue(next);
+      pending = true;
+    }
+    if constexpr (L.cnt > 1) ct_fft_io<N, true, true, CW, T, 1, R0>(W, 1, CW, TWs, load, store);
+  }
+  // a copy still in flight (timeout path): wait for it, bounded, before the block exits
+  if (pending) tc::mbar_wait_bounded(mb, phase, 1000000000ull, err, EXT_ERR_TIMEOUT);
+}
+
 // Inverse row pass of Z writing the component planes of G (k = k0 + item / nblk).
 template <int N>
 __global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, 1)
@@ -972,6 +1067,8 @@ k_rows_inv_components_pipe(const float2* __restrict__ Z, int h, int k0, int nk, 
 template <int N>
 struct FftOps {
   using C = LineCfg<N>;
+  static bool cols_inv_corr_tma(const CUtensorMap& tmH, int w, int br, const float2* S, int k0, int nk, float2* Z,
+                                const float2* tw, int* err, int sms, cudaStream_t st);
   static void rows_r2c(const float* H, int h, float2* Hh, const float2* tw, cudaStream_t st);
   static void rows_fwd_phase(const float* H, const float* alpha, int h, int k0, int nk, float2* A,
                              const float2* tw, cudaStream_t st);
@@ -1132,6 +1229,21 @@ bool FftOps<N>::cols_inv_corr_pipe(const float2* Hh, int w, const float2* S, int
     (void)once;
     const int grid = pipe_grid<N>(items, sms, PipeCfg<N>::COL_SMEM, C::COL_THREADS);
     k_cols_inv_corr_pipe<N, true><<<grid, C::COL_THREADS, PipeCfg<N>::COL_SMEM, st>>>(Hh, w, S, k0, nk, Z, tw);
+    return true;
+  }
+}
+
+template <int N>
+bool FftOps<N>::cols_inv_corr_tma(const CUtensorMap& tmH, int w, int br, const float2* S, int k0, int nk, float2* Z,
+                                  const float2* tw, int* err, int sms, cudaStream_t st) {
+  if constexpr (!TmaColCfg<N>::OK) {
+    return false;
+  } else {
+    static const bool once = (ext_set_smem(k_cols_inv_corr_tma<N>, TmaColCfg<N>::SMEM), true);
+    (void)once;
+    const int items = ((w + C::CW - 1) / C::CW) * nk;
+    const int grid = pipe_grid<N>(items, sms, TmaColCfg<N>::SMEM, C::COL_THREADS);
+    k_cols_inv_corr_tma<N><<<grid, C::COL_THREADS, TmaColCfg<N>::SMEM, st>>>(tmH, w, br, S, k0, nk, Z, tw, err);
     return true;
   }
 }

@@ -131,3 +131,36 @@ bool fft_cols_inv_full_pipe(int h, const float2* H, int w, const float2* S, int 
   switch (h) { EXT_FFT_SIZES(EXT_C1) default: return false; }
 }
 #undef EXT_C1
+
+#define EXT_C1(N) case N: return FftOps<N>::cols_inv_corr_tma(tmH, w, br, S, k0, nk, Z, tw, err, sms, st);
+bool fft_cols_inv_corr_tma(int h, const CUtensorMap& tmH, int w, int br, const float2* S, int k0, int nk, float2* Z,
+                           const float2* tw, int* err, int sms, cudaStream_t st) {
+  switch (h) { EXT_FFT_SIZES(EXT_C1) default: return false; }
+}
+#undef EXT_C1
+
+bool fft_cols_tma_ok(int h) {
+  switch (h) {
+#define EXT_CASE(N) case N: return TmaColCfg<N>::OK;
+    EXT_FFT_SIZES(EXT_CASE)
+#undef EXT_CASE
+    default: return false;
+  }
+}
+
+// Full spectrum from the half spectrum of a real signal (Hermitian symmetry):
+// Hf[v][u] = Hh[v][u] for u <= w/2, conj(Hh[(h-v) % h][w-u]) otherwise.
+__global__ void k_expand_hermitian(const float2* __restrict__ Hh, int h, int w, float2* __restrict__ Hf) {
+  const int wh = w / 2 + 1;
+  const long long n = (long long)h * w;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(i / w), u = (int)(i % w);
+    Hf[i] = u < wh ? Hh[(size_t)v * wh + u] : c_conj(Hh[(size_t)((h - v) % h) * wh + (w - u)]);
+  }
+}
+
+void launch_expand_hermitian(const float2* Hh, int h, int w, float2* Hf, int sms, cudaStream_t st) {
+  long long b = ((long long)h * w + 255) / 256;
+  if (b > (long long)sms * 8) b = (long long)sms * 8;
+  if (b > 0) k_expand_hermitian<<<(unsigned)b, 256, 0, st>>>(Hh, h, w, Hf);
+}

@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -44,6 +45,13 @@ bool fft_cols_inv_corr_pipe(int h, const float2* Hh, int w, const float2* S, int
                             const float2* tw, int sms, cudaStream_t st);
 bool fft_rows_inv_components_pipe(int w, const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
                                   int sms, cudaStream_t st);
+// Inverse column pass staged by the tensor memory accelerator: tmH maps the
+// FULL spectrum (h rows of 2w floats, boxes of 2 * col_tile floats x br rows);
+// false if this length has no such variant.
+bool fft_cols_tma_ok(int h);
+bool fft_cols_inv_corr_tma(int h, const CUtensorMap& tmH, int w, int br, const float2* S, int k0, int nk, float2* Z,
+                           const float2* tw, int* err, int sms, cudaStream_t st);
+void launch_expand_hermitian(const float2* Hh, int h, int w, float2* Hf, int sms, cudaStream_t st);
 // 3D building blocks: in-place complex column pass over planes; inverse row
 // pass into real channel planes; full-spectrum product column pass.
 void fft_cols_c2c(int h, float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st);

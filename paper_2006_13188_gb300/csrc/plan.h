@@ -81,6 +81,7 @@ struct ext_plan_s {
   int sms = 0;           // multiprocessors of the device
   int kchunk = 0;        // components per inverse launch (0 = by L2 budget)
   bool pipelined = true; // persistent prefetching passes where they fit
+  bool tma = true;       // tensor-memory-accelerator staged column pass where it fits
   int* dev_err = nullptr; // device-side status word (bounded waits)
   // batched correlation: captured CUDA graph of the last batch and its key
   cudaGraphExec_t batch_exec = nullptr;
@@ -162,6 +163,7 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Host/device staging of one argument.
 struct Staged {
   const void* user = nullptr;
   void* dev = nullptr;
