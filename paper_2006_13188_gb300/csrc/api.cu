@@ -312,7 +312,7 @@ ext_status run_components(ext_plan plan, const float* H, int h, int w, const ext
     piped = false;
     if (plan->pipelined)
       launch(plan, "rows_inv_components_pipe", st, [&] {
-        piped = fft_rows_inv_components_pipe(w, (const float2*)Z, h, k0, nk, G, tw_w, plan->sms, st);
+        piped = fft_rows_inv_components_pipe(w, (const float2*)Z, h, k0, nk, G, tw_w, plan->dev_err, plan->sms, st);
       });
     if (!piped)
       launch(plan, "rows_inv_components", st,
@@ -823,7 +823,8 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
       if (!fft_cols_inv_corr_pipe(h, (const float2*)dHh[b], w, (const float2*)dS[b], 0, K + 1, (float2*)dZ[b], tw_h,
                                   plan->sms, bs))
         fft_cols_inv_corr(h, (const float2*)dHh[b], w, (const float2*)dS[b], 0, K + 1, (float2*)dZ[b], tw_h, bs);
-      if (!fft_rows_inv_components_pipe(w, (const float2*)dZ[b], h, 0, K + 1, (float*)dG[b], tw_w, plan->sms, bs))
+      if (!fft_rows_inv_components_pipe(w, (const float2*)dZ[b], h, 0, K + 1, (float*)dG[b], tw_w, plan->dev_err,
+                                        plan->sms, bs))
         fft_rows_inv_components(w, (const float2*)dZ[b], h, 0, K + 1, (float*)dG[b], tw_w, bs);
       ss = run_sweep(plan, (const float*)dG[b], (long long)P, K, d.n_angles, d.max_out, d.argmax, precision, bs);
     }

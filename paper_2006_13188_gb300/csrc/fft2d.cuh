@@ -1009,37 +1009,52 @@ k_cols_inv_corr_tma(const __grid_constant__ CUtensorMap tmH, int w, int br, cons
 }
 
 // Inverse row pass of Z writing the component planes of G (k = k0 + item / nblk).
+// The RL rows of the next item (contiguous in Z) arrive by one bulk copy
+// completing on an mbarrier, issued by thread 0 as soon as the first
+// butterfly stage has consumed the staging buffer; waits are bounded (err =
+// EXT_ERR_TIMEOUT, the block stops).
 template <int N>
 __global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, 1)
 k_rows_inv_components_pipe(const float2* __restrict__ Z, int h, int k0, int nk, float* __restrict__ G,
-                           const float2* __restrict__ tw) {
+                           const float2* __restrict__ tw, int* __restrict__ err) {
   using C = LineCfg<N>;
   constexpr int T = C::ROW_THREADS;
   constexpr int RL = C::RL;
+  static_assert((RL * C::LS) % 2 == 0, "staging buffer must be 16-byte aligned");
   extern __shared__ float2 sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int abort_flag;
   float2* W = sm;
   float2* ZS = sm + RL * C::LS;   // RL * N linear
   const float2* TWs = stage_twiddles<N, RL * C::LS + RL * N>(sm, tw, T);
   const size_t P = (size_t)h * N;
   const int nblk = (h + RL - 1) / RL;
   const int nitems = nblk * nk;
-
-  auto prefetch = [&](int item) {
+  const uint32_t mb = tc::smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    tc::mbar_init(mb, 1);
+  }
+  __syncthreads();
+  auto prefetch = [&](int item) {   // thread 0
     const int kk = item / nblk, y0 = (item % nblk) * RL;
-    const float2* src = Z + (size_t)kk * P + (size_t)y0 * N;
     const int rows = (h - y0) < RL ? (h - y0) : RL;
-    for (int q = threadIdx.x; q < RL * N / 2; q += T) {
-      const bool valid = 2 * q < rows * N;
-      cp_async16(ZS + 2 * q, valid ? src + 2 * q : Z, valid);
-    }
-    cp_async_commit();
+    const uint32_t bytes = (uint32_t)rows * N * 8u;
+    tc::fence_proxy_async();
+    tc::mbar_expect_tx(mb, bytes);
+    tc::bulk_load(tc::smem_u32(ZS), Z + (size_t)kk * P + (size_t)y0 * N, bytes, mb);
   };
 
+  uint32_t phase = 0;
   int item = blockIdx.x;
-  if (item < nitems) prefetch(item);
+  bool pending = item < nitems;
+  if (pending && threadIdx.x == 0) prefetch(item);
   for (; item < nitems; item += gridDim.x) {
-    cp_async_wait_all();
+    if (!tc::mbar_wait_bounded(mb, phase, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_flag = 1;
     __syncthreads();
+    if (abort_flag) break;
+    phase ^= 1u;
+    pending = false;
     const int kk = item / nblk, y0 = (item % nblk) * RL;
     const int k = k0 + kk;
     float* re = G + (k == 0 ? 0 : (size_t)(2 * k - 1) * P);
@@ -1057,10 +1072,13 @@ k_rows_inv_components_pipe(const float2* __restrict__ Z, int h, int k0, int nk, 
     constexpr RadixList L = factor_radices(N);
     constexpr int R0 = L.r[0];
     ct_stage_io<N, R0, 1, true, false, RL, T, true, L.cnt == 1>(W, C::LS, 1, TWs, load, store);
-    if (next < nitems) prefetch(next);
+    if (next < nitems) {
+      if (threadIdx.x == 0) prefetch(next);
+      pending = true;
+    }
     if constexpr (L.cnt > 1) ct_fft_io<N, true, false, RL, T, 1, R0>(W, C::LS, 1, TWs, load, store);
   }
-  cp_async_wait_all();
+  if (pending) tc::mbar_wait_bounded(mb, phase, 1000000000ull, err, EXT_ERR_TIMEOUT);
 }
 
 // ------------------------------------------------------------- launchers ---
@@ -1097,7 +1115,7 @@ struct FftOps {
   static bool cols_inv_corr_pipe(const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
                                  const float2* tw, int sms, cudaStream_t st);
   static bool rows_inv_components_pipe(const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
-                                       int sms, cudaStream_t st);
+                                       int* err, int sms, cudaStream_t st);
 };
 
 template <typename KernelT>
@@ -1292,7 +1310,7 @@ void FftOps<N>::rows_inv_channels(const float2* Z, int rows, int k0, int nk, con
 
 template <int N>
 bool FftOps<N>::rows_inv_components_pipe(const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
-                                         int sms, cudaStream_t st) {
+                                         int* err, int sms, cudaStream_t st) {
   if constexpr (!PipeCfg<N>::ROW_OK) {
     return false;
   } else {
@@ -1300,7 +1318,7 @@ bool FftOps<N>::rows_inv_components_pipe(const float2* Z, int h, int k0, int nk,
     (void)once;
     const int items = ((h + C::RL - 1) / C::RL) * nk;
     const int grid = pipe_grid<N>(items, sms, PipeCfg<N>::ROW_SMEM, C::ROW_THREADS);
-    k_rows_inv_components_pipe<N><<<grid, C::ROW_THREADS, PipeCfg<N>::ROW_SMEM, st>>>(Z, h, k0, nk, G, tw);
+    k_rows_inv_components_pipe<N><<<grid, C::ROW_THREADS, PipeCfg<N>::ROW_SMEM, st>>>(Z, h, k0, nk, G, tw, err);
     return true;
   }
 }

@@ -98,9 +98,9 @@ bool fft_cols_inv_corr_pipe(int h, const float2* Hh, int w, const float2* S, int
 }
 #undef EXT_C1
 
-#define EXT_C1(N) case N: return FftOps<N>::rows_inv_components_pipe(Z, h, k0, nk, G, tw, sms, st);
+#define EXT_C1(N) case N: return FftOps<N>::rows_inv_components_pipe(Z, h, k0, nk, G, tw, err, sms, st);
 bool fft_rows_inv_components_pipe(int w, const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
-                                  int sms, cudaStream_t st) {
+                                  int* err, int sms, cudaStream_t st) {
   switch (w) { EXT_FFT_SIZES(EXT_C1) default: return false; }
 }
 #undef EXT_C1

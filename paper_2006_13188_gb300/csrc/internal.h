@@ -44,7 +44,7 @@ void fft_cols_inv_corr(int h, const float2* Hh, int w, const float2* S, int k0, 
 bool fft_cols_inv_corr_pipe(int h, const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
                             const float2* tw, int sms, cudaStream_t st);
 bool fft_rows_inv_components_pipe(int w, const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
-                                  int sms, cudaStream_t st);
+                                  int* err, int sms, cudaStream_t st);
 // Inverse column pass staged by the tensor memory accelerator: tmH maps the
 // FULL spectrum (h rows of 2w floats, boxes of 2 * col_tile floats x br rows);
 // false if this length has no such variant.
