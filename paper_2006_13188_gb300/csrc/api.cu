@@ -687,7 +687,7 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
   EXT_CUDA(cudaSetDevice(plan->device));
   cudaStream_t st = (cudaStream_t)stream;
   // ---- validate, size the workspaces, pack the filter data
-  size_t max_S = 0, max_grid = 0, max_Hh = 0, max_Z = 0, max_G = 0, max_polar = 0;
+  size_t max_S = 0, max_grid = 0, max_Hh = 0, max_Hf = 0, max_Z = 0, max_G = 0, max_polar = 0;
   std::vector<size_t> off_in(n), off_coef(n);
   std::vector<int> nr(n);
   size_t host_bytes = 0, coef_bytes = 0;
@@ -708,6 +708,7 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
     max_S = std::max(max_S, sizeof(float2) * (size_t)(K + 1) * ((d.w + cw - 1) / cw) * d.h * cw);
     max_grid = std::max(max_grid, sizeof(float2) * P * std::min<size_t>(K + 1, std::max<size_t>(1, (512ull << 20) / (8 * P))));
     max_Hh = std::max(max_Hh, sizeof(float2) * (size_t)d.h * (d.w / 2 + 1));
+    max_Hf = std::max(max_Hf, sizeof(float2) * P);
     max_Z = std::max(max_Z, sizeof(float2) * P * (K + 1));
     max_G = std::max(max_G, sizeof(float) * P * (2 * K + 1));
     const size_t nk = (size_t)(2 * K + 1);
@@ -730,22 +731,27 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
   }
   key = fnv1a(key, &precision, sizeof(int));
   // independent images run on NB parallel branches of the graph, each with its own workspace set
-  const int NB = n < 4 ? n : 4;
-  static const char* kS[4] = {"Sbatch0", "Sbatch1", "Sbatch2", "Sbatch3"};
-  static const char* kGrid[4] = {"grid0", "grid1", "grid2", "grid3"};
-  static const char* kHh[4] = {"Hh0", "Hh1", "Hh2", "Hh3"};
-  static const char* kZ[4] = {"Z0", "Z1", "Z2", "Z3"};
-  static const char* kG[4] = {"G0", "G1", "G2", "G3"};
-  static const char* kP[4] = {"fpolar0", "fpolar1", "fpolar2", "fpolar3"};
-  void *dS[4], *dgrid[4], *dHh[4], *dZ[4], *dG[4], *dpolar[4], *din, *dcoef;
+  constexpr int NBMAX = 8;
+  const int NB = n < NBMAX ? n : NBMAX;
+  std::string kS[NBMAX], kGrid[NBMAX], kHh[NBMAX], kHf[NBMAX], kZ[NBMAX], kG[NBMAX], kP[NBMAX];
+  void *dS[NBMAX], *dgrid[NBMAX], *dHh[NBMAX], *dHf[NBMAX], *dZ[NBMAX], *dG[NBMAX], *dpolar[NBMAX], *din, *dcoef;
   for (int b = 0; b < NB; ++b) {
-    EXT_TRY(ensure(plan, kS[b], max_S, &dS[b]));
-    EXT_TRY(ensure(plan, kGrid[b], max_grid, &dgrid[b]));
-    EXT_TRY(ensure(plan, kHh[b], max_Hh, &dHh[b]));
-    EXT_TRY(ensure(plan, kZ[b], max_Z, &dZ[b]));
-    EXT_TRY(ensure(plan, kG[b], max_G, &dG[b]));
-    EXT_TRY(ensure(plan, kP[b], std::max<size_t>(max_polar, 8), &dpolar[b]));
-    for (void* q : {dS[b], dgrid[b], dHh[b], dZ[b], dG[b], dpolar[b]}) key = fnv1a(key, &q, sizeof(q));
+    const std::string t = std::to_string(b);
+    kS[b] = "Sbatch" + t;
+    kGrid[b] = "grid" + t;
+    kHh[b] = "Hh" + t;
+    kHf[b] = "Hf" + t;
+    kZ[b] = "Z" + t;
+    kG[b] = "G" + t;
+    kP[b] = "fpolar" + t;
+    EXT_TRY(ensure(plan, kS[b].c_str(), max_S, &dS[b]));
+    EXT_TRY(ensure(plan, kGrid[b].c_str(), max_grid, &dgrid[b]));
+    EXT_TRY(ensure(plan, kHh[b].c_str(), max_Hh, &dHh[b]));
+    EXT_TRY(ensure(plan, kHf[b].c_str(), plan->tma ? max_Hf : 16, &dHf[b]));
+    EXT_TRY(ensure(plan, kZ[b].c_str(), max_Z, &dZ[b]));
+    EXT_TRY(ensure(plan, kG[b].c_str(), max_G, &dG[b]));
+    EXT_TRY(ensure(plan, kP[b].c_str(), std::max<size_t>(max_polar, 8), &dpolar[b]));
+    for (void* q : {dS[b], dgrid[b], dHh[b], dHf[b], dZ[b], dG[b], dpolar[b]}) key = fnv1a(key, &q, sizeof(q));
   }
   EXT_TRY(ensure(plan, "batch_in", host_bytes, &din));
   EXT_TRY(ensure(plan, "batch_coef", coef_bytes, &dcoef));
@@ -781,8 +787,8 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
     }
     const bool profiling = plan->profiling;
     plan->profiling = false;   // no event records inside the graph
-    cudaStream_t cs = nullptr, br[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t cs = nullptr, br[NBMAX] = {};
+    cudaEvent_t fork = nullptr, join[NBMAX] = {};
     EXT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     for (int b = 0; b < NB; ++b) {
       EXT_CUDA(cudaStreamCreateWithFlags(&br[b], cudaStreamNonBlocking));
@@ -812,7 +818,7 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
       auto sample = [&](int k0, int nk, float2* grid) {
         launch_component_grid(kind, K, k0, coef, nr[i], dr, F->sigma, F->R, h, w, grid, bs, nk);
       };
-      ss = build_spectra(plan, h, w, K + 1, SPEC_CORR, bs, sample, (float2*)dS[b], kGrid[b]);
+      ss = build_spectra(plan, h, w, K + 1, SPEC_CORR, bs, sample, (float2*)dS[b], kGrid[b].c_str());
       if (ss != EXT_OK) break;
       const float2 *tw_w = nullptr, *tw_h = nullptr;
       twiddle(plan, w, bs, &tw_w);
@@ -820,8 +826,17 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
       const int wh = w / 2 + 1;
       fft_rows_r2c(w, d.H, h, (float2*)dHh[b], tw_w, bs);
       fft_cols_fwd_half(h, (float2*)dHh[b], wh, tw_h, bs);
-      if (!fft_cols_inv_corr_pipe(h, (const float2*)dHh[b], w, (const float2*)dS[b], 0, K + 1, (float2*)dZ[b], tw_h,
-                                  plan->sms, bs))
+      bool done = false;
+      const int cw = fft_col_tile(h);
+      const int brows = plan->tma && fft_cols_tma_ok(h) ? tma_rows(h, cw) : 0;
+      CUtensorMap tmH;
+      if (brows > 0 && spectrum_tmap((const float2*)dHf[b], h, w, cw, brows, &tmH)) {
+        launch_expand_hermitian((const float2*)dHh[b], h, w, (float2*)dHf[b], plan->sms, bs);
+        done = fft_cols_inv_corr_tma(h, tmH, w, brows, (const float2*)dS[b], 0, K + 1, (float2*)dZ[b], tw_h,
+                                     plan->dev_err, plan->sms, bs);
+      }
+      if (!done && !fft_cols_inv_corr_pipe(h, (const float2*)dHh[b], w, (const float2*)dS[b], 0, K + 1,
+                                           (float2*)dZ[b], tw_h, plan->sms, bs))
         fft_cols_inv_corr(h, (const float2*)dHh[b], w, (const float2*)dS[b], 0, K + 1, (float2*)dZ[b], tw_h, bs);
       if (!fft_rows_inv_components_pipe(w, (const float2*)dZ[b], h, 0, K + 1, (float*)dG[b], tw_w, plan->dev_err,
                                         plan->sms, bs))
