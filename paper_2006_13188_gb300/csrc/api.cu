@@ -219,24 +219,6 @@ ext_status check_size(int h, int w) {
   return EXT_OK;
 }
 
-// ----- tensor maps (driver entry point, no link against libcuda)
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_tiled() {
-  static EncodeTiledFn fn = [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      p = nullptr;
-    cudaGetLastError();
-    return reinterpret_cast<EncodeTiledFn>(p);
-  }();
-  return fn;
-}
-
 // Rows per tensor copy of the H tile: a divisor of h, at most 256, whose box
 // (br rows x cw complex) is a multiple of 128 bytes; 0 if none.
 int tma_rows(int h, int cw) {
@@ -248,15 +230,8 @@ int tma_rows(int h, int cw) {
 // Tensor map of the full h x w complex spectrum as h rows of 2w floats, box
 // 2 cw floats x br rows.
 bool spectrum_tmap(const float2* Hf, int h, int w, int cw, int br, CUtensorMap* out) {
-  EncodeTiledFn fn = encode_tiled();
-  if (!fn) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)2 * w, (cuuint64_t)h};
-  const cuuint64_t strides[1] = {(cuuint64_t)2 * w * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)(2 * cw), (cuuint32_t)br};
-  const cuuint32_t estr[2] = {1, 1};
-  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(Hf), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return make_tmap_2d_f32(Hf, (unsigned long long)2 * w, (unsigned long long)h, (unsigned long long)2 * w * sizeof(float),
+                          (unsigned)(2 * cw), (unsigned)br, out);
 }
 
 // G_k = H (*) F_k for k = 0..K into G (device, planes G_0, Re G_1, Im G_1, ...).

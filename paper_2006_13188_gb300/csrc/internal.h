@@ -45,6 +45,10 @@ bool fft_cols_inv_corr_pipe(int h, const float2* Hh, int w, const float2* S, int
                             const float2* tw, int sms, cudaStream_t st);
 bool fft_rows_inv_components_pipe(int w, const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
                                   int* err, int sms, cudaStream_t st);
+// 2D FP32 tensor map (dim0 fastest, row pitch stride1_bytes, box box0 x box1);
+// false if the driver entry point is missing or alignment rules are not met.
+bool make_tmap_2d_f32(const void* base, unsigned long long dim0, unsigned long long dim1,
+                      unsigned long long stride1_bytes, unsigned box0, unsigned box1, CUtensorMap* out);
 // Inverse column pass staged by the tensor memory accelerator: tmH maps the
 // FULL spectrum (h rows of 2w floats, boxes of 2 * col_tile floats x br rows);
 // false if this length has no such variant.

@@ -16,6 +16,7 @@
 // through an mbarrier; every wait is bounded in time and reports a timeout
 // through the error word instead of hanging.
 #include "internal.h"
+#include "tc_common.cuh"
 
 #include <cuda_bf16.h>
 
@@ -277,11 +278,224 @@ bool dispatch_j(const float* G, long long P, int K, int J, const float* B, int c
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined variant.  The component planes of a 128-pixel tile (G_0 and the
+// 2K channels: a [2K+1][128] FP32 box) arrive by one tensor copy into a ring
+// of NST stages, issued NST tiles ahead; each thread splits its pixel's
+// channels into BF16 hi / lo blocks; the three products A_hi B_hi, A_hi B_lo,
+// A_lo B_hi accumulate into one of two TMEM accumulators, so the MMA of tile
+// i runs while the max/argmax of tile i-1 is read from the other.  Waits are
+// bounded; on expiry err = EXT_ERR_TIMEOUT and the block stops after its
+// copies in flight have landed (bounded as well).
+template <int KC, int JP, int NST>
+struct Tc2Cfg {
+  static constexpr int C1 = 2 * KC + 1;                 // box rows: G_0 + up to 2 KC channels (padded)
+  static constexpr int STAGE_BYTES = 128 * 4 * 33;      // room for the largest box (K = 16: 33 rows)
+  static constexpr int A_BYTES = TILE_M * KC * 2;       // one BF16 block of a tile
+  static constexpr int B_BYTES = JP * KC * 2;
+  static constexpr int SBO = (KC / 8) * 128;
+  static constexpr int OFF_A = NST * STAGE_BYTES;       // A_hi[2], A_lo[2]
+  static constexpr int OFF_B = OFF_A + 4 * A_BYTES;     // B_hi, B_lo
+  static constexpr int SMEM = OFF_B + 2 * B_BYTES + 1024;
+  static constexpr int TCOLS = 2 * JP <= 32 ? 32 : (2 * JP <= 64 ? 64 : (2 * JP <= 128 ? 128 : 256));
+};
+
+template <int KC, int JP, int NST>
+__global__ void __launch_bounds__(THREADS, 1) k_sweep_tc2(const __grid_constant__ CUtensorMap tmG, long long P, int C2,
+                                                         int J, const float* __restrict__ B, int cp,
+                                                         float* __restrict__ maxv, int32_t* __restrict__ argmax,
+                                                         int* __restrict__ err, unsigned long long limit_ns) {
+  using CF = Tc2Cfg<KC, JP, NST>;
+  constexpr uint32_t IDESC = make_idesc(TILE_M, JP);
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
+  __shared__ __align__(8) uint64_t full[NST];
+  __shared__ __align__(8) uint64_t mma_done[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* Bhi = smem + CF::OFF_B;
+  unsigned char* Blo = Bhi + CF::B_BYTES;
+  // B split into hi / lo blocks, rows = angles, K-major core matrices
+  for (int q = tid; q < JP * (KC / 8); q += THREADS) {
+    const int n = q / (KC / 8), kb = q % (KC / 8);
+    uint32_t wh[4], wl[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float eh[2], el[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c = kb * 8 + 2 * t + u;
+        const float b = (n < J && c < C2) ? B[(size_t)n * cp + c] : 0.f;
+        eh[u] = __bfloat162float(__float2bfloat16_rn(b));
+        el[u] = b - eh[u];
+      }
+      wh[t] = pack_bf16(eh[0], eh[1]);
+      wl[t] = pack_bf16(el[0], el[1]);
+    }
+    const int off = (n / 8) * CF::SBO + kb * 128 + (n % 8) * 16;
+    *reinterpret_cast<uint4*>(Bhi + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+    *reinterpret_cast<uint4*>(Blo + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < NST; ++s) tc::mbar_init(tc::smem_u32(&full[s]), 1);
+    tc::mbar_init(tc::smem_u32(&mma_done[0]), 1);
+    tc::mbar_init(tc::smem_u32(&mma_done[1]), 1);
+  }
+  if (warp == 0) tc::tmem_alloc<CF::TCOLS>(tc::smem_u32(&tmem_slot));
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_slot;
+  const long long ntiles = (P + TILE_M - 1) / TILE_M;
+  const int rows = C2 + 1;
+  const uint32_t stage_tx = (uint32_t)rows * TILE_M * 4u;
+  auto tile_of = [&](long long li) { return (long long)blockIdx.x + li * gridDim.x; };
+  auto issue = [&](long long li) {   // thread 0
+    const int s = (int)(li % NST);
+    tc::fence_proxy_async();
+    tc::mbar_expect_tx(tc::smem_u32(&full[s]), stage_tx);
+    tc::tma_load_2d(tc::smem_u32(smem + s * CF::STAGE_BYTES), &tmG, (int)(tile_of(li) * TILE_M), 0,
+                    tc::smem_u32(&full[s]));
+  };
+  long long nloc = 0;   // tiles of this block
+  if ((long long)blockIdx.x < ntiles) nloc = (ntiles - 1 - blockIdx.x) / gridDim.x + 1;
+  if (tid == 0)
+    for (long long li = 0; li < NST && li < nloc; ++li) issue(li);
+  long long issued = nloc < NST ? nloc : NST;
+  float g0_prev = 0.f;
+  long long li = 0;
+  // max/argmax of tile li_e (accumulator li_e & 1) to global memory
+  auto epilogue = [&](long long li_e, float g0) {
+    const int b = (int)(li_e & 1);
+    if (!tc::mbar_wait_bounded(tc::smem_u32(&mma_done[b]), (uint32_t)((li_e >> 1) & 1), limit_ns, err,
+                               EXT_ERR_TIMEOUT))
+      abort_flag = 1;
+    tc::fence_after();
+    float best = 0.f;
+    int bj = 0;
+#pragma unroll
+    for (int c0 = 0; c0 < JP; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * JP + c0), v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int j = c0 + i;
+        if (j == 0) {
+          best = v[i];
+        } else if ((JP == 16 || j < J) && v[i] > best) {
+          best = v[i];
+          bj = j;
+        }
+      }
+    }
+    const long long p = tile_of(li_e) * TILE_M + tid;
+    if (p < P && !abort_flag) {
+      maxv[p] = g0 + best;
+      argmax[p] = bj;
+    }
+    tc::fence_before();
+  };
+  for (; li < nloc; ++li) {
+    const int s = (int)(li % NST);
+    const int b = (int)(li & 1);
+    if (!tc::mbar_wait_bounded(tc::smem_u32(&full[s]), (uint32_t)((li / NST) & 1), limit_ns, err, EXT_ERR_TIMEOUT))
+      abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    // this thread's pixel: channels from the stage, split into the A blocks of accumulator b
+    const float* st = reinterpret_cast<const float*>(smem + s * CF::STAGE_BYTES);
+    const float g0 = st[tid];
+    unsigned char* Ahi = smem + CF::OFF_A + b * CF::A_BYTES;
+    unsigned char* Alo = smem + CF::OFF_A + (2 + b) * CF::A_BYTES;
+    const int rowoff = (tid / 8) * CF::SBO + (tid % 8) * 16;
+#pragma unroll
+    for (int kb = 0; kb < KC / 8; ++kb) {
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int c = kb * 8 + 2 * t;
+        const float x0 = c < C2 ? st[(c + 1) * TILE_M + tid] : 0.f;
+        const float x1 = c + 1 < C2 ? st[(c + 2) * TILE_M + tid] : 0.f;
+        const float h0 = __bfloat162float(__float2bfloat16_rn(x0)), h1 = __bfloat162float(__float2bfloat16_rn(x1));
+        hi[t] = pack_bf16(x0, x1);
+        lo[t] = pack_bf16(x0 - h0, x1 - h1);
+      }
+      *reinterpret_cast<uint4*>(Ahi + rowoff + kb * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(Alo + rowoff + kb * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      if (issued < nloc) issue(issued);   // the stage just consumed takes tile `issued` (= li + NST)
+      const uint32_t d = tmem + (uint32_t)(b * JP);
+      const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo), bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+#pragma unroll
+      for (int k = 0; k < KC / 16; ++k) {
+        tc::mma_bf16(d, tc::make_desc(ah + k * 256, 128, CF::SBO), tc::make_desc(bh + k * 256, 128, CF::SBO), IDESC,
+                     k > 0 ? 1u : 0u);
+        tc::mma_bf16(d, tc::make_desc(ah + k * 256, 128, CF::SBO), tc::make_desc(bl + k * 256, 128, CF::SBO), IDESC,
+                     1u);
+        tc::mma_bf16(d, tc::make_desc(al + k * 256, 128, CF::SBO), tc::make_desc(bh + k * 256, 128, CF::SBO), IDESC,
+                     1u);
+      }
+      tc::mma_commit(tc::smem_u32(&mma_done[b]));
+    }
+    if (issued < nloc) ++issued;
+    // the previous tile's max/argmax while this tile's MMAs run
+    if (li > 0) epilogue(li - 1, g0_prev);
+    g0_prev = g0;
+  }
+  if (!abort_flag && nloc > 0) epilogue(nloc - 1, g0_prev);
+  // copies and MMAs still in flight after an abort: let them finish (bounded) before the block exits
+  if (abort_flag && tid == 0) {
+    for (long long q = li; q < issued; ++q)
+      tc::mbar_wait_bounded(tc::smem_u32(&full[q % NST]), (uint32_t)((q / NST) & 1), limit_ns, err, EXT_ERR_TIMEOUT);
+    if (li > 0)
+      tc::mbar_wait_bounded(tc::smem_u32(&mma_done[(li - 1) & 1]), (uint32_t)(((li - 1) >> 1) & 1), limit_ns, err,
+                            EXT_ERR_TIMEOUT);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc<CF::TCOLS>(tmem);
+  }
+}
+
+template <int KC, int JP>
+bool launch_tc2(const float* G, long long P, int K, int J, const float* B, int cp, float* maxv, int32_t* argmax,
+                int* err, int sms, cudaStream_t st) {
+  constexpr int NST = 2;
+  using CF = Tc2Cfg<KC, JP, NST>;
+  CUtensorMap tm;
+  // G as rows of P floats: plane 0 = G_0, planes 1..2K the channels; one box = 2K+1 planes x 128 pixels
+  if (P % 4 != 0 || !make_tmap_2d_f32(G, (unsigned long long)P, (unsigned long long)(2 * K + 1),
+                                      (unsigned long long)P * 4, TILE_M, (unsigned)(2 * K + 1), &tm))
+    return false;
+  static const bool once =
+      (cudaFuncSetAttribute(k_sweep_tc2<KC, JP, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM), true);
+  (void)once;
+  const long long ntiles = (P + TILE_M - 1) / TILE_M;
+  const int per_sm = (227 * 1024) / (CF::SMEM + 1024) < 1 ? 1 : (227 * 1024) / (CF::SMEM + 1024);
+  long long grid = (long long)sms * (per_sm < 512 / CF::TCOLS ? per_sm : 512 / CF::TCOLS);
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  k_sweep_tc2<KC, JP, NST><<<(unsigned)grid, THREADS, CF::SMEM, st>>>(tm, P, 2 * K, J, B, cp, maxv, argmax, err,
+                                                                      1000000000ull);
+  return true;
+}
+
 }  // namespace
 
 bool sweep_bf16x3(const float* G, long long P, int K, int J, const float* B, int cp, float* maxv, int32_t* argmax,
                   int* err, int sms, cudaStream_t st) {
   if (K < 1 || K > 16 || J < 1 || J > 128) return false;
+  // the pipelined tensor-copy variant for the common shapes; the register-prefetch one otherwise
+  if (K > 8 && (J + 15) / 16 * 16 == 64 && launch_tc2<32, 64>(G, P, K, J, B, cp, maxv, argmax, err, sms, st))
+    return true;
   if (2 * K <= 16) return dispatch_j<16>(G, P, K, J, B, cp, maxv, argmax, err, sms, st);
   return dispatch_j<32>(G, P, K, J, B, cp, maxv, argmax, err, sms, st);
 }
