@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",
                     help="plan, warm-up and timed steps only (for ncu launch lists)")
+    ap.add_argument("--so3-size", type=int, default=128,
+                    help="so3 / so3p: volume side (128 is the workload; smaller only for profiling captures)")
     ap.add_argument("--train-steps", type=int, default=6000,
                     help="so3p: Adam steps of the proposal network (setup, not timed)")
     ap.add_argument("--workload", default="so2", choices=["so2", "scale", "batched", "so3", "so3p"],
@@ -397,7 +399,8 @@ def bench_so3(args, world, rank, local):
     import synth
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    prob = synth.so3_match_problem(seed=synth.seed_for(5) + rank)
+    prob = synth.so3_match_problem(seed=synth.seed_for(5) + rank, size=args.so3_size,
+                                     n_plant=16 if args.so3_size >= 128 else 4)
     grid = synth.so3_rotation_grid()
     n = prob["V"].shape[0]
     P = n ** 3
@@ -453,7 +456,8 @@ def bench_so3(args, world, rank, local):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 FFT + bf16x3 sweep (f32 accumulate)", "data": "synthetic",
-            "config": {"workload": SO3_WORKLOAD, "plan_ms": plan_ms, "l2": "256 MB written between steps"},
+            "config": {"workload": SO3_WORKLOAD, "volume_side": n, "plan_ms": plan_ms,
+                       "l2": "256 MB written between steps"},
             "clocks": clk.summary(),
             "plain_fp32": {"value": world * plain_steps * P / (plain * 1e-3) / 1e6, "unit": "Mvox/s",
                            "ms_per_step": plain / plain_steps},
@@ -480,7 +484,8 @@ def bench_so3p(args, world, rank, local):
     import synth
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    prob = synth.so3_match_problem(seed=synth.seed_for(5) + rank)
+    prob = synth.so3_match_problem(seed=synth.seed_for(5) + rank, size=args.so3_size,
+                                     n_plant=16 if args.so3_size >= 128 else 4)
     tables, grid = prob["tables"], synth.so3_rotation_grid()
     n = prob["V"].shape[0]
     P = n ** 3
@@ -577,7 +582,8 @@ def bench_so3p(args, world, rank, local):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 FFT + bf16 MLP + f32 refinement + bf16x3 sweep", "data": "synthetic",
-            "config": {"workload": SO3P_WORKLOAD, "plan_ms": plan_ms, "train_ms": train_ms, "bound": bound,
+            "config": {"workload": SO3P_WORKLOAD, "volume_side": n, "plan_ms": plan_ms, "train_ms": train_ms,
+                       "bound": bound,
                        "train_loss_first_last": [float(losses[:50].mean()), float(losses[-50:].mean())],
                        "voxels_ub_ge_B": nub, "candidates": nc, "swept": nf, "l2": "256 MB written between steps"},
             "clocks": clk.summary(),

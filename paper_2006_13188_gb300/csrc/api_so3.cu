@@ -713,7 +713,7 @@ ext_status ext_so3_upper_bound(ext_plan plan, const float* G, int64_t n_vox, int
   const So3Steer* tab = nullptr;
   EXT_TRY(steer_table(plan, L, st, &tab));
   launch(plan, "so3_upper_bound", st,
-         [&] { launch_so3_upper_bound((const float*)sG.dev, n_vox, tab, (float*)sU.dev, plan->sms, st); });
+         [&] { launch_so3_upper_bound((const float*)sG.dev, n_vox, tab, (float*)sU.dev, L, plan->sms, st); });
   EXT_CUDA(cudaGetLastError());
   EXT_TRY(stage_out_finish(sU, st));
   return finish_host(plan, sG.host || sU.host, st);
@@ -828,7 +828,7 @@ ext_status so3_propose(ext_plan plan, const float* G, long long P, int L, ext_ml
   EXT_TRY(ensure(plan, "prop_scratch", compact_scratch_bytes(P), &scratch));
   int* dcnt = (int*)cnt;
   // stage 1: the Frobenius bound over every voxel
-  launch(plan, "so3_upper_bound", st, [&] { launch_so3_upper_bound(G, P, tab, (float*)ub, plan->sms, st); });
+  launch(plan, "so3_upper_bound", st, [&] { launch_so3_upper_bound(G, P, tab, (float*)ub, L, plan->sms, st); });
   launch(plan, "compact", st, [&] { compact((const float*)ub, P, bound, 0, (int32_t*)cand1, dcnt, scratch, st); });
   launch(plan, "so3_fill", st, [&] { launch_so3_fill(P, score, quat, grid_idx, st); });
   EXT_CUDA(cudaGetLastError());

@@ -144,7 +144,8 @@ struct So3Steer {
   unsigned char l[256];  // degree of each entry (entries are ordered by degree)
   float coef[7][256];
 };
-void launch_so3_upper_bound(const float* G, long long P, const So3Steer* tab, float* ub, int sms, cudaStream_t st);
+void launch_so3_upper_bound(const float* G, long long P, const So3Steer* tab, float* ub, int L, int sms,
+                            cudaStream_t st);
 // ordered compaction: idx[k] = the k-th i with (below ? v[i] < thr : v[i] >= thr); *count = their number
 size_t compact_scratch_bytes(long long n);
 void compact(const float* v, long long n, float thr, int below, int32_t* idx, int* count, void* scratch,

@@ -113,46 +113,47 @@ __device__ void load_steer(const So3Steer* __restrict__ tab, float (*coef)[256],
 }  // namespace
 
 // ------------------------------------------------------------ upper bound ---
-// UB(p) = sum_l sqrt(2l+1) |G_l(p)|_F, |G_l|_F^2 = G_self^2 + 2 sum over the
-// pair entries of degree l of |G_l^ab|^2; the unique entries come ordered by l.
-__global__ void k_so3_upper_bound(const float* __restrict__ G, long long P, const So3Steer* __restrict__ tab,
-                                  float* __restrict__ ub) {
-  __shared__ uint32_t meta[256];
-  __shared__ unsigned char lv[256];
-  const int nent = tab->n;
-  for (int i = threadIdx.x; i < nent; i += blockDim.x) {
-    meta[i] = tab->meta[i];
-    lv[i] = tab->l[i];
-  }
-  __syncthreads();
+// UB(p) = sum_l sqrt(2l+1) |G_l(p)|_F.  In the channel layout degree l owns
+// the (2l+1)^2 channels from l(2l-1)(2l+1)/3 on: first its self channel
+// (weight 1 in |G_l|_F^2), then Re/Im pairs standing for two entries each
+// (weight 2).  One voxel per thread; the channel loop is unrolled so that
+// many independent loads are in flight.
+template <int L>
+__global__ void __launch_bounds__(256) k_so3_upper_bound(const float* __restrict__ G, long long P,
+                                                         float* __restrict__ ub) {
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
-    float u = 0.f, acc = 0.f;
-    int cur = 0;
-    for (int e = 0; e < nent; ++e) {
-      const int l = lv[e];
-      if (l != cur) {
-        u += sqrtf((2.f * cur + 1.f) * acc);
-        acc = 0.f;
-        cur = l;
+    float u = 0.f;
+#pragma unroll
+    for (int l = 0; l <= L; ++l) {
+      const int c0 = l * (2 * l - 1) * (2 * l + 1) / 3, c1 = c0 + (2 * l + 1) * (2 * l + 1);
+      const float g0 = __ldg(G + (size_t)c0 * P + p);
+      float acc = g0 * g0, acc2 = 0.f;
+#pragma unroll 8
+      for (int c = c0 + 1; c < c1; ++c) {
+        const float x = __ldg(G + (size_t)c * P + p);
+        acc2 = fmaf(x, x, acc2);
       }
-      const uint32_t m = meta[e];
-      const int ch = m & 1023u;
-      const float re = __ldg(G + (size_t)ch * P + p);
-      if (m & (1u << 10)) {
-        acc += re * re;
-      } else {
-        const float im = __ldg(G + (size_t)(ch + 1) * P + p);
-        acc += 2.f * (re * re + im * im);
-      }
+      u += sqrtf((2.f * l + 1.f) * (acc + 2.f * acc2));
     }
-    ub[p] = u + sqrtf((2.f * cur + 1.f) * acc);
+    ub[p] = u;
   }
 }
 
-void launch_so3_upper_bound(const float* G, long long P, const So3Steer* tab, float* ub, int sms, cudaStream_t st) {
+void launch_so3_upper_bound(const float* G, long long P, const So3Steer* tab, float* ub, int L, int sms,
+                            cudaStream_t st) {
+  (void)tab;
   long long b = (P + 255) / 256;
-  if (b > (long long)sms * 8) b = (long long)sms * 8;
-  if (P > 0) k_so3_upper_bound<<<(unsigned)b, 256, 0, st>>>(G, P, tab, ub);
+  if (b > (long long)sms * 16) b = (long long)sms * 16;
+  if (P <= 0) return;
+  switch (L) {
+    case 0: k_so3_upper_bound<0><<<(unsigned)b, 256, 0, st>>>(G, P, ub); break;
+    case 1: k_so3_upper_bound<1><<<(unsigned)b, 256, 0, st>>>(G, P, ub); break;
+    case 2: k_so3_upper_bound<2><<<(unsigned)b, 256, 0, st>>>(G, P, ub); break;
+    case 3: k_so3_upper_bound<3><<<(unsigned)b, 256, 0, st>>>(G, P, ub); break;
+    case 4: k_so3_upper_bound<4><<<(unsigned)b, 256, 0, st>>>(G, P, ub); break;
+    case 5: k_so3_upper_bound<5><<<(unsigned)b, 256, 0, st>>>(G, P, ub); break;
+    default: k_so3_upper_bound<6><<<(unsigned)b, 256, 0, st>>>(G, P, ub); break;
+  }
 }
 
 // ------------------------------------------------------- ordered compaction ---
@@ -581,29 +582,33 @@ void launch_check_index(const int32_t* idx, long long n, long long upper, int* b
 // inequality; rank R <= m - 2), with |P|_* = sqrt(|P|_F^2 + 2 sqrt(det P P^H))
 // in closed form; q1, q2 from one block power step G G^H on the two columns of
 // largest norm.  Per degree the smaller of this and sqrt(m) |G_l|_F is kept;
-// small margins cover FP32 rounding.  One warp per row of X.
+// small margins cover FP32 rounding.  One half-warp per row of X.
 __global__ void __launch_bounds__(128) k_so3_refined_bound(const float* __restrict__ X, int ldx, int n,
                                                            const So3Steer* __restrict__ tab, int L,
                                                            float* __restrict__ out) {
   __shared__ uint32_t meta[256];
   __shared__ unsigned char lv[256];
-  __shared__ float2 Gs[4][13][13];
-  __shared__ float2 Vs[4][2][13];
+  __shared__ float2 Gs[8][13][13];
+  __shared__ float2 Vs[8][2][13];
   const int nent = tab->n;
   for (int i = threadIdx.x; i < nent; i += blockDim.x) {
     meta[i] = tab->meta[i];
     lv[i] = tab->l[i];
   }
   __syncthreads();
+  // one voxel per half-warp (m = 2l+1 <= 13 <= 16 lanes)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float2(*G)[13] = Gs[warp];
-  float2(*Vw)[13] = Vs[warp];
-  auto wsum = [](float v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int sub = lane & 15, grp = lane >> 4;
+  float2(*G)[13] = Gs[warp * 2 + grp];
+  float2(*Vw)[13] = Vs[warp * 2 + grp];
+  auto hsum = [](float v) {
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
   };
-  for (int i = blockIdx.x * 4 + warp; i < n; i += gridDim.x * 4) {
-    const float* row = X + (size_t)i * ldx;
+  for (int base = (blockIdx.x * 4 + warp) * 2; base < n; base += gridDim.x * 8) {
+    const int i = base + grp;
+    const bool valid = i < n;
+    const float* row = X + (size_t)(valid ? i : base) * ldx;   // the spare half of a warp repeats a real row
     float total = 0.f;
     int e0 = 0;
     for (int l = 0; l <= L; ++l) {
@@ -611,7 +616,7 @@ __global__ void __launch_bounds__(128) k_so3_refined_bound(const float* __restri
       int e1 = e0;
       while (e1 < nent && lv[e1] == l) ++e1;
       __syncwarp();
-      for (int e = e0 + lane; e < e1; e += 32) {
+      for (int e = e0 + sub; e < e1; e += 16) {
         const uint32_t mt = meta[e];
         const int ks = (int)((mt >> 11) & 31u) - 12, kd = (int)((mt >> 16) & 31u) - 12;
         const int a = (ks - kd) / 2, b = (ks + kd) / 2, ch = mt & 1023u;
@@ -622,122 +627,114 @@ __global__ void __launch_bounds__(128) k_so3_refined_bound(const float* __restri
       }
       __syncwarp();
       e0 = e1;
-      // column norms; the two largest columns j1, j2
       float cn = -1.f;
-      if (lane < m) {
+      if (sub < m) {
         cn = 0.f;
-        for (int r = 0; r < m; ++r) cn += G[r][lane].x * G[r][lane].x + G[r][lane].y * G[r][lane].y;
+        for (int r = 0; r < m; ++r) cn += G[r][sub].x * G[r][sub].x + G[r][sub].y * G[r][sub].y;
       }
-      const float fro2 = wsum(lane < m ? cn : 0.f);
+      const float fro2 = hsum(sub < m ? cn : 0.f);
       const float fro_bound = sqrtf((float)m * fro2);
-      if (m < 3 || !(fro2 > 0.f)) {
-        // m = 1: |G_0|_* = |G_0|; m = 3 and below handled by the general path otherwise
-        if (m == 1) {
-          total += sqrtf(fro2);
-          continue;
-        }
+      if (m == 1) {
+        total += sqrtf(fro2);
+        continue;
       }
+      // the two columns of largest norm
       float best = cn;
-      int j1 = lane;
-      for (int o = 16; o > 0; o >>= 1) {
+      int j1 = sub;
+      for (int o = 8; o > 0; o >>= 1) {
         const float ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oj = __shfl_xor_sync(0xffffffffu, j1, o);
         if (ob > best || (ob == best && oj < j1)) { best = ob; j1 = oj; }
       }
-      best = (lane == j1) ? -1.f : cn;
-      int j2 = lane;
-      for (int o = 16; o > 0; o >>= 1) {
+      best = (sub == j1) ? -1.f : cn;
+      int j2 = sub;
+      for (int o = 8; o > 0; o >>= 1) {
         const float ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oj = __shfl_xor_sync(0xffffffffu, j2, o);
         if (ob > best || (ob == best && oj < j2)) { best = ob; j2 = oj; }
       }
-      // w_t = G^H g_{j_t} (lane = column index)
+      // w_t = G^H g_{j_t} (sub = column), v_t = G w_t (sub = row)
       float2 w1 = make_float2(0.f, 0.f), w2 = make_float2(0.f, 0.f);
-      if (lane < m) {
+      if (sub < m) {
         for (int r = 0; r < m; ++r) {
-          const float2 gr = G[r][lane], a1 = G[r][j1], a2 = G[r][j2];
+          const float2 gr = G[r][sub], a1 = G[r][j1], a2 = G[r][j2];
           w1.x += gr.x * a1.x + gr.y * a1.y;
           w1.y += gr.x * a1.y - gr.y * a1.x;
           w2.x += gr.x * a2.x + gr.y * a2.y;
           w2.y += gr.x * a2.y - gr.y * a2.x;
         }
-        Vw[0][lane] = w1;
-        Vw[1][lane] = w2;
+        Vw[0][sub] = w1;
+        Vw[1][sub] = w2;
       }
       __syncwarp();
-      // v_t = G w_t (lane = row index)
       float2 v1 = make_float2(0.f, 0.f), v2 = make_float2(0.f, 0.f);
-      if (lane < m) {
+      if (sub < m) {
         for (int j = 0; j < m; ++j) {
-          const float2 g = G[lane][j], a1 = Vw[0][j], a2 = Vw[1][j];
+          const float2 g = G[sub][j], a1 = Vw[0][j], a2 = Vw[1][j];
           v1.x += g.x * a1.x - g.y * a1.y;
           v1.y += g.x * a1.y + g.y * a1.x;
           v2.x += g.x * a2.x - g.y * a2.y;
           v2.y += g.x * a2.y + g.y * a2.x;
         }
       }
-      // Gram-Schmidt (lane = row index)
-      const float n1 = sqrtf(wsum(v1.x * v1.x + v1.y * v1.y));
-      float bound_l = fro_bound;
-      if (n1 > 0.f) {
-        const float2 q1 = make_float2(v1.x / n1, v1.y / n1);
-        const float n2raw = sqrtf(wsum(v2.x * v2.x + v2.y * v2.y));
-        // v2 is nearly parallel to v1 after the power step: orthogonalise twice
-        for (int pass = 0; pass < 2; ++pass) {
-          const float dre = wsum(q1.x * v2.x + q1.y * v2.y), dim = wsum(q1.x * v2.y - q1.y * v2.x);   // <q1, v2>
-          v2.x -= q1.x * dre - q1.y * dim;
-          v2.y -= q1.x * dim + q1.y * dre;
-        }
-        const float n2 = sqrtf(wsum(v2.x * v2.x + v2.y * v2.y));
-        const int k = (n2 > 1e-6f * n2raw && n2 > 0.f) ? 2 : 1;
-        const float2 q2 = k == 2 ? make_float2(v2.x / n2, v2.y / n2) : make_float2(0.f, 0.f);
-        __syncwarp();
-        if (lane < m) {
-          Vw[0][lane] = q1;
-          Vw[1][lane] = q2;
-        }
-        __syncwarp();
-        // p_t[j] = sum_r conj(q_t[r]) G[r][j] (lane = column index)
-        float2 p1 = make_float2(0.f, 0.f), p2 = make_float2(0.f, 0.f);
-        if (lane < m) {
-          for (int r = 0; r < m; ++r) {
-            const float2 g = G[r][lane], a1 = Vw[0][r], a2 = Vw[1][r];
-            p1.x += a1.x * g.x + a1.y * g.y;
-            p1.y += a1.x * g.y - a1.y * g.x;
-            p2.x += a2.x * g.x + a2.y * g.y;
-            p2.y += a2.x * g.y - a2.y * g.x;
-          }
-        }
-        const float a11 = wsum(p1.x * p1.x + p1.y * p1.y), a22 = wsum(p2.x * p2.x + p2.y * p2.y);
-        const float c_re = wsum(p1.x * p2.x + p1.y * p2.y), c_im = wsum(p1.x * p2.y - p1.y * p2.x);
-        // residual R[r][j] = G[r][j] - q1[r] p1[j] - q2[r] p2[j] (lane = row index; p through shuffles)
-        float rr = 0.f;
-        for (int j = 0; j < m; ++j) {
-          const float p1x = __shfl_sync(0xffffffffu, p1.x, j), p1y = __shfl_sync(0xffffffffu, p1.y, j);
-          const float p2x = __shfl_sync(0xffffffffu, p2.x, j), p2y = __shfl_sync(0xffffffffu, p2.y, j);
-          if (lane < m) {
-            const float2 g = G[lane][j];
-            const float rx = g.x - (q1.x * p1x - q1.y * p1y) - (q2.x * p2x - q2.y * p2y);
-            const float ry = g.y - (q1.x * p1y + q1.y * p1x) - (q2.x * p2y + q2.y * p2x);
-            rr += rx * rx + ry * ry;
-          }
-        }
-        rr = wsum(rr);
-        const float det = fmaxf(a11 * a22 - (c_re * c_re + c_im * c_im), 0.f) + 4.8e-7f * a11 * a22;
-        const float nucP = sqrtf(a11 + a22 + 2.f * sqrtf(det));
-        const float defl = nucP * (1.f + 1e-5f) + sqrtf((float)(m - k)) * sqrtf(rr) + 1e-5f * fro_bound;
-        bound_l = fminf(fro_bound, defl);
+      // Gram-Schmidt, the second vector orthogonalised twice
+      const float n1 = sqrtf(hsum(v1.x * v1.x + v1.y * v1.y));
+      const float inv1 = n1 > 0.f ? 1.f / n1 : 0.f;
+      const float2 q1 = make_float2(v1.x * inv1, v1.y * inv1);
+      const float n2raw = sqrtf(hsum(v2.x * v2.x + v2.y * v2.y));
+      for (int pass = 0; pass < 2; ++pass) {
+        const float dre = hsum(q1.x * v2.x + q1.y * v2.y), dim = hsum(q1.x * v2.y - q1.y * v2.x);
+        v2.x -= q1.x * dre - q1.y * dim;
+        v2.y -= q1.x * dim + q1.y * dre;
       }
-      total += bound_l;
+      const float n2 = sqrtf(hsum(v2.x * v2.x + v2.y * v2.y));
+      const int k = (n2 > 1e-6f * n2raw && n2 > 0.f) ? 2 : 1;
+      const float inv2 = k == 2 ? 1.f / n2 : 0.f;
+      const float2 q2 = make_float2(v2.x * inv2, v2.y * inv2);
+      __syncwarp();
+      if (sub < m) {
+        Vw[0][sub] = q1;
+        Vw[1][sub] = q2;
+      }
+      __syncwarp();
+      // P = [q1 q2]^H G (sub = column), R = G - [q1 q2] P (sub = row)
+      float2 p1 = make_float2(0.f, 0.f), p2 = make_float2(0.f, 0.f);
+      if (sub < m) {
+        for (int r = 0; r < m; ++r) {
+          const float2 g = G[r][sub], a1 = Vw[0][r], a2 = Vw[1][r];
+          p1.x += a1.x * g.x + a1.y * g.y;
+          p1.y += a1.x * g.y - a1.y * g.x;
+          p2.x += a2.x * g.x + a2.y * g.y;
+          p2.y += a2.x * g.y - a2.y * g.x;
+        }
+      }
+      const float a11 = hsum(p1.x * p1.x + p1.y * p1.y), a22 = hsum(p2.x * p2.x + p2.y * p2.y);
+      const float c_re = hsum(p1.x * p2.x + p1.y * p2.y), c_im = hsum(p1.x * p2.y - p1.y * p2.x);
+      float rr = 0.f;
+      for (int j = 0; j < m; ++j) {
+        const float p1x = __shfl_sync(0xffffffffu, p1.x, j, 16), p1y = __shfl_sync(0xffffffffu, p1.y, j, 16);
+        const float p2x = __shfl_sync(0xffffffffu, p2.x, j, 16), p2y = __shfl_sync(0xffffffffu, p2.y, j, 16);
+        if (sub < m) {
+          const float2 g = G[sub][j];
+          const float rx = g.x - (q1.x * p1x - q1.y * p1y) - (q2.x * p2x - q2.y * p2y);
+          const float ry = g.y - (q1.x * p1y + q1.y * p1x) - (q2.x * p2y + q2.y * p2x);
+          rr += rx * rx + ry * ry;
+        }
+      }
+      rr = hsum(rr);
+      const float det = fmaxf(a11 * a22 - (c_re * c_re + c_im * c_im), 0.f) + 4.8e-7f * a11 * a22;
+      const float nucP = sqrtf(a11 + a22 + 2.f * sqrtf(det));
+      const float defl = nucP * (1.f + 1e-5f) + sqrtf((float)(m - k)) * sqrtf(rr) + 1e-5f * fro_bound;
+      total += n1 > 0.f ? fminf(fro_bound, defl) : fro_bound;
     }
-    if (lane == 0) out[i] = total;
+    if (sub == 0 && valid) out[i] = total;
   }
 }
 
 void launch_so3_refined_bound(const float* X, int ldx, int n, const So3Steer* tab, int L, float* out, int sms,
                               cudaStream_t st) {
   if (n <= 0) return;
-  long long b = (n + 3) / 4;
+  long long b = (n + 7) / 8;
   if (b > (long long)sms * 16) b = (long long)sms * 16;
   k_so3_refined_bound<<<(unsigned)b, 128, 0, st>>>(X, ldx, n, tab, L, out);
 }
