@@ -133,10 +133,18 @@ ext_status so3_components(ext_plan plan, const float* V, int nz, int ny, int nx,
       ok = fft_cols_inv_full_pipe(nz, (const float2*)Hf, w2, S, k0, nk, (float2*)Z, tw_z, plan->sms, st);
     });
     if (!ok) return fail(EXT_ERR_UNSUPPORTED, "no pipelined z pass for this volume depth");
-    launch(plan, "so3_cols_y", st, [&] { fft_cols_c2c(ny, (float2*)Z, nx, nz * nk, true, tw_y, st); });
-    launch(plan, "so3_rows_x", st, [&] {
-      fft_rows_inv_channels(nx, (const float2*)Z, nz * ny, k0, nk, (const int2*)dchan, G, tw_x, st);
-    });
+    bool fused = false;
+    if (ny == nx && plan->pipelined)
+      launch(plan, "so3_planes_yx", st, [&] {
+        fused = fft_planes_inv_channels(nx, (const float2*)Z, nz, k0, nk, (const int2*)dchan, G, tw_x, plan->dev_err,
+                                        plan->sms, st);
+      });
+    if (!fused) {
+      launch(plan, "so3_cols_y", st, [&] { fft_cols_c2c(ny, (float2*)Z, nx, nz * nk, true, tw_y, st); });
+      launch(plan, "so3_rows_x", st, [&] {
+        fft_rows_inv_channels(nx, (const float2*)Z, nz * ny, k0, nk, (const int2*)dchan, G, tw_x, st);
+      });
+    }
   }
   EXT_CUDA(cudaGetLastError());
   return EXT_OK;

@@ -726,6 +726,107 @@ k_rows_inv_channels(const float2* __restrict__ Z, int rows, int k0, const int2* 
   });
 }
 
+// Fused inverse y and x passes of the SO(3) components: one block per
+// (component, z) plane of N x N complex values (after the z pass), with the
+// whole plane resident in shared memory (rows of pitch LS).  The plane comes
+// in by N bulk copies (one per row) on an mbarrier; column FFTs run in
+// groups of 32 columns in place, then row FFTs in groups of 32 rows write the
+// real channel planes of G.  As soon as a row group has been read, its rows
+// of the block's next plane are requested, so the next plane streams in
+// while this one finishes.  Waits are bounded (err = EXT_ERR_TIMEOUT).
+template <int N>
+struct PlaneCfg {
+  using C = LineCfg<N>;
+  static constexpr int LINES = 32;
+  static constexpr int THREADS = ((LINES * C::TPL + 31) / 32) * 32;
+  static constexpr int PB = N * C::LS;               // plane, rows of pitch LS
+  static constexpr int WB = LINES * C::LS;           // work buffer of a 16-line group
+  static constexpr int SMEM = (PB + WB + N) * 8;
+  static constexpr bool OK = (N % LINES == 0) && SMEM <= 227 * 1024 && (C::LS * 8) % 16 == 0;
+};
+
+template <int N>
+__global__ void __launch_bounds__(PlaneCfg<N>::THREADS, 1)
+k_planes_inv_channels(const float2* __restrict__ Z, int nz, int k0, int nk, const int2* __restrict__ chan,
+                      float* __restrict__ G, const float2* __restrict__ tw, int* __restrict__ err) {
+  using C = LineCfg<N>;
+  using PC = PlaneCfg<N>;
+  constexpr int T = PC::THREADS;
+  constexpr int LINES = PC::LINES;
+  constexpr int LS = C::LS;
+  extern __shared__ float2 sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int abort_flag;
+  float2* PBuf = sm;
+  float2* W = sm + PC::PB;
+  const float2* TWs = stage_twiddles<N, PC::PB + PC::WB>(sm, tw, T);
+  const size_t plane = (size_t)N * N;
+  const size_t P = plane * nz;
+  const int nplanes = nk * nz;
+  const uint32_t mb = tc::smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    tc::mbar_init(mb, 1);
+  }
+  __syncthreads();
+  // thread 0: rows [r0, r1) of plane pz into the plane buffer (first call of a plane sets the byte count)
+  auto fetch_rows = [&](int pz, int r0, int r1) {
+    const float2* src = Z + (size_t)pz * plane;
+    if (r0 == 0) {
+      tc::fence_proxy_async();
+      tc::mbar_expect_tx(mb, (uint32_t)(plane * 8));
+    }
+    for (int y = r0; y < r1; ++y) tc::bulk_load(tc::smem_u32(PBuf + y * LS), src + (size_t)y * N, N * 8u, mb);
+  };
+  int pz = blockIdx.x;
+  uint32_t phase = 0;
+  bool pending = pz < nplanes;
+  if (pending && threadIdx.x == 0) fetch_rows(pz, 0, N);
+  constexpr RadixList L = factor_radices(N);
+  constexpr int R0 = L.r[0];
+  for (; pz < nplanes; pz += gridDim.x) {
+    if (!tc::mbar_wait_bounded(mb, phase, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    phase ^= 1u;
+    pending = false;
+    // y pass: groups of LINES columns, in place
+    for (int g = 0; g < N / LINES; ++g) {
+      const int x0 = g * LINES;
+      auto load = [&](int c, int v) -> float2 { return PBuf[v * LS + x0 + c]; };
+      auto store = [&](int c, int v, float2 val) { PBuf[v * LS + x0 + c] = val; };
+      ct_stage_io<N, R0, 1, true, true, LINES, T, true, L.cnt == 1>(W, 1, LINES, TWs, load, store);
+      if constexpr (L.cnt > 1) ct_fft_io<N, true, true, LINES, T, 1, R0>(W, 1, LINES, TWs, load, store);
+      __syncthreads();
+    }
+    // x pass: groups of LINES rows, written to the channel planes
+    const int kk = pz / nz, z = pz % nz;
+    const int2 ch = chan[k0 + kk];
+    float* re = G + (size_t)ch.x * P + (size_t)z * plane;
+    float* im = G + (size_t)(ch.y < 0 ? ch.x : ch.y) * P + (size_t)z * plane;
+    const int next = pz + gridDim.x;
+    for (int g = 0; g < N / LINES; ++g) {
+      const int y0 = g * LINES;
+      auto load = [&](int l, int x) -> float2 { return PBuf[(y0 + l) * LS + x]; };
+      auto store = [&](int l, int x, float2 val) {
+        const size_t idx = (size_t)(y0 + l) * N + x;
+        re[idx] = val.x;
+        if (ch.y >= 0) im[idx] = val.y;
+      };
+      ct_stage_io<N, R0, 1, true, false, LINES, T, true, L.cnt == 1>(W, LS, 1, TWs, load, store);
+      // the first stage has read these rows: the next plane may fill them
+      if (next < nplanes) {
+        if (threadIdx.x == 0) tc::fence_proxy_async();
+        if (threadIdx.x == 0) fetch_rows(next, y0, y0 + LINES);
+        pending = true;
+      }
+      if constexpr (L.cnt > 1) ct_fft_io<N, true, false, LINES, T, 1, R0>(W, LS, 1, TWs, load, store);
+      __syncthreads();
+    }
+  }
+  if (pending) tc::mbar_wait_bounded(mb, phase, 1000000000ull, err, EXT_ERR_TIMEOUT);
+}
+
 // ------------------------------------------------- pipelined hot passes ---
 // Persistent versions of the two passes that run once per filter component
 // in the correlation path.  Each block owns one SM (grid = min(items, SMs))
@@ -1087,6 +1188,8 @@ struct FftOps {
   using C = LineCfg<N>;
   static bool cols_inv_corr_tma(const CUtensorMap& tmH, int w, int br, const float2* S, int k0, int nk, float2* Z,
                                 const float2* tw, int* err, int sms, cudaStream_t st);
+  static bool planes_inv_channels(const float2* Z, int nz, int k0, int nk, const int2* chan, float* G,
+                                  const float2* tw, int* err, int sms, cudaStream_t st);
   static void rows_r2c(const float* H, int h, float2* Hh, const float2* tw, cudaStream_t st);
   static void rows_fwd_phase(const float* H, const float* alpha, int h, int k0, int nk, float2* A,
                              const float2* tw, cudaStream_t st);
@@ -1262,6 +1365,21 @@ bool FftOps<N>::cols_inv_corr_tma(const CUtensorMap& tmH, int w, int br, const f
     const int items = ((w + C::CW - 1) / C::CW) * nk;
     const int grid = pipe_grid<N>(items, sms, TmaColCfg<N>::SMEM, C::COL_THREADS);
     k_cols_inv_corr_tma<N><<<grid, C::COL_THREADS, TmaColCfg<N>::SMEM, st>>>(tmH, w, br, S, k0, nk, Z, tw, err);
+    return true;
+  }
+}
+
+template <int N>
+bool FftOps<N>::planes_inv_channels(const float2* Z, int nz, int k0, int nk, const int2* chan, float* G,
+                                    const float2* tw, int* err, int sms, cudaStream_t st) {
+  if constexpr (!PlaneCfg<N>::OK) {
+    return false;
+  } else {
+    static const bool once = (ext_set_smem(k_planes_inv_channels<N>, PlaneCfg<N>::SMEM), true);
+    (void)once;
+    const int planes = nk * nz;
+    const int grid = planes < sms ? planes : sms;
+    k_planes_inv_channels<N><<<grid, PlaneCfg<N>::THREADS, PlaneCfg<N>::SMEM, st>>>(Z, nz, k0, nk, chan, G, tw, err);
     return true;
   }
 }

@@ -164,3 +164,11 @@ void launch_expand_hermitian(const float2* Hh, int h, int w, float2* Hf, int sms
   if (b > (long long)sms * 8) b = (long long)sms * 8;
   if (b > 0) k_expand_hermitian<<<(unsigned)b, 256, 0, st>>>(Hh, h, w, Hf);
 }
+
+// fused y and x inverse passes of square N x N planes (N = ny = nx)
+#define EXT_C1(N) case N: return FftOps<N>::planes_inv_channels(Z, nz, k0, nk, chan, G, tw, err, sms, st);
+bool fft_planes_inv_channels(int n, const float2* Z, int nz, int k0, int nk, const int2* chan, float* G,
+                             const float2* tw, int* err, int sms, cudaStream_t st) {
+  switch (n) { EXT_FFT_SIZES(EXT_C1) default: return false; }
+}
+#undef EXT_C1

@@ -61,6 +61,9 @@ void launch_expand_hermitian(const float2* Hh, int h, int w, float2* Hf, int sms
 void fft_cols_c2c(int h, float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st);
 void fft_rows_inv_channels(int w, const float2* Z, int rows, int k0, int nk, const int2* chan, float* G,
                            const float2* tw, cudaStream_t st);
+// fused inverse y and x passes over nk * nz planes of n x n (false: not available for n)
+bool fft_planes_inv_channels(int n, const float2* Z, int nz, int k0, int nk, const int2* chan, float* G,
+                             const float2* tw, int* err, int sms, cudaStream_t st);
 bool fft_cols_inv_full_pipe(int h, const float2* H, int w, const float2* S, int k0, int nk, float2* Z,
                             const float2* tw, int sms, cudaStream_t st);
 void fft_cols_conv(int h, const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
