@@ -737,12 +737,15 @@ k_rows_inv_channels(const float2* __restrict__ Z, int rows, int k0, const int2* 
 template <int N>
 struct PlaneCfg {
   using C = LineCfg<N>;
-  static constexpr int LINES = 32;
-  static constexpr int THREADS = ((LINES * C::TPL + 31) / 32) * 32;
+  // lines per group: as many as the shared memory left by the plane allows (up to N)
   static constexpr int PB = N * C::LS;               // plane, rows of pitch LS
-  static constexpr int WB = LINES * C::LS;           // work buffer of a 16-line group
+  static constexpr int LINES_FIT = (227 * 1024 / 8 - PB - N) / C::LS;
+  static constexpr int LINES = LINES_FIT >= 64 && N % 64 == 0 ? 64 : (LINES_FIT >= 32 && N % 32 == 0 ? 32 : 16);
+  static constexpr int THREADS = ((LINES * C::TPL + 31) / 32) * 32 > 1024 ? 1024 : ((LINES * C::TPL + 31) / 32) * 32;
+  static constexpr int WB = LINES * C::LS;           // work buffer of one group of lines
   static constexpr int SMEM = (PB + WB + N) * 8;
-  static constexpr bool OK = (N % LINES == 0) && SMEM <= 227 * 1024 && (C::LS * 8) % 16 == 0;
+  static constexpr bool OK = (N % LINES == 0) && SMEM <= 227 * 1024 && (C::LS * 8) % 16 == 0 &&
+                             THREADS >= LINES * N / FFT_MAXE;
 };
 
 template <int N>
@@ -1378,7 +1381,11 @@ bool FftOps<N>::planes_inv_channels(const float2* Z, int nz, int k0, int nk, con
     static const bool once = (ext_set_smem(k_planes_inv_channels<N>, PlaneCfg<N>::SMEM), true);
     (void)once;
     const int planes = nk * nz;
-    const int grid = planes < sms ? planes : sms;
+    int per_sm = (227 * 1024) / (PlaneCfg<N>::SMEM + 1024);
+    const int by_threads = 2048 / PlaneCfg<N>::THREADS;
+    if (per_sm > by_threads) per_sm = by_threads;
+    if (per_sm < 1) per_sm = 1;
+    const int grid = planes < sms * per_sm ? planes : sms * per_sm;
     k_planes_inv_channels<N><<<grid, PlaneCfg<N>::THREADS, PlaneCfg<N>::SMEM, st>>>(Z, nz, k0, nk, chan, G, tw, err);
     return true;
   }

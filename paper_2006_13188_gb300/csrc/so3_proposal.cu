@@ -128,10 +128,13 @@ __global__ void __launch_bounds__(256) k_so3_upper_bound(const float* __restrict
       const int c0 = l * (2 * l - 1) * (2 * l + 1) / 3, c1 = c0 + (2 * l + 1) * (2 * l + 1);
       const float g0 = __ldg(G + (size_t)c0 * P + p);
       float acc = g0 * g0, acc2 = 0.f;
-#pragma unroll 8
-      for (int c = c0 + 1; c < c1; ++c) {
-        const float x = __ldg(G + (size_t)c * P + p);
-        acc2 = fmaf(x, x, acc2);
+      // loads in batches of 24, all in flight before their squares are summed
+      for (int cb = c0 + 1; cb < c1; cb += 24) {
+        float x[24];
+#pragma unroll
+        for (int t = 0; t < 24; ++t) x[t] = cb + t < c1 ? __ldg(G + (size_t)(cb + t) * P + p) : 0.f;
+#pragma unroll
+        for (int t = 0; t < 24; ++t) acc2 = fmaf(x[t], x[t], acc2);
       }
       u += sqrtf((2.f * l + 1.f) * (acc + 2.f * acc2));
     }
