@@ -51,7 +51,7 @@ def parse_args():
                     help="so3 / so3p: volume side (128 is the workload; smaller only for profiling captures)")
     ap.add_argument("--train-steps", type=int, default=6000,
                     help="so3p: Adam steps of the proposal network (setup, not timed)")
-    ap.add_argument("--workload", default="so2", choices=["so2", "scale", "batched", "so3", "so3p"],
+    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p"],
                     help="so2: the pattern-matching sweep (default, the headline metric); "
                          "scale: scale-adaptive smoothing of a 4096x4096x3 image; "
                          "batched: 512 uneven images in one captured graph; "
@@ -208,6 +208,81 @@ def algorithmic_bytes(kernel, h, w, K, kc):
     if kernel in ("sweep_fp32", "sweep_bf16x3"):
         return (2 * K + 1) * 4 * P + 8 * P
     return None
+
+
+# --------------------------------------------------------- conv workload ---
+CONV_WORKLOAD = ("SO(2) extended convolution: 256^2 f32 image (blurred uniform noise), analytic filter K=4 "
+                 "(a_k r^|k| exp(-r^2/72)), 31x31 box, per-pixel angle field; one image per call")
+
+
+def bench_conv(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_2006_13188_gb300 as ec
+    import synth
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    prob = synth.so2_conv_problem(seed=synth.seed_for(1) + rank)
+    n = prob["H"].shape[0]
+    P = n * n
+    plan = ec.Plan(local)
+    F = ec.FilterSO2.analytic(prob["a"], prob["sigma"], prob["radius"])
+    H = torch.from_numpy(prob["H"]).to(device)
+    al = torch.from_numpy(prob["alpha"]).to(device)
+    out = torch.empty_like(H)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    def call():
+        ec.ext_conv_so2(plan, H, n, n, F, al, out)
+    call()
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    barrier(world)
+    total = 0.0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+    total = reduce_max(total, world, device)
+    plan.profile_read()
+    plan.profile(True)
+    call()
+    torch.cuda.synchronize()
+    prof = {k: v for k, v in plan.profile_read().items() if v[1] > 0}
+    plan.profile(False)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle.filters_so2 import AnalyticGaussPow
+        from oracle.so2 import ext_conv_so2_at
+        rng = np.random.default_rng(0)
+        pix = rng.integers(0, n, (2048, 2))
+        t0 = time.perf_counter()
+        ext_conv_so2_at(prob["H"].astype(np.float64), AnalyticGaussPow(prob["a"], prob["sigma"]),
+                        prob["alpha"].astype(np.float64), prob["radius"], pix)
+        t = time.perf_counter() - t0
+        cpu = {"value": len(pix) / t / 1e6, "unit": "Mpx/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 brute-force scatter-form convolution at {len(pix)} random pixels ({t:.1f} s)"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "SO(2) extended-convolution Mpx/s", "value": world * args.steps * P / (total * 1e-3) / 1e6,
+            "unit": "Mpx/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": CONV_WORKLOAD, "l2": "256 MB written between steps",
+                       "note": "a single 256^2 image is launch- and latency-bound"},
+            "clocks": clk.summary(), "gpu_launches": int(sum(v[1] for v in prof.values())),
+            "kernels": {k: {"ms_per_call": v[0], "launches": v[1]} for k, v in prof.items()},
+            "cpu_baseline": cpu}))
+    plan.close()
+    return 0
 
 
 # ------------------------------------------------------- scale workload ---
@@ -602,6 +677,8 @@ def bench_so3p(args, world, rank, local):
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args.gpus)
+    if args.workload == "conv" and args.impl == "ours":
+        return bench_conv(args, world, rank, local)
     if args.workload == "scale" and args.impl == "ours":
         return bench_scale(args, world, rank, local)
     if args.workload == "batched" and args.impl == "ours":

@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sweep_tc2(const __grid_constant_
     tc::fence_after();
     float best = 0.f;
     int bj = 0;
+    const bool full = (J == JP);   // no padded angle columns to skip
 #pragma unroll
     for (int c0 = 0; c0 < JP; c0 += 32) {
       float v[32];
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sweep_tc2(const __grid_constant_
         const int j = c0 + i;
         if (j == 0) {
           best = v[i];
-        } else if ((JP == 16 || j < J) && v[i] > best) {
+        } else if ((full || j < J) && v[i] > best) {
           best = v[i];
           bj = j;
         }
@@ -418,9 +419,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_sweep_tc2(const __grid_constant_
         const int c = kb * 8 + 2 * t;
         const float x0 = c < C2 ? st[(c + 1) * TILE_M + tid] : 0.f;
         const float x1 = c + 1 < C2 ? st[(c + 2) * TILE_M + tid] : 0.f;
-        const float h0 = __bfloat162float(__float2bfloat16_rn(x0)), h1 = __bfloat162float(__float2bfloat16_rn(x1));
-        hi[t] = pack_bf16(x0, x1);
-        lo[t] = pack_bf16(x0 - h0, x1 - h1);
+        // packed conversions: one instruction rounds both values
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(x0, x1);
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(x0 - __low2float(hb), x1 - __high2float(hb));
+        hi[t] = *reinterpret_cast<const uint32_t*>(&hb);
+        lo[t] = *reinterpret_cast<const uint32_t*>(&lb);
       }
       *reinterpret_cast<uint4*>(Ahi + rowoff + kb * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<uint4*>(Alo + rowoff + kb * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
