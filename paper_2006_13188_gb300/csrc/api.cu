@@ -524,9 +524,9 @@ ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_f
   const size_t P = (size_t)h * w;
   const int K = F->K;
   Staged sH, sAl, sO, sA;
-  EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P, st, &sH));
-  EXT_TRY(stage_out_alloc(plan, "out_0", out_or_max, sizeof(float) * P, &sO));
   if (alpha) {
+    EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P, st, &sH));
+    EXT_TRY(stage_out_alloc(plan, "out_0", out_or_max, sizeof(float) * P, &sO));
     EXT_TRY(stage_in(plan, "in_alpha", alpha, sizeof(float) * P, st, &sAl));
     const float2* S = nullptr;
     EXT_TRY(spectra(plan, F, h, w, SPEC_CORR, st, &S));
@@ -547,15 +547,26 @@ ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_f
     EXT_TRY(stage_out_finish(sO, st));
     return finish_host(plan, sH.host || sAl.host || sO.host, st);
   }
-  EXT_TRY(stage_out_alloc(plan, "out_1", argmax, sizeof(int32_t) * P, &sA));
+  // max and argmax are written once, by the sweep: page-locked host outputs are
+  // written in place (K >= 1).  (Reading a page-locked H in place in the first row
+  // pass measured no faster than the staged copy.)
+  EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P, st, &sH));
+  Staged sM;
+  if (K >= 1) {
+    EXT_TRY(stage_out_direct(plan, "out_0", out_or_max, sizeof(float) * P, &sM));
+    EXT_TRY(stage_out_direct(plan, "out_1", argmax, sizeof(int32_t) * P, &sA));
+  } else {
+    EXT_TRY(stage_out_alloc(plan, "out_0", out_or_max, sizeof(float) * P, &sM));
+    EXT_TRY(stage_out_alloc(plan, "out_1", argmax, sizeof(int32_t) * P, &sA));
+  }
   void* G = nullptr;
   EXT_TRY(ensure(plan, "G", sizeof(float) * P * (2 * K + 1), &G));
   EXT_TRY(run_components(plan, (const float*)sH.dev, h, w, F, (float*)G, st));
-  EXT_TRY(run_sweep(plan, (const float*)G, (long long)P, K, n_angles, (float*)sO.dev, (int32_t*)sA.dev, precision,
+  EXT_TRY(run_sweep(plan, (const float*)G, (long long)P, K, n_angles, (float*)sM.dev, (int32_t*)sA.dev, precision,
                     st));
-  EXT_TRY(stage_out_finish(sO, st));
+  EXT_TRY(stage_out_finish(sM, st));
   EXT_TRY(stage_out_finish(sA, st));
-  return finish_host(plan, sH.host || sO.host || sA.host, st);
+  return finish_host(plan, sH.host || sM.host || sA.host || sM.mapped || sA.mapped, st);
 }
 
 ext_status ext_conv_so2(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, const float* alpha,

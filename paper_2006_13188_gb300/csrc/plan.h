@@ -168,7 +168,8 @@ struct Staged {
   const void* user = nullptr;
   void* dev = nullptr;
   size_t bytes = 0;
-  bool host = false;
+  bool host = false;     // staged through a device buffer and copied
+  bool mapped = false;   // page-locked host memory written in place through its device mapping
 };
 
 ext_status stage_in(ext_plan plan, const char* name, const void* user, size_t bytes, cudaStream_t st,
@@ -194,6 +195,26 @@ ext_status stage_out_alloc(ext_plan plan, const char* name, void* user, size_t b
     return EXT_OK;
   }
   return ensure(plan, name, bytes, &s->dev);
+}
+
+// An output written exactly once, by plain stores of the call's last kernel:
+// page-locked host memory with a device mapping is written in place, so the
+// transfer to the host overlaps that kernel instead of following it as a
+// copy; other host memory is staged as usual.
+ext_status stage_out_direct(ext_plan plan, const char* name, void* user, size_t bytes, Staged* s) {
+  if (user && !is_device_ptr(user)) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, user) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+      s->user = user;
+      s->bytes = bytes;
+      s->dev = at.devicePointer;
+      s->host = false;
+      s->mapped = true;
+      return EXT_OK;
+    }
+    cudaGetLastError();
+  }
+  return stage_out_alloc(plan, name, user, bytes, s);
 }
 
 ext_status stage_out_finish(const Staged& s, cudaStream_t st) {

@@ -132,6 +132,30 @@ def test_field_host_buffers_match_device(ec, plan):
     np.testing.assert_array_equal(out_h, out_d.cpu().numpy())
 
 
+@pytest.mark.parametrize("precision", ["EXT_PREC_BF16X3", "EXT_PREC_FP32"])
+def test_sweep_host_outputs_match_device(ec, plan, precision):
+    """Sweep outputs in device memory, in page-locked host memory (written in
+    place by the sweep through the device mapping) and in pageable host memory
+    (staged, then copied) are identical."""
+    prec = getattr(ec, precision)
+    p2 = synth.so2_match_problem(seed=9, size=(96, 128), n_plant=1, radius=12, K=6, J=40)
+    F = ec.FilterSO2.sampled(p2["template"], p2["K"], p2["dr"], p2["n_theta"])
+    shape = p2["H"].shape
+    mx_d = torch.empty(shape, dtype=torch.float32, device="cuda")
+    am_d = torch.empty(shape, dtype=torch.int32, device="cuda")
+    ec.ext_corr_so2(plan, dev(p2["H"]), *shape, F, None, p2["J"], mx_d, am_d, prec)
+    mx_p = torch.full(shape, -1.0, dtype=torch.float32).pin_memory()
+    am_p = torch.full(shape, -1, dtype=torch.int32).pin_memory()
+    ec.ext_corr_so2(plan, torch.from_numpy(p2["H"]).pin_memory(), *shape, F, None, p2["J"], mx_p, am_p, prec)
+    mx_h = np.full(shape, -1.0, np.float32)
+    am_h = np.full(shape, -1, np.int32)
+    ec.ext_corr_so2(plan, p2["H"], *shape, F, None, p2["J"], mx_h, am_h, prec)
+    np.testing.assert_array_equal(mx_p.numpy(), mx_d.cpu().numpy())
+    np.testing.assert_array_equal(am_p.numpy(), am_d.cpu().numpy())
+    np.testing.assert_array_equal(mx_h, mx_d.cpu().numpy())
+    np.testing.assert_array_equal(am_h, am_d.cpu().numpy())
+
+
 # ------------------------------------------------------------------ sweeps ---
 
 def _check_sweep(mx, am, S, what):
