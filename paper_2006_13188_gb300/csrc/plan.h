@@ -236,8 +236,16 @@ ext_status device_status(ext_plan plan) {
 
 ext_status finish_host(ext_plan plan, bool any_host, cudaStream_t st) {
   if (any_host) {
+    // the status word rides on the stream with the outputs: one synchronisation
+    if (!plan->pinned) EXT_CUDA(cudaMallocHost(&plan->pinned, 64));
+    int* word = plan->pinned + 15;
+    EXT_CUDA(cudaMemcpyAsync(word, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     EXT_CUDA(cudaStreamSynchronize(st));
-    return device_status(plan);
+    if (*word != 0) {
+      const int e = *word;
+      EXT_CUDA(cudaMemset(plan->dev_err, 0, sizeof(int)));
+      return fail((ext_status)e, "a device-side wait timed out; results of the affected call are invalid");
+    }
   }
   return EXT_OK;
 }
