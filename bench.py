@@ -197,12 +197,10 @@ def algorithmic_bytes(kernel, h, w, K, kc):
     half = h * wh * 8
     if kernel == "rows_r2c":
         return 4 * P + half
-    if kernel == "cols_fwd_half":
-        return 2 * half
+    if kernel == "cols_fwd_half":   # half spectrum in place, plus the full spectrum for the TMA column pass
+        return 2 * half + 8 * P
     if kernel in ("cols_inv_corr", "cols_inv_corr_pipe", "cols_inv_corr_tma"):   # H once, kc spectra in, kc products out
         return half + kc * (8 * P) + kc * (8 * P)
-    if kernel == "expand_hermitian":   # half spectrum in, full spectrum out
-        return half + 8 * P
     if kernel in ("rows_inv_components", "rows_inv_components_pipe"):   # kc products in, 2 planes out each
         return kc * 8 * P + kc * 8 * P
     if kernel in ("sweep_fp32", "sweep_bf16x3"):

@@ -246,8 +246,20 @@ ext_status run_components(ext_plan plan, const float* H, int h, int w, const ext
   const int wh = w / 2 + 1;
   void* Hh = nullptr;
   EXT_TRY(ensure(plan, "Hh", sizeof(float2) * (size_t)h * wh, &Hh));
+  // TMA-staged column pass on the full spectrum where the tile shape allows it;
+  // the forward column pass then writes the full spectrum as well
+  CUtensorMap tmH;
+  const int cw = fft_col_tile(h);
+  const int br = plan->tma && fft_cols_tma_ok(h) ? tma_rows(h, cw) : 0;
+  bool use_tma = false;
+  void* Hf = nullptr;
+  if (br > 0) {
+    EXT_TRY(ensure(plan, "Hf", sizeof(float2) * (size_t)h * w, &Hf));
+    use_tma = spectrum_tmap((const float2*)Hf, h, w, cw, br, &tmH);
+  }
   launch(plan, "rows_r2c", st, [&] { fft_rows_r2c(w, H, h, (float2*)Hh, tw_w, st); });
-  launch(plan, "cols_fwd_half", st, [&] { fft_cols_fwd_half(h, (float2*)Hh, wh, tw_h, st); });
+  launch(plan, "cols_fwd_half", st,
+         [&] { fft_cols_fwd_half(h, (float2*)Hh, wh, tw_h, st, use_tma ? (float2*)Hf : nullptr, w); });
   // All components go through each inverse pass in one launch: measured on
   // 2048^2 x 17 components, one launch beats per-component launches that keep
   // the partial products L2-resident (tail imbalance dominates), at the cost
@@ -257,19 +269,6 @@ ext_status run_components(ext_plan plan, const float* H, int h, int w, const ext
   if (plan->kchunk > 0) kc = plan->kchunk < K + 1 ? plan->kchunk : K + 1;
   void* Z = nullptr;
   EXT_TRY(ensure(plan, "Z", plane * kc, &Z));
-  // TMA-staged column pass on the full spectrum where the tile shape allows it
-  CUtensorMap tmH;
-  const int cw = fft_col_tile(h);
-  const int br = plan->tma && fft_cols_tma_ok(h) ? tma_rows(h, cw) : 0;
-  bool use_tma = false;
-  if (br > 0) {
-    void* Hf = nullptr;
-    EXT_TRY(ensure(plan, "Hf", sizeof(float2) * (size_t)h * w, &Hf));
-    use_tma = spectrum_tmap((const float2*)Hf, h, w, cw, br, &tmH);
-    if (use_tma)
-      launch(plan, "expand_hermitian", st,
-             [&] { launch_expand_hermitian((const float2*)Hh, h, w, (float2*)Hf, plan->sms, st); });
-  }
   for (int k0 = 0; k0 <= K; k0 += kc) {
     const int nk = (k0 + kc <= K + 1) ? kc : (K + 1 - k0);
     bool piped = false;
@@ -810,17 +809,16 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
       twiddle(plan, w, bs, &tw_w);
       twiddle(plan, h, bs, &tw_h);
       const int wh = w / 2 + 1;
-      fft_rows_r2c(w, d.H, h, (float2*)dHh[b], tw_w, bs);
-      fft_cols_fwd_half(h, (float2*)dHh[b], wh, tw_h, bs);
       bool done = false;
       const int cw = fft_col_tile(h);
       const int brows = plan->tma && fft_cols_tma_ok(h) ? tma_rows(h, cw) : 0;
       CUtensorMap tmH;
-      if (brows > 0 && spectrum_tmap((const float2*)dHf[b], h, w, cw, brows, &tmH)) {
-        launch_expand_hermitian((const float2*)dHh[b], h, w, (float2*)dHf[b], plan->sms, bs);
+      const bool tma_ok = brows > 0 && spectrum_tmap((const float2*)dHf[b], h, w, cw, brows, &tmH);
+      fft_rows_r2c(w, d.H, h, (float2*)dHh[b], tw_w, bs);
+      fft_cols_fwd_half(h, (float2*)dHh[b], wh, tw_h, bs, tma_ok ? (float2*)dHf[b] : nullptr, w);
+      if (tma_ok)
         done = fft_cols_inv_corr_tma(h, tmH, w, brows, (const float2*)dS[b], 0, K + 1, (float2*)dZ[b], tw_h,
                                      plan->dev_err, plan->sms, bs);
-      }
       if (!done && !fft_cols_inv_corr_pipe(h, (const float2*)dHh[b], w, (const float2*)dS[b], 0, K + 1,
                                            (float2*)dZ[b], tw_h, plan->sms, bs))
         fft_cols_inv_corr(h, (const float2*)dHh[b], w, (const float2*)dS[b], 0, K + 1, (float2*)dZ[b], tw_h, bs);

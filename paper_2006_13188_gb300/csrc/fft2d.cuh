@@ -534,7 +534,7 @@ __device__ __forceinline__ void cols_store_sm(float2* sm, const float2* v) {
 // Forward column pass of the half spectrum, in place (pitch ncols).
 template <int N>
 __global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, LineCfg<N>::COL_MINB)
-k_cols_fwd_half(float2* Hh, int ncols, const float2* __restrict__ tw) {
+k_cols_fwd_half(float2* Hh, int ncols, const float2* __restrict__ tw, float2* __restrict__ Hf, int w) {
   using C = LineCfg<N>;
   constexpr int T = C::COL_THREADS;
   extern __shared__ float2 sm[];
@@ -550,8 +550,15 @@ k_cols_fwd_half(float2* Hh, int ncols, const float2* __restrict__ tw) {
   __syncthreads();
   col_fft<N, false>(sm, twl);
   for_elems<C::CW * N, T>([&](int i, int e) {
-    const int u = u0 + e % C::CW;
-    if (u < ncols) Hh[(size_t)(e / C::CW) * ncols + u] = sm[e % C::CW + sidx(e / C::CW) * C::CW];
+    const int u = u0 + e % C::CW, v = e / C::CW;
+    if (u < ncols) {
+      const float2 x = sm[e % C::CW + sidx(v) * C::CW];
+      Hh[(size_t)v * ncols + u] = x;
+      if (Hf) {   // the full spectrum too: Hf(v, u) = x and, by Hermitian symmetry, Hf(-v, w - u) = conj x
+        Hf[(size_t)v * w + u] = x;
+        if (u > 0 && 2 * u < w) Hf[(size_t)((N - v) % N) * w + (w - u)] = c_conj(x);
+      }
+    }
   });
 }
 
@@ -1205,7 +1212,7 @@ struct FftOps {
   static void rows_inv_field(const float2* Z, int h, int K, const float* alpha, float* out,
                              const float2* tw, cudaStream_t st);
   static void rows_inv_real(const float2* Y, int h, float* out, const float2* tw, cudaStream_t st);
-  static void cols_fwd_half(float2* Hh, int ncols, const float2* tw, cudaStream_t st);
+  static void cols_fwd_half(float2* Hh, int ncols, const float2* tw, cudaStream_t st, float2* Hf, int w);
   static void cols_fwd_spectrum(const float2* X, int w, int conj_out, float scale, float2* S,
                                 const float2* tw, cudaStream_t st, int nplanes, float scale_rest);
   static void cols_inv_corr(const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
@@ -1286,11 +1293,11 @@ void FftOps<N>::rows_inv_real(const float2* Y, int h, float* out, const float2* 
 }
 
 template <int N>
-void FftOps<N>::cols_fwd_half(float2* Hh, int ncols, const float2* tw, cudaStream_t st) {
+void FftOps<N>::cols_fwd_half(float2* Hh, int ncols, const float2* tw, cudaStream_t st, float2* Hf, int w) {
   static const bool once = (ext_set_smem(k_cols_fwd_half<N>, C::COL_SMEM), true);
   (void)once;
   dim3 grid((ncols + C::CW - 1) / C::CW);
-  k_cols_fwd_half<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(Hh, ncols, tw);
+  k_cols_fwd_half<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(Hh, ncols, tw, Hf, w);
 }
 
 template <int N>

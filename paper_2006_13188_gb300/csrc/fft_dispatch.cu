@@ -64,8 +64,8 @@ void fft_rows_inv_real(int w, const float2* Y, int h, float* out, const float2* 
 }
 #undef EXT_C1
 
-#define EXT_C1(N) case N: FftOps<N>::cols_fwd_half(Hh, ncols, tw, st); return;
-void fft_cols_fwd_half(int h, float2* Hh, int ncols, const float2* tw, cudaStream_t st) {
+#define EXT_C1(N) case N: FftOps<N>::cols_fwd_half(Hh, ncols, tw, st, Hf, w); return;
+void fft_cols_fwd_half(int h, float2* Hh, int ncols, const float2* tw, cudaStream_t st, float2* Hf, int w) {
   switch (h) { EXT_FFT_SIZES(EXT_C1) default: return; }
 }
 #undef EXT_C1
@@ -146,23 +146,6 @@ bool fft_cols_tma_ok(int h) {
 #undef EXT_CASE
     default: return false;
   }
-}
-
-// Full spectrum from the half spectrum of a real signal (Hermitian symmetry):
-// Hf[v][u] = Hh[v][u] for u <= w/2, conj(Hh[(h-v) % h][w-u]) otherwise.
-__global__ void k_expand_hermitian(const float2* __restrict__ Hh, int h, int w, float2* __restrict__ Hf) {
-  const int wh = w / 2 + 1;
-  const long long n = (long long)h * w;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(i / w), u = (int)(i % w);
-    Hf[i] = u < wh ? Hh[(size_t)v * wh + u] : c_conj(Hh[(size_t)((h - v) % h) * wh + (w - u)]);
-  }
-}
-
-void launch_expand_hermitian(const float2* Hh, int h, int w, float2* Hf, int sms, cudaStream_t st) {
-  long long b = ((long long)h * w + 255) / 256;
-  if (b > (long long)sms * 8) b = (long long)sms * 8;
-  if (b > 0) k_expand_hermitian<<<(unsigned)b, 256, 0, st>>>(Hh, h, w, Hf);
 }
 
 // fused y and x inverse passes of square N x N planes (N = ny = nx)

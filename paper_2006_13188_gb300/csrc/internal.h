@@ -36,7 +36,9 @@ void fft_rows_inv_components(int w, const float2* Z, int h, int k0, int nk, floa
 void fft_rows_inv_field(int w, const float2* Z, int h, int K, const float* alpha, float* out,
                         const float2* tw, cudaStream_t st);
 void fft_rows_inv_real(int w, const float2* Y, int h, float* out, const float2* tw, cudaStream_t st);
-void fft_cols_fwd_half(int h, float2* Hh, int ncols, const float2* tw, cudaStream_t st);
+// Hf (optional): the full h x w spectrum written as well (Hermitian mirror of the half spectrum)
+void fft_cols_fwd_half(int h, float2* Hh, int ncols, const float2* tw, cudaStream_t st, float2* Hf = nullptr,
+                       int w = 0);
 void fft_cols_fwd_spectrum(int h, const float2* X, int w, int conj_out, float scale, float2* S,
                            const float2* tw, cudaStream_t st, int nplanes = 1, float scale_rest = 0.f);
 void fft_cols_inv_corr(int h, const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
@@ -55,7 +57,6 @@ bool make_tmap_2d_f32(const void* base, unsigned long long dim0, unsigned long l
 bool fft_cols_tma_ok(int h);
 bool fft_cols_inv_corr_tma(int h, const CUtensorMap& tmH, int w, int br, const float2* S, int k0, int nk, float2* Z,
                            const float2* tw, int* err, int sms, cudaStream_t st);
-void launch_expand_hermitian(const float2* Hh, int h, int w, float2* Hf, int sms, cudaStream_t st);
 // 3D building blocks: in-place complex column pass over planes; inverse row
 // pass into real channel planes; full-spectrum product column pass.
 void fft_cols_c2c(int h, float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st);
