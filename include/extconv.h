@@ -355,6 +355,35 @@ ext_status ext_corr_so3_propose(ext_plan plan, const float* V, int nz, int ny, i
                                 void* stream);
 
 /*
+ * Pattern detection front end (Sec. 5 "Defining the Filter and Transformation
+ * Field").  Signal and field of an image I (Eq. signal, Eq. theta):
+ *   H_out = |grad I|,  theta_out = atan2(dI/dy, dI/dx)  (radians),
+ * with central differences and periodic indices,
+ *   dI/dx(y, x) = (I(y, x+1) - I(y, x-1)) / 2,  x = column, y = row.
+ * I, H_out, theta_out: h x w float32, row-major (host or device).  H_out and
+ * theta_out feed ext_conv_so2 as the signal and the rotation field.
+ */
+ext_status ext_gradient_field(ext_plan plan, const float* I, int h, int w, float* H_out, float* theta_out,
+                              void* stream);
+
+/*
+ * Consensus filter (Sec. 5, Eq. opt_filt; the appendix derives it as the
+ * filter maximising the extended-convolution response at the centre): every
+ * pixel q of the pattern P with |q - c| <= eps votes with weight |grad P(q)|
+ * (gradient as in ext_gradient_field, periodic within P, FP64) into the bin
+ *   d = R(-theta_P(q)) (c - q),  R(a) = [[cos a, -sin a], [sin a, cos a]],
+ * the unit impulse being a bilinear splat onto integer offsets.  P: hp x wp
+ * float64 row-major; c = (cy, cx) a pixel of P; F_out: (2R+1) x (2R+1)
+ * float64 with R = ext_consensus_radius(eps) = ceil(eps) + 1, offset (dx, dy)
+ * at F_out[(dy + R)(2R + 1) + dx + R].  Use it as a SAMPLED ext_filter_so2
+ * (img = F_out, R) for ext_conv_so2.  EXT_ERR_INVALID_ARG for an empty
+ * pattern, a centre outside it or eps outside [0, 4096].
+ */
+int ext_consensus_radius(double eps);
+ext_status ext_consensus_filter(ext_plan plan, const double* P, int hp, int wp, int cy, int cx, double eps,
+                                double* F_out, void* stream);
+
+/*
  * Allocation-free variant of the FP32 angular sweep (the paper has no
  * counterpart: this entry point exists for callers that cannot let a library
  * allocate device memory -- an application whose device memory is all owned

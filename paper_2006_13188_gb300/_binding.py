@@ -38,7 +38,8 @@ EXPORTED = (
     "ext_so3_channels", "ext_so3_wigner", "ext_corr_so3_components", "ext_sweep_so3", "ext_corr_so3",
     "ext_mlp_create", "ext_mlp_destroy", "ext_mlp_set_params", "ext_mlp_get_params", "ext_mlp_forward",
     "ext_mlp_grads", "ext_mlp_train", "ext_so3_upper_bound", "ext_so3_refined_bound", "ext_so3_gather", "ext_so3_augment", "ext_so3_refine",
-    "ext_so3_propose", "ext_corr_so3_propose",
+    "ext_so3_propose", "ext_corr_so3_propose", "ext_gradient_field", "ext_consensus_radius",
+    "ext_consensus_filter",
 )
 
 
@@ -117,8 +118,11 @@ def lib():
         L.ext_corr_so3_propose.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, dbl, i32, vp, vp, i32, f32, vp, vp,
                                            vp, i32, vp, vp]
         L.ext_conv_scale.argtypes = [vp, vp, i32, i32, i32, vp, i32, dbl, dbl, dbl, dbl, vp, i32, vp, vp]
+        L.ext_gradient_field.argtypes = [vp, vp, i32, i32, vp, vp, vp]
+        L.ext_consensus_radius.argtypes = [dbl]
+        L.ext_consensus_filter.argtypes = [vp, vp, i32, i32, i32, i32, dbl, vp, vp]
         for name in EXPORTED:
-            if name not in ("ext_status_string", "ext_last_error", "ext_so3_channels"):
+            if name not in ("ext_status_string", "ext_last_error", "ext_so3_channels", "ext_consensus_radius"):
                 getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -428,3 +432,17 @@ def ext_corr_so3_propose(plan: Plan, V, nz, ny, nx, tables, dr, R, net, quats, b
                                       q.shape[0], float(bound), _ptr(score), _ptr(quat), _ptr(grid_idx),
                                       int(precision), _ptr(counts), _stream(stream)))
     return int(counts[0]), int(counts[1]), int(counts[2])
+
+
+def ext_gradient_field(plan: Plan, I, h, w, H_out, theta_out, stream=None):
+    _check(lib().ext_gradient_field(plan.handle, _ptr(I), int(h), int(w), _ptr(H_out), _ptr(theta_out),
+                                    _stream(stream)))
+
+
+def ext_consensus_radius(eps):
+    return int(lib().ext_consensus_radius(float(eps)))
+
+
+def ext_consensus_filter(plan: Plan, P, hp, wp, cy, cx, eps, F_out, stream=None):
+    _check(lib().ext_consensus_filter(plan.handle, _ptr(P), int(hp), int(wp), int(cy), int(cx), float(eps),
+                                      _ptr(F_out), _stream(stream)))
