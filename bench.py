@@ -51,7 +51,7 @@ def parse_args():
                     help="so3 / so3p: volume side (128 is the workload; smaller only for profiling captures)")
     ap.add_argument("--train-steps", type=int, default=6000,
                     help="so3p: Adam steps of the proposal network (setup, not timed)")
-    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p"],
+    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght"],
                     help="so2: the pattern-matching sweep (default, the headline metric); "
                          "scale: scale-adaptive smoothing of a 4096x4096x3 image; "
                          "batched: 512 uneven images in one captured graph; "
@@ -279,6 +279,124 @@ def bench_conv(args, world, rank, local):
             "clocks": clk.summary(), "gpu_launches": int(sum(v[1] for v in prof.values())),
             "kernels": {k: {"ms_per_call": v[0], "launches": v[1]} for k, v in prof.items()},
             "cpu_baseline": cpu}))
+    plan.close()
+    return 0
+
+
+# --------------------------------------------------------- GHT workload ---
+GHT_WORKLOAD = ("pattern detection (Sec. 5 generalised Hough transform): 2048x2048 f32 image (noise 0.05 blurred "
+                "sigma 1 + 12 planted 49x49 patterns at random angles); consensus filter eps=22 (47x47 box), K=16; "
+                "per step: gradient signal and field, extended convolution")
+
+
+def bench_ght(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_2006_13188_gb300 as ec
+    from paper_2006_13188_gb300 import ght
+    import synth
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    prob = synth.ght_problem(seed=synth.seed_for(6) + rank)
+    h, w = prob["I"].shape
+    P = h * w
+    K, eps = 16, 22.0
+    r = prob["radius"]
+    plan = ec.Plan(local)
+    t0 = time.perf_counter()
+    filt, _ = ght.consensus_filter(plan, prob["pattern"], (r, r), eps, K)
+    I = torch.from_numpy(prob["I"]).to(device)
+    out = torch.empty_like(I)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    def call():
+        ght.detect(plan, I, h, w, filt, out)
+    call()
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    barrier(world)
+    total = 0.0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+    total = reduce_max(total, world, device)
+    plan.profile_read()
+    plan.profile(True)
+    prof_steps = 5
+    for _ in range(prof_steps):
+        call()
+    torch.cuda.synchronize()
+    prof = {k: v for k, v in plan.profile_read().items() if v[1] > 0}
+    plan.profile(False)
+    # detection check: planted centres whose 7x7 neighbourhood beats every pixel away from all centres
+    resp = out.cpu().numpy()
+    away = np.ones(resp.shape, bool)
+    for cy, cx in prob["centres"]:
+        away[max(cy - 3, 0):cy + 4, max(cx - 3, 0):cx + 4] = False
+    background = float(resp[away].max())
+    peaks = [float(resp[max(cy - 3, 0):cy + 4, max(cx - 3, 0):cx + 4].max()) for cy, cx in prob["centres"]]
+    found = sum(p > background for p in peaks)
+    # end to end through the C ABI with pinned host buffers (image in, response written in place)
+    Ih = torch.from_numpy(prob["I"]).pin_memory()
+    oh = torch.empty((h, w), dtype=torch.float32).pin_memory()
+    e2e_steps = max(5, min(args.steps, 50))
+    ght.detect(plan, Ih, h, w, filt, oh)
+    barrier(world)
+    t1 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ght.detect(plan, Ih, h, w, filt, oh)
+    e2e_s = reduce_max(time.perf_counter() - t1, world, device)
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    avg_ms = dom_ms / dom_n
+    kc = K + 1
+    alg = {"cols_conv": kc * 8 * P * 2 + 8 * P, "rows_fwd_phase": 8 * P + kc * 8 * P}.get(dom_name)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
+    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
+                "kernels": {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps}
+                            for k, v in prof.items()}}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle.filters_so2 import decompose_sampled
+        from oracle.ght import consensus_filter as cf_ref, consensus_radius, gradient_field
+        from oracle.so2 import ext_conv_so2_at
+        rng = np.random.default_rng(0)
+        pix = rng.integers(0, h, (256, 2))
+        t2 = time.perf_counter()
+        Hr, Tr = gradient_field(prob["I"])
+        fr = decompose_sampled(cf_ref(prob["pattern"], (r, r), eps), K, 0.25, 128)
+        ext_conv_so2_at(Hr, fr, Tr, consensus_radius(eps), pix)
+        t = time.perf_counter() - t2
+        cpu = {"value": len(pix) / t / 1e6, "unit": "Mpx/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 gradient field of the whole image, consensus filter, brute-force extended "
+                         f"convolution at {len(pix)} random pixels ({t:.1f} s)"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "GHT pattern detection Mpx/s", "value": world * args.steps * P / (total * 1e-3) / 1e6,
+            "unit": "Mpx/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (filter FP64)", "data": "synthetic",
+            "config": {"workload": GHT_WORKLOAD, "l2": "256 MB written between steps", "plan_ms": plan_ms,
+                       "planted_found": f"{found}/{len(prob['centres'])}",
+                       "weakest_peak_over_background": min(peaks) / background},
+            "clocks": clk.summary(),
+            "e2e": {"value": world * e2e_steps * P / e2e_s / 1e6, "unit": "Mpx/s", "h2d_bytes_per_step": 4 * P,
+                    "d2h_bytes_per_step": 4 * P, "steps": e2e_steps},
+            "gpu_launches": int(sum(v[1] for v in prof.values()) // prof_steps),
+            "roofline": roofline, "cpu_baseline": cpu}))
     plan.close()
     return 0
 
@@ -677,6 +795,8 @@ def main():
     world, rank, local = dist_setup(args.gpus)
     if args.workload == "conv" and args.impl == "ours":
         return bench_conv(args, world, rank, local)
+    if args.workload == "ght" and args.impl == "ours":
+        return bench_ght(args, world, rank, local)
     if args.workload == "scale" and args.impl == "ours":
         return bench_scale(args, world, rank, local)
     if args.workload == "batched" and args.impl == "ours":

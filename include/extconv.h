@@ -384,6 +384,16 @@ ext_status ext_consensus_filter(ext_plan plan, const double* P, int hp, int wp, 
                                 double* F_out, void* stream);
 
 /*
+ * Pattern detection (Sec. 5): the response {H, theta} * F of Eq. Def-EConv
+ * with the signal H = |grad I| and field theta of ext_gradient_field, F
+ * typically the consensus filter of ext_consensus_filter (as a SAMPLED
+ * filter).  I, out: h x w float32 (host or device); the gradient and the
+ * steered transforms stay in plan workspace.
+ */
+ext_status ext_ght_detect(ext_plan plan, const float* I, int h, int w, const ext_filter_so2* F, float* out,
+                          void* stream);
+
+/*
  * Allocation-free variant of the FP32 angular sweep (the paper has no
  * counterpart: this entry point exists for callers that cannot let a library
  * allocate device memory -- an application whose device memory is all owned

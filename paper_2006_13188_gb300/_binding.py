@@ -39,7 +39,7 @@ EXPORTED = (
     "ext_mlp_create", "ext_mlp_destroy", "ext_mlp_set_params", "ext_mlp_get_params", "ext_mlp_forward",
     "ext_mlp_grads", "ext_mlp_train", "ext_so3_upper_bound", "ext_so3_refined_bound", "ext_so3_gather", "ext_so3_augment", "ext_so3_refine",
     "ext_so3_propose", "ext_corr_so3_propose", "ext_gradient_field", "ext_consensus_radius",
-    "ext_consensus_filter",
+    "ext_consensus_filter", "ext_ght_detect",
 )
 
 
@@ -121,6 +121,7 @@ def lib():
         L.ext_gradient_field.argtypes = [vp, vp, i32, i32, vp, vp, vp]
         L.ext_consensus_radius.argtypes = [dbl]
         L.ext_consensus_filter.argtypes = [vp, vp, i32, i32, i32, i32, dbl, vp, vp]
+        L.ext_ght_detect.argtypes = [vp, vp, i32, i32, fp, vp, vp]
         for name in EXPORTED:
             if name not in ("ext_status_string", "ext_last_error", "ext_so3_channels", "ext_consensus_radius"):
                 getattr(L, name).restype = i32
@@ -446,3 +447,7 @@ def ext_consensus_radius(eps):
 def ext_consensus_filter(plan: Plan, P, hp, wp, cy, cx, eps, F_out, stream=None):
     _check(lib().ext_consensus_filter(plan.handle, _ptr(P), int(hp), int(wp), int(cy), int(cx), float(eps),
                                       _ptr(F_out), _stream(stream)))
+
+
+def ext_ght_detect(plan: Plan, I, h, w, F: FilterSO2, out, stream=None):
+    _check(lib().ext_ght_detect(plan.handle, _ptr(I), int(h), int(w), F.ref(), _ptr(out), _stream(stream)))

@@ -296,6 +296,28 @@ ext_status run_components(ext_plan plan, const float* H, int h, int w, const ext
   return EXT_OK;
 }
 
+// Extended convolution of device buffers (Sec. 2.2 Eq. Def-EConv, the algorithm
+// of Sec. 4.1): out = Re sum_k (H e^{-ik alpha}) * F_k.
+ext_status run_conv_so2(ext_plan plan, const float* H, const float* alpha, int h, int w, const ext_filter_so2* F,
+                        float* out, cudaStream_t st) {
+  const size_t P = (size_t)h * w;
+  const int K = F->K;
+  const float2* S = nullptr;
+  EXT_TRY(spectra(plan, F, h, w, SPEC_CONV, st, &S));
+  const float2 *tw_w = nullptr, *tw_h = nullptr;
+  EXT_TRY(twiddle(plan, w, st, &tw_w));
+  EXT_TRY(twiddle(plan, h, st, &tw_h));
+  void *A = nullptr, *Y = nullptr;
+  EXT_TRY(ensure(plan, "Aall", sizeof(float2) * P * (K + 1), &A));
+  EXT_TRY(ensure(plan, "Y", sizeof(float2) * P, &Y));
+  launch(plan, "rows_fwd_phase", st,
+         [&] { fft_rows_fwd_phase(w, H, alpha, h, 0, K + 1, (float2*)A, tw_w, st); });
+  launch(plan, "cols_conv", st, [&] { fft_cols_conv(h, (const float2*)A, w, K, S, (float2*)Y, tw_h, st); });
+  launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, out, tw_w, st); });
+  EXT_CUDA(cudaGetLastError());
+  return EXT_OK;
+}
+
 ext_status run_sweep(ext_plan plan, const float* G, long long P, int K, int J, float* maxv, int32_t* argmax,
                      int precision, cudaStream_t st) {
   if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3)
@@ -578,26 +600,37 @@ ext_status ext_conv_so2(ext_plan plan, const float* H, int h, int w, const ext_f
   EXT_CUDA(cudaSetDevice(plan->device));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t P = (size_t)h * w;
-  const int K = F->K;
   Staged sH, sAl, sO;
   EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P, st, &sH));
   EXT_TRY(stage_in(plan, "in_alpha", alpha, sizeof(float) * P, st, &sAl));
   EXT_TRY(stage_out_alloc(plan, "out_0", out, sizeof(float) * P, &sO));
-  const float2* S = nullptr;
-  EXT_TRY(spectra(plan, F, h, w, SPEC_CONV, st, &S));
-  const float2 *tw_w = nullptr, *tw_h = nullptr;
-  EXT_TRY(twiddle(plan, w, st, &tw_w));
-  EXT_TRY(twiddle(plan, h, st, &tw_h));
-  void *A = nullptr, *Y = nullptr;
-  EXT_TRY(ensure(plan, "Aall", sizeof(float2) * P * (K + 1), &A));
-  EXT_TRY(ensure(plan, "Y", sizeof(float2) * P, &Y));
-  launch(plan, "rows_fwd_phase", st,
-         [&] { fft_rows_fwd_phase(w, (const float*)sH.dev, (const float*)sAl.dev, h, 0, K + 1, (float2*)A, tw_w, st); });
-  launch(plan, "cols_conv", st, [&] { fft_cols_conv(h, (const float2*)A, w, K, S, (float2*)Y, tw_h, st); });
-  launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, (float*)sO.dev, tw_w, st); });
-  EXT_CUDA(cudaGetLastError());
+  EXT_TRY(run_conv_so2(plan, (const float*)sH.dev, (const float*)sAl.dev, h, w, F, (float*)sO.dev, st));
   EXT_TRY(stage_out_finish(sO, st));
   return finish_host(plan, sH.host || sAl.host || sO.host, st);
+}
+
+ext_status ext_ght_detect(ext_plan plan, const float* I, int h, int w, const ext_filter_so2* F, float* out,
+                          void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_TRY(check_filter(F));
+  EXT_TRY(check_size(h, w));
+  if (h == 0 || w == 0) return EXT_OK;
+  if (!I || !out) return fail(EXT_ERR_INVALID_ARG, "NULL buffer");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)h * w;
+  Staged sI, sO;
+  EXT_TRY(stage_in(plan, "in_I", I, sizeof(float) * P, st, &sI));
+  // the response is written once, by the last row pass: page-locked host output in place
+  EXT_TRY(stage_out_direct(plan, "out_0", out, sizeof(float) * P, &sO));
+  void *Hs = nullptr, *Ts = nullptr;
+  EXT_TRY(ensure(plan, "ght_H", sizeof(float) * P, &Hs));
+  EXT_TRY(ensure(plan, "ght_theta", sizeof(float) * P, &Ts));
+  launch(plan, "gradient_field", st,
+         [&] { launch_gradient_field((const float*)sI.dev, h, w, (float*)Hs, (float*)Ts, plan->sms, st); });
+  EXT_TRY(run_conv_so2(plan, (const float*)Hs, (const float*)Ts, h, w, F, (float*)sO.dev, st));
+  EXT_TRY(stage_out_finish(sO, st));
+  return finish_host(plan, sI.host || sO.host || sO.mapped, st);
 }
 
 ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, int w, const double* mellin_c, int n_h,

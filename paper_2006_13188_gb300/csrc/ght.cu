@@ -61,6 +61,12 @@ __global__ void k_consensus_vote(const double* __restrict__ P, int hp, int wp, i
 
 }  // namespace
 
+void launch_gradient_field(const float* I, int h, int w, float* H, float* theta, int sms, cudaStream_t st) {
+  long long b = ((long long)h * w + 255) / 256;
+  if (b > (long long)sms * 16) b = (long long)sms * 16;
+  if (b > 0) k_gradient_field<<<(unsigned)b, 256, 0, st>>>(I, h, w, H, theta);
+}
+
 extern "C" {
 
 ext_status ext_gradient_field(ext_plan plan, const float* I, int h, int w, float* H_out, float* theta_out,
@@ -76,10 +82,8 @@ ext_status ext_gradient_field(ext_plan plan, const float* I, int h, int w, float
   EXT_TRY(stage_in(plan, "in_I", I, sizeof(float) * P, st, &sI));
   EXT_TRY(stage_out_alloc(plan, "out_0", H_out, sizeof(float) * P, &sH));
   EXT_TRY(stage_out_alloc(plan, "out_1", theta_out, sizeof(float) * P, &sT));
-  long long b = ((long long)P + 255) / 256;
-  if (b > (long long)plan->sms * 16) b = (long long)plan->sms * 16;
   launch(plan, "gradient_field", st, [&] {
-    k_gradient_field<<<(unsigned)b, 256, 0, st>>>((const float*)sI.dev, h, w, (float*)sH.dev, (float*)sT.dev);
+    launch_gradient_field((const float*)sI.dev, h, w, (float*)sH.dev, (float*)sT.dev, plan->sms, st);
   });
   EXT_CUDA(cudaGetLastError());
   EXT_TRY(stage_out_finish(sH, st));

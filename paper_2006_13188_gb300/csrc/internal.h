@@ -83,6 +83,9 @@ void launch_component_grid_mellin(double2 ck, double omega, double r_min, double
 void launch_scale_finalize(const float* H, const float* s, const float* N, const float* D, int channels, long long P,
                            int mode, float cd, float* out, int sms, cudaStream_t st);
 
+// ----- pattern detection front end (ght.cu): H = |grad I|, theta = atan2(dI/dy, dI/dx)
+void launch_gradient_field(const float* I, int h, int w, float* H, float* theta, int sms, cudaStream_t st);
+
 // ----- sweep (sweep.cu)
 // B: J rows of cp floats (cp = 2K rounded up to a multiple of 4).
 bool sweep_fp32(const float* G, long long P, int K, int J, const float* B, int cp, float* maxv,

@@ -22,16 +22,8 @@ def consensus_filter(plan, P, centre, eps, K, dr=0.25, n_theta=128):
     return b.FilterSO2.sampled(F, K, dr, n_theta), F
 
 
-def detect(plan, I, h, w, filt, out, H=None, theta=None, stream=None):
+def detect(plan, I, h, w, filt, out, stream=None):
     """Detection response {|grad I|, theta_grad I} * F (Eq. Def-EConv) of image
-    I into `out` (h x w float32); H and theta (h x w float32 scratch, device
-    when I is) receive the signal and the field."""
-    import torch
-    dev = I.device if hasattr(I, "device") else None
-    if H is None:
-        H = torch.empty((h, w), dtype=torch.float32, device=dev) if dev is not None else np.empty((h, w), np.float32)
-    if theta is None:
-        theta = torch.empty((h, w), dtype=torch.float32, device=dev) if dev is not None else np.empty((h, w), np.float32)
-    b.ext_gradient_field(plan, I, h, w, H, theta, stream)
-    b.ext_conv_so2(plan, H, h, w, filt, theta, out, stream)
+    I into `out` (h x w float32, host or device)."""
+    b.ext_ght_detect(plan, I, h, w, filt, out, stream)
     return out

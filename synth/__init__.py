@@ -177,6 +177,27 @@ def so2_match_problem(seed: int | None = None, size: int | tuple = 2048, n_plant
                 radius=radius, K=K, J=J, dr=0.25, n_theta=128)
 
 
+# ------------------------------------------------- pattern detection (GHT) ---
+
+def ght_problem(seed: int | None = None, size: int | tuple = 2048, n_plant: int = 12, radius: int = 24,
+                noise_sigma: float = 0.05, blur: float = 3.0):
+    """Pattern-detection input for the generalised Hough transform of Sec. 5:
+    a smooth random pattern ((2R+1)^2, as smooth_random_template, scaled to
+    peak |value| 1) and an image of Gaussian noise (sigma 0.05, periodic blur
+    sigma 1) plus ``n_plant`` copies of the pattern rotated by
+    beta ~ U[0, 2 pi) at centres at least 2R+1 apart, float32."""
+    rng = np.random.default_rng(seed_for(6) if seed is None else seed)
+    h, w = (size, size) if np.isscalar(size) else size
+    pattern = smooth_random_template(rng, radius, blur)
+    pattern /= np.abs(pattern).max()
+    I = periodic_gaussian_blur(rng.normal(0.0, noise_sigma, (h, w)), 1.0)
+    centres = _place_centres(rng, h, w, n_plant, 2 * radius + 1)
+    betas = rng.uniform(0.0, 2 * math.pi, n_plant)
+    for c, b in zip(centres, betas):
+        plant_rotated(I, pattern, c, b)
+    return dict(I=I.astype(np.float32), pattern=pattern, centres=centres, betas=betas, radius=radius)
+
+
 # ------------------------------------------------------------- workload 4 ---
 
 def batched_descriptors(seed: int | None = None, n_images: int = 512,
