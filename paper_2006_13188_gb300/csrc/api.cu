@@ -312,7 +312,18 @@ ext_status run_conv_so2(ext_plan plan, const float* H, const float* alpha, int h
   EXT_TRY(ensure(plan, "Y", sizeof(float2) * P, &Y));
   launch(plan, "rows_fwd_phase", st,
          [&] { fft_rows_fwd_phase(w, H, alpha, h, 0, K + 1, (float2*)A, tw_w, st); });
-  launch(plan, "cols_conv", st, [&] { fft_cols_conv(h, (const float2*)A, w, K, S, (float2*)Y, tw_h, st); });
+  // tensor-copy staged column pass where the tile shape allows it
+  const int cw = fft_col_tile(h);
+  const int br = plan->tma && fft_cols_tma_ok(h) ? tma_rows(h, cw) : 0;
+  CUtensorMap tmA;
+  bool done = false;
+  if (br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w, (unsigned long long)(K + 1) * h,
+                                 (unsigned long long)2 * w * sizeof(float), (unsigned)(2 * cw), (unsigned)br, &tmA))
+    launch(plan, "cols_conv_tma", st, [&] {
+      done = fft_cols_conv_tma(h, tmA, w, br, K, S, (float2*)Y, tw_h, plan->dev_err, plan->sms, st);
+    });
+  if (!done)
+    launch(plan, "cols_conv", st, [&] { fft_cols_conv(h, (const float2*)A, w, K, S, (float2*)Y, tw_h, st); });
   launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, out, tw_w, st); });
   EXT_CUDA(cudaGetLastError());
   return EXT_OK;

@@ -1119,6 +1119,118 @@ k_cols_inv_corr_tma(const __grid_constant__ CUtensorMap tmH, int w, int br, cons
   if (pending) tc::mbar_wait_bounded(mb, phase, 1000000000ull, err, EXT_ERR_TIMEOUT);
 }
 
+// Convolution column pass (extended convolution, Sec. 4.1 last paragraph:
+// Y = sum_k FFT(A_k) F^_k, then the inverse column transform) with the
+// steered signals and the spectra staged by the tensor memory accelerator:
+// per (column tile, k) one set of 2D tensor copies of the A_k tile (A seen as
+// (K+1) h rows of 2w floats) and one bulk copy of the spectrum tile, each on
+// its own mbarrier.  The next A tile is requested as soon as the first
+// butterfly stage has read the current one, the next spectrum tile as soon as
+// the products have been accumulated (in registers).  Column tiles are
+// strided over the blocks; waits are bounded (err = EXT_ERR_TIMEOUT, the
+// block stops).
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, 1)
+k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, const float2* __restrict__ S,
+                float2* __restrict__ Y, const float2* __restrict__ tw, int* __restrict__ err) {
+  using C = LineCfg<N>;
+  using TC = TmaColCfg<N>;
+  constexpr int T = C::COL_THREADS;
+  constexpr int CW = C::CW;
+  constexpr int TILE = TC::TILE;
+  extern __shared__ float2 sm_raw[];
+  __shared__ __align__(8) uint64_t bar_a, bar_s;
+  __shared__ int abort_flag;
+  float2* sm = reinterpret_cast<float2*>(sm_raw) + ((128 - (tc::smem_u32(sm_raw) & 127)) & 127) / 8;
+  float2* W = sm;
+  float2* SS = sm + TC::OFF_S;
+  float2* AS = sm + TC::OFF_H;
+  const float2* TWs = stage_twiddles<N, TC::OFF_TW>(sm, tw, T);
+  const int ntiles = (w + CW - 1) / CW;
+  const uint32_t ma = tc::smem_u32(&bar_a), ms = tc::smem_u32(&bar_s);
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    tc::mbar_init(ma, 1);
+    tc::mbar_init(ms, 1);
+  }
+  __syncthreads();
+  auto issue_a = [&](int tile, int k) {   // thread 0
+    tc::fence_proxy_async();
+    tc::mbar_expect_tx(ma, TILE * 8u);
+    for (int y = 0; y < N; y += br) tc::tma_load_2d(tc::smem_u32(AS + y * CW), &tmA, 2 * tile * CW, k * N + y, ma);
+  };
+  auto issue_s = [&](int tile, int k) {   // thread 0
+    tc::fence_proxy_async();
+    tc::mbar_expect_tx(ms, TILE * 8u);
+    tc::bulk_load(tc::smem_u32(SS), S + ((size_t)k * ntiles + tile) * TILE, TILE * 8u, ms);
+  };
+  constexpr RadixList L = factor_radices(N);
+  constexpr int R0 = L.r[0];
+  static_assert(L.cnt > 1, "at least two radix stages");
+  uint32_t pa = 0, ps = 0;
+  bool pend_a = false, pend_s = false;
+  if ((int)blockIdx.x < ntiles) {
+    if (threadIdx.x == 0) {
+      issue_a(blockIdx.x, 0);
+      issue_s(blockIdx.x, 0);
+    }
+    pend_a = pend_s = true;
+  }
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int u0 = tile * CW;
+    const int next_tile = tile + gridDim.x;
+    float2 acc[C::COL_EPT];
+    for_elems<C::CW * N, T>([&](int i, int e) { acc[i] = make_float2(0.f, 0.f); });
+    for (int k = 0; k <= K; ++k) {
+      const bool more = k < K || next_tile < ntiles;
+      const int nt = k < K ? tile : next_tile, nk = k < K ? k + 1 : 0;
+      if (!tc::mbar_wait_bounded(ma, pa, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_flag = 1;
+      __syncthreads();
+      if (abort_flag) break;
+      pa ^= 1u;
+      pend_a = false;
+      auto load = [&](int c, int v) -> float2 { return AS[v * CW + c]; };
+      auto nostore = [](int, int, float2) {};
+      ct_stage_io<N, R0, 1, false, true, CW, T, true, false>(W, 1, CW, TWs, load, nostore);
+      if (more) {   // the first stage has read the A tile
+        if (threadIdx.x == 0) issue_a(nt, nk);
+        pend_a = true;
+      }
+      ct_fft<N, false, true, CW, T, 1, R0>(W, 1, CW, TWs);
+      if (!tc::mbar_wait_bounded(ms, ps, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_flag = 1;
+      __syncthreads();
+      if (abort_flag) break;
+      ps ^= 1u;
+      pend_s = false;
+      for_elems<C::CW * N, T>([&](int i, int e) {
+        const float2 sp = SS[e];
+        const float2 x = W[e % CW + sidx(e / CW) * CW];
+        acc[i].x = fmaf(x.x, sp.x, fmaf(-x.y, sp.y, acc[i].x));
+        acc[i].y = fmaf(x.x, sp.y, fmaf(x.y, sp.x, acc[i].y));
+      });
+      __syncthreads();   // products read W and the spectrum tile
+      if (more) {
+        if (threadIdx.x == 0) issue_s(nt, nk);
+        pend_s = true;
+      }
+    }
+    if (abort_flag) break;
+    cols_store_sm<N>(W, acc);
+    __syncthreads();
+    col_fft<N, true>(W, TWs);
+    for_elems<C::CW * N, T>([&](int i, int e) {
+      const int u = u0 + e % CW;
+      if (u < w) Y[(size_t)(e / CW) * w + u] = W[e % CW + sidx(e / CW) * CW];
+    });
+    __syncthreads();
+  }
+  // copies still in flight (timeout path): wait for them, bounded, before the block exits
+  if (threadIdx.x == 0) {
+    if (pend_a) tc::mbar_wait_bounded(ma, pa, 1000000000ull, err, EXT_ERR_TIMEOUT);
+    if (pend_s) tc::mbar_wait_bounded(ms, ps, 1000000000ull, err, EXT_ERR_TIMEOUT);
+  }
+}
+
 // Inverse row pass of Z writing the component planes of G (k = k0 + item / nblk).
 // The RL rows of the next item (contiguous in Z) arrive by one bulk copy
 // completing on an mbarrier, issued by thread 0 as soon as the first
@@ -1219,6 +1331,8 @@ struct FftOps {
                             const float2* tw, cudaStream_t st);
   static void cols_conv(const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
                         cudaStream_t st);
+  static bool cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
+                            const float2* tw, int* err, int sms, cudaStream_t st);
   static void cols_c2c(float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st);
   static void rows_inv_channels(const float2* Z, int rows, int k0, int nk, const int2* chan, float* G,
                                 const float2* tw, cudaStream_t st);
@@ -1375,6 +1489,21 @@ bool FftOps<N>::cols_inv_corr_tma(const CUtensorMap& tmH, int w, int br, const f
     const int items = ((w + C::CW - 1) / C::CW) * nk;
     const int grid = pipe_grid<N>(items, sms, TmaColCfg<N>::SMEM, C::COL_THREADS);
     k_cols_inv_corr_tma<N><<<grid, C::COL_THREADS, TmaColCfg<N>::SMEM, st>>>(tmH, w, br, S, k0, nk, Z, tw, err);
+    return true;
+  }
+}
+
+template <int N>
+bool FftOps<N>::cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
+                              const float2* tw, int* err, int sms, cudaStream_t st) {
+  if constexpr (!TmaColCfg<N>::OK || factor_radices(N).cnt < 2) {
+    return false;
+  } else {
+    static const bool once = (ext_set_smem(k_cols_conv_tma<N>, TmaColCfg<N>::SMEM), true);
+    (void)once;
+    const int tiles = (w + C::CW - 1) / C::CW;
+    const int grid = pipe_grid<N>(tiles, sms, TmaColCfg<N>::SMEM, C::COL_THREADS);
+    k_cols_conv_tma<N><<<grid, C::COL_THREADS, TmaColCfg<N>::SMEM, st>>>(tmA, w, br, K, S, Y, tw, err);
     return true;
   }
 }

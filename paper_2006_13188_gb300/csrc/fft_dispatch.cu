@@ -132,6 +132,13 @@ bool fft_cols_inv_full_pipe(int h, const float2* H, int w, const float2* S, int 
 }
 #undef EXT_C1
 
+#define EXT_C1(N) case N: return FftOps<N>::cols_conv_tma(tmA, w, br, K, S, Y, tw, err, sms, st);
+bool fft_cols_conv_tma(int h, const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
+                       const float2* tw, int* err, int sms, cudaStream_t st) {
+  switch (h) { EXT_FFT_SIZES(EXT_C1) default: return false; }
+}
+#undef EXT_C1
+
 #define EXT_C1(N) case N: return FftOps<N>::cols_inv_corr_tma(tmH, w, br, S, k0, nk, Z, tw, err, sms, st);
 bool fft_cols_inv_corr_tma(int h, const CUtensorMap& tmH, int w, int br, const float2* S, int k0, int nk, float2* Z,
                            const float2* tw, int* err, int sms, cudaStream_t st) {

@@ -69,6 +69,11 @@ bool fft_cols_inv_full_pipe(int h, const float2* H, int w, const float2* S, int 
                             const float2* tw, int sms, cudaStream_t st);
 void fft_cols_conv(int h, const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
                    cudaStream_t st);
+// The same pass with the A_k and spectrum tiles staged by the tensor memory
+// accelerator: tmA maps A as (K+1) h rows of 2w floats, boxes of 2 * col_tile
+// floats x br rows; false if this length has no such variant.
+bool fft_cols_conv_tma(int h, const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
+                       const float2* tw, int* err, int sms, cudaStream_t st);
 
 // ----- filter side, FP64 (filter.cu)
 void launch_twiddle(float2* tw, int n, cudaStream_t st);
