@@ -335,7 +335,7 @@ k_rows_r2c(const float* __restrict__ H, int h, float2* __restrict__ Hh, const fl
 
 // Forward transform of the steered signals A_k = H exp(-i k alpha) (Sec. 4.1,
 // extended convolution: the signal is pre-multiplied before convolving with
-// F_k).  blockIdx.y selects k = k0 + blockIdx.y.
+// F_k).  blockIdx.x selects k = k0 + blockIdx.x, blockIdx.y the row block.
 template <int N>
 __global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
 k_rows_fwd_phase(const float* __restrict__ H, const float* __restrict__ alpha, int h, int k0,
@@ -344,8 +344,10 @@ k_rows_fwd_phase(const float* __restrict__ H, const float* __restrict__ alpha, i
   constexpr int T = C::ROW_THREADS;
   extern __shared__ float2 sm[];
   const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
-  const int y0 = blockIdx.x * C::RL;
-  const int k = k0 + blockIdx.y;
+  // blockIdx.x = component (fastest): the blocks of all components of one row
+  // block run together, so H and alpha are read from HBM once and then from L2
+  const int y0 = blockIdx.y * C::RL;
+  const int k = k0 + blockIdx.x;
   float hv[STAGE_G], av[STAGE_G];
   for_elems_staged<C::RL * N, T, STAGE_G>(
       [&](int i, int e) {
@@ -361,7 +363,7 @@ k_rows_fwd_phase(const float* __restrict__ H, const float* __restrict__ alpha, i
       });
   __syncthreads();
   row_fft<N, false>(sm, twl);
-  float2* out = A + (size_t)blockIdx.y * h * N;
+  float2* out = A + (size_t)blockIdx.x * h * N;
   for_elems<C::RL * N, T>([&](int i, int e) {
     const int y = y0 + e / N;
     if (y < h) out[(size_t)y * N + e % N] = sm[(e / N) * C::LS + sidx(e % N)];
@@ -1364,7 +1366,7 @@ void FftOps<N>::rows_fwd_phase(const float* H, const float* alpha, int h, int k0
                                const float2* tw, cudaStream_t st) {
   static const bool once = (ext_set_smem(k_rows_fwd_phase<N>, C::ROW_SMEM), true);
   (void)once;
-  dim3 grid((h + C::RL - 1) / C::RL, nk);
+  dim3 grid(nk, (h + C::RL - 1) / C::RL);
   k_rows_fwd_phase<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, alpha, h, k0, A, tw);
 }
 
