@@ -360,11 +360,13 @@ def bench_ght(args, world, rank, local):
     dom_name, (dom_ms, dom_n) = dom
     avg_ms = dom_ms / dom_n
     kc = K + 1
-    alg = {"cols_conv": kc * 8 * P * 2 + 8 * P, "rows_fwd_phase": 8 * P + kc * 8 * P}.get(dom_name)
+    alg = {"cols_conv": kc * 8 * P * 2 + 8 * P, "cols_conv_tma": kc * 8 * P * 2 + 8 * P,
+           "rows_fwd_phase": 8 * P + kc * 8 * P}.get(dom_name)
     peak, peak_kind = measured_peaks()
     achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
     roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
-                "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": committed_traffic().get((dom_name, f"{h}x{w}K{K}")),
                 "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
                 "kernels": {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps}
                             for k, v in prof.items()}}
