@@ -51,7 +51,7 @@ def parse_args():
                     help="so3 / so3p: volume side (128 is the workload; smaller only for profiling captures)")
     ap.add_argument("--train-steps", type=int, default=6000,
                     help="so3p: Adam steps of the proposal network (setup, not timed)")
-    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght"],
+    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght", "lic"],
                     help="so2: the pattern-matching sweep (default, the headline metric); "
                          "scale: scale-adaptive smoothing of a 4096x4096x3 image; "
                          "batched: 512 uneven images in one captured graph; "
@@ -396,6 +396,113 @@ def bench_ght(args, world, rank, local):
                        "weakest_peak_over_background": min(peaks) / background},
             "clocks": clk.summary(),
             "e2e": {"value": world * e2e_steps * P / e2e_s / 1e6, "unit": "Mpx/s", "h2d_bytes_per_step": 4 * P,
+                    "d2h_bytes_per_step": 4 * P, "steps": e2e_steps},
+            "gpu_launches": int(sum(v[1] for v in prof.values()) // prof_steps),
+            "roofline": roofline, "cpu_baseline": cpu}))
+    plan.close()
+    return 0
+
+
+# --------------------------------------------------------- LIC workload ---
+LIC_WORKLOAD = ("normalised extended convolution (Sec. 8, Line Integral Convolution): 2048x2048 f32 U[0,1] noise, "
+                "low-frequency angle field, anisotropic Gaussian sigma 8 x 1 px (closed-form angular components, "
+                "K=16, radius 24), numerator and denominator")
+
+
+def bench_lic(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_2006_13188_gb300 as ec
+    import synth
+    from oracle.normalized import aniso_gauss_table   # closed-form filter table (input preparation)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    n = 2048
+    P = n * n
+    rng = np.random.default_rng(synth.seed_for(7) + rank)
+    Hn = rng.uniform(0, 1, (n, n)).astype(np.float32)
+    an = synth.random_angle_field(synth.seed_for(7) + rank, n, n).astype(np.float32)
+    K, R, su, sv = 16, 24, 8.0, 1.0
+    fk = aniso_gauss_table(su, sv, K, 0.25, float(R))
+    F = ec.FilterSO2.table(fk, 0.25, R)
+    plan = ec.Plan(local)
+    H = torch.from_numpy(Hn).to(device)
+    al = torch.from_numpy(an).to(device)
+    out = torch.empty_like(H)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    def call():
+        ec.ext_conv_so2_normalized(plan, H, 1, n, n, F, al, out)
+    t0 = time.perf_counter()
+    call()
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    barrier(world)
+    total = 0.0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+    total = reduce_max(total, world, device)
+    plan.profile_read()
+    plan.profile(True)
+    prof_steps = 5
+    for _ in range(prof_steps):
+        call()
+    torch.cuda.synchronize()
+    prof = {k: v for k, v in plan.profile_read().items() if v[1] > 0}
+    plan.profile(False)
+    Hh = torch.from_numpy(Hn).pin_memory()
+    ah = torch.from_numpy(an).pin_memory()
+    oh = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    e2e_steps = max(5, min(args.steps, 50))
+    ec.ext_conv_so2_normalized(plan, Hh, 1, n, n, F, ah, oh)
+    barrier(world)
+    t1 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ec.ext_conv_so2_normalized(plan, Hh, 1, n, n, F, ah, oh)
+    e2e_s = reduce_max(time.perf_counter() - t1, world, device)
+    dom_name, (dom_ms, dom_n) = max(prof.items(), key=lambda kv: kv[1][0])
+    avg_ms = dom_ms / dom_n
+    kc = K + 1
+    alg = {"cols_conv_tma": kc * 8 * P * 2 + 8 * P, "cols_conv": kc * 8 * P * 2 + 8 * P,
+           "rows_fwd_phase": 8 * P + kc * 8 * P}.get(dom_name)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
+    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": committed_traffic().get((dom_name, f"{n}x{n}K{K}")),
+                "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
+                "kernels": {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps}
+                            for k, v in prof.items()}}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle.filters_so2 import RadialTable
+        from oracle.normalized import normalized_conv_so2_at
+        pix = np.random.default_rng(0).integers(0, n, (128, 2))
+        t2 = time.perf_counter()
+        normalized_conv_so2_at(Hn, RadialTable(fk, 0.25), an, R, pix)
+        t = time.perf_counter() - t2
+        cpu = {"value": len(pix) / t / 1e6, "unit": "Mpx/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 brute-force numerator and denominator at {len(pix)} random pixels ({t:.1f} s)"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "normalised extended convolution (LIC) Mpx/s",
+            "value": world * args.steps * P / (total * 1e-3) / 1e6, "unit": "Mpx/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": LIC_WORKLOAD, "l2": "256 MB written between steps", "plan_ms": plan_ms},
+            "clocks": clk.summary(),
+            "e2e": {"value": world * e2e_steps * P / e2e_s / 1e6, "unit": "Mpx/s", "h2d_bytes_per_step": 8 * P,
                     "d2h_bytes_per_step": 4 * P, "steps": e2e_steps},
             "gpu_launches": int(sum(v[1] for v in prof.values()) // prof_steps),
             "roofline": roofline, "cpu_baseline": cpu}))
@@ -799,6 +906,8 @@ def main():
         return bench_conv(args, world, rank, local)
     if args.workload == "ght" and args.impl == "ours":
         return bench_ght(args, world, rank, local)
+    if args.workload == "lic" and args.impl == "ours":
+        return bench_lic(args, world, rank, local)
     if args.workload == "scale" and args.impl == "ours":
         return bench_scale(args, world, rank, local)
     if args.workload == "batched" and args.impl == "ours":

@@ -146,6 +146,21 @@ ext_status ext_conv_so2(ext_plan plan, const float* H, int h, int w, const ext_f
                         const float* alpha, float* out, void* stream);
 
 /*
+ * Normalised extended convolution with a rotation field (Sec. 8, Eq.
+ * normalization; the Line Integral Convolution application): for every
+ * channel c,
+ *   out_c = ({H_c, alpha} * F) / ({1, alpha} * F),
+ * each extended convolution as in ext_conv_so2, so that every output is the
+ * weighted average of the values scattered onto it (for rotations no
+ * division of the signal by |T|^2 is needed).  H, out: channels x h x w
+ * float32 (channel-major); alpha: h x w float32 radians.  The denominator is
+ * not guarded: a filter whose band-limited response to 1 changes sign gives
+ * unbounded outputs there.  EXT_ERR_INVALID_ARG for channels outside [1, 64].
+ */
+ext_status ext_conv_so2_normalized(ext_plan plan, const float* H, int channels, int h, int w,
+                                   const ext_filter_so2* F, const float* alpha, float* out, void* stream);
+
+/*
  * Extended correlation with a rotation field (Sec. 2.1 Eq. Def-ECorr; Sec. 4.1
  * "Linear Combination"):
  *   field mode (alpha != NULL): out(p) = sum_k e^{ik alpha(p)} G_k(p),

@@ -39,7 +39,7 @@ EXPORTED = (
     "ext_mlp_create", "ext_mlp_destroy", "ext_mlp_set_params", "ext_mlp_get_params", "ext_mlp_forward",
     "ext_mlp_grads", "ext_mlp_train", "ext_so3_upper_bound", "ext_so3_refined_bound", "ext_so3_gather", "ext_so3_augment", "ext_so3_refine",
     "ext_so3_propose", "ext_corr_so3_propose", "ext_gradient_field", "ext_consensus_radius",
-    "ext_consensus_filter", "ext_ght_detect",
+    "ext_consensus_filter", "ext_ght_detect", "ext_conv_so2_normalized",
 )
 
 
@@ -122,6 +122,7 @@ def lib():
         L.ext_consensus_radius.argtypes = [dbl]
         L.ext_consensus_filter.argtypes = [vp, vp, i32, i32, i32, i32, dbl, vp, vp]
         L.ext_ght_detect.argtypes = [vp, vp, i32, i32, fp, vp, vp]
+        L.ext_conv_so2_normalized.argtypes = [vp, vp, i32, i32, i32, fp, vp, vp, vp]
         for name in EXPORTED:
             if name not in ("ext_status_string", "ext_last_error", "ext_so3_channels", "ext_consensus_radius"):
                 getattr(L, name).restype = i32
@@ -451,3 +452,8 @@ def ext_consensus_filter(plan: Plan, P, hp, wp, cy, cx, eps, F_out, stream=None)
 
 def ext_ght_detect(plan: Plan, I, h, w, F: FilterSO2, out, stream=None):
     _check(lib().ext_ght_detect(plan.handle, _ptr(I), int(h), int(w), F.ref(), _ptr(out), _stream(stream)))
+
+
+def ext_conv_so2_normalized(plan: Plan, H, channels, h, w, F: FilterSO2, alpha, out, stream=None):
+    _check(lib().ext_conv_so2_normalized(plan.handle, _ptr(H), int(channels), int(h), int(w), F.ref(), _ptr(alpha),
+                                         _ptr(out), _stream(stream)))

@@ -620,6 +620,36 @@ ext_status ext_conv_so2(ext_plan plan, const float* H, int h, int w, const ext_f
   return finish_host(plan, sH.host || sAl.host || sO.host, st);
 }
 
+ext_status ext_conv_so2_normalized(ext_plan plan, const float* H, int channels, int h, int w, const ext_filter_so2* F,
+                                   const float* alpha, float* out, void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_TRY(check_filter(F));
+  EXT_TRY(check_size(h, w));
+  if (channels < 1 || channels > 64) return fail(EXT_ERR_INVALID_ARG, "channels must be in [1, 64]");
+  if (h == 0 || w == 0) return EXT_OK;
+  if (!H || !alpha || !out) return fail(EXT_ERR_INVALID_ARG, "NULL buffer");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)h * w;
+  Staged sH, sAl, sO;
+  EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P * channels, st, &sH));
+  EXT_TRY(stage_in(plan, "in_alpha", alpha, sizeof(float) * P, st, &sAl));
+  EXT_TRY(stage_out_alloc(plan, "out_0", out, sizeof(float) * P * channels, &sO));
+  void* D = nullptr;
+  EXT_TRY(ensure(plan, "norm_D", sizeof(float) * P, &D));
+  // denominator: the response to the constant signal 1 (the phase row pass's H = NULL)
+  EXT_TRY(run_conv_so2(plan, nullptr, (const float*)sAl.dev, h, w, F, (float*)D, st));
+  for (int c = 0; c < channels; ++c)
+    EXT_TRY(run_conv_so2(plan, (const float*)sH.dev + P * c, (const float*)sAl.dev, h, w, F, (float*)sO.dev + P * c,
+                         st));
+  launch(plan, "divide_channels", st, [&] {
+    launch_divide_channels((float*)sO.dev, (const float*)D, (long long)P, channels, plan->sms, st);
+  });
+  EXT_CUDA(cudaGetLastError());
+  EXT_TRY(stage_out_finish(sO, st));
+  return finish_host(plan, sH.host || sAl.host || sO.host, st);
+}
+
 ext_status ext_ght_detect(ext_plan plan, const float* I, int h, int w, const ext_filter_so2* F, float* out,
                           void* stream) {
   if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");

@@ -336,6 +336,8 @@ k_rows_r2c(const float* __restrict__ H, int h, float2* __restrict__ Hh, const fl
 // Forward transform of the steered signals A_k = H exp(-i k alpha) (Sec. 4.1,
 // extended convolution: the signal is pre-multiplied before convolving with
 // F_k).  blockIdx.x selects k = k0 + blockIdx.x, blockIdx.y the row block.
+// H == nullptr stands for the constant signal 1 (the denominator of Eq.
+// normalization).
 template <int N>
 __global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
 k_rows_fwd_phase(const float* __restrict__ H, const float* __restrict__ alpha, int h, int k0,
@@ -353,7 +355,7 @@ k_rows_fwd_phase(const float* __restrict__ H, const float* __restrict__ alpha, i
       [&](int i, int e) {
         const int y = y0 + e / N;
         const size_t idx = (size_t)y * N + e % N;
-        hv[i] = (y < h) ? __ldg(H + idx) : 0.f;
+        hv[i] = (y < h) ? (H ? __ldg(H + idx) : 1.0f) : 0.f;
         av[i] = (y < h) ? __ldg(alpha + idx) : 0.f;
       },
       [&](int i, int e) {

@@ -91,6 +91,9 @@ void launch_scale_finalize(const float* H, const float* s, const float* N, const
 // ----- pattern detection front end (ght.cu): H = |grad I|, theta = atan2(dI/dy, dI/dx)
 void launch_gradient_field(const float* I, int h, int w, float* H, float* theta, int sms, cudaStream_t st);
 
+// out[c][p] /= D[p] for c < channels (normalize.cu)
+void launch_divide_channels(float* out, const float* D, long long P, int channels, int sms, cudaStream_t st);
+
 // ----- sweep (sweep.cu)
 // B: J rows of cp floats (cp = 2K rounded up to a multiple of 4).
 bool sweep_fp32(const float* G, long long P, int K, int J, const float* B, int cp, float* maxv,
