@@ -51,7 +51,7 @@ def parse_args():
                     help="so3 / so3p: volume side (128 is the workload; smaller only for profiling captures)")
     ap.add_argument("--train-steps", type=int, default=6000,
                     help="so3p: Adam steps of the proposal network (setup, not timed)")
-    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght", "lic"],
+    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght", "lic", "defocus"],
                     help="so2: the pattern-matching sweep (default, the headline metric); "
                          "scale: scale-adaptive smoothing of a 4096x4096x3 image; "
                          "batched: 512 uneven images in one captured graph; "
@@ -511,6 +511,9 @@ def bench_lic(args, world, rank, local):
 
 
 # ------------------------------------------------------- scale workload ---
+DEFOCUS_WORKLOAD = ("depth-defocus smoothing (Sec. 8): 2048x2048x3 f32 wire-frame-like image (600 one-pixel line "
+                    "segments), scale field 1 + 7 |Z - Z(p0)| / max from a smooth depth map, radially smoothed disk "
+                    "(logistic edge 0.1 in log-radius) with 64 Mellin frequencies, radii 1-16, normalised mode")
 SCALE_WORKLOAD = ("scale-adaptive smoothing: 4096x4096x3 f32 Voronoi image, scale field in [1,8] px, "
                   "24 Mellin harmonics, radii 1-64, normalised (unit-integral) mode")
 
@@ -522,7 +525,12 @@ def bench_scale(args, world, rank, local):
     import synth
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    prob = synth.scale_smoothing_problem(seed=synth.seed_for(3) + rank)
+    if args.workload == "defocus":   # Sec. 8 depth defocus: smoothed disk, 64 Mellin frequencies
+        d = synth.depth_defocus_problem(seed=synth.seed_for(8) + rank)
+        prob = dict(img=d["img"], s=d["s"], c=synth.mellin_disk_coeffs(), log_period=8.0, r_min=1.0, r_max=16.0,
+                    centre_tap=1.0)
+    else:
+        prob = synth.scale_smoothing_problem(seed=synth.seed_for(3) + rank)
     img, s, c = prob["img"], prob["s"], prob["c"]
     h, w = s.shape
     P = h * w
@@ -581,10 +589,12 @@ def bench_scale(args, world, rank, local):
                "sample": f"FP64 gather-form smoothing at {len(pix)} random pixels ({t:.1f} s)"}
     if rank == 0:
         print(json.dumps({
-            "metric": "scale-adaptive smoothing Mpx/s", "value": value, "unit": "Mpx/s", "n_gpus": world,
+            "metric": ("depth-defocus smoothing Mpx/s" if args.workload == "defocus" else
+                       "scale-adaptive smoothing Mpx/s"), "value": value, "unit": "Mpx/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": SCALE_WORKLOAD, "plan_ms": plan_ms, "l2": "256 MB written between steps"},
+            "config": {"workload": DEFOCUS_WORKLOAD if args.workload == "defocus" else SCALE_WORKLOAD,
+                       "plan_ms": plan_ms, "l2": "256 MB written between steps"},
             "clocks": clk.summary(), "gpu_launches": launches,
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "peak_kind": kind,
                          "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": None,
@@ -908,7 +918,7 @@ def main():
         return bench_ght(args, world, rank, local)
     if args.workload == "lic" and args.impl == "ours":
         return bench_lic(args, world, rank, local)
-    if args.workload == "scale" and args.impl == "ours":
+    if args.workload in ("scale", "defocus") and args.impl == "ours":
         return bench_scale(args, world, rank, local)
     if args.workload == "batched" and args.impl == "ours":
         return bench_batched(args, world, rank, local)

@@ -720,13 +720,27 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
   const float omega_step = (float)(two_pi / log_period);
   const int unit = mode == 2 ? 1 : 0;
   const int nsig = channels + (mode == 0 ? 0 : 1);
+  // tensor-copy staged column pass where the tile shape allows it
+  const int cw = fft_col_tile(h);
+  const int br = plan->tma && fft_cols_tma_ok(h) ? tma_rows(h, cw) : 0;
+  CUtensorMap tmA;
+  const bool tma_A = br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w, (unsigned long long)n_h * h,
+                                                (unsigned long long)2 * w * sizeof(float), (unsigned)(2 * cw),
+                                                (unsigned)br, &tmA);
   for (int sig = 0; sig < nsig; ++sig) {
     const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
     float* dst = sig < channels ? (float*)Nb + P * sig : (float*)Db;
     launch(plan, "rows_fwd_scale", st, [&] {
       fft_rows_fwd_scale(w, src, (const float*)sS.dev, h, 0, n_h, omega_step, unit, (float2*)A, tw_w, st);
     });
-    launch(plan, "cols_conv", st, [&] { fft_cols_conv(h, (const float2*)A, w, n_h - 1, S, (float2*)Y, tw_h, st); });
+    bool done = false;
+    if (tma_A)
+      launch(plan, "cols_conv_tma", st, [&] {
+        done = fft_cols_conv_tma(h, tmA, w, br, n_h - 1, S, (float2*)Y, tw_h, plan->dev_err, plan->sms, st);
+      });
+    if (!done)
+      launch(plan, "cols_conv", st,
+             [&] { fft_cols_conv(h, (const float2*)A, w, n_h - 1, S, (float2*)Y, tw_h, st); });
     launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, dst, tw_w, st); });
   }
   launch(plan, "scale_finalize", st, [&] {

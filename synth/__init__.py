@@ -235,6 +235,25 @@ def batched_image(desc: dict, noise_sigma: float = 0.1, blur: float = 3.0):
 
 # ------------------------------------------------------------- workload 3 ---
 
+def _mellin_fit(target, n_h, log_period, u_lo, u_hi, ridge, n_fit):
+    """Least-squares coefficients c_k, k = 0..n_h-1 (c_{-k} = conj(c_k)), of
+    P(u) = sum_k c_k exp(i w_k u), w_k = 2 pi k / log_period, fitted (ridge
+    ``ridge``) to target(u) on u in [u_lo, u_hi].  Returns complex128 (n_h,)."""
+    u = np.linspace(u_lo, u_hi, n_fit)
+    w = 2 * math.pi * np.arange(n_h) / log_period
+    cols = [np.ones_like(u)]
+    for k in range(1, n_h):
+        cols += [np.cos(w[k] * u), np.sin(w[k] * u)]
+    A = np.stack(cols, axis=1)
+    coef = np.linalg.solve(A.T @ A + ridge * np.eye(A.shape[1]), A.T @ target(u))
+    c = np.zeros(n_h, np.complex128)
+    c[0] = coef[0]
+    for k in range(1, n_h):
+        # 2 Re(c_k e^{iwu}) = 2 Re(c_k) cos - 2 Im(c_k) sin
+        c[k] = 0.5 * (coef[2 * k - 1] - 1j * coef[2 * k])
+    return c
+
+
 def mellin_gaussian_coeffs(n_h: int = 24, log_period: float = 8.0,
                            u_lo: float = -math.log(8.0), u_hi: float = math.log(64.0),
                            ridge: float = 1e-10, n_fit: int = 4001):
@@ -243,20 +262,17 @@ def mellin_gaussian_coeffs(n_h: int = 24, log_period: float = 8.0,
     w_k = 2 pi k / log_period, least-squares fitted (ridge ``ridge``) to the
     unit Gaussian profile exp(-e^{2u}/2) on u in [u_lo, u_hi].  With
     u = ln r - ln s this gives exp(-r^2 / (2 s^2)).  Returns complex128 (n_h,)."""
-    u = np.linspace(u_lo, u_hi, n_fit)
-    target = np.exp(-np.exp(2 * u) / 2)
-    w = 2 * math.pi * np.arange(n_h) / log_period
-    cols = [np.ones_like(u)]
-    for k in range(1, n_h):
-        cols += [np.cos(w[k] * u), np.sin(w[k] * u)]
-    A = np.stack(cols, axis=1)
-    coef = np.linalg.solve(A.T @ A + ridge * np.eye(A.shape[1]), A.T @ target)
-    c = np.zeros(n_h, np.complex128)
-    c[0] = coef[0]
-    for k in range(1, n_h):
-        # 2 Re(c_k e^{iwu}) = 2 Re(c_k) cos - 2 Im(c_k) sin
-        c[k] = 0.5 * (coef[2 * k - 1] - 1j * coef[2 * k])
-    return c
+    return _mellin_fit(lambda u: np.exp(-np.exp(2 * u) / 2), n_h, log_period, u_lo, u_hi, ridge, n_fit)
+
+
+def mellin_disk_coeffs(n_h: int = 64, log_period: float = 8.0, tau: float = 0.1,
+                       u_lo: float = -math.log(8.0), u_hi: float = math.log(64.0),
+                       ridge: float = 1e-10, n_fit: int = 4001):
+    """The depth-defocus filter of Sec. 8: the indicator of the disk of radius
+    s, smoothed along the radial direction, as P(u) = 1 / (1 + e^{u / tau})
+    (u = ln r - ln s, so P ~ 1 inside the disk, 0 outside, a logistic edge
+    of width tau in log-radius), fitted with n_h = 64 Mellin frequencies."""
+    return _mellin_fit(lambda u: 1.0 / (1.0 + np.exp(u / tau)), n_h, log_period, u_lo, u_hi, ridge, n_fit)
 
 
 def voronoi_image(rng, h, w, n_cells=500, block=8, noise=0.05):
@@ -308,6 +324,33 @@ def scale_smoothing_problem(seed: int | None = None, size: int | tuple = 4096,
 
 
 # ------------------------------------------------------------- workload 5 ---
+
+def depth_defocus_problem(seed: int | None = None, size: int | tuple = 2048, n_lines: int = 600,
+                          s_min: float = 1.0, s_max: float = 8.0):
+    """Depth-defocus input (Sec. 8, the wire-frame example): a 3-channel image
+    of one-pixel-wide random line segments (random colours) on a dark
+    background, a smooth depth field Z in [0, 1] (periodic blur sigma 64 of
+    Gaussian noise, rescaled) and the scale field
+    s = s_min + (s_max - s_min) |Z - Z(p0)| / max |Z - Z(p0)|, p0 the image
+    centre (the focal point).  float32 arrays (3, h, w) and (h, w)."""
+    rng = np.random.default_rng(seed_for(8) if seed is None else seed)
+    h, w = (size, size) if np.isscalar(size) else size
+    img = np.full((3, h, w), 0.05)
+    for _ in range(n_lines):
+        y0, x0 = rng.uniform(0, h), rng.uniform(0, w)
+        ang, length = rng.uniform(0, math.pi), rng.uniform(20, 200)
+        col = rng.uniform(0.3, 1.0, 3)
+        t = np.linspace(0.0, length, int(4 * length) + 1)
+        ys = np.round(y0 + t * math.sin(ang)).astype(np.int64) % h
+        xs = np.round(x0 + t * math.cos(ang)).astype(np.int64) % w
+        for c in range(3):
+            img[c, ys, xs] = col[c]
+    Z = periodic_gaussian_blur(rng.standard_normal((h, w)), 64.0)
+    Z = (Z - Z.min()) / (Z.max() - Z.min())
+    dz = np.abs(Z - Z[h // 2, w // 2])
+    s = s_min + (s_max - s_min) * dz / dz.max()
+    return dict(img=img.astype(np.float32), s=s.astype(np.float32), Z=Z)
+
 
 def so3_filter_tables(seed: int, L: int = 6, r_max: float = 8.0, dr: float = 0.125):
     """Random smooth radial profiles f_l^a(r), l <= L, |a| <= l, sampled at

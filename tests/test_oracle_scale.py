@@ -90,3 +90,28 @@ def test_unnormalised_smoothing_darkens_small_scales():
     img = np.ones((1, h, w))
     raw = smooth(img, s, small_filter(), mode=0)[0]
     assert raw[:, 3:9].mean() < raw[:, 15:21].mean()
+
+
+def test_disk_profile_matches_the_smoothed_disk():
+    """Depth-defocus filter (Sec. 8): 64 Mellin frequencies reproduce the
+    radially smoothed disk indicator 1 / (1 + e^{(ln r - ln s) / tau}) to 1e-6."""
+    f = MellinFilter(synth.mellin_disk_coeffs(), 8.0, 1.0, 64.0, 1.0)
+    u = np.linspace(-math.log(8), math.log(64), 5001)
+    assert np.max(np.abs(f.profile(u) - 1.0 / (1.0 + np.exp(u / 0.1)))) < 1e-6
+    d = np.arange(1, 30, dtype=np.float64)
+    for s in (2.0, 5.5):
+        np.testing.assert_allclose(f.scaled(d, 0 * d, s), 1.0 / (1.0 + (d / s) ** 10), atol=1e-6)
+
+
+def test_disk_integral_scales_with_the_square_of_the_scale():
+    """Sum of the lattice taps / s^2 against 2 pi int P(ln r) r dr (a 1D
+    quadrature of the smoothed disk, about pi): the lattice sum converges to
+    the integral as the disk grows, within the design range s <= 8 (the fit
+    covers u = ln r - ln s >= -ln 8 on radii r >= 1; beyond it the
+    log-periodic basis repeats and the centre of a larger disk is lost)."""
+    f = MellinFilter(synth.mellin_disk_coeffs(), 8.0, 1.0, 64.0, 1.0)
+    r = np.linspace(1e-6, 64.0, 400001)
+    area = 2 * math.pi * np.trapezoid(r / (1.0 + r ** 10), r)
+    dy, dx = np.mgrid[-64:65, -64:65]
+    for s, tol in ((2.0, 3e-2), (4.0, 1e-3), (8.0, 1e-5)):
+        assert abs(np.sum(f.scaled(dx, dy, s)) / (s * s) - area) <= tol * area
