@@ -314,13 +314,16 @@ ext_status run_conv_so2(ext_plan plan, const float* H, const float* alpha, int h
          [&] { fft_rows_fwd_phase(w, H, alpha, h, 0, K + 1, (float2*)A, tw_w, st); });
   // tensor-copy staged column pass where the tile shape allows it
   const int cw = fft_col_tile(h);
-  const int br = plan->tma && fft_cols_tma_ok(h) ? tma_rows(h, cw) : 0;
+  bool gtw = false;
+  const int br = plan->tma && fft_cols_conv_tma_ok(h, &gtw) ? tma_rows(h, cw) : 0;
+  const float2* stw = nullptr;
+  if (br > 0 && gtw) EXT_TRY(stage_table(plan, h, st, &stw));
   CUtensorMap tmA;
   bool done = false;
   if (br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w, (unsigned long long)(K + 1) * h,
                                  (unsigned long long)2 * w * sizeof(float), (unsigned)(2 * cw), (unsigned)br, &tmA))
     launch(plan, "cols_conv_tma", st, [&] {
-      done = fft_cols_conv_tma(h, tmA, w, br, K, S, (float2*)Y, tw_h, plan->dev_err, plan->sms, st);
+      done = fft_cols_conv_tma(h, tmA, w, br, K, S, (float2*)Y, tw_h, stw, plan->dev_err, plan->sms, st);
     });
   if (!done)
     launch(plan, "cols_conv", st, [&] { fft_cols_conv(h, (const float2*)A, w, K, S, (float2*)Y, tw_h, st); });
@@ -722,7 +725,10 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
   const int nsig = channels + (mode == 0 ? 0 : 1);
   // tensor-copy staged column pass where the tile shape allows it
   const int cw = fft_col_tile(h);
-  const int br = plan->tma && fft_cols_tma_ok(h) ? tma_rows(h, cw) : 0;
+  bool gtw = false;
+  const int br = plan->tma && fft_cols_conv_tma_ok(h, &gtw) ? tma_rows(h, cw) : 0;
+  const float2* stw = nullptr;
+  if (br > 0 && gtw) EXT_TRY(stage_table(plan, h, st, &stw));
   CUtensorMap tmA;
   const bool tma_A = br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w, (unsigned long long)n_h * h,
                                                 (unsigned long long)2 * w * sizeof(float), (unsigned)(2 * cw),
@@ -736,7 +742,7 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
     bool done = false;
     if (tma_A)
       launch(plan, "cols_conv_tma", st, [&] {
-        done = fft_cols_conv_tma(h, tmA, w, br, n_h - 1, S, (float2*)Y, tw_h, plan->dev_err, plan->sms, st);
+        done = fft_cols_conv_tma(h, tmA, w, br, n_h - 1, S, (float2*)Y, tw_h, stw, plan->dev_err, plan->sms, st);
       });
     if (!done)
       launch(plan, "cols_conv", st,

@@ -1053,6 +1053,9 @@ struct TmaColCfg {
   static constexpr int OFF_TW = OFF_H + ((TILE + 15) / 16) * 16;
   static constexpr int SMEM = (OFF_TW + N) * 8 + 128;   // + slack to align the base to 128 bytes
   static constexpr bool OK = SMEM <= 227 * 1024 && C::CW % 2 == 0;
+  // without the twiddle copy (the stage table read from global memory through L1)
+  static constexpr int SMEM_GTW = OFF_TW * 8 + 128;
+  static constexpr bool OK_GTW = !OK && SMEM_GTW <= 227 * 1024 && C::CW % 2 == 0;
 };
 
 template <int N>
@@ -1136,7 +1139,8 @@ k_cols_inv_corr_tma(const __grid_constant__ CUtensorMap tmH, int w, int br, cons
 template <int N>
 __global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, 1)
 k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, const float2* __restrict__ S,
-                float2* __restrict__ Y, const float2* __restrict__ tw, int* __restrict__ err) {
+                float2* __restrict__ Y, const float2* __restrict__ tw, const float2* __restrict__ stw_g,
+                int* __restrict__ err) {
   using C = LineCfg<N>;
   using TC = TmaColCfg<N>;
   constexpr int T = C::COL_THREADS;
@@ -1149,7 +1153,9 @@ k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, c
   float2* W = sm;
   float2* SS = sm + TC::OFF_S;
   float2* AS = sm + TC::OFF_H;
-  const float2* TWs = stage_twiddles<N, TC::OFF_TW>(sm, tw, T);
+  // stage twiddles: copied into shared memory where they fit, else the global stage table (stw_g)
+  const float2* TWs = stw_g;
+  if constexpr (TC::OK) TWs = stage_twiddles<N, TC::OFF_TW>(sm, tw, T);
   const int ntiles = (w + CW - 1) / CW;
   const uint32_t ma = tc::smem_u32(&bar_a), ms = tc::smem_u32(&bar_s);
   if (threadIdx.x == 0) {
@@ -1336,7 +1342,7 @@ struct FftOps {
   static void cols_conv(const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
                         cudaStream_t st);
   static bool cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
-                            const float2* tw, int* err, int sms, cudaStream_t st);
+                            const float2* tw, const float2* stw_g, int* err, int sms, cudaStream_t st);
   static void cols_c2c(float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st);
   static void rows_inv_channels(const float2* Z, int rows, int k0, int nk, const int2* chan, float* G,
                                 const float2* tw, cudaStream_t st);
@@ -1499,17 +1505,26 @@ bool FftOps<N>::cols_inv_corr_tma(const CUtensorMap& tmH, int w, int br, const f
 
 template <int N>
 bool FftOps<N>::cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
-                              const float2* tw, int* err, int sms, cudaStream_t st) {
-  if constexpr (!TmaColCfg<N>::OK || factor_radices(N).cnt < 2) {
+                              const float2* tw, const float2* stw_g, int* err, int sms, cudaStream_t st) {
+  using TC = TmaColCfg<N>;
+  if constexpr (!(TC::OK || TC::OK_GTW) || factor_radices(N).cnt < 2) {
     return false;
   } else {
-    static const bool once = (ext_set_smem(k_cols_conv_tma<N>, TmaColCfg<N>::SMEM), true);
+    if (!TC::OK && !stw_g) return false;
+    constexpr int smem = TC::OK ? TC::SMEM : TC::SMEM_GTW;
+    static const bool once = (ext_set_smem(k_cols_conv_tma<N>, smem), true);
     (void)once;
     const int tiles = (w + C::CW - 1) / C::CW;
-    const int grid = pipe_grid<N>(tiles, sms, TmaColCfg<N>::SMEM, C::COL_THREADS);
-    k_cols_conv_tma<N><<<grid, C::COL_THREADS, TmaColCfg<N>::SMEM, st>>>(tmA, w, br, K, S, Y, tw, err);
+    const int grid = pipe_grid<N>(tiles, sms, smem, C::COL_THREADS);
+    k_cols_conv_tma<N><<<grid, C::COL_THREADS, smem, st>>>(tmA, w, br, K, S, Y, tw, stw_g, err);
     return true;
   }
+}
+
+// Stage twiddle table of length n (the layout stage_twiddles builds) in global memory.
+template <int N>
+__global__ void k_stage_table(const float2* __restrict__ tw, float2* __restrict__ out) {
+  stage_twiddles<N, 0>(out, tw, blockDim.x);
 }
 
 template <int N>

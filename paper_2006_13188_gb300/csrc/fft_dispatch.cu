@@ -132,12 +132,33 @@ bool fft_cols_inv_full_pipe(int h, const float2* H, int w, const float2* S, int 
 }
 #undef EXT_C1
 
-#define EXT_C1(N) case N: return FftOps<N>::cols_conv_tma(tmA, w, br, K, S, Y, tw, err, sms, st);
+#define EXT_C1(N) case N: return FftOps<N>::cols_conv_tma(tmA, w, br, K, S, Y, tw, stw_g, err, sms, st);
 bool fft_cols_conv_tma(int h, const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
-                       const float2* tw, int* err, int sms, cudaStream_t st) {
+                       const float2* tw, const float2* stw_g, int* err, int sms, cudaStream_t st) {
   switch (h) { EXT_FFT_SIZES(EXT_C1) default: return false; }
 }
 #undef EXT_C1
+
+bool fft_cols_conv_tma_ok(int h, bool* needs_stage_table) {
+  switch (h) {
+#define EXT_CASE(N)                                         \
+  case N:                                                   \
+    *needs_stage_table = !TmaColCfg<N>::OK;                 \
+    return TmaColCfg<N>::OK || TmaColCfg<N>::OK_GTW;
+    EXT_FFT_SIZES(EXT_CASE)
+#undef EXT_CASE
+    default: return false;
+  }
+}
+
+void fft_build_stage_table(int n, const float2* tw, float2* out, cudaStream_t st) {
+  switch (n) {
+#define EXT_CASE(N) case N: k_stage_table<N><<<1, 256, 0, st>>>(tw, out); return;
+    EXT_FFT_SIZES(EXT_CASE)
+#undef EXT_CASE
+    default: return;
+  }
+}
 
 #define EXT_C1(N) case N: return FftOps<N>::cols_inv_corr_tma(tmH, w, br, S, k0, nk, Z, tw, err, sms, st);
 bool fft_cols_inv_corr_tma(int h, const CUtensorMap& tmH, int w, int br, const float2* S, int k0, int nk, float2* Z,

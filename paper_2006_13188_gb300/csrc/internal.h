@@ -73,7 +73,12 @@ void fft_cols_conv(int h, const float2* A, int w, int K, const float2* S, float2
 // accelerator: tmA maps A as (K+1) h rows of 2w floats, boxes of 2 * col_tile
 // floats x br rows; false if this length has no such variant.
 bool fft_cols_conv_tma(int h, const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
-                       const float2* tw, int* err, int sms, cudaStream_t st);
+                       const float2* tw, const float2* stw_g, int* err, int sms, cudaStream_t st);
+// whether the staged convolution pass exists for column length h, and whether it
+// reads its stage twiddles from a global table (fft_build_stage_table) instead of
+// a shared-memory copy
+bool fft_cols_conv_tma_ok(int h, bool* needs_stage_table);
+void fft_build_stage_table(int n, const float2* tw, float2* out, cudaStream_t st);
 
 // ----- filter side, FP64 (filter.cu)
 void launch_twiddle(float2* tw, int n, cudaStream_t st);

@@ -152,6 +152,23 @@ ext_status twiddle(ext_plan plan, int n, cudaStream_t st, const float2** out) {
   return EXT_OK;
 }
 
+// Stage twiddle table of length n in device memory (cached in the twiddle map
+// under the key -n), for passes whose shared memory has no room for a copy.
+ext_status stage_table(ext_plan plan, int n, cudaStream_t st, const float2** out) {
+  auto it = plan->twiddles.find(-n);
+  if (it == plan->twiddles.end()) {
+    const float2* tw = nullptr;
+    EXT_TRY(twiddle(plan, n, st, &tw));
+    float2* t = nullptr;
+    EXT_CUDA(cudaMalloc(&t, sizeof(float2) * n));
+    fft_build_stage_table(n, tw, t, st);
+    EXT_CUDA(cudaGetLastError());
+    it = plan->twiddles.emplace(-n, t).first;
+  }
+  *out = it->second;
+  return EXT_OK;
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
