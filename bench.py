@@ -51,7 +51,7 @@ def parse_args():
                     help="so3 / so3p: volume side (128 is the workload; smaller only for profiling captures)")
     ap.add_argument("--train-steps", type=int, default=6000,
                     help="so3p: Adam steps of the proposal network (setup, not timed)")
-    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght", "lic", "defocus"],
+    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght", "lic", "defocus", "budget"],
                     help="so2: the pattern-matching sweep (default, the headline metric); "
                          "scale: scale-adaptive smoothing of a 4096x4096x3 image; "
                          "batched: 512 uneven images in one captured graph; "
@@ -510,6 +510,84 @@ def bench_lic(args, world, rank, local):
     return 0
 
 
+# ------------------------------------------------------ budget workload ---
+BUDGET_WORKLOAD = ("fixed-budget component selection (Sec. 5 Band-Limiting Revisited): the 2048x2048 sweep workload "
+                   "(20 planted 65x65 templates, K=16, 64 angles, BF16x3), budgets of 5 and 9 components chosen by "
+                   "lattice energy or as the lowest orders, against the full 17-component sweep")
+
+
+def bench_budget(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_2006_13188_gb300 as ec
+    from paper_2006_13188_gb300 import selection
+    import synth
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    prob = synth.so2_match_problem(seed=synth.seed_for(2) + rank)
+    K, J = prob["K"], prob["J"]
+    h, w = prob["H"].shape
+    P = h * w
+    plan = ec.Plan(local)
+    F = ec.FilterSO2.sampled(prob["template"], K, prob["dr"], prob["n_theta"])
+    H = torch.from_numpy(prob["H"]).to(device)
+    E = ec.ext_filter_so2_energy(plan, F)
+    total_e = E[0] + 2 * E[1:].sum()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    full_m = torch.empty((h, w), dtype=torch.float32, device=device)
+    full_a = torch.empty((h, w), dtype=torch.int32, device=device)
+    ec.ext_corr_so2(plan, H, h, w, F, None, J, full_m, full_a, ec.EXT_PREC_BF16X3)
+    torch.cuda.synchronize()
+    ref_a = full_a.cpu().numpy()
+    pix = [(cy + dy, cx + dx) for cy, cx in prob["centres"] for dy in range(-2, 3) for dx in range(-2, 3)]
+    pix = np.array(pix) % np.array([h, w])
+    rows = []
+    with ClockSampler(local) as clk:
+        for budget in (5, 9, K + 1):
+            for rule in (("energy", "lowest") if budget <= K else ("all",)):
+                ks = selection.select(plan, F, budget) if rule == "energy" else selection.lowest(F, budget)
+                mx = torch.empty((h, w), dtype=torch.float32, device=device)
+                am = torch.empty((h, w), dtype=torch.int32, device=device)
+
+                def call():
+                    ec.ext_corr_so2_subset(plan, H, h, w, F, ks, J, mx, am, ec.EXT_PREC_BF16X3)
+                call()
+                torch.cuda.synchronize()
+                for _ in range(args.warmup):
+                    call()
+                torch.cuda.synchronize()
+                barrier(world)
+                t = 0.0
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    call()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    t += e0.elapsed_time(e1)
+                t = reduce_max(t, world, device)
+                a = am.cpu().numpy()
+                dropped = sum(2 * E[k] for k in range(1, K + 1) if k not in ks)
+                rows.append({"budget": budget, "rule": rule, "components": ks,
+                             "mpx_s": world * args.steps * P / (t * 1e-3) / 1e6, "ms_per_step": t / args.steps,
+                             "rel_steering_error": float(np.sqrt(dropped / total_e)),
+                             "argmax_agreement_image": float((a == ref_a).mean()),
+                             "argmax_agreement_templates": float((a[pix[:, 0], pix[:, 1]] == ref_a[pix[:, 0], pix[:, 1]]).mean())})
+    if rank == 0:
+        head = next(r for r in rows if r["budget"] == 9 and r["rule"] == "energy")
+        print(json.dumps({
+            "metric": "component-budget sweep Mpx/s (9 of 17 components, chosen by energy)",
+            "value": head["mpx_s"], "unit": "Mpx/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 FFT + bf16x3 sweep (f32 accumulate)", "data": "synthetic",
+            "config": {"workload": BUDGET_WORKLOAD, "l2": "256 MB written between steps"},
+            "clocks": clk.summary(), "budgets": rows, "cpu_baseline": None}))
+    plan.close()
+    return 0
+
+
 # ------------------------------------------------------- scale workload ---
 DEFOCUS_WORKLOAD = ("depth-defocus smoothing (Sec. 8): 2048x2048x3 f32 wire-frame-like image (600 one-pixel line "
                     "segments), scale field 1 + 7 |Z - Z(p0)| / max from a smooth depth map, radially smoothed disk "
@@ -918,6 +996,8 @@ def main():
         return bench_ght(args, world, rank, local)
     if args.workload == "lic" and args.impl == "ours":
         return bench_lic(args, world, rank, local)
+    if args.workload == "budget" and args.impl == "ours":
+        return bench_budget(args, world, rank, local)
     if args.workload in ("scale", "defocus") and args.impl == "ours":
         return bench_scale(args, world, rank, local)
     if args.workload == "batched" and args.impl == "ours":

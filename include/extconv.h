@@ -177,6 +177,26 @@ ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_f
                         int precision, void* stream);
 
 /*
+ * Fixed-budget component selection (Sec. 5 "Band-Limiting Revisited": with a
+ * budget of standard convolutions the least-squares best choice, averaged
+ * over rotations, is the components with the largest coefficients).
+ * ext_filter_so2_energy writes the lattice energies
+ *   E_k = sum_{d in [-R, R]^2} |F_k(d)|^2,  k = 0..K,
+ * (F_k(0) = 0 for k != 0; FP64) to HOST memory energy_out (K+1 doubles): the
+ * rotation-averaged squared error of steering with a subset is the energy of
+ * the components left out (each k >= 1 counts twice, with -k).
+ * ext_corr_so2_subset is ext_corr_so2 in sweep mode restricted to the listed
+ * components: ks[0] = 0 (G_0, the angle-independent mean, always kept), then
+ * nks - 1 <= 16 ascending components 1 <= ks[i] <= K;
+ *   S(p, j) = G_0(p) + 2 sum_{i >= 1} Re(e^{i 2 pi ks[i] j / J} G_{ks[i]}(p)),
+ * max_out(p) = max_j S(p, j), argmax(p) = the smallest maximising j.  Its
+ * cost is that of ext_corr_so2 with K = nks - 1.
+ */
+ext_status ext_filter_so2_energy(ext_plan plan, const ext_filter_so2* F, double* energy_out);
+ext_status ext_corr_so2_subset(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, const int* ks,
+                               int nks, int n_angles, float* max_out, int32_t* argmax, int precision, void* stream);
+
+/*
  * The component correlations G_k = H (*) F_k, k = 0..K (Sec. 4.1 "Standard
  * Correlation"), as 2K+1 planes of h*w float32: plane 0 = G_0 (real for a
  * real filter), plane 2k-1 = Re G_k, plane 2k = Im G_k.

@@ -39,7 +39,8 @@ EXPORTED = (
     "ext_mlp_create", "ext_mlp_destroy", "ext_mlp_set_params", "ext_mlp_get_params", "ext_mlp_forward",
     "ext_mlp_grads", "ext_mlp_train", "ext_so3_upper_bound", "ext_so3_refined_bound", "ext_so3_gather", "ext_so3_augment", "ext_so3_refine",
     "ext_so3_propose", "ext_corr_so3_propose", "ext_gradient_field", "ext_consensus_radius",
-    "ext_consensus_filter", "ext_ght_detect", "ext_conv_so2_normalized",
+    "ext_consensus_filter", "ext_ght_detect", "ext_conv_so2_normalized", "ext_filter_so2_energy",
+    "ext_corr_so2_subset",
 )
 
 
@@ -123,6 +124,8 @@ def lib():
         L.ext_consensus_filter.argtypes = [vp, vp, i32, i32, i32, i32, dbl, vp, vp]
         L.ext_ght_detect.argtypes = [vp, vp, i32, i32, fp, vp, vp]
         L.ext_conv_so2_normalized.argtypes = [vp, vp, i32, i32, i32, fp, vp, vp, vp]
+        L.ext_filter_so2_energy.argtypes = [vp, fp, vp]
+        L.ext_corr_so2_subset.argtypes = [vp, vp, i32, i32, fp, vp, i32, i32, vp, vp, i32, vp]
         for name in EXPORTED:
             if name not in ("ext_status_string", "ext_last_error", "ext_so3_channels", "ext_consensus_radius"):
                 getattr(L, name).restype = i32
@@ -457,3 +460,17 @@ def ext_ght_detect(plan: Plan, I, h, w, F: FilterSO2, out, stream=None):
 def ext_conv_so2_normalized(plan: Plan, H, channels, h, w, F: FilterSO2, alpha, out, stream=None):
     _check(lib().ext_conv_so2_normalized(plan.handle, _ptr(H), int(channels), int(h), int(w), F.ref(), _ptr(alpha),
                                          _ptr(out), _stream(stream)))
+
+
+def ext_filter_so2_energy(plan: Plan, F: FilterSO2):
+    """Lattice energies E_k, k = 0..K, of the filter's angular components (float64 array)."""
+    E = np.zeros(F.K + 1, np.float64)
+    _check(lib().ext_filter_so2_energy(plan.handle, F.ref(), _ptr(E)))
+    return E
+
+
+def ext_corr_so2_subset(plan: Plan, H, h, w, F: FilterSO2, ks, n_angles, max_out, argmax, precision=EXT_PREC_FP32,
+                        stream=None):
+    k = np.ascontiguousarray(np.asarray(ks, np.int32))
+    _check(lib().ext_corr_so2_subset(plan.handle, _ptr(H), int(h), int(w), F.ref(), _ptr(k), int(len(k)),
+                                     int(n_angles), _ptr(max_out), _ptr(argmax), int(precision), _stream(stream)))

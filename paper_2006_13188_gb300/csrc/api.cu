@@ -193,6 +193,58 @@ ext_status spectra(ext_plan plan, const ext_filter_so2* F, int h, int w, SpecMod
   return cs;
 }
 
+// Spectra of the listed components ks[0..nks) (ks[0] = 0), in list order.
+ext_status spectra_list(ext_plan plan, const ext_filter_so2* F, const int* ks, int nks, int h, int w, SpecMode mode,
+                        cudaStream_t st, const float2** out) {
+  uint64_t key = fnv1a(filter_key(F), &nks, sizeof(int));
+  key = fnv1a(key, ks, sizeof(int) * nks);
+  const double2* coef = nullptr;
+  int n_r = 0;
+  double dr = 0;
+  ext_status cs = EXT_OK;
+  bool have = false;
+  const int kind = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? EXT_FILTER_ANALYTIC_GAUSSPOW : EXT_FILTER_TABLE;
+  const size_t plane = (size_t)h * w;
+  auto sample = [&](int p0, int np, float2* grid) {
+    if (!have) {
+      cs = filter_coefficients(plan, F, st, &coef, &n_r, &dr);
+      have = true;
+    }
+    if (cs == EXT_OK)
+      for (int i = 0; i < np; ++i)
+        launch_component_grid(kind, F->K, ks[p0 + i], coef, n_r, dr, F->sigma, F->R, h, w, grid + plane * i, st, 1);
+  };
+  EXT_TRY(spectra_generic(plan, key, h, w, nks, mode, st, sample, out));
+  return cs;
+}
+
+// Steering weights of a component list (ks[0] = 0): B[j][2(i-1)] = 2 cos(2 pi ks[i] j / J),
+// B[j][2(i-1)+1] = -2 sin(2 pi ks[i] j / J), i = 1..nks-1; rows padded to cp floats.
+ext_status sweep_table_list(ext_plan plan, const int* ks, int nks, int J, cudaStream_t st, const float** out,
+                            int* cp_out) {
+  const int K = nks - 1;
+  const int cp = (2 * K + 3) / 4 * 4;
+  uint64_t key = fnv1a(0x5eedull, &J, sizeof(int));
+  key = fnv1a(key, ks, sizeof(int) * nks) | 1ull;   // odd: apart from the (K << 32 | J) keys
+  auto it = plan->sweep_tables.find(key);
+  if (it == plan->sweep_tables.end()) {
+    float* B = nullptr;
+    EXT_CUDA(cudaMalloc(&B, sizeof(float) * (size_t)J * (cp > 0 ? cp : 4)));
+    if (cp > 0) {
+      void* dks = nullptr;
+      EXT_TRY(ensure(plan, "sweep_ks", sizeof(int) * nks, &dks));
+      EXT_CUDA(cudaMemcpyAsync(dks, ks, sizeof(int) * nks, cudaMemcpyHostToDevice, st));
+      launch_sweep_table_list((const int*)dks, K, J, cp, B, st);
+      EXT_CUDA(cudaStreamSynchronize(st));   // the host list may go out of scope
+    }
+    EXT_CUDA(cudaGetLastError());
+    it = plan->sweep_tables.emplace(key, B).first;
+  }
+  *out = it->second;
+  *cp_out = cp;
+  return EXT_OK;
+}
+
 ext_status sweep_table(ext_plan plan, int K, int J, cudaStream_t st, const float** out, int* cp_out) {
   const int cp = (2 * K + 3) / 4 * 4;
   const uint64_t key = ((uint64_t)K << 32) | (uint32_t)J;
@@ -234,12 +286,16 @@ bool spectrum_tmap(const float2* Hf, int h, int w, int cw, int br, CUtensorMap* 
                           (unsigned)(2 * cw), (unsigned)br, out);
 }
 
-// G_k = H (*) F_k for k = 0..K into G (device, planes G_0, Re G_1, Im G_1, ...).
+// G_k = H (*) F_k for k = 0..K into G (device, planes G_0, Re G_1, Im G_1, ...);
+// with a component list ks (ks[0] = 0), for the listed components in list order.
 ext_status run_components(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, float* G,
-                          cudaStream_t st) {
-  const int K = F->K;
+                          cudaStream_t st, const int* ks = nullptr, int nks = 0) {
+  const int K = ks ? nks - 1 : F->K;
   const float2* S = nullptr;
-  EXT_TRY(spectra(plan, F, h, w, SPEC_CORR, st, &S));
+  if (ks)
+    EXT_TRY(spectra_list(plan, F, ks, nks, h, w, SPEC_CORR, st, &S));
+  else
+    EXT_TRY(spectra(plan, F, h, w, SPEC_CORR, st, &S));
   const float2 *tw_w = nullptr, *tw_h = nullptr;
   EXT_TRY(twiddle(plan, w, st, &tw_w));
   EXT_TRY(twiddle(plan, h, st, &tw_h));
@@ -602,6 +658,87 @@ ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_f
   EXT_TRY(stage_out_finish(sM, st));
   EXT_TRY(stage_out_finish(sA, st));
   return finish_host(plan, sH.host || sM.host || sA.host || sM.mapped || sA.mapped, st);
+}
+
+ext_status ext_corr_so2_subset(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, const int* ks,
+                               int nks, int n_angles, float* max_out, int32_t* argmax, int precision, void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_TRY(check_filter(F));
+  EXT_TRY(check_size(h, w));
+  if (!ks || nks < 1 || nks > 17) return fail(EXT_ERR_INVALID_ARG, "component list must hold 1..17 entries");
+  if (ks[0] != 0) return fail(EXT_ERR_INVALID_ARG, "the component list must start with 0");
+  for (int i = 1; i < nks; ++i)
+    if (ks[i] <= ks[i - 1] || ks[i] > F->K)
+      return fail(EXT_ERR_INVALID_ARG, "components must ascend and lie in 1..K");
+  if (n_angles < 1) return fail(EXT_ERR_INVALID_ARG, "n_angles must be >= 1");
+  if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3)
+    return fail(EXT_ERR_INVALID_ARG, "unknown precision");
+  if (precision == EXT_PREC_BF16X3 && n_angles > 128)
+    return fail(EXT_ERR_UNSUPPORTED, "BF16x3 sweep supports at most 128 angles");
+  if (h == 0 || w == 0) return EXT_OK;
+  if (!H || !max_out || !argmax) return fail(EXT_ERR_INVALID_ARG, "NULL buffer");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)h * w;
+  const int Ks = nks - 1;
+  Staged sH, sM, sA;
+  EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P, st, &sH));
+  if (Ks >= 1) {
+    EXT_TRY(stage_out_direct(plan, "out_0", max_out, sizeof(float) * P, &sM));
+    EXT_TRY(stage_out_direct(plan, "out_1", argmax, sizeof(int32_t) * P, &sA));
+  } else {
+    EXT_TRY(stage_out_alloc(plan, "out_0", max_out, sizeof(float) * P, &sM));
+    EXT_TRY(stage_out_alloc(plan, "out_1", argmax, sizeof(int32_t) * P, &sA));
+  }
+  void* G = nullptr;
+  EXT_TRY(ensure(plan, "G", sizeof(float) * P * (2 * Ks + 1), &G));
+  EXT_TRY(run_components(plan, (const float*)sH.dev, h, w, F, (float*)G, st, ks, nks));
+  if (Ks == 0) {   // only G_0: the same score at every angle, the first angle
+    EXT_CUDA(cudaMemcpyAsync(sM.dev, G, sizeof(float) * P, cudaMemcpyDeviceToDevice, st));
+    EXT_CUDA(cudaMemsetAsync(sA.dev, 0, sizeof(int32_t) * P, st));
+  } else {
+    const float* B = nullptr;
+    int cp = 0;
+    EXT_TRY(sweep_table_list(plan, ks, nks, n_angles, st, &B, &cp));
+    bool ok = true;
+    if (precision == EXT_PREC_BF16X3)
+      launch(plan, "sweep_bf16x3", st, [&] {
+        ok = sweep_bf16x3((const float*)G, (long long)P, Ks, n_angles, B, cp, (float*)sM.dev, (int32_t*)sA.dev,
+                          plan->dev_err, plan->sms, st);
+      });
+    else
+      launch(plan, "sweep_fp32", st, [&] {
+        ok = sweep_fp32((const float*)G, (long long)P, Ks, n_angles, B, cp, (float*)sM.dev, (int32_t*)sA.dev, st);
+      });
+    if (!ok) return fail(EXT_ERR_UNSUPPORTED, "sweep shape");
+  }
+  EXT_CUDA(cudaGetLastError());
+  EXT_TRY(stage_out_finish(sM, st));
+  EXT_TRY(stage_out_finish(sA, st));
+  return finish_host(plan, sH.host || sM.host || sA.host || sM.mapped || sA.mapped, st);
+}
+
+ext_status ext_filter_so2_energy(ext_plan plan, const ext_filter_so2* F, double* energy_out) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_TRY(check_filter(F));
+  if (!energy_out) return fail(EXT_ERR_INVALID_ARG, "NULL buffer");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = 0;
+  const double2* coef = nullptr;
+  int n_r = 0;
+  double dr = 0;
+  EXT_TRY(filter_coefficients(plan, F, st, &coef, &n_r, &dr));
+  const int kind = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? EXT_FILTER_ANALYTIC_GAUSSPOW : EXT_FILTER_TABLE;
+  void* E = nullptr;
+  EXT_TRY(ensure(plan, "energy", sizeof(double) * (F->K + 1), &E));
+  EXT_CUDA(cudaMemsetAsync(E, 0, sizeof(double) * (F->K + 1), st));
+  launch(plan, "component_energy", st, [&] {
+    launch_component_energy(kind, F->K, coef, n_r, dr, F->sigma, F->R, (double*)E, st);
+  });
+  EXT_CUDA(cudaGetLastError());
+  EXT_CUDA(cudaMemcpyAsync(energy_out, E, sizeof(double) * (F->K + 1), cudaMemcpyDeviceToHost, st));
+  EXT_CUDA(cudaStreamSynchronize(st));
+  return EXT_OK;
 }
 
 ext_status ext_conv_so2(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, const float* alpha,

@@ -193,6 +193,58 @@ void launch_sweep_table(int K, int J, int cp, float* B, cudaStream_t st) {
   k_sweep_table<<<J, 64, 0, st>>>(K, J, cp, B);
 }
 
+// Steering weights of a component list: as k_sweep_table with k = ks[c / 2 + 1].
+__global__ void k_sweep_table_list(const int* __restrict__ ks, int K, int J, int cp, float* __restrict__ B) {
+  const int j = blockIdx.x;
+  for (int c = threadIdx.x; c < cp; c += blockDim.x) {
+    float val = 0.f;
+    if (c < 2 * K) {
+      const int k = ks[c / 2 + 1];
+      const int m = (int)(((long long)k * j) % J);
+      double s, co;
+      sincospi(2.0 * (double)m / (double)J, &s, &co);
+      val = (c & 1) ? (float)(-2.0 * s) : (float)(2.0 * co);
+    }
+    B[(size_t)j * cp + c] = val;
+  }
+}
+
+void launch_sweep_table_list(const int* ks, int K, int J, int cp, float* B, cudaStream_t st) {
+  k_sweep_table_list<<<J, 64, 0, st>>>(ks, K, J, cp, B);
+}
+
+// Lattice energy of every component, E_k = sum_{d in [-R, R]^2} |F_k(d)|^2
+// (F_k(0) = 0 for k != 0), FP64, one thread per (offset, k = blockIdx.y).
+__global__ void k_component_energy(int kind, int K, const double2* __restrict__ coef, int n_r, double dr,
+                                   double sigma, int R, double* __restrict__ E) {
+  const int k = blockIdx.y;
+  const int side = 2 * R + 1;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (idx < (long long)side * side) {
+    const int dy = (int)(idx / side) - R, dx = (int)(idx % side) - R;
+    const double r = hypot((double)dx, (double)dy);
+    double2 f;
+    if (kind == EXT_FILTER_ANALYTIC_GAUSSPOW) {
+      const double2 a = coef[k + K];
+      const double mag = pow(r, (double)k) * exp(-r * r / (2.0 * sigma * sigma));
+      f = make_double2(a.x * mag, a.y * mag);
+    } else {
+      f = radial_table(coef + (size_t)(k + K) * n_r, n_r, dr, k, r);
+    }
+    if (r > 0.0 || k == 0) e = f.x * f.x + f.y * f.y;   // |e^{ik theta}| = 1
+  }
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0 && e != 0.0) atomicAdd(E + k, e);
+}
+
+void launch_component_energy(int kind, int K, const double2* coef, int n_r, double dr, double sigma, int R,
+                             double* E, cudaStream_t st) {
+  const long long n = (long long)(2 * R + 1) * (2 * R + 1);
+  dim3 grid((unsigned)((n + 255) / 256), K + 1);
+  k_component_energy<<<grid, 256, 0, st>>>(kind, K, coef, n_r, dr, sigma, R, E);
+}
+
 // ------------------------------------------------------ Mellin components ---
 // Scale harmonics of Sec. 8, F_k(r) = e^{i w_k ln r} (times the constant f_k of
 // a radially symmetric filter): M_k(d) = c_k exp(i w_k ln|d|) on the annulus

@@ -88,6 +88,11 @@ void launch_decompose_sampled(const double* img, int side, double dr, int n_r, i
 void launch_component_grid(int kind, int K, int k, const double2* coef, int n_r, double dr, double sigma,
                            int R, int h, int w, float2* grid, cudaStream_t st, int ncomp = 1);
 void launch_sweep_table(int K, int J, int cp, float* B, cudaStream_t st);
+// the same for a component list (ks[0] = 0, ks[1..K] the steered components, device)
+void launch_sweep_table_list(const int* ks, int K, int J, int cp, float* B, cudaStream_t st);
+// E_k = sum over the box [-R, R]^2 of |F_k(d)|^2, k = 0..K, accumulated into E (zeroed by the caller)
+void launch_component_energy(int kind, int K, const double2* coef, int n_r, double dr, double sigma, int R,
+                             double* E, cudaStream_t st);
 void launch_component_grid_mellin(double2 ck, double omega, double r_min, double r_max, int R, int h, int w,
                                   float2* grid, cudaStream_t st);
 void launch_scale_finalize(const float* H, const float* s, const float* N, const float* D, int channels, long long P,
