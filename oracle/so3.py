@@ -318,3 +318,75 @@ def refine(chan, L: int, q0, steps: int = 5, theta0: float = 0.25, tries: int = 
         if not moved:
             break
     return q, s
+
+
+# ------------------------------------------- extended convolution (scatter) ---
+# Eq. Def-EConv with a rotation at every INPUT voxel (Sec. 2.2; Sec. 9 for the
+# SO(3) component form):
+#     O(p) = sum_q V(q) (T_{R(q)} F)(p - q) = sum_{d in B} V(p - d) F(R(p - d)^-1 d),
+# periodic mod the volume shape.  Expanding T_R F = sum_{l,a,b} f_l^a C^l_ab(R) Y_l^b
+# gives the component form
+#     O = sum_{l,a,b} (V C^l_ab(R(.))) (*) (f_l^a Y_l^b)      (standard convolution),
+# i.e. the signal is modulated by each matrix entry of its own voxel's rotation
+# and convolved with one fixed function per (l, a, b) (the SO(3) analogue of
+# pre-multiplying H by e^{-ik Theta} in Sec. 4.1).
+
+def quat_field_matrices(Q):
+    """Rotation matrices (..., 3, 3) of a field of quaternions (..., 4) = (w, x, y, z)."""
+    Q = np.asarray(Q, np.float64)
+    n = np.linalg.norm(Q, axis=-1, keepdims=True)
+    w, x, y, z = np.moveaxis(Q / n, -1, 0)
+    return np.stack([np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+                     np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+                     np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], -2)
+
+
+def conv_so3_at(V, F: SHFilter, radius: int, Q, voxels):
+    """O(p) at the given output voxels (rows (z, y, x)) by the brute-force sum
+    over the box, each input voxel's filter rotated by its own rotation and
+    evaluated at R^-1 d straight from the closed form.  Q: (nz, ny, nx, 4)."""
+    V = np.asarray(V, np.float64)
+    nz, ny, nx = V.shape
+    dx, dy, dz = box_offsets3(radius)
+    fx, fy, fz = dx.astype(np.float64), dy.astype(np.float64), dz.astype(np.float64)
+    out = np.zeros(len(voxels), np.complex128)
+    for i, (pz, py, px) in enumerate(np.asarray(voxels, np.int64).reshape(-1, 3)):
+        qz, qy, qx = (pz - dz) % nz, (py - dy) % ny, (px - dx) % nx
+        Rm = quat_field_matrices(np.asarray(Q)[qz, qy, qx])          # (n_d, 3, 3)
+        # R^-1 d = R^T d
+        x = Rm[:, 0, 0] * fx + Rm[:, 1, 0] * fy + Rm[:, 2, 0] * fz
+        y = Rm[:, 0, 1] * fx + Rm[:, 1, 1] * fy + Rm[:, 2, 1] * fz
+        z = Rm[:, 0, 2] * fx + Rm[:, 1, 2] * fy + Rm[:, 2, 2] * fz
+        out[i] = np.sum(V[qz, qy, qx] * filter_eval(F, x, y, z))
+    return out
+
+
+def conv_so3(V, F: SHFilter, radius: int, Q):
+    """O at every voxel by the brute force (small volumes only)."""
+    nz, ny, nx = np.asarray(V).shape
+    vox = np.stack(np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij"), -1).reshape(-1, 3)
+    return conv_so3_at(V, F, radius, Q, vox).reshape(nz, ny, nx)
+
+
+def conv_so3_from_components(V, F: SHFilter, radius: int, Q):
+    """O by the component form: every voxel's C^l(R(q)) from its definition
+    (wigner_by_projection), the modulated signals V C^l_ab, and a direct
+    periodic convolution of each with f_l^a Y_l^b over the box."""
+    V = np.asarray(V, np.float64)
+    shape = V.shape
+    Rms = quat_field_matrices(np.asarray(Q).reshape(-1, 4))
+    dx, dy, dz = box_offsets3(radius)
+    r, th, ph = to_spherical(dx.astype(np.float64), dy.astype(np.float64), dz.astype(np.float64))
+    out = np.zeros(shape, np.complex128)
+    for l in range(F.L + 1):
+        Cs = np.stack([wigner_by_projection(l, Rm) for Rm in Rms])   # (P, 2l+1, 2l+1)
+        for a in range(-l, l + 1):
+            for b in range(-l, l + 1):
+                g = F.radial(l, a, r) * sph_harm(l, b, th, ph)
+                if l > 0:
+                    g = np.where(r == 0, 0.0, g)
+                U = V * Cs[:, a + l, b + l].reshape(shape)
+                for n in range(dx.size):
+                    if g[n] != 0:
+                        out += np.roll(U, (dz[n], dy[n], dx[n]), axis=(0, 1, 2)) * g[n]
+    return out
