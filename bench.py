@@ -51,11 +51,13 @@ def parse_args():
                     help="so3 / so3p: volume side (128 is the workload; smaller only for profiling captures)")
     ap.add_argument("--train-steps", type=int, default=6000,
                     help="so3p: Adam steps of the proposal network (setup, not timed)")
-    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght", "lic", "defocus", "budget"],
+    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght", "lic", "defocus", "budget",
+                             "so3conv"],
                     help="so2: the pattern-matching sweep (default, the headline metric); "
                          "scale: scale-adaptive smoothing of a 4096x4096x3 image; "
                          "batched: 512 uneven images in one captured graph; "
-                         "so3: 128^3 volume, L=6, 4608-rotation sweep")
+                         "so3: 128^3 volume, L=6, 4608-rotation sweep; "
+                         "so3conv: SO(3) extended convolution of a 128^3 volume, L=6, smooth rotation field")
     ap.add_argument("--n-images", type=int, default=512)
     return ap.parse_args()
 
@@ -986,6 +988,115 @@ def bench_so3p(args, world, rank, local):
     return 0
 
 
+# ----------------------------------------------------- SO(3) convolution ---
+SO3CONV_WORKLOAD = ("SO(3) extended convolution (Eq. Def-EConv, scatter, component form of Sec. 9): 128^3 f32 volume "
+                    "(periodic Gaussian-blurred noise, sigma 1.5), random band-limited filter of SH degree L=6 "
+                    "(231 unique (l,a,b) components), box radius 8, smooth per-voxel rotation field (blurred "
+                    "4-vector noise, sigma 4, normalised)")
+
+
+def bench_so3conv(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_2006_13188_gb300 as ec
+    import synth
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    n = args.so3_size
+    P = n ** 3
+    prob = synth.so3_conv_problem(seed=synth.seed_for(9) + rank, shape=(n, n, n))
+    tables, dr, R = prob["tables"], prob["dr"], prob["radius"]
+    plan = ec.Plan(local)
+    V = torch.from_numpy(prob["V"]).to(device)
+    Q = torch.from_numpy(prob["Q"]).to(device)
+    out = torch.empty_like(V)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    def call():
+        ec.ext_conv_so3(plan, V, n, n, n, tables, dr, R, Q, out)
+    t0 = time.perf_counter()
+    call()
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    barrier(world)
+    total = 0.0
+    steps = args.steps
+    with ClockSampler(local) as clk:
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+    total = reduce_max(total, world, device)
+    if args.only_timed:
+        plan.close()
+        return 0
+    plan.profile_read()
+    plan.profile(True)
+    prof_steps = 3
+    for _ in range(prof_steps):
+        call()
+    torch.cuda.synchronize()
+    prof = {k: v for k, v in plan.profile_read().items() if v[1] > 0}
+    plan.profile(False)
+    Vh = torch.from_numpy(prob["V"]).pin_memory()
+    Qh = torch.from_numpy(prob["Q"]).pin_memory()
+    oh = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(steps, 20))
+    ec.ext_conv_so3(plan, Vh, n, n, n, tables, dr, R, Qh, oh)
+    barrier(world)
+    t1 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ec.ext_conv_so3(plan, Vh, n, n, n, tables, dr, R, Qh, oh)
+    e2e_s = reduce_max(time.perf_counter() - t1, world, device)
+    dom_name, (dom_ms, dom_n) = max(prof.items(), key=lambda kv: kv[1][0])
+    avg_ms = dom_ms / dom_n
+    nc = sum(2 * l * (l + 1) + 1 for l in range(len(tables)))   # unique (l, a, b)
+    alg = {"so3c_cols_z_conv_tma": nc * 16 * P + 8 * P, "so3c_cols_z_conv": nc * 16 * P + 8 * P,
+           "so3c_rows_x": nc * 16 * P, "so3c_cols_y": nc * 16 * P,
+           "so3c_modulate": 20 * P + nc * 8 * P}.get(dom_name)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
+    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": committed_traffic().get((dom_name, f"{n}^3L6")),
+                "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
+                "kernels": {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps}
+                            for k, v in prof.items()}}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle.so3 import SHFilter, conv_so3_at
+        vox = np.random.default_rng(0).integers(0, n, (120, 3))
+        t2 = time.perf_counter()
+        conv_so3_at(prob["V"], SHFilter(tables, dr), R, prob["Q"], vox)
+        t = time.perf_counter() - t2
+        cpu = {"value": len(vox) / t / 1e6, "unit": "Mvox/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 brute-force scatter sum (filter rotated per input voxel) at {len(vox)} random "
+                         f"voxels ({t:.1f} s)"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "SO(3) extended convolution Mvox/s",
+            "value": world * steps * P / (total * 1e-3) / 1e6, "unit": "Mvox/s", "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": total / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SO3CONV_WORKLOAD, "volume_side": n, "components": nc,
+                       "l2": "256 MB written between steps; working set > L2", "plan_ms": plan_ms},
+            "clocks": clk.summary(),
+            "e2e": {"value": world * e2e_steps * P / e2e_s / 1e6, "unit": "Mvox/s", "h2d_bytes_per_step": 20 * P,
+                    "d2h_bytes_per_step": 4 * P, "steps": e2e_steps},
+            "gpu_launches": int(sum(v[1] for v in prof.values()) // prof_steps),
+            "roofline": roofline, "cpu_baseline": cpu}))
+    plan.close()
+    return 0
+
+
 # ------------------------------------------------------------------ main ---
 def main():
     args = parse_args()
@@ -1006,6 +1117,8 @@ def main():
         return bench_so3(args, world, rank, local)
     if args.workload == "so3p" and args.impl == "ours":
         return bench_so3p(args, world, rank, local)
+    if args.workload == "so3conv" and args.impl == "ours":
+        return bench_so3conv(args, world, rank, local)
 
     import numpy as np
     import synth

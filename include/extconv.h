@@ -285,6 +285,22 @@ ext_status ext_corr_so3_components(ext_plan plan, const float* V, int nz, int ny
  * per voxel max_R S and the first maximising rotation index. */
 ext_status ext_sweep_so3(ext_plan plan, const float* G, int64_t n_vox, int L, const double* quats, int n_rot,
                          float* max_out, int32_t* argmax, int precision, void* stream);
+/*
+ * SO(3) extended convolution (Eq. Def-EConv, scatter form, with a rotation at
+ * every INPUT voxel; component form of Sec. 9):
+ *   out(p) = sum_q V(q) (T_{R(q)} F)(p - q)
+ *          = sum_{l,a,b} ((V C^l_ab(R(.))) (*) (f_l^a Y_l^b))(p),
+ * periodic, with the volume, filter tables, box and C^l_ab conventions of
+ * ext_corr_so3 above (a real filter, so out is real).  quats: nz*ny*nx unit
+ * quaternions (w, x, y, z) as float32 [n_vox][4], HOST or device (a device
+ * pointer 16-byte aligned, else EXT_ERR_INVALID_ARG); they are
+ * normalised on use and a zero quaternion acts as the identity.  V, out:
+ * nz*ny*nx float32.  Cost: one complex 3D transform per unique (l, a, b)
+ * (231 for L = 6) and one inverse; the component spectra are cached per
+ * filter and volume shape.  Workspace: up to 4 GiB of modulated planes.
+ */
+ext_status ext_conv_so3(ext_plan plan, const float* V, int nz, int ny, int nx, const double* tables, int L, int n_r,
+                        double dr, int R, const float* quats, float* out, void* stream);
 /* Components then sweep. */
 ext_status ext_corr_so3(ext_plan plan, const float* V, int nz, int ny, int nx, const double* tables, int L, int n_r,
                         double dr, int R, const double* quats, int n_rot, float* max_out, int32_t* argmax,

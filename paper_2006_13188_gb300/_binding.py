@@ -40,7 +40,7 @@ EXPORTED = (
     "ext_mlp_grads", "ext_mlp_train", "ext_so3_upper_bound", "ext_so3_refined_bound", "ext_so3_gather", "ext_so3_augment", "ext_so3_refine",
     "ext_so3_propose", "ext_corr_so3_propose", "ext_gradient_field", "ext_consensus_radius",
     "ext_consensus_filter", "ext_ght_detect", "ext_conv_so2_normalized", "ext_filter_so2_energy",
-    "ext_corr_so2_subset",
+    "ext_corr_so2_subset", "ext_conv_so3",
 )
 
 
@@ -102,6 +102,7 @@ def lib():
         L.ext_corr_so3_components.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, vp]
         L.ext_sweep_so3.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp, i32, vp]
         L.ext_corr_so3.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, i32, vp, vp, i32, vp]
+        L.ext_conv_so3.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, vp, vp]
         dbl, f32 = ctypes.c_double, ctypes.c_float
         L.ext_mlp_create.argtypes = [vp, i32, i32, ctypes.POINTER(vp)]
         L.ext_mlp_destroy.argtypes = [vp]
@@ -337,6 +338,17 @@ def ext_corr_so3(plan: Plan, V, nz, ny, nx, tables, dr, R, quats, max_out, argma
     _check(lib().ext_corr_so3(plan.handle, _ptr(V), int(nz), int(ny), int(nx), _ptr(t.view(np.float64)), L, t.shape[1],
                               float(dr), int(R), _ptr(q), q.shape[0], _ptr(max_out), _ptr(argmax), int(precision),
                               _stream(stream)))
+
+
+def ext_conv_so3(plan: Plan, V, nz, ny, nx, tables, dr, R, quats, out, stream=None):
+    """SO(3) extended convolution (scatter) with one quaternion (w, x, y, z)
+    per voxel; quats float32 [nz*ny*nx][4], host array or device tensor."""
+    t = so3_pack_tables(tables)
+    L = len(tables) - 1
+    if isinstance(quats, np.ndarray):
+        quats = np.ascontiguousarray(quats, np.float32)
+    _check(lib().ext_conv_so3(plan.handle, _ptr(V), int(nz), int(ny), int(nx), _ptr(t.view(np.float64)), L, t.shape[1],
+                              float(dr), int(R), _ptr(quats), _ptr(out), _stream(stream)))
 
 
 class MLP:

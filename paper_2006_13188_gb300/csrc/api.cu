@@ -271,14 +271,6 @@ ext_status check_size(int h, int w) {
   return EXT_OK;
 }
 
-// Rows per tensor copy of the H tile: a divisor of h, at most 256, whose box
-// (br rows x cw complex) is a multiple of 128 bytes; 0 if none.
-int tma_rows(int h, int cw) {
-  for (int br = 256; br >= 1; --br)
-    if (h % br == 0 && (br * cw * 8) % 128 == 0) return br;
-  return 0;
-}
-
 // Tensor map of the full h x w complex spectrum as h rows of 2w floats, box
 // 2 cw floats x br rows.
 bool spectrum_tmap(const float2* Hf, int h, int w, int cw, int br, CUtensorMap* out) {

@@ -40,78 +40,109 @@ ext_status check_so3_args(int nz, int ny, int nx, int L, int n_r, double dr, int
   return EXT_OK;
 }
 
+// Component spectra FFT(f_l^a Y_l^b) / P of every unique (l, a, b) in the
+// column-tiled layout of the z pass (conj_out: their conjugates, as the
+// correlation uses them), cached per filter, volume shape and kind.  dcomp,
+// dtab: device copies of the layout and of the host `tables`.
+ext_status so3_spectra(ext_plan plan, int ncomp, const int4* dcomp, const double* tables, const double2* dtab, int L,
+                       int n_r, double dr, int R, int nz, int ny, int nx, int conj_out, cudaStream_t st,
+                       const float2** out) {
+  const size_t P = (size_t)nz * ny * nx;
+  const int w2 = ny * nx;   // z-pass: a 2D array of nz rows and ny*nx columns
+  const size_t tab_bytes = sizeof(double2) * (size_t)(L + 1) * (L + 1) * n_r;
+  const float2 *tw_x, *tw_y, *tw_z;
+  EXT_TRY(twiddle(plan, nx, st, &tw_x));
+  EXT_TRY(twiddle(plan, ny, st, &tw_y));
+  EXT_TRY(twiddle(plan, nz, st, &tw_z));
+  uint64_t key = conj_out ? 0x503503503ull : 0x503c0503c0ull;
+  key = fnv1a(key, tables, tab_bytes);
+  int meta[5] = {L, n_r, R, nz, ny};
+  key = fnv1a(key, meta, sizeof(meta));
+  key = fnv1a(key, &dr, sizeof(dr));
+  key = fnv1a(key, &nx, sizeof(nx));
+  const int cw = fft_col_tile(nz);
+  const size_t per_k = (size_t)((w2 + cw - 1) / cw) * nz * cw;
+  const float scale = 1.0f / (float)P;
+  auto build = [&](float2* Sdst) -> ext_status {
+    int chunk = (int)((1024ull << 20) / (sizeof(float2) * P));
+    chunk = std::max(1, std::min(chunk, ncomp));
+    void* grid;
+    EXT_TRY(ensure(plan, "grid", sizeof(float2) * P * chunk, &grid));
+    for (int k0 = 0; k0 < ncomp; k0 += chunk) {
+      const int nk = std::min(chunk, ncomp - k0);
+      EXT_CUDA(cudaMemsetAsync(grid, 0, sizeof(float2) * P * nk, st));
+      launch_so3_component_grid(dcomp, k0, nk, dtab, n_r, dr, L, R, nz, ny, nx, (float2*)grid, st);
+      fft_rows_c2c(nx, (const float2*)grid, nz * ny, nk, (float2*)grid, false, tw_x, st);
+      fft_cols_c2c(ny, (float2*)grid, nx, nz * nk, false, tw_y, st);
+      fft_cols_fwd_spectrum(nz, (const float2*)grid, w2, conj_out, scale, Sdst + per_k * k0, tw_z, st, nk, scale);
+    }
+    EXT_CUDA(cudaGetLastError());
+    return EXT_OK;
+  };
+  for (auto& e : plan->specs)
+    if (e.key == key) {
+      e.stamp = ++plan->clock;
+      *out = e.S;
+      return EXT_OK;
+    }
+  if (plan->specs.size() >= plan->max_specs) {
+    size_t oldest = 0;
+    for (size_t i = 1; i < plan->specs.size(); ++i)
+      if (plan->specs[i].stamp < plan->specs[oldest].stamp) oldest = i;
+    EXT_CUDA(cudaStreamSynchronize(st));
+    EXT_CUDA(cudaFree(plan->specs[oldest].S));
+    plan->specs.erase(plan->specs.begin() + oldest);
+  }
+  SpecEntry e;
+  e.key = key;
+  e.bytes = sizeof(float2) * per_k * ncomp;
+  EXT_CUDA(cudaMalloc(&e.S, e.bytes));
+  ext_status bs = build(e.S);
+  if (bs != EXT_OK) {
+    cudaFree(e.S);
+    return bs;
+  }
+  e.stamp = ++plan->clock;
+  plan->specs.push_back(e);
+  *out = e.S;
+  return EXT_OK;
+}
+
+// Device copies of the layout (components, channels) and of the radial tables.
+ext_status so3_upload(ext_plan plan, const So3Layout& lay, const double* tables, int L, int n_r, cudaStream_t st,
+                      const int4** dcomp, const int2** dchan, const double2** dtab) {
+  const int ncomp = (int)lay.comp.size();
+  void *c, *h, *t;
+  EXT_TRY(ensure(plan, "so3_comp", sizeof(int4) * ncomp, &c));
+  EXT_TRY(ensure(plan, "so3_chan", sizeof(int2) * ncomp, &h));
+  const size_t tab_bytes = sizeof(double2) * (size_t)(L + 1) * (L + 1) * n_r;
+  EXT_TRY(ensure(plan, "so3_tab", tab_bytes, &t));
+  EXT_CUDA(cudaMemcpyAsync(c, lay.comp.data(), sizeof(int4) * ncomp, cudaMemcpyHostToDevice, st));
+  EXT_CUDA(cudaMemcpyAsync(h, lay.chan.data(), sizeof(int2) * ncomp, cudaMemcpyHostToDevice, st));
+  EXT_CUDA(cudaMemcpyAsync(t, tables, tab_bytes, cudaMemcpyHostToDevice, st));
+  *dcomp = (const int4*)c;
+  *dchan = (const int2*)h;
+  *dtab = (const double2*)t;
+  return EXT_OK;
+}
+
 // G (nchan planes of nz*ny*nx floats) for volume V (device).
 ext_status so3_components(ext_plan plan, const float* V, int nz, int ny, int nx, const double* tables, int L, int n_r,
                           double dr, int R, float* G, cudaStream_t st) {
   const So3Layout lay = so3_layout(L);
   const int ncomp = (int)lay.comp.size();
   const size_t P = (size_t)nz * ny * nx;
-  const int w2 = ny * nx;   // z-pass: a 2D array of nz rows and ny*nx columns
-  // device copies of the layout and the tables
-  void *dcomp, *dchan, *dtab;
-  EXT_TRY(ensure(plan, "so3_comp", sizeof(int4) * ncomp, &dcomp));
-  EXT_TRY(ensure(plan, "so3_chan", sizeof(int2) * ncomp, &dchan));
-  const size_t tab_bytes = sizeof(double2) * (size_t)(L + 1) * (L + 1) * n_r;
-  EXT_TRY(ensure(plan, "so3_tab", tab_bytes, &dtab));
-  EXT_CUDA(cudaMemcpyAsync(dcomp, lay.comp.data(), sizeof(int4) * ncomp, cudaMemcpyHostToDevice, st));
-  EXT_CUDA(cudaMemcpyAsync(dchan, lay.chan.data(), sizeof(int2) * ncomp, cudaMemcpyHostToDevice, st));
-  EXT_CUDA(cudaMemcpyAsync(dtab, tables, tab_bytes, cudaMemcpyHostToDevice, st));
+  const int w2 = ny * nx;
+  const int4* dcomp;
+  const int2* dchan;
+  const double2* dtab;
+  EXT_TRY(so3_upload(plan, lay, tables, L, n_r, st, &dcomp, &dchan, &dtab));
   const float2 *tw_x, *tw_y, *tw_z;
   EXT_TRY(twiddle(plan, nx, st, &tw_x));
   EXT_TRY(twiddle(plan, ny, st, &tw_y));
   EXT_TRY(twiddle(plan, nz, st, &tw_z));
-  // component spectra, cached per filter and volume shape
-  uint64_t key = 0x503503503ull;
-  key = fnv1a(key, tables, tab_bytes);
-  int meta[5] = {L, n_r, R, nz, ny};
-  key = fnv1a(key, meta, sizeof(meta));
-  key = fnv1a(key, &dr, sizeof(dr));
-  key = fnv1a(key, &nx, sizeof(nx));
   const float2* S = nullptr;
-  {
-    const int cw = fft_col_tile(nz);
-    const size_t per_k = (size_t)((w2 + cw - 1) / cw) * nz * cw;
-    const float scale = 1.0f / (float)P;
-    auto build = [&](float2* Sdst) -> ext_status {
-      int chunk = (int)((1024ull << 20) / (sizeof(float2) * P));
-      chunk = std::max(1, std::min(chunk, ncomp));
-      void* grid;
-      EXT_TRY(ensure(plan, "grid", sizeof(float2) * P * chunk, &grid));
-      for (int k0 = 0; k0 < ncomp; k0 += chunk) {
-        const int nk = std::min(chunk, ncomp - k0);
-        EXT_CUDA(cudaMemsetAsync(grid, 0, sizeof(float2) * P * nk, st));
-        launch_so3_component_grid((const int4*)dcomp, k0, nk, (const double2*)dtab, n_r, dr, L, R, nz, ny, nx,
-                                  (float2*)grid, st);
-        fft_rows_c2c(nx, (const float2*)grid, nz * ny, nk, (float2*)grid, false, tw_x, st);
-        fft_cols_c2c(ny, (float2*)grid, nx, nz * nk, false, tw_y, st);
-        fft_cols_fwd_spectrum(nz, (const float2*)grid, w2, 1, scale, Sdst + per_k * k0, tw_z, st, nk, scale);
-      }
-      EXT_CUDA(cudaGetLastError());
-      return EXT_OK;
-    };
-    bool hit = false;
-    for (auto& e : plan->specs)
-      if (e.key == key) { e.stamp = ++plan->clock; S = e.S; hit = true; }
-    if (!hit) {
-      if (plan->specs.size() >= plan->max_specs) {
-        size_t oldest = 0;
-        for (size_t i = 1; i < plan->specs.size(); ++i)
-          if (plan->specs[i].stamp < plan->specs[oldest].stamp) oldest = i;
-        EXT_CUDA(cudaStreamSynchronize(st));
-        EXT_CUDA(cudaFree(plan->specs[oldest].S));
-        plan->specs.erase(plan->specs.begin() + oldest);
-      }
-      SpecEntry e;
-      e.key = key;
-      e.bytes = sizeof(float2) * per_k * ncomp;
-      EXT_CUDA(cudaMalloc(&e.S, e.bytes));
-      ext_status bs = build(e.S);
-      if (bs != EXT_OK) { cudaFree(e.S); return bs; }
-      e.stamp = ++plan->clock;
-      plan->specs.push_back(e);
-      S = e.S;
-    }
-  }
+  EXT_TRY(so3_spectra(plan, ncomp, dcomp, tables, dtab, L, n_r, dr, R, nz, ny, nx, 1, st, &S));
   // forward transform of the volume (full complex spectrum)
   void* Hf;
   EXT_TRY(ensure(plan, "so3_H", sizeof(float2) * P, &Hf));
@@ -502,9 +533,104 @@ ext_status mlp_backward(ext_mlp net, int n, const float* qt, float* loss_dev, cu
   return EXT_OK;
 }
 
+// SO(3) extended convolution (scatter) of volume V (device) with the rotation
+// field Q (device, P quaternions) into out (device):
+//   U_e = w_e V C_e(R(.))               (k_so3_modulate, every unique entry e)
+//   U^_e over x and y                   (in-place complex row / column passes)
+//   Y = IFFT_z sum_e FFT_z(U^_e) S_e    (column pass accumulating the products)
+//   out = Re IFFT_yx Y                  (S_e carries the 1 / P of the inverse)
+// The entries go in chunks when all of them do not fit the workspace budget,
+// their partial Y summed.
+ext_status so3_conv(ext_plan plan, const float* V, int nz, int ny, int nx, const double* tables, int L, int n_r,
+                    double dr, int R, const float* Q, float* out, cudaStream_t st) {
+  const So3Layout lay = so3_layout(L);
+  const int ncomp = (int)lay.comp.size();
+  const long long P = (long long)nz * ny * nx;
+  const int w2 = ny * nx;
+  const int4* dcomp;
+  const int2* dchan;
+  const double2* dtab;
+  EXT_TRY(so3_upload(plan, lay, tables, L, n_r, st, &dcomp, &dchan, &dtab));
+  const float2 *tw_x, *tw_y, *tw_z;
+  EXT_TRY(twiddle(plan, nx, st, &tw_x));
+  EXT_TRY(twiddle(plan, ny, st, &tw_y));
+  EXT_TRY(twiddle(plan, nz, st, &tw_z));
+  const float2* S = nullptr;
+  EXT_TRY(so3_spectra(plan, ncomp, dcomp, tables, dtab, L, n_r, dr, R, nz, ny, nx, 0, st, &S));
+  const int cw = fft_col_tile(nz);
+  const size_t per_k = (size_t)((w2 + cw - 1) / cw) * nz * cw;
+  int chunk = (int)((4096ull << 20) / (sizeof(float2) * (size_t)P));
+  chunk = std::max(1, std::min(chunk, ncomp));
+  void *U, *Y, *Yk = nullptr, *dch;
+  EXT_TRY(ensure(plan, "so3c_U", sizeof(float2) * P * chunk, &U));
+  EXT_TRY(ensure(plan, "so3c_Y", sizeof(float2) * P, &Y));
+  if (chunk < ncomp) EXT_TRY(ensure(plan, "so3c_Yk", sizeof(float2) * P, &Yk));
+  EXT_TRY(ensure(plan, "so3c_chan", sizeof(int2), &dch));
+  const int2 real_only = make_int2(0, -1);
+  EXT_CUDA(cudaMemcpyAsync(dch, &real_only, sizeof(int2), cudaMemcpyHostToDevice, st));
+  bool gtw = false;
+  const int br = plan->tma && fft_cols_conv_tma_ok(nz, &gtw) ? tma_rows(nz, cw) : 0;
+  const float2* stw = nullptr;
+  if (br > 0 && gtw) EXT_TRY(stage_table(plan, nz, st, &stw));
+  for (int e0 = 0; e0 < ncomp; e0 += chunk) {
+    const int ne = std::min(chunk, ncomp - e0);
+    float2* Ydst = (float2*)(e0 == 0 ? Y : Yk);
+    launch(plan, "so3c_modulate", st,
+           [&] { launch_so3_modulate(V, Q, P, L, e0, ne, (float2*)U, plan->sms, st); });
+    launch(plan, "so3c_rows_x", st,
+           [&] { fft_rows_c2c(nx, (const float2*)U, nz * ny, ne, (float2*)U, false, tw_x, st); });
+    launch(plan, "so3c_cols_y", st, [&] { fft_cols_c2c(ny, (float2*)U, nx, nz * ne, false, tw_y, st); });
+    CUtensorMap tmU;
+    bool done = false;
+    if (br > 0 && make_tmap_2d_f32(U, (unsigned long long)2 * w2, (unsigned long long)ne * nz,
+                                   (unsigned long long)2 * w2 * sizeof(float), (unsigned)(2 * cw), (unsigned)br, &tmU))
+      launch(plan, "so3c_cols_z_conv_tma", st, [&] {
+        done = fft_cols_conv_tma(nz, tmU, w2, br, ne - 1, S + per_k * e0, Ydst, tw_z, stw, plan->dev_err, plan->sms,
+                                 st);
+      });
+    if (!done)
+      launch(plan, "so3c_cols_z_conv", st,
+             [&] { fft_cols_conv(nz, (const float2*)U, w2, ne - 1, S + per_k * e0, Ydst, tw_z, st); });
+    if (e0 > 0) launch(plan, "so3c_add", st, [&] { launch_add_complex((float2*)Y, (const float2*)Yk, P, plan->sms, st); });
+  }
+  bool fused = false;
+  if (ny == nx && plan->pipelined)
+    launch(plan, "so3c_planes_yx", st, [&] {
+      fused = fft_planes_inv_channels(nx, (const float2*)Y, nz, 0, 1, (const int2*)dch, out, tw_x, plan->dev_err,
+                                      plan->sms, st);
+    });
+  if (!fused) {
+    launch(plan, "so3c_cols_y_inv", st, [&] { fft_cols_c2c(ny, (float2*)Y, nx, nz, true, tw_y, st); });
+    launch(plan, "so3c_rows_x_inv", st, [&] {
+      fft_rows_inv_channels(nx, (const float2*)Y, nz * ny, 0, 1, (const int2*)dch, out, tw_x, st);
+    });
+  }
+  EXT_CUDA(cudaGetLastError());
+  return EXT_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+ext_status ext_conv_so3(ext_plan plan, const float* V, int nz, int ny, int nx, const double* tables, int L, int n_r,
+                        double dr, int R, const float* quats, float* out, void* stream) {
+  if (!plan || !V || !tables || !quats || !out) return fail(EXT_ERR_INVALID_ARG, "NULL argument");
+  EXT_TRY(check_so3_args(nz, ny, nx, L, n_r, dr, R));
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)nz * ny * nx;
+  Staged sV, sQ, sO;
+  EXT_TRY(stage_in(plan, "in_V", V, sizeof(float) * P, st, &sV));
+  EXT_TRY(stage_in(plan, "in_Q", quats, sizeof(float) * 4 * P, st, &sQ));
+  if (reinterpret_cast<uintptr_t>(sQ.dev) % 16 != 0)
+    return fail(EXT_ERR_INVALID_ARG, "device quaternion field must be 16-byte aligned");
+  EXT_TRY(stage_out_direct(plan, "out_O", out, sizeof(float) * P, &sO));
+  EXT_TRY(so3_conv(plan, (const float*)sV.dev, nz, ny, nx, tables, L, n_r, dr, R, (const float*)sQ.dev,
+                   (float*)sO.dev, st));
+  EXT_TRY(stage_out_finish(sO, st));
+  return finish_host(plan, sV.host || sQ.host || sO.host || sO.mapped, st);
+}
 
 ext_status ext_mlp_create(ext_plan plan, int n_in, int hidden, ext_mlp* out) {
   if (!plan || !out) return fail(EXT_ERR_INVALID_ARG, "NULL argument");

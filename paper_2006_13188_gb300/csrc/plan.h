@@ -152,6 +152,14 @@ ext_status twiddle(ext_plan plan, int n, cudaStream_t st, const float2** out) {
   return EXT_OK;
 }
 
+// Rows per tensor copy of the H tile: a divisor of h, at most 256, whose box
+// (br rows x cw complex) is a multiple of 128 bytes; 0 if none.
+int tma_rows(int h, int cw) {
+  for (int br = 256; br >= 1; --br)
+    if (h % br == 0 && (br * cw * 8) % 128 == 0) return br;
+  return 0;
+}
+
 // Stage twiddle table of length n in device memory (cached in the twiddle map
 // under the key -n), for passes whose shared memory has no room for a copy.
 ext_status stage_table(ext_plan plan, int n, cudaStream_t st, const float2** out) {

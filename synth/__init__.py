@@ -15,6 +15,12 @@ from its number alone.  Workload numbering:
 3. Scale-adaptive smoothing, Voronoi image with block noise, scale field in
    [1, 8] px (see :func:`scale_smoothing_problem`).
 4. Batched uneven SO(2) correlation (see :func:`batched_descriptors`).
+5. SO(3) matching, 128^3 volume, 16 planted templates, L = 6.
+6. Pattern detection (gradient signal and field, consensus filter).
+7. Normalised orientation-adaptive smoothing (line integral convolution).
+8. Depth-defocus blur with a Mellin disk filter.
+9. SO(3) orientation-adaptive filtering, 128^3 volume, L = 6, smooth
+   rotation field (see :func:`so3_conv_problem`).
 """
 from __future__ import annotations
 
@@ -323,7 +329,7 @@ def scale_smoothing_problem(seed: int | None = None, size: int | tuple = 4096,
                 centre_tap=centre_tap)
 
 
-# ------------------------------------------------------------- workload 5 ---
+# ------------------------------------------------------------- workload 8 ---
 
 def depth_defocus_problem(seed: int | None = None, size: int | tuple = 2048, n_lines: int = 600,
                           s_min: float = 1.0, s_max: float = 8.0):
@@ -483,6 +489,34 @@ def so3_match_problem(seed: int | None = None, size: int = 128, n_plant: int = 1
         V[np.ix_(zi, yi, xi)] += block
     return dict(V=V.astype(np.float32), tables=tables, dr=dr, radius=radius, L=L,
                 centres=np.array(centres), quats=quats)
+
+
+def so3_rotation_field(seed: int, shape, sigma: float = 4.0):
+    """Smooth field of unit quaternions (w, x, y, z), float32 (*shape, 4): four
+    i.i.d. N(0,1) volumes, each Gaussian-blurred (sigma voxels, periodic) and
+    rescaled to unit variance, then normalised per voxel."""
+    rng = np.random.default_rng(seed)
+    comps = []
+    for _ in range(4):
+        c = ndimage.gaussian_filter(rng.standard_normal(shape), sigma, mode="wrap")
+        comps.append(c / c.std())
+    q = np.stack(comps, axis=-1)
+    q /= np.linalg.norm(q, axis=-1, keepdims=True)
+    return q.astype(np.float32)
+
+
+def so3_conv_problem(seed: int | None = None, shape=(128, 128, 128), L: int = 6, radius: int = 8,
+                     dr: float = 0.125, field_sigma: float = 4.0):
+    """Orientation-adaptive 3D filtering input: a volume of Gaussian-blurred
+    (sigma 1.5, periodic) N(0,1) noise, the band-limited random filter of
+    so3_filter_tables (degree L, support radius `radius`) and a smooth rotation
+    field (so3_rotation_field).  Volume float32 (z, y, x)."""
+    rng = np.random.default_rng(seed_for(9) if seed is None else seed)
+    tables = so3_filter_tables(int(rng.integers(0, 2**31 - 1)), L, float(radius), dr)
+    V = ndimage.gaussian_filter(rng.standard_normal(shape), 1.5, mode="wrap")
+    V = (V / V.std()).astype(np.float32)
+    Q = so3_rotation_field(int(rng.integers(0, 2**31 - 1)), shape, field_sigma)
+    return dict(V=V, Q=Q, tables=tables, dr=dr, radius=radius, L=L)
 
 
 def mlp_init(seed: int, n_in: int, hidden: int = 256):
