@@ -49,6 +49,8 @@ def parse_args():
                     help="plan, warm-up and timed steps only (for ncu launch lists)")
     ap.add_argument("--so3-size", type=int, default=128,
                     help="so3 / so3p: volume side (128 is the workload; smaller only for profiling captures)")
+    ap.add_argument("--so3-L", type=int, default=6,
+                    help="so3conv: filter degree (6 is the workload; lower only for profiling captures)")
     ap.add_argument("--train-steps", type=int, default=6000,
                     help="so3p: Adam steps of the proposal network (setup, not timed)")
     ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght", "lic", "defocus", "budget",
@@ -1004,7 +1006,7 @@ def bench_so3conv(args, world, rank, local):
     device = torch.device("cuda", local)
     n = args.so3_size
     P = n ** 3
-    prob = synth.so3_conv_problem(seed=synth.seed_for(9) + rank, shape=(n, n, n))
+    prob = synth.so3_conv_problem(seed=synth.seed_for(9) + rank, shape=(n, n, n), L=args.so3_L)
     tables, dr, R = prob["tables"], prob["dr"], prob["radius"]
     plan = ec.Plan(local)
     V = torch.from_numpy(prob["V"]).to(device)
@@ -1060,13 +1062,13 @@ def bench_so3conv(args, world, rank, local):
     avg_ms = dom_ms / dom_n
     nc = sum(2 * l * (l + 1) + 1 for l in range(len(tables)))   # unique (l, a, b)
     alg = {"so3c_cols_z_conv_tma": nc * 16 * P + 8 * P, "so3c_cols_z_conv": nc * 16 * P + 8 * P,
-           "so3c_rows_x": nc * 16 * P, "so3c_cols_y": nc * 16 * P,
+           "so3c_rows_x": nc * 16 * P, "so3c_cols_y": nc * 16 * P, "so3c_planes_yx_fwd": nc * 16 * P,
            "so3c_modulate": 20 * P + nc * 8 * P}.get(dom_name)
     peak, peak_kind = measured_peaks()
     achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
     roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                 "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": committed_traffic().get((dom_name, f"{n}^3L6")),
+                "traffic": committed_traffic().get((dom_name, f"{n}^3L{len(tables) - 1}")),
                 "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
                 "kernels": {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps}
                             for k, v in prof.items()}}

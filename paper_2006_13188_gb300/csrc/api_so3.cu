@@ -536,7 +536,8 @@ ext_status mlp_backward(ext_mlp net, int n, const float* qt, float* loss_dev, cu
 // SO(3) extended convolution (scatter) of volume V (device) with the rotation
 // field Q (device, P quaternions) into out (device):
 //   U_e = w_e V C_e(R(.))               (k_so3_modulate, every unique entry e)
-//   U^_e over x and y                   (in-place complex row / column passes)
+//   U^_e over x and y                   (in place: one fused plane pass for square
+//                                        slices, else a row and a column pass)
 //   Y = IFFT_z sum_e FFT_z(U^_e) S_e    (column pass accumulating the products)
 //   out = Re IFFT_yx Y                  (S_e carries the 1 / P of the inverse)
 // The entries go in chunks when all of them do not fit the workspace budget,
@@ -577,9 +578,16 @@ ext_status so3_conv(ext_plan plan, const float* V, int nz, int ny, int nx, const
     float2* Ydst = (float2*)(e0 == 0 ? Y : Yk);
     launch(plan, "so3c_modulate", st,
            [&] { launch_so3_modulate(V, Q, P, L, e0, ne, (float2*)U, plan->sms, st); });
-    launch(plan, "so3c_rows_x", st,
-           [&] { fft_rows_c2c(nx, (const float2*)U, nz * ny, ne, (float2*)U, false, tw_x, st); });
-    launch(plan, "so3c_cols_y", st, [&] { fft_cols_c2c(ny, (float2*)U, nx, nz * ne, false, tw_y, st); });
+    bool planes = false;
+    if (ny == nx && plan->pipelined)
+      launch(plan, "so3c_planes_yx_fwd", st, [&] {
+        planes = fft_planes_fwd_c2c(nx, (float2*)U, ne * nz, tw_x, plan->dev_err, plan->sms, st);
+      });
+    if (!planes) {
+      launch(plan, "so3c_rows_x", st,
+             [&] { fft_rows_c2c(nx, (const float2*)U, nz * ny, ne, (float2*)U, false, tw_x, st); });
+      launch(plan, "so3c_cols_y", st, [&] { fft_cols_c2c(ny, (float2*)U, nx, nz * ne, false, tw_y, st); });
+    }
     CUtensorMap tmU;
     bool done = false;
     if (br > 0 && make_tmap_2d_f32(U, (unsigned long long)2 * w2, (unsigned long long)ne * nz,

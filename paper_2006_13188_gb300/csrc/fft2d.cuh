@@ -841,6 +841,87 @@ k_planes_inv_channels(const float2* __restrict__ Z, int nz, int k0, int nk, cons
   if (pending) tc::mbar_wait_bounded(mb, phase, 1000000000ull, err, EXT_ERR_TIMEOUT);
 }
 
+// Fused forward x and y passes of the SO(3) convolution's modulated planes,
+// in place: one block per (entry, z) plane of N x N complex values at a time
+// (persistent over planes), the same structure as k_planes_inv_channels.
+// The plane comes in by N bulk copies on an mbarrier; the column (y) FFTs run
+// in groups of LINES columns in shared memory, then the row (x) FFTs store
+// their last stage straight back to the plane in global memory.  The 2D DFT
+// is separable, so transforming y before x gives the same spectrum.  Rows of
+// the block's next plane are requested as soon as a row group has been read.
+// Waits are bounded (err = EXT_ERR_TIMEOUT).
+template <int N>
+__global__ void __launch_bounds__(PlaneCfg<N>::THREADS, 1)
+k_planes_fwd_c2c(float2* __restrict__ U, int nplanes, const float2* __restrict__ tw, int* __restrict__ err) {
+  using C = LineCfg<N>;
+  using PC = PlaneCfg<N>;
+  constexpr int T = PC::THREADS;
+  constexpr int LINES = PC::LINES;
+  constexpr int LS = C::LS;
+  extern __shared__ float2 sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int abort_flag;
+  float2* PBuf = sm;
+  float2* W = sm + PC::PB;
+  const float2* TWs = stage_twiddles<N, PC::PB + PC::WB>(sm, tw, T);
+  const size_t plane = (size_t)N * N;
+  const uint32_t mb = tc::smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    tc::mbar_init(mb, 1);
+  }
+  __syncthreads();
+  auto fetch_rows = [&](int pz, int r0, int r1) {
+    const float2* src = U + (size_t)pz * plane;
+    if (r0 == 0) {
+      tc::fence_proxy_async();
+      tc::mbar_expect_tx(mb, (uint32_t)(plane * 8));
+    }
+    for (int y = r0; y < r1; ++y) tc::bulk_load(tc::smem_u32(PBuf + y * LS), src + (size_t)y * N, N * 8u, mb);
+  };
+  int pz = blockIdx.x;
+  uint32_t phase = 0;
+  bool pending = pz < nplanes;
+  if (pending && threadIdx.x == 0) fetch_rows(pz, 0, N);
+  constexpr RadixList L = factor_radices(N);
+  constexpr int R0 = L.r[0];
+  for (; pz < nplanes; pz += gridDim.x) {
+    if (!tc::mbar_wait_bounded(mb, phase, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    phase ^= 1u;
+    pending = false;
+    // y pass: groups of LINES columns, in place in shared memory
+    for (int g = 0; g < N / LINES; ++g) {
+      const int x0 = g * LINES;
+      auto load = [&](int c, int v) -> float2 { return PBuf[v * LS + x0 + c]; };
+      auto store = [&](int c, int v, float2 val) { PBuf[v * LS + x0 + c] = val; };
+      ct_stage_io<N, R0, 1, false, true, LINES, T, true, L.cnt == 1>(W, 1, LINES, TWs, load, store);
+      if constexpr (L.cnt > 1) ct_fft_io<N, false, true, LINES, T, 1, R0>(W, 1, LINES, TWs, load, store);
+      __syncthreads();
+    }
+    // x pass: groups of LINES rows, stored back to the plane
+    float2* dst = U + (size_t)pz * plane;
+    const int next = pz + gridDim.x;
+    for (int g = 0; g < N / LINES; ++g) {
+      const int y0 = g * LINES;
+      auto load = [&](int l, int x) -> float2 { return PBuf[(y0 + l) * LS + x]; };
+      auto store = [&](int l, int x, float2 val) { dst[(size_t)(y0 + l) * N + x] = val; };
+      ct_stage_io<N, R0, 1, false, false, LINES, T, true, L.cnt == 1>(W, LS, 1, TWs, load, store);
+      if constexpr (L.cnt == 1) __syncthreads();   // a single-stage transform has no barrier after its reads
+      // the first stage has read these rows: the next plane may fill them
+      if (next < nplanes) {
+        if (threadIdx.x == 0) tc::fence_proxy_async();
+        if (threadIdx.x == 0) fetch_rows(next, y0, y0 + LINES);
+        pending = true;
+      }
+      if constexpr (L.cnt > 1) ct_fft_io<N, false, false, LINES, T, 1, R0>(W, LS, 1, TWs, load, store);
+      __syncthreads();
+    }
+  }
+  if (pending) tc::mbar_wait_bounded(mb, phase, 1000000000ull, err, EXT_ERR_TIMEOUT);
+}
+
 // ------------------------------------------------- pipelined hot passes ---
 // Persistent versions of the two passes that run once per filter component
 // in the correlation path.  Each block owns one SM (grid = min(items, SMs))
@@ -1320,6 +1401,7 @@ struct FftOps {
   using C = LineCfg<N>;
   static bool cols_inv_corr_tma(const CUtensorMap& tmH, int w, int br, const float2* S, int k0, int nk, float2* Z,
                                 const float2* tw, int* err, int sms, cudaStream_t st);
+  static bool planes_fwd_c2c(float2* U, int nplanes, const float2* tw, int* err, int sms, cudaStream_t st);
   static bool planes_inv_channels(const float2* Z, int nz, int k0, int nk, const int2* chan, float* G,
                                   const float2* tw, int* err, int sms, cudaStream_t st);
   static void rows_r2c(const float* H, int h, float2* Hh, const float2* tw, cudaStream_t st);
@@ -1525,6 +1607,23 @@ bool FftOps<N>::cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, cons
 template <int N>
 __global__ void k_stage_table(const float2* __restrict__ tw, float2* __restrict__ out) {
   stage_twiddles<N, 0>(out, tw, blockDim.x);
+}
+
+template <int N>
+bool FftOps<N>::planes_fwd_c2c(float2* U, int nplanes, const float2* tw, int* err, int sms, cudaStream_t st) {
+  if constexpr (!PlaneCfg<N>::OK) {
+    return false;
+  } else {
+    static const bool once = (ext_set_smem(k_planes_fwd_c2c<N>, PlaneCfg<N>::SMEM), true);
+    (void)once;
+    int per_sm = (227 * 1024) / (PlaneCfg<N>::SMEM + 1024);
+    const int by_threads = 2048 / PlaneCfg<N>::THREADS;
+    if (per_sm > by_threads) per_sm = by_threads;
+    if (per_sm < 1) per_sm = 1;
+    const int grid = nplanes < sms * per_sm ? nplanes : sms * per_sm;
+    k_planes_fwd_c2c<N><<<grid, PlaneCfg<N>::THREADS, PlaneCfg<N>::SMEM, st>>>(U, nplanes, tw, err);
+    return true;
+  }
 }
 
 template <int N>

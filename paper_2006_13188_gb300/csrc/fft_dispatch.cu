@@ -177,6 +177,12 @@ bool fft_cols_tma_ok(int h) {
 }
 
 // fused y and x inverse passes of square N x N planes (N = ny = nx)
+#define EXT_C1(N) case N: return FftOps<N>::planes_fwd_c2c(U, nplanes, tw, err, sms, st);
+bool fft_planes_fwd_c2c(int n, float2* U, int nplanes, const float2* tw, int* err, int sms, cudaStream_t st) {
+  switch (n) { EXT_FFT_SIZES(EXT_C1) default: return false; }
+}
+#undef EXT_C1
+
 #define EXT_C1(N) case N: return FftOps<N>::planes_inv_channels(Z, nz, k0, nk, chan, G, tw, err, sms, st);
 bool fft_planes_inv_channels(int n, const float2* Z, int nz, int k0, int nk, const int2* chan, float* G,
                              const float2* tw, int* err, int sms, cudaStream_t st) {

@@ -62,6 +62,9 @@ bool fft_cols_inv_corr_tma(int h, const CUtensorMap& tmH, int w, int br, const f
 void fft_cols_c2c(int h, float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st);
 void fft_rows_inv_channels(int w, const float2* Z, int rows, int k0, int nk, const int2* chan, float* G,
                            const float2* tw, cudaStream_t st);
+// fused forward y and x passes, in place, over nplanes planes of n x n complex
+// values (false: not available for n)
+bool fft_planes_fwd_c2c(int n, float2* U, int nplanes, const float2* tw, int* err, int sms, cudaStream_t st);
 // fused inverse y and x passes over nk * nz planes of n x n (false: not available for n)
 bool fft_planes_inv_channels(int n, const float2* Z, int nz, int k0, int nk, const int2* chan, float* G,
                              const float2* tw, int* err, int sms, cudaStream_t st);
