@@ -491,6 +491,15 @@ def so3_match_problem(seed: int | None = None, size: int = 128, n_plant: int = 1
                 centres=np.array(centres), quats=quats)
 
 
+def aniso_gauss_template(sigma_u: float, sigma_v: float, radius: int):
+    """The anisotropic Gaussian exp(-x^2 / 2 sigma_u^2 - y^2 / 2 sigma_v^2)
+    sampled on the (2R+1)^2 box (x = column offset, y = row offset): the
+    oriented brush of line integral convolution, as a template image."""
+    d = np.arange(-radius, radius + 1, dtype=np.float64)
+    y, x = np.meshgrid(d, d, indexing="ij")
+    return np.exp(-x * x / (2 * sigma_u ** 2) - y * y / (2 * sigma_v ** 2))
+
+
 def so3_rotation_field(seed: int, shape, sigma: float = 4.0):
     """Smooth field of unit quaternions (w, x, y, z), float32 (*shape, 4): four
     i.i.d. N(0,1) volumes, each Gaussian-blurred (sigma voxels, periodic) and
