@@ -54,12 +54,13 @@ def parse_args():
     ap.add_argument("--train-steps", type=int, default=6000,
                     help="so3p: Adam steps of the proposal network (setup, not timed)")
     ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght", "lic", "defocus", "budget",
-                             "so3conv"],
+                             "so3conv", "similarity"],
                     help="so2: the pattern-matching sweep (default, the headline metric); "
                          "scale: scale-adaptive smoothing of a 4096x4096x3 image; "
                          "batched: 512 uneven images in one captured graph; "
                          "so3: 128^3 volume, L=6, 4608-rotation sweep; "
-                         "so3conv: SO(3) extended convolution of a 128^3 volume, L=6, smooth rotation field")
+                         "so3conv: SO(3) extended convolution of a 128^3 volume, L=6, smooth rotation field; "
+                         "similarity: smoothing of a 2048x2048x3 image under joint rotation and scale fields")
     ap.add_argument("--n-images", type=int, default=512)
     return ap.parse_args()
 
@@ -1099,6 +1100,118 @@ def bench_so3conv(args, world, rank, local):
     return 0
 
 
+# ------------------------------------------- rotation x scale smoothing ---
+SIMIL_WORKLOAD = ("smoothing under joint rotation and scale fields (rotations and isotropic scales, log-polar "
+                  "harmonics; Eq. Def-EConv, Sec. 4.1 x Sec. 8): 2048x2048x3 f32 Voronoi image (300 cells), "
+                  "low-frequency angle field, smooth scale field in [1, 3], oriented brush A(phi) B(ln r) with "
+                  "|k| <= 4 and 8 log-radial harmonics (68 unique harmonics), radii 1-16, normalised with H/s^2 "
+                  "(mode 2: 3 channels + denominator)")
+
+
+def bench_similarity(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_2006_13188_gb300 as ec
+    import synth
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    p = synth.similarity_problem(seed=synth.seed_for(10) + rank)
+    C, h, w = p["img"].shape
+    P = h * w
+    K, nj = p["c"].shape[0] - 1, p["c"].shape[1]
+    n_h = (nj + 1) // 2
+    nc = n_h + K * nj
+    plan = ec.Plan(local)
+    img = torch.from_numpy(p["img"]).to(device)
+    al = torch.from_numpy(p["alpha"]).to(device)
+    sf = torch.from_numpy(p["s"]).to(device)
+    out = torch.empty_like(img)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    fargs = (p["c"], p["log_period"], p["r_min"], p["r_max"], p["centre_tap"])
+
+    def call():
+        ec.ext_conv_similarity(plan, img, C, h, w, *fargs, al, sf, 2, out)
+    t0 = time.perf_counter()
+    call()
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    barrier(world)
+    total = 0.0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+    total = reduce_max(total, world, device)
+    if args.only_timed:
+        plan.close()
+        return 0
+    plan.profile_read()
+    plan.profile(True)
+    prof_steps = 3
+    for _ in range(prof_steps):
+        call()
+    torch.cuda.synchronize()
+    prof = {k: v for k, v in plan.profile_read().items() if v[1] > 0}
+    plan.profile(False)
+    ih = torch.from_numpy(p["img"]).pin_memory()
+    ah = torch.from_numpy(p["alpha"]).pin_memory()
+    sh = torch.from_numpy(p["s"]).pin_memory()
+    oh = torch.empty((C, h, w), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    ec.ext_conv_similarity(plan, ih, C, h, w, *fargs, ah, sh, 2, oh)
+    barrier(world)
+    t1 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ec.ext_conv_similarity(plan, ih, C, h, w, *fargs, ah, sh, 2, oh)
+    e2e_s = reduce_max(time.perf_counter() - t1, world, device)
+    dom_name, (dom_ms, dom_n) = max(prof.items(), key=lambda kv: kv[1][0])
+    avg_ms = dom_ms / dom_n
+    alg = {"cols_conv_tma": nc * 16 * P + 8 * P, "cols_conv": nc * 16 * P + 8 * P,
+           "rows_fwd_simil": 12 * P + nc * 8 * P}.get(dom_name)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
+    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": committed_traffic().get((dom_name, f"{h}x{w}simil{nc}")),
+                "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
+                "kernels": {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps}
+                            for k, v in prof.items()}}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle.similarity import SimilarityFilter, smooth
+        pix = np.random.default_rng(0).integers(0, h, (300, 2))
+        t2 = time.perf_counter()
+        smooth(p["img"], p["alpha"], p["s"], SimilarityFilter(*fargs), 2, pixels=pix)
+        t = time.perf_counter() - t2
+        cpu = {"value": len(pix) / t / 1e6, "unit": "Mpx/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 brute-force gather (3 channels and the denominator) at {len(pix)} random pixels "
+                         f"({t:.1f} s)"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "rotation x scale smoothing Mpx/s",
+            "value": world * args.steps * P / (total * 1e-3) / 1e6, "unit": "Mpx/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SIMIL_WORKLOAD, "harmonics": nc, "l2": "256 MB written between steps",
+                       "plan_ms": plan_ms},
+            "clocks": clk.summary(),
+            "e2e": {"value": world * e2e_steps * P / e2e_s / 1e6, "unit": "Mpx/s",
+                    "h2d_bytes_per_step": (4 * C + 8) * P, "d2h_bytes_per_step": 4 * C * P, "steps": e2e_steps},
+            "gpu_launches": int(sum(v[1] for v in prof.values()) // prof_steps),
+            "roofline": roofline, "cpu_baseline": cpu}))
+    plan.close()
+    return 0
+
+
 # ------------------------------------------------------------------ main ---
 def main():
     args = parse_args()
@@ -1121,6 +1234,8 @@ def main():
         return bench_so3p(args, world, rank, local)
     if args.workload == "so3conv" and args.impl == "ours":
         return bench_so3conv(args, world, rank, local)
+    if args.workload == "similarity" and args.impl == "ours":
+        return bench_similarity(args, world, rank, local)
 
     import numpy as np
     import synth

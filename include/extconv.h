@@ -254,6 +254,32 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
                           float* out, void* stream);
 
 /*
+ * Extended convolution with a joint rotation x scale field (transformation
+ * fields of rotations and isotropic scales; Eq. Def-EConv with the angular
+ * harmonics of Sec. 4.1 and the log-radial harmonics of Sec. 8).  Filter in
+ * log-polar harmonics,
+ *   F(d) = sum_{|k|<=K} sum_{|j|<n_h} c_{k,j} e^{i k theta(d)} e^{i w_j ln|d|}
+ *          for r_min <= |d| <= r_max,  F(0) = centre_tap,  else 0,
+ *   w_j = 2 pi j / log_period,  c_{-k,-j} = conj(c_{k,j})  (F real);
+ * coef (HOST): c_{k,j} for k = 0..K, j = -(n_h-1)..n_h-1 as interleaved
+ * complex doubles, row k, column j + n_h - 1 (row k = 0 is read for j >= 0
+ * only).  The similarity g(q) = (alpha(q), s(q)) multiplies harmonic (k, j)
+ * by e^{-i k alpha} e^{-i w_j ln s} on the same support (the centre tap is
+ * invariant), i.e. (T_g F)(d) is F's log-polar expansion at (theta(d) -
+ * alpha, ln|d| - ln s).  Modes as for ext_conv_scale:
+ *   mode 0: out_c = {H_c, g} * F
+ *   mode 1: out_c = {H_c, g} * F / {1, g} * F
+ *   mode 2: out_c = {H_c / s^2, g} * F / {1 / s^2, g} * F
+ * H, out: channels planes of h x w float32; alpha (radians), s (> 0): h x w
+ * float32.  Cost: one steered transform per unique harmonic, n_h + K (2 n_h
+ * - 1) of them, per signal (channels, plus the denominator in modes 1, 2);
+ * EXT_ERR_UNSUPPORTED when their spectra would exceed 8 GiB.
+ */
+ext_status ext_conv_similarity(ext_plan plan, const float* H, int channels, int h, int w, const double* coef, int K,
+                               int n_h, double log_period, double r_min, double r_max, double centre_tap,
+                               const float* alpha, const float* s, int mode, float* out, void* stream);
+
+/*
  * SO(3) extended correlation (Sec. 9).  Volume V: nz x ny x nx float32
  * (z slowest; x = column, y = row, z = slice), periodic.  Filter
  *   F(x) = sum_{l<=L} sum_{|a|<=l} f_l^a(|x|) Y_l^a(x^)

@@ -40,7 +40,7 @@ EXPORTED = (
     "ext_mlp_grads", "ext_mlp_train", "ext_so3_upper_bound", "ext_so3_refined_bound", "ext_so3_gather", "ext_so3_augment", "ext_so3_refine",
     "ext_so3_propose", "ext_corr_so3_propose", "ext_gradient_field", "ext_consensus_radius",
     "ext_consensus_filter", "ext_ght_detect", "ext_conv_so2_normalized", "ext_filter_so2_energy",
-    "ext_corr_so2_subset", "ext_conv_so3",
+    "ext_corr_so2_subset", "ext_conv_so3", "ext_conv_similarity",
 )
 
 
@@ -103,6 +103,8 @@ def lib():
         L.ext_sweep_so3.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp, i32, vp]
         L.ext_corr_so3.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, i32, vp, vp, i32, vp]
         L.ext_conv_so3.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, vp, vp]
+        L.ext_conv_similarity.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, vp, vp, i32, vp, vp]
         dbl, f32 = ctypes.c_double, ctypes.c_float
         L.ext_mlp_create.argtypes = [vp, i32, i32, ctypes.POINTER(vp)]
         L.ext_mlp_destroy.argtypes = [vp]
@@ -338,6 +340,17 @@ def ext_corr_so3(plan: Plan, V, nz, ny, nx, tables, dr, R, quats, max_out, argma
     _check(lib().ext_corr_so3(plan.handle, _ptr(V), int(nz), int(ny), int(nx), _ptr(t.view(np.float64)), L, t.shape[1],
                               float(dr), int(R), _ptr(q), q.shape[0], _ptr(max_out), _ptr(argmax), int(precision),
                               _stream(stream)))
+
+
+def ext_conv_similarity(plan: Plan, H, channels, h, w, coef, log_period, r_min, r_max, centre_tap, alpha, s, mode,
+                        out, stream=None):
+    """Extended convolution with rotation and scale fields; coef complex
+    [K + 1][2 n_h - 1] (row k, column j + n_h - 1)."""
+    c = np.ascontiguousarray(np.asarray(coef, np.complex128))
+    K, nj = c.shape
+    _check(lib().ext_conv_similarity(plan.handle, _ptr(H), int(channels), int(h), int(w), _ptr(c.view(np.float64)),
+                                     K - 1, (nj + 1) // 2, float(log_period), float(r_min), float(r_max),
+                                     float(centre_tap), _ptr(alpha), _ptr(s), int(mode), _ptr(out), _stream(stream)))
 
 
 def ext_conv_so3(plan: Plan, V, nz, ny, nx, tables, dr, R, quats, out, stream=None):

@@ -887,6 +887,107 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
   return finish_host(plan, sH.host || sS.host || sO.host, st);
 }
 
+ext_status ext_conv_similarity(ext_plan plan, const float* H, int channels, int h, int w, const double* coef, int K,
+                               int n_h, double log_period, double r_min, double r_max, double centre_tap,
+                               const float* alpha, const float* s, int mode, float* out, void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_TRY(check_size(h, w));
+  if (h == 0 || w == 0) return EXT_OK;
+  if (!H || !alpha || !s || !out || !coef) return fail(EXT_ERR_INVALID_ARG, "NULL buffer");
+  if (channels < 1 || channels > 64) return fail(EXT_ERR_INVALID_ARG, "channels must be in [1, 64]");
+  if (K < 0 || K > 64) return fail(EXT_ERR_INVALID_ARG, "K must be in [0, 64]");
+  if (n_h < 1 || n_h > 64) return fail(EXT_ERR_INVALID_ARG, "n_h must be in [1, 64]");
+  if (!(log_period > 0)) return fail(EXT_ERR_INVALID_ARG, "log_period must be > 0");
+  if (!(r_min > 0) || !(r_max >= r_min) || r_max > 1024) return fail(EXT_ERR_INVALID_ARG, "need 0 < r_min <= r_max <= 1024");
+  if (mode < 0 || mode > 2) return fail(EXT_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
+  const size_t P = (size_t)h * w;
+  // unique harmonics up to the pairing (k, j) <-> (-k, -j): (0, 0), (0, j > 0), (k > 0, any j)
+  const int nj = 2 * n_h - 1;
+  std::vector<int2> kj;
+  std::vector<double2> ck;
+  for (int k = 0; k <= K; ++k)
+    for (int j = (k == 0 ? 0 : -(n_h - 1)); j < n_h; ++j) {
+      kj.push_back(make_int2(k, j));
+      const size_t at = 2 * ((size_t)k * nj + (size_t)(j + n_h - 1));
+      ck.push_back(make_double2(coef[at], coef[at + 1]));
+    }
+  const int ncomp = (int)kj.size();
+  if (sizeof(float2) * P * ncomp > (8ull << 30))
+    return fail(EXT_ERR_UNSUPPORTED, "steered spectra of all harmonics exceed 8 GiB");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  Staged sH, sA, sS, sO;
+  EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P * channels, st, &sH));
+  EXT_TRY(stage_in(plan, "in_alpha", alpha, sizeof(float) * P, st, &sA));
+  EXT_TRY(stage_in(plan, "in_s", s, sizeof(float) * P, st, &sS));
+  EXT_TRY(stage_out_alloc(plan, "out_0", out, sizeof(float) * P * channels, &sO));
+  void *dkj = nullptr, *dck = nullptr;
+  EXT_TRY(ensure(plan, "simil_kj", sizeof(int2) * ncomp, &dkj));
+  EXT_TRY(ensure(plan, "simil_coef", sizeof(double2) * ncomp, &dck));
+  EXT_CUDA(cudaMemcpyAsync(dkj, kj.data(), sizeof(int2) * ncomp, cudaMemcpyHostToDevice, st));
+  EXT_CUDA(cudaMemcpyAsync(dck, ck.data(), sizeof(double2) * ncomp, cudaMemcpyHostToDevice, st));
+  // spectra of the harmonics, cached per filter and size
+  uint64_t key = 0x5e5e5e1a1a1a1ull;
+  key = fnv1a(key, ck.data(), sizeof(double2) * ncomp);
+  key = fnv1a(key, &K, sizeof(int));
+  key = fnv1a(key, &n_h, sizeof(int));
+  key = fnv1a(key, &log_period, sizeof(double));
+  key = fnv1a(key, &r_min, sizeof(double));
+  key = fnv1a(key, &r_max, sizeof(double));
+  const int R = (int)r_max;
+  const double two_pi = 6.283185307179586476925286766559;
+  auto sample = [&](int k0, int nk, float2* grid) {
+    launch_component_grid_simil((const double2*)dck, (const int2*)dkj, k0, nk, two_pi / log_period, r_min, r_max, R,
+                                h, w, grid, st);
+  };
+  const float2* S = nullptr;
+  EXT_TRY(spectra_generic(plan, key, h, w, ncomp, SPEC_CONV, st, sample, &S));
+  const float2 *tw_w = nullptr, *tw_h = nullptr;
+  EXT_TRY(twiddle(plan, w, st, &tw_w));
+  EXT_TRY(twiddle(plan, h, st, &tw_h));
+  void *A = nullptr, *Y = nullptr, *Nb = nullptr, *Db = nullptr;
+  EXT_TRY(ensure(plan, "Aall", sizeof(float2) * P * ncomp, &A));
+  EXT_TRY(ensure(plan, "Y", sizeof(float2) * P, &Y));
+  EXT_TRY(ensure(plan, "Nscale", sizeof(float) * P * channels, &Nb));
+  EXT_TRY(ensure(plan, "Dscale", sizeof(float) * P, &Db));
+  const float omega_step = (float)(two_pi / log_period);
+  const int unit = mode == 2 ? 1 : 0;
+  const int nsig = channels + (mode == 0 ? 0 : 1);
+  const int cw = fft_col_tile(h);
+  bool gtw = false;
+  const int br = plan->tma && fft_cols_conv_tma_ok(h, &gtw) ? tma_rows(h, cw) : 0;
+  const float2* stw = nullptr;
+  if (br > 0 && gtw) EXT_TRY(stage_table(plan, h, st, &stw));
+  CUtensorMap tmA;
+  const bool tma_A = br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w, (unsigned long long)ncomp * h,
+                                                (unsigned long long)2 * w * sizeof(float), (unsigned)(2 * cw),
+                                                (unsigned)br, &tmA);
+  for (int sig = 0; sig < nsig; ++sig) {
+    const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
+    float* dst = sig < channels ? (float*)Nb + P * sig : (float*)Db;
+    launch(plan, "rows_fwd_simil", st, [&] {
+      fft_rows_fwd_simil(w, src, (const float*)sA.dev, (const float*)sS.dev, h, (const int2*)dkj, ncomp, omega_step,
+                         unit, (float2*)A, tw_w, st);
+    });
+    bool done = false;
+    if (tma_A)
+      launch(plan, "cols_conv_tma", st, [&] {
+        done = fft_cols_conv_tma(h, tmA, w, br, ncomp - 1, S, (float2*)Y, tw_h, stw, plan->dev_err, plan->sms, st);
+      });
+    if (!done)
+      launch(plan, "cols_conv", st,
+             [&] { fft_cols_conv(h, (const float2*)A, w, ncomp - 1, S, (float2*)Y, tw_h, st); });
+    launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, dst, tw_w, st); });
+  }
+  launch(plan, "scale_finalize", st, [&] {
+    launch_scale_finalize((const float*)sH.dev, (const float*)sS.dev, (const float*)Nb, (const float*)Db, channels,
+                          (long long)P, mode, (float)centre_tap, (float*)sO.dev, plan->sms, st);
+  });
+  EXT_CUDA(cudaGetLastError());
+  EXT_TRY(stage_out_finish(sO, st));
+  return finish_host(plan, sH.host || sA.host || sS.host || sO.host, st);
+}
+
 ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, int precision, void* stream) {
   if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
   if (n < 0 || (n > 0 && !imgs)) return fail(EXT_ERR_INVALID_ARG, "bad image list");

@@ -105,6 +105,14 @@ bool fft_rows_inv_components_pipe(int w, const float2* Z, int h, int k0, int nk,
 }
 #undef EXT_C1
 
+#define EXT_C1(N) \
+  case N: FftOps<N>::rows_fwd_simil(H, alpha, s, h, kj, ncomp, omega_step, unit_integral, A, tw, st); return;
+void fft_rows_fwd_simil(int w, const float* H, const float* alpha, const float* s, int h, const int2* kj, int ncomp,
+                        float omega_step, int unit_integral, float2* A, const float2* tw, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
 #define EXT_C1(N) case N: FftOps<N>::rows_fwd_scale(H, s, h, k0, nk, omega_step, unit_integral, A, tw, st); return;
 void fft_rows_fwd_scale(int w, const float* H, const float* s, int h, int k0, int nk, float omega_step,
                         int unit_integral, float2* A, const float2* tw, cudaStream_t st) {

@@ -279,6 +279,41 @@ void launch_component_grid_mellin(double2 ck, double omega, double r_min, double
   k_component_grid_mellin<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ck, omega, r_min, r_max, R, h, w, wrap, grid);
 }
 
+// Log-polar harmonic (k, j) of a similarity filter on its support window,
+// coef e^{i (k theta + w_j ln r)}, one plane per blockIdx.y (FP64, plan time).
+__global__ void k_component_grid_simil(const double2* __restrict__ coef, const int2* __restrict__ kj, int k0,
+                                       double omega_step, double r_min, double r_max, int R, int h, int w, int wrap,
+                                       float2* __restrict__ grid) {
+  const int side = 2 * R + 1;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)side * side) return;
+  const int dy = (int)(idx / side) - R, dx = (int)(idx % side) - R;
+  const double r = hypot((double)dx, (double)dy);
+  if (r < r_min || r > r_max || r == 0.0) return;
+  const int c = k0 + (int)blockIdx.y;
+  const double2 ck = coef[c];
+  double s, co;
+  sincos((double)kj[c].x * atan2((double)dy, (double)dx) + omega_step * kj[c].y * log(r), &s, &co);
+  const double2 val = make_double2(ck.x * co - ck.y * s, ck.x * s + ck.y * co);
+  const int gy = ((dy % h) + h) % h, gx = ((dx % w) + w) % w;
+  float2* cell = grid + (size_t)blockIdx.y * h * w + (size_t)gy * w + gx;
+  if (wrap) {
+    atomicAdd(&cell->x, (float)val.x);
+    atomicAdd(&cell->y, (float)val.y);
+  } else {
+    *cell = make_float2((float)val.x, (float)val.y);
+  }
+}
+
+void launch_component_grid_simil(const double2* coef, const int2* kj, int k0, int nk, double omega_step, double r_min,
+                                 double r_max, int R, int h, int w, float2* grid, cudaStream_t st) {
+  const int side = 2 * R + 1;
+  const long long n = (long long)side * side;
+  const int wrap = (side > h || side > w) ? 1 : 0;
+  dim3 g((unsigned)((n + 255) / 256), (unsigned)nk);
+  k_component_grid_simil<<<g, 256, 0, st>>>(coef, kj, k0, omega_step, r_min, r_max, R, h, w, wrap, grid);
+}
+
 // ------------------------------------------------ smoothing epilogue ---
 // Adds the centre tap c_delta A(p) to every accumulated convolution and, for
 // modes 1 and 2, divides each channel by the denominator (Eq. normalization):

@@ -27,6 +27,9 @@ int fft_col_tile(int n);   // columns per block of the length-n column passes
 void fft_rows_r2c(int w, const float* H, int h, float2* Hh, const float2* tw, cudaStream_t st);
 void fft_rows_fwd_phase(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
                         const float2* tw, cudaStream_t st);
+// similarity-steered signals: component c < ncomp has (k, j) = kj[c]
+void fft_rows_fwd_simil(int w, const float* H, const float* alpha, const float* s, int h, const int2* kj, int ncomp,
+                        float omega_step, int unit_integral, float2* A, const float2* tw, cudaStream_t st);
 void fft_rows_fwd_scale(int w, const float* H, const float* s, int h, int k0, int nk, float omega_step,
                         int unit_integral, float2* A, const float2* tw, cudaStream_t st);
 void fft_rows_c2c(int w, const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
@@ -98,6 +101,10 @@ void launch_component_energy(int kind, int K, const double2* coef, int n_r, doub
                              double* E, cudaStream_t st);
 void launch_component_grid_mellin(double2 ck, double omega, double r_min, double r_max, int R, int h, int w,
                                   float2* grid, cudaStream_t st);
+// log-polar harmonic grids coef[c] e^{i (k theta + w_j ln r)}, (k, j) = kj[c],
+// w_j = omega_step j, for c = k0 .. k0 + nk - 1 (one h x w plane each)
+void launch_component_grid_simil(const double2* coef, const int2* kj, int k0, int nk, double omega_step, double r_min,
+                                 double r_max, int R, int h, int w, float2* grid, cudaStream_t st);
 void launch_scale_finalize(const float* H, const float* s, const float* N, const float* D, int channels, long long P,
                            int mode, float cd, float* out, int sms, cudaStream_t st);
 

@@ -21,6 +21,8 @@ from its number alone.  Workload numbering:
 8. Depth-defocus blur with a Mellin disk filter.
 9. SO(3) orientation-adaptive filtering, 128^3 volume, L = 6, smooth
    rotation field (see :func:`so3_conv_problem`).
+10. Smoothing under joint rotation and scale fields, 2048^2 x 3 (see
+    :func:`similarity_problem`).
 """
 from __future__ import annotations
 
@@ -326,6 +328,45 @@ def scale_smoothing_problem(seed: int | None = None, size: int | tuple = 4096,
     s = scale_field_from_image(img)
     c = mellin_gaussian_coeffs(n_h, log_period)
     return dict(img=img, s=s, c=c, log_period=log_period, r_min=r_min, r_max=r_max,
+                centre_tap=centre_tap)
+
+
+# ------------------------------------------------------------ workload 10 ---
+
+def similarity_brush_coeffs(K: int = 4, n_h: int = 8, kappa: float = 1.5, sigma: float = 2.0,
+                            log_period: float = 6.0, u_lo: float = -math.log(3.0), u_hi: float = math.log(16.0),
+                            ridge: float = 1e-10, n_fit: int = 4001):
+    """Filter design for smoothing under rotation and scale fields: an oriented
+    brush F(r, phi) = A(phi) B(ln r), separable in log-polar coordinates, with
+    A(phi) = exp(kappa (cos phi - 1)) (a comet-shaped stroke pointing along
+    phi = 0) band-limited to |k| <= K by its Fourier coefficients a_k (from
+    512 equispaced samples), and B(u) = exp(-e^{2u} / (2 sigma^2)) (a Gaussian
+    in r) fitted with n_h Mellin harmonics on [u_lo, u_hi].  Returns
+    c[k, j + n_h - 1] = a_k b_j, k = 0..K, |j| < n_h (complex128)."""
+    phi = 2 * math.pi * np.arange(512) / 512
+    a = np.fft.fft(np.exp(kappa * (np.cos(phi) - 1.0))) / 512
+    b = _mellin_fit(lambda u: np.exp(-np.exp(2 * u) / (2 * sigma * sigma)), n_h, log_period, u_lo, u_hi,
+                    ridge, n_fit)
+    bj = np.concatenate([np.conj(b[:0:-1]), b])        # j = -(n_h-1) .. n_h-1
+    return np.outer(a[:K + 1], bj)
+
+
+def similarity_problem(seed: int | None = None, size: int | tuple = 2048, K: int = 4, n_h: int = 8,
+                       s_min: float = 1.0, s_max: float = 3.0, log_period: float = 6.0, r_min: float = 1.0,
+                       r_max: float = 16.0, centre_tap: float = 1.0):
+    """Smoothing under joint rotation and scale fields: a 3-channel torus
+    Voronoi image (300 cells, as workload 3), the low-frequency angle field of
+    workload 1, a smooth scale field (periodic blur sigma 48 of N(0,1) noise,
+    rescaled to [s_min, s_max]) and the brush of similarity_brush_coeffs."""
+    rng = np.random.default_rng(seed_for(10) if seed is None else seed)
+    h, w = (size, size) if np.isscalar(size) else size
+    img = voronoi_image(rng, h, w, 300)
+    alpha = random_angle_field(int(rng.integers(0, 2**31 - 1)), h, w).astype(np.float32)
+    z = periodic_gaussian_blur(rng.standard_normal((h, w)), 48.0)
+    z = (z - z.min()) / max(z.max() - z.min(), 1e-12)
+    s = (s_min + (s_max - s_min) * z).astype(np.float32)
+    c = similarity_brush_coeffs(K, n_h, log_period=log_period)
+    return dict(img=img, alpha=alpha, s=s, c=c, log_period=log_period, r_min=r_min, r_max=r_max,
                 centre_tap=centre_tap)
 
 
