@@ -962,12 +962,18 @@ ext_status ext_conv_similarity(ext_plan plan, const float* H, int channels, int 
   const bool tma_A = br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w, (unsigned long long)ncomp * h,
                                                 (unsigned long long)2 * w * sizeof(float), (unsigned)(2 * cw),
                                                 (unsigned)br, &tmA);
+  void* UV = nullptr;
+  EXT_TRY(ensure(plan, "simil_uv", sizeof(float4) * P, &UV));
+  launch(plan, "simil_phasors", st, [&] {
+    launch_simil_phasors((const float*)sA.dev, (const float*)sS.dev, (long long)P, omega_step, (float4*)UV,
+                         plan->sms, st);
+  });
   for (int sig = 0; sig < nsig; ++sig) {
     const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
     float* dst = sig < channels ? (float*)Nb + P * sig : (float*)Db;
     launch(plan, "rows_fwd_simil", st, [&] {
-      fft_rows_fwd_simil(w, src, (const float*)sA.dev, (const float*)sS.dev, h, (const int2*)dkj, ncomp, omega_step,
-                         unit, (float2*)A, tw_w, st);
+      fft_rows_fwd_simil(w, src, (const float4*)UV, (const float*)sS.dev, h, (const int2*)dkj, ncomp, unit,
+                         (float2*)A, tw_w, st);
     });
     bool done = false;
     if (tma_A)

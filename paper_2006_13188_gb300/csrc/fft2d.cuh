@@ -412,18 +412,33 @@ k_rows_fwd_scale(const float* __restrict__ H, const float* __restrict__ sfield, 
 
 // Forward transform of the similarity-steered signals (rotation and scale
 // fields together, in log-polar harmonics):
-//   A_c = H wgt exp(-i (k alpha + w_j ln s)),  (k, j) = kj[blockIdx.x],
-// w_j = omega_step * j, wgt = 1/s^2 when unit_integral, else 1; H == nullptr
-// stands for the constant signal 1.  blockIdx.x = component (fastest), so H,
-// alpha and s of a row block are read from HBM once and then from L2.  (A
-// variant that carried each element's value from one component to the next
-// by one complex multiplication ran 1.8x slower at 2048 points: the carried
-// state spilled and the blocks, each walking many components, lost
-// occupancy.)
+//   A_c = H wgt exp(-i (k alpha + w_j ln s)) = H wgt u^k v^j,  (k, j) = kj[blockIdx.x],
+// with the per-pixel phasors uv = (u, v) = (e^{-i alpha}, e^{-i w_1 ln s})
+// formed once per call (k_simil_phasors) and raised to the harmonic's powers
+// by repeated squaring (|k|, |j| <= 64: at most 7 squarings each);
+// wgt = 1/s^2 when unit_integral, else 1; H == nullptr stands for the constant
+// signal 1.  blockIdx.x = component (fastest), so the row block's inputs come
+// from L2 for all harmonics.  (A variant that carried each element's value
+// from one harmonic to the next ran 1.8x slower at 2048 points: the carried
+// state spilled and its long blocks lost occupancy.)
+__device__ __forceinline__ float2 c_pow(float2 b, int e) {
+  float2 r = make_float2(1.f, 0.f);
+  if (e < 0) {
+    b.y = -b.y;
+    e = -e;
+  }
+  while (e) {
+    if (e & 1) r = c_mul(r, b);
+    b = c_mul(b, b);
+    e >>= 1;
+  }
+  return r;
+}
+
 template <int N>
 __global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
-k_rows_fwd_simil(const float* __restrict__ H, const float* __restrict__ alpha, const float* __restrict__ sfield,
-                 int h, const int2* __restrict__ kj, float omega_step, int unit_integral, float2* __restrict__ A,
+k_rows_fwd_simil(const float* __restrict__ H, const float4* __restrict__ uv, const float* __restrict__ sfield,
+                 int h, const int2* __restrict__ kj, int unit_integral, float2* __restrict__ A,
                  const float2* __restrict__ tw) {
   using C = LineCfg<N>;
   constexpr int T = C::ROW_THREADS;
@@ -431,23 +446,20 @@ k_rows_fwd_simil(const float* __restrict__ H, const float* __restrict__ alpha, c
   const float2* twl = stage_twiddles<N, C::RL * C::LS>(sm, tw, C::ROW_THREADS);
   const int y0 = blockIdx.y * C::RL;
   const int2 c = kj[blockIdx.x];
-  const float wj = omega_step * (float)c.y;
-  float hv[STAGE_G], av[STAGE_G], sv[STAGE_G];
+  float hv[STAGE_G], sv[STAGE_G];
+  float4 pv[STAGE_G];
   for_elems_staged<C::RL * N, T, STAGE_G>(
       [&](int i, int e) {
         const int y = y0 + e / N;
         const size_t idx = (size_t)y * N + e % N;
         hv[i] = (y < h) ? (H ? __ldg(H + idx) : 1.0f) : 0.f;
-        av[i] = (y < h) ? __ldg(alpha + idx) : 0.f;
-        sv[i] = (y < h) ? __ldg(sfield + idx) : 1.0f;
+        sv[i] = (y < h && unit_integral) ? __ldg(sfield + idx) : 1.0f;
+        pv[i] = (y < h) ? __ldg(uv + idx) : make_float4(1.f, 0.f, 1.f, 0.f);
       },
       [&](int i, int e) {
-        float s1, c1, s2, c2;
-        sincos_kalpha(c.x, av[i], &s1, &c1);
-        sincos_wx(wj, logf(sv[i]), &s2, &c2);
         const float a = unit_integral ? hv[i] / (sv[i] * sv[i]) : hv[i];
-        // exp(-i (k alpha + w ln s)) = conj(exp(i k alpha) exp(i w ln s))
-        sm[(e / N) * C::LS + sidx(e % N)] = make_float2(a * (c1 * c2 - s1 * s2), -a * (s1 * c2 + c1 * s2));
+        const float2 z = c_mul(c_pow(make_float2(pv[i].x, pv[i].y), c.x), c_pow(make_float2(pv[i].z, pv[i].w), c.y));
+        sm[(e / N) * C::LS + sidx(e % N)] = make_float2(a * z.x, a * z.y);
       });
   __syncthreads();
   row_fft<N, false>(sm, twl);
@@ -1457,8 +1469,8 @@ struct FftOps {
                              const float2* tw, cudaStream_t st);
   static void rows_c2c(const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
                        cudaStream_t st);
-  static void rows_fwd_simil(const float* H, const float* alpha, const float* s, int h, const int2* kj, int ncomp,
-                             float omega_step, int unit_integral, float2* A, const float2* tw, cudaStream_t st);
+  static void rows_fwd_simil(const float* H, const float4* uv, const float* s, int h, const int2* kj, int ncomp,
+                             int unit_integral, float2* A, const float2* tw, cudaStream_t st);
   static void rows_fwd_scale(const float* H, const float* s, int h, int k0, int nk, float omega_step,
                              int unit_integral, float2* A, const float2* tw, cudaStream_t st);
   static void rows_inv_components(const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
@@ -1753,12 +1765,12 @@ bool FftOps<N>::rows_inv_components_pipe(const float2* Z, int h, int k0, int nk,
 }
 
 template <int N>
-void FftOps<N>::rows_fwd_simil(const float* H, const float* alpha, const float* s, int h, const int2* kj, int ncomp,
-                               float omega_step, int unit_integral, float2* A, const float2* tw, cudaStream_t st) {
+void FftOps<N>::rows_fwd_simil(const float* H, const float4* uv, const float* s, int h, const int2* kj, int ncomp,
+                               int unit_integral, float2* A, const float2* tw, cudaStream_t st) {
   static const bool once = (ext_set_smem(k_rows_fwd_simil<N>, C::ROW_SMEM), true);
   (void)once;
   dim3 grid(ncomp, (h + C::RL - 1) / C::RL);
-  k_rows_fwd_simil<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, alpha, s, h, kj, omega_step, unit_integral, A, tw);
+  k_rows_fwd_simil<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, uv, s, h, kj, unit_integral, A, tw);
 }
 
 template <int N>

@@ -2,6 +2,8 @@
 #include "fft2d.cuh"
 #include "internal.h"
 
+#include <algorithm>
+
 #define EXT_EXTERN(N) extern template struct FftOps<N>;
 EXT_FFT_SIZES(EXT_EXTERN)
 #undef EXT_EXTERN
@@ -105,13 +107,31 @@ bool fft_rows_inv_components_pipe(int w, const float2* Z, int h, int k0, int nk,
 }
 #undef EXT_C1
 
-#define EXT_C1(N) \
-  case N: FftOps<N>::rows_fwd_simil(H, alpha, s, h, kj, ncomp, omega_step, unit_integral, A, tw, st); return;
-void fft_rows_fwd_simil(int w, const float* H, const float* alpha, const float* s, int h, const int2* kj, int ncomp,
-                        float omega_step, int unit_integral, float2* A, const float2* tw, cudaStream_t st) {
+#define EXT_C1(N) case N: FftOps<N>::rows_fwd_simil(H, uv, s, h, kj, ncomp, unit_integral, A, tw, st); return;
+void fft_rows_fwd_simil(int w, const float* H, const float4* uv, const float* s, int h, const int2* kj, int ncomp,
+                        int unit_integral, float2* A, const float2* tw, cudaStream_t st) {
   switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
 }
 #undef EXT_C1
+
+// Per-pixel phasors of the similarity field: (e^{-i alpha}, e^{-i w_1 ln s}),
+// phases by the two-product range reduction of sincos_kalpha / sincos_wx.
+__global__ void k_simil_phasors(const float* __restrict__ alpha, const float* __restrict__ sfield, long long P,
+                                float omega_step, float4* __restrict__ uv) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    float s1, c1, s2, c2;
+    sincos_kalpha(1, __ldg(alpha + p), &s1, &c1);
+    sincos_wx(omega_step, logf(__ldg(sfield + p)), &s2, &c2);
+    uv[p] = make_float4(c1, -s1, c2, -s2);
+  }
+}
+
+void launch_simil_phasors(const float* alpha, const float* s, long long P, float omega_step, float4* uv, int sms,
+                          cudaStream_t st) {
+  if (P <= 0) return;
+  const int blocks = (int)std::min<long long>((P + 255) / 256, (long long)sms * 8);
+  k_simil_phasors<<<blocks, 256, 0, st>>>(alpha, s, P, omega_step, uv);
+}
 
 #define EXT_C1(N) case N: FftOps<N>::rows_fwd_scale(H, s, h, k0, nk, omega_step, unit_integral, A, tw, st); return;
 void fft_rows_fwd_scale(int w, const float* H, const float* s, int h, int k0, int nk, float omega_step,

@@ -27,9 +27,12 @@ int fft_col_tile(int n);   // columns per block of the length-n column passes
 void fft_rows_r2c(int w, const float* H, int h, float2* Hh, const float2* tw, cudaStream_t st);
 void fft_rows_fwd_phase(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
                         const float2* tw, cudaStream_t st);
-// similarity-steered signals: component c < ncomp has (k, j) = kj[c]
-void fft_rows_fwd_simil(int w, const float* H, const float* alpha, const float* s, int h, const int2* kj, int ncomp,
-                        float omega_step, int unit_integral, float2* A, const float2* tw, cudaStream_t st);
+// similarity-steered signals: component c < ncomp has (k, j) = kj[c]; uv the
+// per-pixel phasors (e^{-i alpha}, e^{-i w_1 ln s}) of launch_simil_phasors
+void fft_rows_fwd_simil(int w, const float* H, const float4* uv, const float* s, int h, const int2* kj, int ncomp,
+                        int unit_integral, float2* A, const float2* tw, cudaStream_t st);
+void launch_simil_phasors(const float* alpha, const float* s, long long P, float omega_step, float4* uv, int sms,
+                          cudaStream_t st);
 void fft_rows_fwd_scale(int w, const float* H, const float* s, int h, int k0, int nk, float omega_step,
                         int unit_integral, float2* A, const float2* tw, cudaStream_t st);
 void fft_rows_c2c(int w, const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
