@@ -1225,12 +1225,16 @@ k_cols_inv_corr_tma(const __grid_constant__ CUtensorMap tmH, int w, int br, cons
     tc::mbar_init(mb, 1);
   }
   __syncthreads();
+  // The image spectrum is read once per component: keep it in L2 (evict_last)
+  // while the component spectra, read once, stream through (evict_first).
+  const uint64_t keep = tc::policy_evict_last(), once = tc::policy_evict_first();
   auto issue = [&](int item) {   // thread 0
     const int kk = item / ntiles, tile = item % ntiles;
     tc::fence_proxy_async();      // earlier generic-proxy reads of the staging tiles come first
     tc::mbar_expect_tx(mb, 2u * TILE * 8u);
-    tc::bulk_load(tc::smem_u32(SS), S + ((size_t)(k0 + kk) * ntiles + tile) * TILE, TILE * 8u, mb);
-    for (int y = 0; y < N; y += br) tc::tma_load_2d(tc::smem_u32(HS + y * CW), &tmH, 2 * tile * CW, y, mb);
+    tc::bulk_load_hint(tc::smem_u32(SS), S + ((size_t)(k0 + kk) * ntiles + tile) * TILE, TILE * 8u, mb, once);
+    for (int y = 0; y < N; y += br)
+      tc::tma_load_2d_hint(tc::smem_u32(HS + y * CW), &tmH, 2 * tile * CW, y, mb, keep);
   };
   uint32_t phase = 0;
   int item = blockIdx.x;
@@ -1252,7 +1256,7 @@ k_cols_inv_corr_tma(const __grid_constant__ CUtensorMap tmH, int w, int br, cons
       return c_mul(HS[e], SS[e]);
     };
     auto store = [&](int c, int v, float2 val) {
-      if (u0 + c < w) dst[(size_t)v * w + u0 + c] = val;
+      if (u0 + c < w) __stcs(dst + (size_t)v * w + u0 + c, val);   // streamed: not re-read by this kernel
     };
     constexpr RadixList L = factor_radices(N);
     constexpr int R0 = L.r[0];
