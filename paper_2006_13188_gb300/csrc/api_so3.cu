@@ -577,7 +577,7 @@ ext_status so3_conv(ext_plan plan, const float* V, int nz, int ny, int nx, const
     const int ne = std::min(chunk, ncomp - e0);
     float2* Ydst = (float2*)(e0 == 0 ? Y : Yk);
     launch(plan, "so3c_modulate", st,
-           [&] { launch_so3_modulate(V, Q, P, L, e0, ne, (float2*)U, plan->sms, st); });
+           [&] { launch_so3_modulate(V, Q, P, L, e0, ne, (float2*)U, st); });
     bool planes = false;
     if (ny == nx && plan->pipelined)
       launch(plan, "so3c_planes_yx_fwd", st, [&] {

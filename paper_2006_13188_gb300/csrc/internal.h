@@ -183,9 +183,9 @@ struct So3Steer {
   float coef[7][256];
 };
 // SO(3) extended convolution: U[i] = w V C^l_ab(R(q)) for the steering
-// entries e0 + i (i < ne), Q the per-voxel quaternions (w, x, y, z), U planes
-// of P complex values; acc += y over n complex values.
-void launch_so3_modulate(const float* V, const float* Q, long long P, int L, int e0, int ne, float2* U, int sms,
+// entries e0 + i (i < ne) of degree <= L, Q the per-voxel quaternions
+// (w, x, y, z), U planes of P complex values; acc += y over n complex values.
+void launch_so3_modulate(const float* V, const float* Q, long long P, int L, int e0, int ne, float2* U,
                          cudaStream_t st);
 void launch_add_complex(float2* acc, const float2* y, long long n, int sms, cudaStream_t st);
 void launch_so3_upper_bound(const float* G, long long P, const So3Steer* tab, float* ub, int L, int sms,

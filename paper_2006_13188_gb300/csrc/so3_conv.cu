@@ -168,11 +168,10 @@ __global__ void k_add_complex(float2* __restrict__ acc, const float2* __restrict
 
 }  // namespace
 
-void launch_so3_modulate(const float* V, const float* Q, long long P, int L, int e0, int ne, float2* U, int sms,
+void launch_so3_modulate(const float* V, const float* Q, long long P, int L, int e0, int ne, float2* U,
                          cudaStream_t st) {
   if (P <= 0 || ne <= 0) return;
   const long long blocks = (P + MOD_THREADS - 1) / MOD_THREADS;
-  (void)sms;
   const float4* q = reinterpret_cast<const float4*>(Q);
   switch (L) {
 #define EXT_MOD(LL) \
