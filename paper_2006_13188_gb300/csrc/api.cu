@@ -344,40 +344,58 @@ ext_status run_components(ext_plan plan, const float* H, int h, int w, const ext
   return EXT_OK;
 }
 
-// Extended convolution of device buffers (Sec. 2.2 Eq. Def-EConv, the algorithm
-// of Sec. 4.1): out = Re sum_k (H e^{-ik alpha}) * F_k.
-ext_status run_conv_so2(ext_plan plan, const float* H, const float* alpha, int h, int w, const ext_filter_so2* F,
-                        float* out, cudaStream_t st) {
+// Extended convolution of nsig signals by the steered-spectrum route of
+// Sec. 4.1 / Sec. 8: for each signal, rows(sig, A) writes the row transforms
+// of its ncomp steered copies into A; the column pass (tensor-copy staged
+// where the tile shape allows) sums their products with the cached spectra S
+// and inverts the columns; the inverse row pass writes the real result to
+// dst(sig).  Workspaces "Aall" and "Y".
+template <class Rows, class Dst>
+ext_status conv_signals(ext_plan plan, int h, int w, int ncomp, int nsig, const float2* S, cudaStream_t st,
+                        const char* row_name, Rows&& rows, Dst&& dst) {
   const size_t P = (size_t)h * w;
-  const int K = F->K;
-  const float2* S = nullptr;
-  EXT_TRY(spectra(plan, F, h, w, SPEC_CONV, st, &S));
   const float2 *tw_w = nullptr, *tw_h = nullptr;
   EXT_TRY(twiddle(plan, w, st, &tw_w));
   EXT_TRY(twiddle(plan, h, st, &tw_h));
   void *A = nullptr, *Y = nullptr;
-  EXT_TRY(ensure(plan, "Aall", sizeof(float2) * P * (K + 1), &A));
+  EXT_TRY(ensure(plan, "Aall", sizeof(float2) * P * ncomp, &A));
   EXT_TRY(ensure(plan, "Y", sizeof(float2) * P, &Y));
-  launch(plan, "rows_fwd_phase", st,
-         [&] { fft_rows_fwd_phase(w, H, alpha, h, 0, K + 1, (float2*)A, tw_w, st); });
-  // tensor-copy staged column pass where the tile shape allows it
   const int cw = fft_col_tile(h);
   bool gtw = false;
   const int br = plan->tma && fft_cols_conv_tma_ok(h, &gtw) ? tma_rows(h, cw) : 0;
   const float2* stw = nullptr;
   if (br > 0 && gtw) EXT_TRY(stage_table(plan, h, st, &stw));
   CUtensorMap tmA;
-  bool done = false;
-  if (br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w, (unsigned long long)(K + 1) * h,
-                                 (unsigned long long)2 * w * sizeof(float), (unsigned)(2 * cw), (unsigned)br, &tmA))
-    launch(plan, "cols_conv_tma", st, [&] {
-      done = fft_cols_conv_tma(h, tmA, w, br, K, S, (float2*)Y, tw_h, stw, plan->dev_err, plan->sms, st);
-    });
-  if (!done)
-    launch(plan, "cols_conv", st, [&] { fft_cols_conv(h, (const float2*)A, w, K, S, (float2*)Y, tw_h, st); });
-  launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, out, tw_w, st); });
+  const bool tma_A = br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w, (unsigned long long)ncomp * h,
+                                                (unsigned long long)2 * w * sizeof(float), (unsigned)(2 * cw),
+                                                (unsigned)br, &tmA);
+  for (int sig = 0; sig < nsig; ++sig) {
+    launch(plan, row_name, st, [&] { rows(sig, (float2*)A, tw_w); });
+    bool done = false;
+    if (tma_A)
+      launch(plan, "cols_conv_tma", st, [&] {
+        done = fft_cols_conv_tma(h, tmA, w, br, ncomp - 1, S, (float2*)Y, tw_h, stw, plan->dev_err, plan->sms, st);
+      });
+    if (!done)
+      launch(plan, "cols_conv", st,
+             [&] { fft_cols_conv(h, (const float2*)A, w, ncomp - 1, S, (float2*)Y, tw_h, st); });
+    launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, dst(sig), tw_w, st); });
+  }
   EXT_CUDA(cudaGetLastError());
   return EXT_OK;
+}
+
+// Extended convolution of device buffers (Sec. 2.2 Eq. Def-EConv, the algorithm
+// of Sec. 4.1): out = Re sum_k (H e^{-ik alpha}) * F_k.
+ext_status run_conv_so2(ext_plan plan, const float* H, const float* alpha, int h, int w, const ext_filter_so2* F,
+                        float* out, cudaStream_t st) {
+  const int K = F->K;
+  const float2* S = nullptr;
+  EXT_TRY(spectra(plan, F, h, w, SPEC_CONV, st, &S));
+  return conv_signals(
+      plan, h, w, K + 1, 1, S, st, "rows_fwd_phase",
+      [&](int, float2* A, const float2* tw_w) { fft_rows_fwd_phase(w, H, alpha, h, 0, K + 1, A, tw_w, st); },
+      [&](int) { return out; });
 }
 
 ext_status run_sweep(ext_plan plan, const float* G, long long P, int K, int J, float* maxv, int32_t* argmax,
@@ -841,43 +859,18 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
   };
   const float2* S = nullptr;
   EXT_TRY(spectra_generic(plan, key, h, w, n_h, SPEC_CONV, st, sample, &S));
-  const float2 *tw_w = nullptr, *tw_h = nullptr;
-  EXT_TRY(twiddle(plan, w, st, &tw_w));
-  EXT_TRY(twiddle(plan, h, st, &tw_h));
-  void *A = nullptr, *Y = nullptr, *Nb = nullptr, *Db = nullptr;
-  EXT_TRY(ensure(plan, "Aall", sizeof(float2) * P * n_h, &A));
-  EXT_TRY(ensure(plan, "Y", sizeof(float2) * P, &Y));
+  void *Nb = nullptr, *Db = nullptr;
   EXT_TRY(ensure(plan, "Nscale", sizeof(float) * P * channels, &Nb));
   EXT_TRY(ensure(plan, "Dscale", sizeof(float) * P, &Db));
   const float omega_step = (float)(two_pi / log_period);
   const int unit = mode == 2 ? 1 : 0;
-  const int nsig = channels + (mode == 0 ? 0 : 1);
-  // tensor-copy staged column pass where the tile shape allows it
-  const int cw = fft_col_tile(h);
-  bool gtw = false;
-  const int br = plan->tma && fft_cols_conv_tma_ok(h, &gtw) ? tma_rows(h, cw) : 0;
-  const float2* stw = nullptr;
-  if (br > 0 && gtw) EXT_TRY(stage_table(plan, h, st, &stw));
-  CUtensorMap tmA;
-  const bool tma_A = br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w, (unsigned long long)n_h * h,
-                                                (unsigned long long)2 * w * sizeof(float), (unsigned)(2 * cw),
-                                                (unsigned)br, &tmA);
-  for (int sig = 0; sig < nsig; ++sig) {
-    const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
-    float* dst = sig < channels ? (float*)Nb + P * sig : (float*)Db;
-    launch(plan, "rows_fwd_scale", st, [&] {
-      fft_rows_fwd_scale(w, src, (const float*)sS.dev, h, 0, n_h, omega_step, unit, (float2*)A, tw_w, st);
-    });
-    bool done = false;
-    if (tma_A)
-      launch(plan, "cols_conv_tma", st, [&] {
-        done = fft_cols_conv_tma(h, tmA, w, br, n_h - 1, S, (float2*)Y, tw_h, stw, plan->dev_err, plan->sms, st);
-      });
-    if (!done)
-      launch(plan, "cols_conv", st,
-             [&] { fft_cols_conv(h, (const float2*)A, w, n_h - 1, S, (float2*)Y, tw_h, st); });
-    launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, dst, tw_w, st); });
-  }
+  EXT_TRY(conv_signals(
+      plan, h, w, n_h, channels + (mode == 0 ? 0 : 1), S, st, "rows_fwd_scale",
+      [&](int sig, float2* A, const float2* tw_w) {
+        const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
+        fft_rows_fwd_scale(w, src, (const float*)sS.dev, h, 0, n_h, omega_step, unit, A, tw_w, st);
+      },
+      [&](int sig) { return sig < channels ? (float*)Nb + P * sig : (float*)Db; }));
   launch(plan, "scale_finalize", st, [&] {
     launch_scale_finalize((const float*)sH.dev, (const float*)sS.dev, (const float*)Nb, (const float*)Db, channels,
                           (long long)P, mode, (float)centre_tap, (float*)sO.dev, plan->sms, st);
@@ -942,49 +935,24 @@ ext_status ext_conv_similarity(ext_plan plan, const float* H, int channels, int 
   };
   const float2* S = nullptr;
   EXT_TRY(spectra_generic(plan, key, h, w, ncomp, SPEC_CONV, st, sample, &S));
-  const float2 *tw_w = nullptr, *tw_h = nullptr;
-  EXT_TRY(twiddle(plan, w, st, &tw_w));
-  EXT_TRY(twiddle(plan, h, st, &tw_h));
-  void *A = nullptr, *Y = nullptr, *Nb = nullptr, *Db = nullptr;
-  EXT_TRY(ensure(plan, "Aall", sizeof(float2) * P * ncomp, &A));
-  EXT_TRY(ensure(plan, "Y", sizeof(float2) * P, &Y));
+  void *Nb = nullptr, *Db = nullptr, *UV = nullptr;
   EXT_TRY(ensure(plan, "Nscale", sizeof(float) * P * channels, &Nb));
   EXT_TRY(ensure(plan, "Dscale", sizeof(float) * P, &Db));
+  EXT_TRY(ensure(plan, "simil_uv", sizeof(float4) * P, &UV));
   const float omega_step = (float)(two_pi / log_period);
   const int unit = mode == 2 ? 1 : 0;
-  const int nsig = channels + (mode == 0 ? 0 : 1);
-  const int cw = fft_col_tile(h);
-  bool gtw = false;
-  const int br = plan->tma && fft_cols_conv_tma_ok(h, &gtw) ? tma_rows(h, cw) : 0;
-  const float2* stw = nullptr;
-  if (br > 0 && gtw) EXT_TRY(stage_table(plan, h, st, &stw));
-  CUtensorMap tmA;
-  const bool tma_A = br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w, (unsigned long long)ncomp * h,
-                                                (unsigned long long)2 * w * sizeof(float), (unsigned)(2 * cw),
-                                                (unsigned)br, &tmA);
-  void* UV = nullptr;
-  EXT_TRY(ensure(plan, "simil_uv", sizeof(float4) * P, &UV));
   launch(plan, "simil_phasors", st, [&] {
     launch_simil_phasors((const float*)sA.dev, (const float*)sS.dev, (long long)P, omega_step, (float4*)UV,
                          plan->sms, st);
   });
-  for (int sig = 0; sig < nsig; ++sig) {
-    const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
-    float* dst = sig < channels ? (float*)Nb + P * sig : (float*)Db;
-    launch(plan, "rows_fwd_simil", st, [&] {
-      fft_rows_fwd_simil(w, src, (const float4*)UV, (const float*)sS.dev, h, (const int2*)dkj, ncomp, unit,
-                         (float2*)A, tw_w, st);
-    });
-    bool done = false;
-    if (tma_A)
-      launch(plan, "cols_conv_tma", st, [&] {
-        done = fft_cols_conv_tma(h, tmA, w, br, ncomp - 1, S, (float2*)Y, tw_h, stw, plan->dev_err, plan->sms, st);
-      });
-    if (!done)
-      launch(plan, "cols_conv", st,
-             [&] { fft_cols_conv(h, (const float2*)A, w, ncomp - 1, S, (float2*)Y, tw_h, st); });
-    launch(plan, "rows_inv_real", st, [&] { fft_rows_inv_real(w, (const float2*)Y, h, dst, tw_w, st); });
-  }
+  EXT_TRY(conv_signals(
+      plan, h, w, ncomp, channels + (mode == 0 ? 0 : 1), S, st, "rows_fwd_simil",
+      [&](int sig, float2* A, const float2* tw_w) {
+        const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
+        fft_rows_fwd_simil(w, src, (const float4*)UV, (const float*)sS.dev, h, (const int2*)dkj, ncomp, unit, A,
+                           tw_w, st);
+      },
+      [&](int sig) { return sig < channels ? (float*)Nb + P * sig : (float*)Db; }));
   launch(plan, "scale_finalize", st, [&] {
     launch_scale_finalize((const float*)sH.dev, (const float*)sS.dev, (const float*)Nb, (const float*)Db, channels,
                           (long long)P, mode, (float)centre_tap, (float*)sO.dev, plan->sms, st);
