@@ -117,3 +117,27 @@ def smooth(img, alpha, s, filt: SimilarityFilter, mode: int = 1, pixels=None):
         return np.stack(num)
     den = op(wgt)
     return np.stack([x / den for x in num])
+
+
+def conv_from_components(A, alpha, s, filt: SimilarityFilter):
+    """The same operator by its harmonic form: for every (k, j), the signal
+    modulated by e^{-ik alpha} e^{-i w_j ln s}, convolved (periodic, direct
+    sum over the window) with c_{k,j} e^{ik theta} e^{i w_j ln r}; plus the
+    centre tap times A.  Real part of the complex sum."""
+    A = np.asarray(A, np.float64)
+    alpha = np.asarray(alpha, np.float64)
+    ls = np.log(np.asarray(s, np.float64))
+    dx, dy = _offsets(filt)
+    r = np.hypot(dx, dy).astype(np.float64)
+    inside = (r >= filt.r_min) & (r <= filt.r_max) & (r > 0)
+    th = np.arctan2(dy, dx)
+    lr = np.log(np.where(r > 0, r, 1.0))
+    out = np.zeros(A.shape, np.complex128)
+    for k in range(-filt.K, filt.K + 1):
+        for j in range(-(filt.n - 1), filt.n):
+            wj = 2 * np.pi * j / filt.L
+            U = A * np.exp(-1j * (k * alpha + wj * ls))
+            g = np.where(inside, filt.coef(k, j) * np.exp(1j * (k * th + wj * lr)), 0.0)
+            for n in np.nonzero(g)[0]:
+                out += np.roll(U, (dy[n], dx[n]), axis=(0, 1)) * g[n]
+    return out.real + filt.centre_tap * A

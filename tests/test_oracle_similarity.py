@@ -140,3 +140,17 @@ def test_normalised_modes_reproduce_constants_and_sampled_form_agrees():
     full = conv(A, alpha, s, f)
     pix = np.array([(0, 0), (5, 17), (15, 3)])
     np.testing.assert_allclose(conv_at(A, alpha, s, f, pix), full[tuple(pix.T)], atol=1e-12)
+
+
+def test_harmonic_form_equals_the_brute_force():
+    """The steering identity the GPU path uses: one convolution per log-polar
+    harmonic of the signal modulated by e^{-ik alpha} e^{-i w_j ln s}."""
+    from oracle.similarity import conv_from_components
+    rng = np.random.default_rng(6)
+    K, n = 2, 3
+    c = rng.standard_normal((K + 1, 2 * n - 1)) + 1j * rng.standard_normal((K + 1, 2 * n - 1))
+    f = SimilarityFilter(c, 5.0, 0.95, 4.5, 0.6)
+    A = rng.standard_normal((12, 13))
+    alpha = rng.uniform(0, 2 * math.pi, A.shape)
+    s = rng.uniform(0.6, 2.2, A.shape)
+    np.testing.assert_allclose(conv_from_components(A, alpha, s, f), conv(A, alpha, s, f), atol=1e-10)
