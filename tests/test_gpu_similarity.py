@@ -126,3 +126,23 @@ def test_rejects_bad_arguments(ec, plan):
     for c, mode in ((p["c"], 3), (np.zeros((66, 3), np.complex128), 1), (np.zeros((2, 129), np.complex128), 1)):
         with pytest.raises(ec.ExtError):
             ec.ext_conv_similarity(plan, p["img"], 1, 32, 32, c, *args, mode, out)
+
+
+def test_window_wider_than_the_image_wraps(ec, plan):
+    """r_max = 20 on a 32 x 48 image: the harmonic grids wrap (accumulated taps)."""
+    p = random_problem(11, 32, 48, 1, 2, 3, r_min=0.95, r_max=20.0)
+    got = run(ec, plan, p, 1)
+    rng = np.random.default_rng(11)
+    pix = np.stack([rng.integers(0, 32, 30), rng.integers(0, 48, 30)], 1)
+    ref = oracle_at(p, 1, pix)
+    assert np.abs(got[0][tuple(pix.T)] - ref[0]).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_high_angular_order(ec, plan):
+    """K = 12 with 2 log-radial harmonics: the phasor powers up to u^12."""
+    p = random_problem(12, 64, 96, 1, 12, 2)
+    got = run(ec, plan, p, 0)
+    rng = np.random.default_rng(12)
+    pix = np.stack([rng.integers(0, 64, 40), rng.integers(0, 96, 40)], 1)
+    ref = oracle_at(p, 0, pix)
+    assert np.abs(got[0][tuple(pix.T)] - ref[0]).max() <= 1e-5 * np.abs(ref).max()
