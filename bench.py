@@ -53,12 +53,19 @@ def parse_args():
                     help="so3conv: filter degree (6 is the workload; lower only for profiling captures)")
     ap.add_argument("--train-steps", type=int, default=6000,
                     help="so3p: Adam steps of the proposal network (setup, not timed)")
-    ap.add_argument("--workload", default="so2", choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght", "lic", "defocus", "budget",
+    ap.add_argument("--workload", default="so2",
+                    choices=["so2", "conv", "scale", "batched", "so3", "so3p", "ght", "lic", "defocus", "budget",
                              "so3conv", "similarity"],
-                    help="so2: the pattern-matching sweep (default, the headline metric); "
-                         "scale: scale-adaptive smoothing of a 4096x4096x3 image; "
+                    help="so2: the pattern-matching sweep, 2048x2048, K=16, 64 angles (default, the headline metric); "
+                         "conv: SO(2) extended convolution of a 256x256 image, K=4; "
+                         "scale: scale-adaptive smoothing of a 4096x4096x3 image, 24 Mellin harmonics; "
+                         "defocus: depth-defocus blur of a 2048x2048x3 image, 64 Mellin harmonics; "
+                         "lic: normalised convolution (line integral convolution) of a 2048x2048 image; "
+                         "ght: pattern detection (gradient field, consensus filter, convolution), 2048x2048; "
+                         "budget: sweeps over 5 and 9 of the 17 components, chosen by energy or lowest order; "
                          "batched: 512 uneven images in one captured graph; "
                          "so3: 128^3 volume, L=6, 4608-rotation sweep; "
+                         "so3p: the same with the learned proposal; "
                          "so3conv: SO(3) extended convolution of a 128^3 volume, L=6, smooth rotation field; "
                          "similarity: smoothing of a 2048x2048x3 image under joint rotation and scale fields")
     ap.add_argument("--n-images", type=int, default=512)
