@@ -137,6 +137,54 @@ def sweep_so2_fft(H, filt, radius: int, J: int, workers: int = -1):
     return best, arg, second
 
 
+def component_correlation_fft(H, filt, k: int, radius: int, workers: int = -1):
+    """G_k of component_correlation through the FFT (Sec. 4.1 "Standard
+    Correlation" done as the paper does it; the FFT is a library step):
+    F_k sampled on the box and wrapped onto the image grid (taps of a box
+    wider than the image accumulate), G_k = IFFT(FFT(H) conj(FFT(F_k)))."""
+    import scipy.fft as sfft
+    H = np.asarray(H, np.float64)
+    h, w = H.shape
+    dx, dy = box_offsets(radius)
+    r = np.hypot(dx, dy).astype(np.float64)
+    th = np.arctan2(dy, dx).astype(np.float64)
+    fk = filt.radial(k, r) * np.exp(1j * k * th)
+    if k != 0:
+        fk = np.where(r == 0, 0.0, fk)
+    grid = np.zeros((h, w), np.complex128)
+    np.add.at(grid, (dy % h, dx % w), fk)
+    return sfft.ifft2(sfft.fft2(H, workers=workers) * np.conj(sfft.fft2(grid, workers=workers)), workers=workers)
+
+
+def sweep_so2_steered(H, filt, K: int, radius: int, J: int, workers: int = -1, chunk: int = 1 << 18):
+    """Whole-image sweep by the paper's own route (Sec. 4.1 for a real filter,
+    then max over the quantised angles of Sec. 5): the K + 1 component
+    correlations through the FFT, then at every alpha_j = 2 pi j / J the
+    linear combination S(p, j) = G_0(p) + 2 sum_{k=1..K} Re(e^{i k alpha_j}
+    G_k(p)) (a matrix product over the components, a library step), then per
+    pixel the maximum and the smallest maximising j.  Returns (best, arg)."""
+    G = [component_correlation_fft(H, filt, k, radius, workers) for k in range(K + 1)]
+    h, w = np.shape(H)
+    P = h * w
+    cols = [G[0].real.ravel()]
+    for k in range(1, K + 1):
+        cols += [G[k].real.ravel(), G[k].imag.ravel()]
+    A = np.stack(cols, axis=1)                                    # (P, 2K + 1)
+    B = np.zeros((2 * K + 1, J))
+    a = 2 * np.pi * np.arange(J) / J
+    B[0] = 1.0
+    for k in range(1, K + 1):
+        B[2 * k - 1] = 2 * np.cos(k * a)                           # 2 Re(e^{ika} G) = 2 cos Re G - 2 sin Im G
+        B[2 * k] = -2 * np.sin(k * a)
+    best = np.empty(P)
+    arg = np.empty(P, np.int64)
+    for c in range(0, P, chunk):
+        S = A[c:c + chunk] @ B
+        arg[c:c + chunk] = np.argmax(S, axis=1)
+        best[c:c + chunk] = S[np.arange(S.shape[0]), arg[c:c + chunk]]
+    return best.reshape(h, w), arg.reshape(h, w)
+
+
 def component_correlation(H, filt, k: int, radius: int):
     """Sec. 4.1 "Standard Correlation": G_k(p) = sum_{d in B} H(p + d) conj(F_k(d)),
     F_k(d) = f_k(|d|) e^{i k theta(d)} (F_k(0) = 0 for k != 0)."""

@@ -11,6 +11,34 @@ from oracle.so3 import (SHFilter, channel_layout, component_correlation_at, quat
                         refine, score_from_channels, upper_bound)
 
 
+def test_mlp_forward_literal_values():
+    """A 3 -> 2 -> 2 -> 4 network with small exact weights, worked by hand:
+    sample 1 keeps unit 1 of layer 1 and both units of layer 2 on; sample 2
+    switches off both layer-1 units and unit 1 of layer 2, so the output is
+    biases alone through W3.
+      x1 = (2, 1, -2):  z1 = (0.5, -1),  h1 = (0.5, 0),  z2 = (0.5, 0.5),
+                        o = (0.5, 1, 1, -0.5),  |o|^2 = 2.5
+      x2 = (-2, 0, 1):  z1 = (-1, -6),   h1 = (0, 0),    z2 = (-0.5, 1),
+                        o = (0, 2, 2, -3),      |o|^2 = 17
+    Loss against q*1 = (1, 0, 0, 0), q*2 = (0, 0, 0, 1): 1 - 0.25/2.5 = 0.9
+    and 1 - 9/17 = 8/17, mean (0.9 + 8/17) / 2."""
+    p = dict(W1=np.array([[1.0, -1.0, 0.5], [0.0, 2.0, -1.0]]), b1=np.array([0.5, -5.0]),
+             W2=np.array([[2.0, 1.0], [-1.0, 3.0]]), b2=np.array([-0.5, 1.0]),
+             W3=np.array([[1.0, 0.0], [0.0, 2.0], [-1.0, 1.0], [3.0, -2.0]]), b3=np.array([0.0, 0.0, 1.0, -1.0]))
+    X = np.array([[2.0, 1.0, -2.0], [-2.0, 0.0, 1.0]])
+    c = mlp.forward(p, X)
+    np.testing.assert_array_equal(c["z1"], [[0.5, -1.0], [-1.0, -6.0]])
+    np.testing.assert_array_equal(c["h1"], [[0.5, 0.0], [0.0, 0.0]])
+    np.testing.assert_array_equal(c["z2"], [[0.5, 0.5], [-0.5, 1.0]])
+    np.testing.assert_array_equal(c["h2"], [[0.5, 0.5], [0.0, 1.0]])
+    np.testing.assert_array_equal(c["o"], [[0.5, 1.0, 1.0, -0.5], [0.0, 2.0, 2.0, -3.0]])
+    q = mlp.quaternion(c["o"])
+    np.testing.assert_allclose(q[0], np.array([0.5, 1.0, 1.0, -0.5]) / np.sqrt(2.5), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(q[1], np.array([0.0, 2.0, 2.0, -3.0]) / np.sqrt(17.0), rtol=0, atol=1e-15)
+    qt = np.array([[1.0, 0, 0, 0], [0, 0, 0, 1.0]])
+    assert abs(mlp.loss(c["o"], qt) - (0.9 + 8.0 / 17.0) / 2) < 1e-15
+
+
 def test_mlp_gradients_match_finite_differences():
     rng = np.random.default_rng(0)
     p = mlp.init_params(rng, 12, hidden=9)

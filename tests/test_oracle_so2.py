@@ -354,6 +354,34 @@ def test_fft_sweep_route_matches_bruteforce_on_sampled_template():
     np.testing.assert_allclose(best[pix[:, 0], pix[:, 1]], S.max(axis=1), atol=1e-12)
 
 
+def test_fft_components_match_bruteforce_components():
+    """component_correlation_fft (FFT route) equals the brute-force sum over
+    the box, also with a box wider than the image (wrapped taps)."""
+    from oracle.so2 import component_correlation, component_correlation_fft
+    H, filt, a, _ = small_problem(seed=33, h=12, w=14, K=3)
+    for R in (3, 9):
+        for k in range(4):
+            np.testing.assert_allclose(component_correlation_fft(H, filt, k, R), component_correlation(H, filt, k, R),
+                                       atol=1e-11)
+
+
+def test_steered_sweep_route_matches_bruteforce_and_fft_routes():
+    """sweep_so2_steered (components by FFT, linear combination at every
+    angle, max) agrees with the per-pixel brute force with rotated filters and
+    with the per-rotated-filter FFT route, maxima and first argmax."""
+    from oracle.so2 import sweep_so2_steered
+    prob = synth.so2_match_problem(seed=834, size=96, n_plant=2, radius=12, K=6, J=24)
+    tab = decompose_sampled(prob["template"], 6, prob["dr"], prob["n_theta"])
+    best, arg = sweep_so2_steered(prob["H"], tab, 6, prob["radius"], 24, chunk=1000)
+    b2, a2, second = sweep_so2_fft(prob["H"], tab, prob["radius"], 24)
+    np.testing.assert_allclose(best, b2, atol=1e-12 * np.abs(b2).max())
+    clear = (b2 - second) > 1e-9 * np.abs(b2).max()
+    assert np.array_equal(arg[clear], a2[clear])
+    pix = np.array([[y, x] for y in range(0, 96, 7) for x in range(0, 96, 5)])
+    S = sweep_so2_at(prob["H"], tab, prob["radius"], 24, pix).real
+    np.testing.assert_allclose(best[pix[:, 0], pix[:, 1]], S.max(axis=1), atol=1e-12 * np.abs(S).max())
+
+
 def test_boundary_taps_are_rotation_invariant():
     """A lattice offset on the support circle |d| = (n-1) dr keeps its value
     under rotation, whatever the rounding of the rotated coordinate."""

@@ -49,3 +49,35 @@ def test_brush_matches_its_design_within_the_fit():
                 q += ckj * np.exp(1j * (k * PH + 2 * math.pi * j / 6.0 * u))
         ref = np.exp(1.5 * (np.cos(PH) - 1)) * np.exp(-(R / s) ** 2 / 8.0)
         assert np.abs(q.real - ref).max() < 1e-2
+
+
+def test_rotation_grid_covering_radius():
+    """Covering radius of the 4608-rotation grid (192 Fibonacci directions x 24
+    in-plane angles): the largest angle from any rotation to its nearest grid
+    rotation, estimated from below by Haar samples refined by local ascent of
+    that distance.  Measured 12.64 degrees; the in-plane spacing alone forces
+    at least 7.5 degrees.  Planted rotations are recovered within this radius
+    plus the score's own resolution."""
+    g = synth.so3_rotation_grid()
+    rng = np.random.default_rng(1)
+
+    def nearest_deg(q):
+        return 2 * np.degrees(np.arccos(np.minimum(1.0, np.abs(q @ g.T).max(axis=1))))
+
+    q = rng.standard_normal((20000, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    a = np.concatenate([nearest_deg(q[i:i + 5000]) for i in range(0, len(q), 5000)])
+    top = q[np.argsort(a)[-50:]]
+    cur = nearest_deg(top)
+    step = 0.02
+    for it in range(200):
+        cand = top + step * rng.standard_normal(top.shape)
+        cand /= np.linalg.norm(cand, axis=1, keepdims=True)
+        c = nearest_deg(cand)
+        upd = c > cur
+        top[upd], cur[upd] = cand[upd], c[upd]
+        if it % 50 == 49:
+            step *= 0.5
+    radius = float(cur.max())
+    print(f"rotation grid covering radius >= {radius:.2f} degrees")
+    assert 12.0 <= radius <= 13.0
