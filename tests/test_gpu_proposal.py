@@ -91,26 +91,52 @@ def test_mlp_forward_matches_oracle(ec, plan):
         np.testing.assert_array_equal(back[k], p[k])
 
 
+def _relu_decisions_agree(p, Xu):
+    """Rows whose every ReLU decision is the same in the FP64 oracle and in
+    the GPU's arithmetic.  The GPU stores the hidden activations in BF16, so
+    its second-layer pre-activations are W2 bf16(h1) + b2 instead of the
+    oracle's W2 h1 + b2; where the two differ in sign (or either lies within
+    the FP32 accumulation error of zero) the ReLU derivative is a different
+    integer decision on the two sides and the row is left out.  The first
+    layer sees identical BF16 operands on both sides; only the accumulation
+    error window applies there."""
+    po = oracle_params(p)
+    z1 = Xu @ po["W1"].T + po["b1"]
+    w1 = np.abs(Xu) @ np.abs(po["W1"]).T
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ po["W2"].T + po["b2"]
+    z2g = bf16(h1) @ po["W2"].T + po["b2"]
+    w2 = bf16(h1) @ np.abs(po["W2"]).T
+    ok1 = np.abs(z1) > 1e-5 * w1
+    ok2 = (np.sign(z2) == np.sign(z2g)) & (np.abs(z2g) > 1e-5 * w2) & (np.abs(z2) > 1e-5 * w2)
+    return np.all(ok1, axis=1) & np.all(ok2, axis=1)
+
+
 @pytest.mark.parametrize("case", ["all_active", "he_init"])
 def test_mlp_gradients_match_oracle(ec, plan, case):
-    """all_active: biases that keep every ReLU unit on (no derivative can
-    switch), the BF16 bar rel-L2 <= 1e-2.  he_init: zero biases, half the
-    units off; a unit whose pre-activation lies within the BF16 rounding of
-    the activations from zero switches its ReLU derivative, adding a
-    full-size entry to the difference (about 20 of 51,200 here; measured
-    rel-L2 2.4e-2, reproduced by a NumPy model of the BF16 arithmetic), so
-    the bar there is rel-L2 <= 5e-2 with cosine >= 0.999."""
+    """all_active: biases that keep every ReLU unit on.  he_init: zero biases,
+    half the units off; rows where a ReLU decision differs between the FP64
+    oracle and the GPU's BF16 activations (a unit whose pre-activation lies
+    within the activations' BF16 rounding of zero) are left out, so that both
+    sides take the same decisions.  Bar for both: rel-L2 <= 1e-2 per tensor,
+    cosine >= 0.999."""
     rng = np.random.default_rng(21)
     n, H = 200, 256
     p = synth.mlp_init(8, NCH, H)
     if case == "all_active":
         p["b1"] = np.full(H, 1.0, np.float32)
         p["b2"] = np.full(H, 10.0, np.float32)
-    rel_bar = 1e-2 if case == "all_active" else 5e-2
-    net = ec.MLP(plan, NCH, H)
-    net.set_params(p)
     X = rng.standard_normal((n, NCH)).astype(np.float32)
     qt = haar(rng, n).astype(np.float32)
+    keep = _relu_decisions_agree(p, bf16(unit_rows(X)))
+    print(f"{case}: {int(keep.sum())} of {n} rows with every ReLU decision the same on both sides")
+    if case == "all_active":
+        assert keep.all()
+    assert keep.sum() >= n // 2
+    X, qt = X[keep], qt[keep]
+    n = len(X)
+    net = ec.MLP(plan, NCH, H)
+    net.set_params(p)
     grads = torch.empty(net.n_params(), dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     ec.ext_mlp_grads(net, dev(X), dev(qt), n, loss, grads)
@@ -129,7 +155,7 @@ def test_mlp_gradients_match_oracle(ec, plan, case):
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         cos = float(np.dot(got, ref) / (np.linalg.norm(got) * np.linalg.norm(ref)))
         print(f"grad {k}: rel-L2 {rel:.2e} cosine {cos:.6f}")
-        assert rel <= rel_bar and cos >= 0.999, k
+        assert rel <= 1e-2 and cos >= 0.999, k
     assert off == g.size
 
 

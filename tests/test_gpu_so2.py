@@ -235,6 +235,57 @@ def test_sweep_full_size_2048_sampled_pixels(ec, plan):
             assert abs(iy - 2) <= 1 and abs(ix - 2) <= 1
 
 
+@pytest.fixture(scope="module")
+def oracle_2048():
+    """The 2048 x 2048, K = 16, 64-angle workload and the oracle's scores over
+    the WHOLE image: one FP64 FFT correlation per rotated filter (the
+    quantised-rotation form of Sec. 5, F evaluated at R(-alpha_j) d from its
+    closed-form expansion), keeping per pixel the best score, its first
+    index and the second-best score."""
+    prob = synth.so2_match_problem()
+    tab = decompose_sampled(prob["template"], prob["K"], prob["dr"], prob["n_theta"])
+    best, arg, second = sweep_so2_fft(prob["H"], tab, prob["radius"], prob["J"])
+    return prob, tab, best, arg, second
+
+
+@pytest.mark.parametrize("precision", ["EXT_PREC_FP32", "EXT_PREC_BF16X3"])
+def test_sweep_full_image_2048_against_fft_oracle(ec, plan, oracle_2048, precision):
+    """Every pixel of the benchmarked call against the FP64 oracle.  FP32:
+    maxima within 1e-5 of the score scale and argmax identical wherever the
+    oracle's best two scores are more than 1e-6 of the scale apart (the tie
+    window).  Split BF16: maxima within 1e-4, argmax identical outside a
+    2e-4 window and on at least 99% of all pixels.  Flips are reported with
+    the oracle's margin between its best score and the score of the angle the
+    GPU chose."""
+    prob, tab, best, arg, second = oracle_2048
+    prec = getattr(ec, precision)
+    K, J, R = prob["K"], prob["J"], prob["radius"]
+    F = ec.FilterSO2.sampled(prob["template"], K, prob["dr"], prob["n_theta"])
+    mx = torch.empty((2048, 2048), dtype=torch.float32, device="cuda")
+    am = torch.empty((2048, 2048), dtype=torch.int32, device="cuda")
+    ec.ext_corr_so2(plan, dev(prob["H"]), 2048, 2048, F, None, J, mx, am, prec)
+    plan.sync()
+    mxn, amn = mx.cpu().numpy().astype(np.float64), am.cpu().numpy()
+    scale = float(np.abs(best).max())
+    tol, window = (1e-5, TIE) if prec == ec.EXT_PREC_FP32 else (BF_TOL, 2 * BF_TOL)
+    err = float(np.max(np.abs(mxn - best))) / scale
+    flips = amn != arg
+    clear = (best - second) > window * scale
+    outside = flips & clear
+    idx = np.argwhere(flips)
+    margins = np.zeros(0)
+    if len(idx):
+        sub = idx[:2000]
+        S = sweep_so2_at(prob["H"], tab, R, J, sub).real
+        margins = (S.max(axis=1) - S[np.arange(len(sub)), amn[sub[:, 0], sub[:, 1]]]) / scale
+    print(f"2048^2 {precision} whole image: max score error {err:.2e} of scale, {int(flips.sum())} argmax flips "
+          f"({int((~clear).sum())} pixels inside the {window:.0e} window, {int(outside.sum())} flips outside it), "
+          f"largest margin of a flip {margins.max() if margins.size else 0.0:.2e} of scale")
+    assert err <= tol
+    assert int(outside.sum()) == 0
+    assert 1.0 - flips.mean() >= 0.99
+
+
 # -------------------------------------------------------------- edge cases ---
 
 def test_edge_cases(ec, plan):
