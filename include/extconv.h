@@ -55,6 +55,7 @@ typedef int ext_status;
 #define EXT_ERR_CUDA 3
 #define EXT_ERR_OOM 4
 #define EXT_ERR_TIMEOUT 5
+#define EXT_ERR_CHECKPOINT 6   /* a checkpoint file is missing, truncated, corrupt or of other shapes */
 
 /* Filter kinds (ext_filter_so2.kind). */
 #define EXT_FILTER_ANALYTIC_GAUSSPOW 0 /* f_k(r) = a_k r^|k| exp(-r^2 / (2 sigma^2))                */
@@ -64,6 +65,7 @@ typedef int ext_status;
 /* Sweep precision (ext_corr_so2 / ext_sweep_so2). */
 #define EXT_PREC_FP32 0   /* plain FP32 on CUDA cores                                              */
 #define EXT_PREC_BF16X3 1 /* split BF16 hi+lo operands on tcgen05 tensor cores, FP32 accumulation */
+#define EXT_PREC_DEFAULT (-1) /* the plan's default precision (ext_options.precision)                */
 
 /*
  * SO(2) filter with angular bandwidth K (|k| <= K) on the box [-R, R]^2:
@@ -101,10 +103,51 @@ const char* ext_status_string(ext_status s);
 /* Thread-local message describing the last error returned on this thread. */
 const char* ext_last_error(void);
 
+/*
+ * Plan options (no counterpart in the paper: run-time policy of the library).
+ *   device          CUDA device ordinal the plan works on.
+ *   precision       EXT_PREC_FP32 or EXT_PREC_BF16X3: the sweep precision used
+ *                   wherever a call passes EXT_PREC_DEFAULT.
+ *   wait_budget_ns  limit of every bounded device-side wait (a kernel waiting
+ *                   for its own bulk copies or tensor-core work); on expiry the
+ *                   kernel records EXT_ERR_TIMEOUT in the plan's status word,
+ *                   waits (bounded) for its own work in flight, frees its
+ *                   tensor memory and returns.  0 = 1 second.
+ *   autotune        EXT_TUNE_ON: the first ext_corr_so2 / ext_batch_corr_so2
+ *                   call of a shape class times the pass variants the library
+ *                   has for it (tensor-copy staged or not, persistent
+ *                   prefetching or not, components per inverse launch) and keeps
+ *                   the fastest; EXT_TUNE_OFF (default): the built-in choice.
+ *   tune_cache      path of the autotuner's cache (text, one line per shape
+ *                   class, keyed by GPU name and driver version), read at plan
+ *                   creation and rewritten when a new class is tuned; NULL:
+ *                   in memory only.  The string is copied.
+ *   fault_inject    EXT_FAULT_ALLOC: after `fault_after` successful device
+ *                   allocations of the plan, the next one fails as if the
+ *                   device were out of memory (EXT_ERR_OOM; once).  For tests
+ *                   of the error paths; EXT_FAULT_NONE (default) in use.
+ * ext_options_init fills the defaults (device 0).  ext_plan_create with
+ * options == NULL uses them.
+ */
+#define EXT_TUNE_OFF 0
+#define EXT_TUNE_ON 1
+#define EXT_FAULT_NONE 0
+#define EXT_FAULT_ALLOC 1
+typedef struct {
+  int device;
+  int precision;
+  uint64_t wait_budget_ns;
+  int autotune;
+  const char* tune_cache;
+  int fault_inject;
+  int fault_after;
+} ext_options;
+void ext_options_init(ext_options* options);
+
 /* Plan: caches twiddle tables, filter spectra (per filter, size and mode),
- * sweep tables and workspace on `device`.  Not thread-safe: one plan per
- * host thread.  ext_plan_destroy frees everything the plan allocated. */
-ext_status ext_plan_create(ext_plan* plan, int device);
+ * sweep tables and workspace on options->device.  Not thread-safe: one plan
+ * per host thread.  ext_plan_destroy frees everything the plan allocated. */
+ext_status ext_plan_create(ext_plan* plan, const ext_options* options);
 ext_status ext_plan_destroy(ext_plan plan);
 /* Frees cached filter spectra and workspace (kept otherwise for reuse). */
 ext_status ext_plan_trim(ext_plan plan);
@@ -115,6 +158,16 @@ ext_status ext_plan_trim(ext_plan plan);
  * affected outputs are invalid).  Calls with host buffers do this check
  * themselves before returning. */
 ext_status ext_plan_sync(ext_plan plan, void* stream);
+
+/*
+ * Self-test of the failure path above (no counterpart in the paper).  Launches
+ * on `stream` one kernel that waits on a shared-memory mbarrier which nothing
+ * will ever complete (no copy, no tensor-core work and no other thread is in
+ * flight), bounded by the plan's wait budget; when the budget runs out the
+ * kernel records EXT_ERR_TIMEOUT and returns, so the next ext_plan_sync
+ * returns EXT_ERR_TIMEOUT (and clears it) and the plan stays usable.
+ */
+ext_status ext_plan_selftest_timeout(ext_plan plan, void* stream);
 
 /* Per-kernel accounting for benchmarks and tracing (no counterpart in the
  * paper).  Every kernel launch of the plan is counted per kernel name; with
@@ -193,6 +246,13 @@ ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_f
  * cost is that of ext_corr_so2 with K = nks - 1.
  */
 ext_status ext_filter_so2_energy(ext_plan plan, const ext_filter_so2* F, double* energy_out);
+/* The selection rule (host only, no device work): from the energies E_k,
+ * k = 0..K (energy, HOST, K+1 doubles) and a budget of standard correlations,
+ * writes ks_out[0] = 0 (G_0 always kept), then the budget - 1 components
+ * k >= 1 of largest energy (ties to the smaller k) in ascending order, and
+ * their count min(budget, K + 1) to *n_out.  ks_out must hold K + 1 ints.
+ * EXT_ERR_INVALID_ARG for K < 0, budget < 1 or a NaN energy. */
+ext_status ext_select_components(const double* energy, int K, int budget, int* ks_out, int* n_out);
 ext_status ext_corr_so2_subset(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, const int* ks,
                                int nks, int n_angles, float* max_out, int32_t* argmax, int precision, void* stream);
 
@@ -377,6 +437,29 @@ ext_status ext_mlp_destroy(ext_mlp net);
 ext_status ext_mlp_set_params(ext_mlp net, const float* W1, const float* b1, const float* W2, const float* b2,
                               const float* W3, const float* b3);
 ext_status ext_mlp_get_params(ext_mlp net, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3);
+/*
+ * Checkpoint of the network's whole training state, so that training resumes
+ * where it stopped: FP32 master weights, both Adam moments and the step count.
+ * File layout (little endian):
+ *   bytes 0..7    magic "EXTMLP01"
+ *   8..11         uint32 version (1)
+ *   12..15        uint32 n_in;   16..19 uint32 hidden;   20..23 uint32 zero
+ *   24..31        uint64 Adam steps taken
+ *   32..39        uint64 n = hidden (n_in + hidden + 6) + 4, floats per block
+ *   40..          float32 weights [n], first moments [n], second moments [n],
+ *                 each block W1, b1, W2, b2, W3, b3 in the shapes of
+ *                 ext_mlp_set_params
+ *   last 4 bytes  uint32 CRC-32 (IEEE 802.3: reflected polynomial 0xEDB88320,
+ *                 initial value and final xor 0xFFFFFFFF) of all bytes before it
+ * ext_mlp_save writes it (after waiting for the device); ext_mlp_load checks
+ * magic, version, length, CRC and that n_in and hidden equal the network's,
+ * and only then replaces the state: EXT_ERR_CHECKPOINT (state unchanged) on
+ * any mismatch or unreadable file.  ext_mlp_checkpoint_info checks a file the
+ * same way on the host alone (no device work) and returns its shapes and step.
+ */
+ext_status ext_mlp_save(ext_mlp net, const char* path);
+ext_status ext_mlp_load(ext_mlp net, const char* path);
+ext_status ext_mlp_checkpoint_info(const char* path, int* n_in, int* hidden, int64_t* step);
 /* q [n][4] = the network's unit quaternion of each row of X [n][n_in]. */
 ext_status ext_mlp_forward(ext_mlp net, const float* X, int n, float* q, void* stream);
 /* Mean loss of rows X [n][n_in] against targets qt [n][4] into *loss (host or
@@ -482,11 +565,16 @@ ext_status ext_ght_detect(ext_plan plan, const float* I, int h, int w, const ext
  * device array inside the library (every GPU that loads the library keeps it
  * until the process exits).  Limits: 1 <= K <= 16, 1 <= n_angles <= 128;
  * larger sizes return EXT_ERR_UNSUPPORTED.  G, max_out and argmax must be
- * DEVICE buffers (EXT_ERR_INVALID_ARG otherwise).  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
- * the one table and each call rewrites it in full on `stream`: calls that
- * overlap on the GPU (different streams, or different threads) race on it.
+ * DEVICE buffers of the current device (EXT_ERR_INVALID_ARG otherwise).  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process; make that first call before any stream capture.  A reset of
+ * the device's primary context (cudaDeviceReset) while the library is loaded
+ * is not supported by this entry point.  If a CUDA error from earlier work is
+ * already pending on the calling thread, the call launches nothing, returns
+ * EXT_ERR_CUDA and leaves that error in place.  All calls share the one table
+ * and each call rewrites it in full on `stream`: calls that overlap on the GPU
+ * (different streams, or different threads) race on it.
  */
 ext_status ext_sweep_so2_noalloc(const float* G, int64_t n_pix, int K, int n_angles, float* max_out,
                                  int32_t* argmax, void* stream);

@@ -12,4 +12,6 @@ from ._binding import (  # noqa: F401
     MLP, ext_mlp_forward, ext_mlp_grads, ext_mlp_train, ext_so3_upper_bound, ext_so3_refined_bound, ext_so3_gather, ext_so3_augment,
     ext_so3_refine, ext_so3_propose, ext_corr_so3_propose, ext_gradient_field, ext_consensus_radius,
     ext_consensus_filter, ext_ght_detect, ext_conv_so2_normalized, ext_filter_so2_energy, ext_corr_so2_subset,
+    EXT_PREC_DEFAULT, EXT_FAULT_ALLOC, EXT_FAULT_NONE, EXT_TUNE_OFF, EXT_TUNE_ON, ext_mlp_checkpoint_info,
+    ext_select_components,
 )

@@ -22,6 +22,7 @@ EXT_ERR_UNSUPPORTED = 2
 EXT_ERR_CUDA = 3
 EXT_ERR_OOM = 4
 EXT_ERR_TIMEOUT = 5
+EXT_ERR_CHECKPOINT = 6
 
 EXT_FILTER_ANALYTIC_GAUSSPOW = 0
 EXT_FILTER_TABLE = 1
@@ -29,6 +30,12 @@ EXT_FILTER_SAMPLED = 2
 
 EXT_PREC_FP32 = 0
 EXT_PREC_BF16X3 = 1
+EXT_PREC_DEFAULT = -1
+
+EXT_TUNE_OFF = 0
+EXT_TUNE_ON = 1
+EXT_FAULT_NONE = 0
+EXT_FAULT_ALLOC = 1
 
 EXPORTED = (
     "ext_status_string", "ext_last_error", "ext_plan_create", "ext_plan_destroy", "ext_plan_trim",
@@ -40,7 +47,8 @@ EXPORTED = (
     "ext_mlp_grads", "ext_mlp_train", "ext_so3_upper_bound", "ext_so3_refined_bound", "ext_so3_gather", "ext_so3_augment", "ext_so3_refine",
     "ext_so3_propose", "ext_corr_so3_propose", "ext_gradient_field", "ext_consensus_radius",
     "ext_consensus_filter", "ext_ght_detect", "ext_conv_so2_normalized", "ext_filter_so2_energy",
-    "ext_corr_so2_subset", "ext_conv_so3", "ext_conv_similarity",
+    "ext_corr_so2_subset", "ext_conv_so3", "ext_conv_similarity", "ext_options_init", "ext_plan_selftest_timeout",
+    "ext_select_components", "ext_mlp_save", "ext_mlp_load", "ext_mlp_checkpoint_info",
 )
 
 
@@ -52,6 +60,14 @@ class ExtError(RuntimeError):
 
 class ext_image_desc(ctypes.Structure):
     pass
+
+
+class ext_options(ctypes.Structure):
+    _fields_ = [
+        ("device", ctypes.c_int), ("precision", ctypes.c_int), ("wait_budget_ns", ctypes.c_uint64),
+        ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("fault_inject", ctypes.c_int),
+        ("fault_after", ctypes.c_int),
+    ]
 
 
 class ext_filter_so2(ctypes.Structure):
@@ -84,7 +100,15 @@ def lib():
         L.ext_status_string.argtypes = [i32]
         L.ext_last_error.restype = ctypes.c_char_p
         L.ext_last_error.argtypes = []
-        L.ext_plan_create.argtypes = [ctypes.POINTER(vp), i32]
+        L.ext_options_init.argtypes = [ctypes.POINTER(ext_options)]
+        L.ext_options_init.restype = None
+        L.ext_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ext_options)]
+        L.ext_plan_selftest_timeout.argtypes = [vp, vp]
+        L.ext_select_components.argtypes = [vp, i32, i32, vp, ctypes.POINTER(i32)]
+        L.ext_mlp_save.argtypes = [vp, ctypes.c_char_p]
+        L.ext_mlp_load.argtypes = [vp, ctypes.c_char_p]
+        L.ext_mlp_checkpoint_info.argtypes = [ctypes.c_char_p, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                              ctypes.POINTER(i64)]
         L.ext_plan_destroy.argtypes = [vp]
         L.ext_plan_trim.argtypes = [vp]
         L.ext_plan_profile.argtypes = [vp, i32]
@@ -130,7 +154,8 @@ def lib():
         L.ext_filter_so2_energy.argtypes = [vp, fp, vp]
         L.ext_corr_so2_subset.argtypes = [vp, vp, i32, i32, fp, vp, i32, i32, vp, vp, i32, vp]
         for name in EXPORTED:
-            if name not in ("ext_status_string", "ext_last_error", "ext_so3_channels", "ext_consensus_radius"):
+            if name not in ("ext_status_string", "ext_last_error", "ext_so3_channels", "ext_consensus_radius",
+                            "ext_options_init"):
                 getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -204,11 +229,33 @@ class FilterSO2:
 
 
 class Plan:
-    def __init__(self, device: int = 0):
+    """A plan (ext_plan) on `device`; the keyword options map to ext_options:
+    precision (default sweep precision), wait_budget_ns, autotune (bool),
+    tune_cache (path), fault_inject / fault_after (host-side injection of an
+    allocation failure, for tests)."""
+
+    def __init__(self, device: int = 0, precision=None, wait_budget_ns=None, autotune=False, tune_cache=None,
+                 fault_inject=None, fault_after=0):
         import weakref
         self.handle = ctypes.c_void_p()
         self._nets = weakref.WeakSet()
-        _check(lib().ext_plan_create(ctypes.byref(self.handle), int(device)))
+        opts = ext_options()
+        lib().ext_options_init(ctypes.byref(opts))
+        opts.device = int(device)
+        if precision is not None:
+            opts.precision = int(precision)
+        if wait_budget_ns is not None:
+            opts.wait_budget_ns = int(wait_budget_ns)
+        opts.autotune = EXT_TUNE_ON if autotune else EXT_TUNE_OFF
+        self._tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
+        opts.tune_cache = self._tune_cache
+        if fault_inject is not None:
+            opts.fault_inject = int(fault_inject)
+            opts.fault_after = int(fault_after)
+        _check(lib().ext_plan_create(ctypes.byref(self.handle), ctypes.byref(opts)))
+
+    def selftest_timeout(self, stream=None):
+        _check(lib().ext_plan_selftest_timeout(self.handle, _stream(stream)))
 
     def close(self):
         if self.handle:
@@ -401,6 +448,30 @@ class MLP:
     def n_params(self):
         H, n = self.hidden, self.n_in
         return H * n + H + H * H + H + 4 * H + 4
+
+    def save(self, path):
+        _check(lib().ext_mlp_save(self.handle, os.fsencode(path)))
+
+    def load(self, path):
+        _check(lib().ext_mlp_load(self.handle, os.fsencode(path)))
+
+
+def ext_mlp_checkpoint_info(path):
+    """(n_in, hidden, step) of a checkpoint file, checked on the host alone."""
+    n_in, hidden, step = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int64(0)
+    _check(lib().ext_mlp_checkpoint_info(os.fsencode(path), ctypes.byref(n_in), ctypes.byref(hidden),
+                                         ctypes.byref(step)))
+    return n_in.value, hidden.value, step.value
+
+
+def ext_select_components(energy, budget):
+    """The component list of ext_select_components for energies E_0..E_K."""
+    E = np.ascontiguousarray(np.asarray(energy, np.float64))
+    K = len(E) - 1
+    ks = np.zeros(max(K + 1, 1), np.int32)
+    n = ctypes.c_int(0)
+    _check(lib().ext_select_components(_ptr(E), int(K), int(budget), _ptr(ks), ctypes.byref(n)))
+    return [int(k) for k in ks[:n.value]]
 
 
 def ext_mlp_forward(net: MLP, X, n, q, stream=None):

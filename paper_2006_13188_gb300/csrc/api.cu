@@ -2,11 +2,37 @@
 // filter caches, and the launch sequences of each operator.
 #include "plan.h"
 
+#include <fstream>
+#include <mutex>
+#include <set>
+#include <sstream>
+#include <tuple>
+
 namespace {
 thread_local std::string g_last_error;
 }  // namespace
 
 void ext_set_error(const char* msg) { g_last_error = msg; }
+
+namespace {
+std::mutex g_optin_mutex;
+std::set<std::tuple<int, const void*, int>> g_optin_done;
+}  // namespace
+
+bool ext_smem_optin(const void* func, int bytes) {
+  if (bytes <= 48 * 1024) return true;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(g_optin_mutex);
+  auto key = std::make_tuple(dev, func, bytes);
+  if (g_optin_done.count(key)) return true;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  g_optin_done.insert(key);
+  return true;
+}
 
 namespace {
 
@@ -160,7 +186,7 @@ ext_status spectra_generic(ext_plan plan, uint64_t key, int h, int w, int ncomp,
   SpecEntry e;
   e.key = key;
   e.bytes = bytes;
-  EXT_CUDA(cudaMalloc(&e.S, bytes));
+  EXT_TRY(plan_malloc(plan, (void**)&e.S, bytes));
   const float2 *tw_w = nullptr, *tw_h = nullptr;
   EXT_TRY(twiddle(plan, w, st, &tw_w));
   EXT_TRY(twiddle(plan, h, st, &tw_h));
@@ -229,7 +255,7 @@ ext_status sweep_table_list(ext_plan plan, const int* ks, int nks, int J, cudaSt
   auto it = plan->sweep_tables.find(key);
   if (it == plan->sweep_tables.end()) {
     float* B = nullptr;
-    EXT_CUDA(cudaMalloc(&B, sizeof(float) * (size_t)J * (cp > 0 ? cp : 4)));
+    EXT_TRY(plan_malloc(plan, (void**)&B, sizeof(float) * (size_t)J * (cp > 0 ? cp : 4)));
     if (cp > 0) {
       void* dks = nullptr;
       EXT_TRY(ensure(plan, "sweep_ks", sizeof(int) * nks, &dks));
@@ -251,7 +277,7 @@ ext_status sweep_table(ext_plan plan, int K, int J, cudaStream_t st, const float
   auto it = plan->sweep_tables.find(key);
   if (it == plan->sweep_tables.end()) {
     float* B = nullptr;
-    EXT_CUDA(cudaMalloc(&B, sizeof(float) * (size_t)J * (cp > 0 ? cp : 4)));
+    EXT_TRY(plan_malloc(plan, (void**)&B, sizeof(float) * (size_t)J * (cp > 0 ? cp : 4)));
     if (cp > 0) launch_sweep_table(K, J, cp, B, st);
     EXT_CUDA(cudaGetLastError());
     it = plan->sweep_tables.emplace(key, B).first;
@@ -344,6 +370,163 @@ ext_status run_components(ext_plan plan, const float* H, int h, int w, const ext
   return EXT_OK;
 }
 
+// ----- autotuner of the component passes (ext_options.autotune)
+// A shape class (h, w, K) has several pass variants that compute the same
+// components: the inverse column pass staged by tensor copies or not, the
+// persistent prefetching passes or the plain ones, and all components per
+// inverse launch or two chunks.  The first call of a class with autotuning on
+// times every variant on the call's own data (one warm-up run, then three
+// timed runs each, CUDA events on the call's stream) and keeps the fastest;
+// the choice is cached per plan and, with a cache file, across processes.
+struct PassVariant {
+  bool tma = true, pipelined = true;
+  int kchunk = 0;
+};
+
+std::string gpu_tag(int device) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  int drv = 0;
+  cudaDriverGetVersion(&drv);
+  std::string name = prop.name;
+  for (char& c : name)
+    if (c == '\t' || c == '\n') c = ' ';
+  return name + " driver " + std::to_string(drv);
+}
+
+void tune_cache_read(ext_plan plan) {
+  if (plan->tune_cache.empty()) return;
+  std::ifstream f(plan->tune_cache);
+  const std::string tag = gpu_tag(plan->device);
+  std::string line;
+  while (std::getline(f, line)) {
+    const size_t a = line.find('\t'), b = line.find('\t', a == std::string::npos ? a : a + 1);
+    if (a == std::string::npos || b == std::string::npos) continue;
+    if (line.compare(0, a, tag) == 0 && a == tag.size()) plan->tuned[line.substr(a + 1, b - a - 1)] = line.substr(b + 1);
+  }
+}
+
+void tune_cache_write(ext_plan plan) {
+  if (plan->tune_cache.empty()) return;
+  const std::string tag = gpu_tag(plan->device);
+  std::vector<std::string> keep;
+  {
+    std::ifstream f(plan->tune_cache);
+    std::string line;
+    while (std::getline(f, line))
+      if (!(line.size() > tag.size() && line.compare(0, tag.size(), tag) == 0 && line[tag.size()] == '\t'))
+        keep.push_back(line);
+  }
+  const std::string tmp = plan->tune_cache + ".tmp";
+  {
+    std::ofstream f(tmp, std::ios::trunc);
+    for (const auto& l : keep) f << l << "\n";
+    for (const auto& kv : plan->tuned) f << tag << "\t" << kv.first << "\t" << kv.second << "\n";
+  }
+  std::rename(tmp.c_str(), plan->tune_cache.c_str());
+}
+
+PassVariant parse_variant(const std::string& v) {
+  PassVariant p;
+  int t = 1, q = 1, k = 0;
+  std::istringstream in(v);
+  in >> t >> q >> k;
+  p.tma = t != 0;
+  p.pipelined = q != 0;
+  p.kchunk = k;
+  return p;
+}
+
+struct VariantScope {   // applies a variant to the plan for one call
+  ext_plan plan;
+  bool tma, pipelined;
+  int kchunk;
+  VariantScope(ext_plan p, const PassVariant& v) : plan(p), tma(p->tma), pipelined(p->pipelined), kchunk(p->kchunk) {
+    p->tma = v.tma;
+    p->pipelined = v.pipelined;
+    p->kchunk = v.kchunk;
+  }
+  ~VariantScope() {
+    plan->tma = tma;
+    plan->pipelined = pipelined;
+    plan->kchunk = kchunk;
+  }
+};
+
+std::string class_key(int h, int w, int K) {
+  return "components " + std::to_string(h) + "x" + std::to_string(w) + " K=" + std::to_string(K);
+}
+
+ext_status tune_components(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, float* G,
+                           cudaStream_t st, PassVariant* best) {
+  const int K = F->K;
+  std::vector<PassVariant> cands;
+  for (int t = 1; t >= 0; --t)
+    for (int q = 1; q >= 0; --q)
+      for (int k : {0, (K + 2) / 2}) {
+        if (k != 0 && k >= K + 1) continue;
+        PassVariant v;
+        v.tma = t != 0;
+        v.pipelined = q != 0;
+        v.kchunk = k;
+        cands.push_back(v);
+      }
+  cudaEvent_t a = take_event(plan), b = take_event(plan);
+  const bool profiling = plan->profiling;
+  plan->profiling = false;
+  float best_ms = -1.f;
+  for (const PassVariant& v : cands) {
+    VariantScope scope(plan, v);
+    ext_status s = run_components(plan, H, h, w, F, G, st);
+    if (s == EXT_OK) {
+      cudaEventRecord(a, st);
+      for (int r = 0; r < 3 && s == EXT_OK; ++r) s = run_components(plan, H, h, w, F, G, st);
+      cudaEventRecord(b, st);
+    }
+    if (s == EXT_OK && cudaEventSynchronize(b) == cudaSuccess && device_status(plan) == EXT_OK) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (best_ms < 0.f || ms < best_ms) {
+        best_ms = ms;
+        *best = v;
+      }
+    }
+    cudaGetLastError();
+  }
+  plan->profiling = profiling;
+  plan->event_pool.push_back(a);
+  plan->event_pool.push_back(b);
+  if (best_ms < 0.f) return fail(EXT_ERR_CUDA, "autotuning: no pass variant ran");
+  char buf[96];
+  std::snprintf(buf, sizeof(buf), "%d %d %d %.4f", best->tma ? 1 : 0, best->pipelined ? 1 : 0, best->kchunk,
+                best_ms / 3.f);
+  plan->tuned[class_key(h, w, K)] = buf;
+  tune_cache_write(plan);
+  return EXT_OK;
+}
+
+// run_components with the tuned variant of its shape class (tuned now if
+// autotuning is on, the class is new and the stream is not being captured).
+ext_status run_components_tuned(ext_plan plan, const float* H, int h, int w, const ext_filter_so2* F, float* G,
+                                cudaStream_t st) {
+  if (!plan->autotune) return run_components(plan, H, h, w, F, G, st);
+  PassVariant v;
+  auto it = plan->tuned.find(class_key(h, w, F->K));
+  if (it != plan->tuned.end()) {
+    v = parse_variant(it->second);
+  } else {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    EXT_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return run_components(plan, H, h, w, F, G, st);
+    EXT_TRY(tune_components(plan, H, h, w, F, G, st, &v));
+  }
+  VariantScope scope(plan, v);
+  return run_components(plan, H, h, w, F, G, st);
+}
+
 // Extended convolution of nsig signals by the steered-spectrum route of
 // Sec. 4.1 / Sec. 8: for each signal, rows(sig, A) writes the row transforms
 // of its ncomp steered copies into A; the column pass (tensor-copy staged
@@ -400,6 +583,7 @@ ext_status run_conv_so2(ext_plan plan, const float* H, const float* alpha, int h
 
 ext_status run_sweep(ext_plan plan, const float* G, long long P, int K, int J, float* maxv, int32_t* argmax,
                      int precision, cudaStream_t st) {
+  precision = resolve_precision(plan, precision);
   if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3)
     return fail(EXT_ERR_INVALID_ARG, "unknown precision");
   if (K == 0) {
@@ -417,6 +601,8 @@ ext_status run_sweep(ext_plan plan, const float* G, long long P, int K, int J, f
     launch(plan, "sweep_bf16x3", st,
            [&] { ok = sweep_bf16x3(G, P, K, J, B, cp, maxv, argmax, plan->dev_err, plan->sms, st); });
   } else {
+    if (!sweep_fp32_fits(K, J))
+      return fail(EXT_ERR_UNSUPPORTED, "FP32 sweep: the steering table of this many angles exceeds shared memory");
     launch(plan, "sweep_fp32", st, [&] { ok = sweep_fp32(G, P, K, J, B, cp, maxv, argmax, st); });
   }
   if (!ok) return fail(EXT_ERR_UNSUPPORTED, "sweep K");
@@ -437,30 +623,87 @@ const char* ext_status_string(ext_status s) {
     case EXT_ERR_CUDA: return "EXT_ERR_CUDA";
     case EXT_ERR_OOM: return "EXT_ERR_OOM";
     case EXT_ERR_TIMEOUT: return "EXT_ERR_TIMEOUT";
+    case EXT_ERR_CHECKPOINT: return "EXT_ERR_CHECKPOINT";
     default: return "EXT_ERR_UNKNOWN";
   }
 }
 
 const char* ext_last_error(void) { return g_last_error.c_str(); }
 
-ext_status ext_plan_create(ext_plan* plan, int device) {
+void ext_options_init(ext_options* o) {
+  if (!o) return;
+  o->device = 0;
+  o->precision = EXT_PREC_FP32;
+  o->wait_budget_ns = 0;
+  o->autotune = EXT_TUNE_OFF;
+  o->tune_cache = nullptr;
+  o->fault_inject = EXT_FAULT_NONE;
+  o->fault_after = 0;
+}
+
+ext_status ext_plan_create(ext_plan* plan, const ext_options* options) {
   if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
   *plan = nullptr;
+  ext_options o;
+  ext_options_init(&o);
+  if (options) o = *options;
+  if (o.precision != EXT_PREC_FP32 && o.precision != EXT_PREC_BF16X3)
+    return fail(EXT_ERR_INVALID_ARG, "options.precision must be EXT_PREC_FP32 or EXT_PREC_BF16X3");
+  if (o.autotune != EXT_TUNE_OFF && o.autotune != EXT_TUNE_ON) return fail(EXT_ERR_INVALID_ARG, "options.autotune");
+  if (o.fault_inject != EXT_FAULT_NONE && o.fault_inject != EXT_FAULT_ALLOC)
+    return fail(EXT_ERR_INVALID_ARG, "options.fault_inject");
+  if (o.fault_after < 0) return fail(EXT_ERR_INVALID_ARG, "options.fault_after must be >= 0");
   int n = 0;
   EXT_CUDA(cudaGetDeviceCount(&n));
-  if (device < 0 || device >= n) return fail(EXT_ERR_INVALID_ARG, "no such device");
-  EXT_CUDA(cudaSetDevice(device));
+  if (o.device < 0 || o.device >= n) return fail(EXT_ERR_INVALID_ARG, "no such device");
+  EXT_CUDA(cudaSetDevice(o.device));
   ext_plan p = new ext_plan_s();
-  p->device = device;
-  cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
-  if (cudaMalloc(&p->dev_err, sizeof(int)) != cudaSuccess || cudaMemset(p->dev_err, 0, sizeof(int)) != cudaSuccess) {
+  p->device = o.device;
+  p->precision = o.precision;
+  p->wait_budget_ns = o.wait_budget_ns ? o.wait_budget_ns : 1000000000ull;
+  p->fault_inject = o.fault_inject;
+  p->fault_countdown = o.fault_inject == EXT_FAULT_ALLOC ? o.fault_after : -1;
+  p->autotune = o.autotune == EXT_TUNE_ON;
+  if (o.tune_cache) p->tune_cache = o.tune_cache;
+  cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, o.device);
+  // status block: the status word at byte 0, the wait budget at byte 8
+  unsigned long long block[2] = {0ull, p->wait_budget_ns};
+  if (cudaMalloc(&p->dev_err, sizeof(block)) != cudaSuccess ||
+      cudaMemcpy(p->dev_err, block, sizeof(block), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (p->dev_err) cudaFree(p->dev_err);
     delete p;
-    return fail(EXT_ERR_CUDA, "cannot allocate the plan status word");
+    return fail(EXT_ERR_CUDA, "cannot allocate the plan status block");
   }
   if (const char* e = getenv("EXT_KCHUNK")) p->kchunk = atoi(e);
   if (const char* e = getenv("EXT_PIPELINED")) p->pipelined = atoi(e) != 0;
   if (const char* e = getenv("EXT_TMA")) p->tma = atoi(e) != 0;
+  if (p->autotune) tune_cache_read(p);
   *plan = p;
+  return EXT_OK;
+}
+
+ext_status ext_plan_selftest_timeout(ext_plan plan, void* stream) {
+  if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  launch(plan, "selftest_timeout", st, [&] { launch_selftest_timeout(plan->dev_err, st); });
+  EXT_CUDA(cudaGetLastError());
+  return EXT_OK;
+}
+
+ext_status ext_select_components(const double* energy, int K, int budget, int* ks_out, int* n_out) {
+  if (!energy || !ks_out || K < 0 || budget < 1) return fail(EXT_ERR_INVALID_ARG, "bad arguments");
+  for (int k = 0; k <= K; ++k)
+    if (energy[k] != energy[k]) return fail(EXT_ERR_INVALID_ARG, "NaN energy");
+  std::vector<int> order;
+  for (int k = 1; k <= K; ++k) order.push_back(k);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return energy[a] > energy[b]; });
+  const int m = std::min(budget, K + 1) - 1;
+  std::vector<int> chosen(order.begin(), order.begin() + m);
+  std::sort(chosen.begin(), chosen.end());
+  ks_out[0] = 0;
+  for (int i = 0; i < m; ++i) ks_out[1 + i] = chosen[i];
+  if (n_out) *n_out = m + 1;
   return EXT_OK;
 }
 
@@ -582,7 +825,7 @@ ext_status ext_corr_so2_components(ext_plan plan, const float* H, int h, int w, 
   Staged sH, sG;
   EXT_TRY(stage_in(plan, "in_H", H, sizeof(float) * P, st, &sH));
   EXT_TRY(stage_out_alloc(plan, "out_G", G, sizeof(float) * P * (2 * F->K + 1), &sG));
-  EXT_TRY(run_components(plan, (const float*)sH.dev, h, w, F, (float*)sG.dev, st));
+  EXT_TRY(run_components_tuned(plan, (const float*)sH.dev, h, w, F, (float*)sG.dev, st));
   EXT_TRY(stage_out_finish(sG, st));
   return finish_host(plan, sH.host || sG.host, st);
 }
@@ -616,6 +859,7 @@ ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_f
   if (!alpha) {
     if (n_angles < 1) return fail(EXT_ERR_INVALID_ARG, "sweep mode needs n_angles >= 1");
     if (!argmax) return fail(EXT_ERR_INVALID_ARG, "sweep mode needs argmax");
+    precision = resolve_precision(plan, precision);
     if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3)
       return fail(EXT_ERR_INVALID_ARG, "unknown precision");
     if (F->K > 16) return fail(EXT_ERR_UNSUPPORTED, "sweep supports K <= 16");
@@ -662,7 +906,7 @@ ext_status ext_corr_so2(ext_plan plan, const float* H, int h, int w, const ext_f
   }
   void* G = nullptr;
   EXT_TRY(ensure(plan, "G", sizeof(float) * P * (2 * K + 1), &G));
-  EXT_TRY(run_components(plan, (const float*)sH.dev, h, w, F, (float*)G, st));
+  EXT_TRY(run_components_tuned(plan, (const float*)sH.dev, h, w, F, (float*)G, st));
   EXT_TRY(run_sweep(plan, (const float*)G, (long long)P, K, n_angles, (float*)sM.dev, (int32_t*)sA.dev, precision,
                     st));
   EXT_TRY(stage_out_finish(sM, st));
@@ -681,6 +925,7 @@ ext_status ext_corr_so2_subset(ext_plan plan, const float* H, int h, int w, cons
     if (ks[i] <= ks[i - 1] || ks[i] > F->K)
       return fail(EXT_ERR_INVALID_ARG, "components must ascend and lie in 1..K");
   if (n_angles < 1) return fail(EXT_ERR_INVALID_ARG, "n_angles must be >= 1");
+  precision = resolve_precision(plan, precision);
   if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3)
     return fail(EXT_ERR_INVALID_ARG, "unknown precision");
   if (precision == EXT_PREC_BF16X3 && n_angles > 128)
@@ -716,6 +961,8 @@ ext_status ext_corr_so2_subset(ext_plan plan, const float* H, int h, int w, cons
         ok = sweep_bf16x3((const float*)G, (long long)P, Ks, n_angles, B, cp, (float*)sM.dev, (int32_t*)sA.dev,
                           plan->dev_err, plan->sms, st);
       });
+    else if (!sweep_fp32_fits(Ks, n_angles))
+      return fail(EXT_ERR_UNSUPPORTED, "FP32 sweep: the steering table of this many angles exceeds shared memory");
     else
       launch(plan, "sweep_fp32", st, [&] {
         ok = sweep_fp32((const float*)G, (long long)P, Ks, n_angles, B, cp, (float*)sM.dev, (int32_t*)sA.dev, st);
@@ -966,6 +1213,7 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
   if (!plan) return fail(EXT_ERR_INVALID_ARG, "plan is NULL");
   if (n < 0 || (n > 0 && !imgs)) return fail(EXT_ERR_INVALID_ARG, "bad image list");
   if (n == 0) return EXT_OK;
+  precision = resolve_precision(plan, precision);
   if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3) return fail(EXT_ERR_INVALID_ARG, "unknown precision");
   EXT_CUDA(cudaSetDevice(plan->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -981,7 +1229,8 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
     EXT_TRY(check_size(d.h, d.w));
     if (d.h == 0 || d.w == 0) return fail(EXT_ERR_INVALID_ARG, "empty image in a batch");
     if (!d.H || !d.max_out || !d.argmax) return fail(EXT_ERR_INVALID_ARG, "NULL buffer in a batch");
-    if (!is_device_ptr(d.H) || !is_device_ptr(d.max_out) || !is_device_ptr(d.argmax))
+    if (!is_device_ptr(d.H, plan->device) || !is_device_ptr(d.max_out, plan->device) ||
+        !is_device_ptr(d.argmax, plan->device))
       return fail(EXT_ERR_INVALID_ARG, "batched images and outputs must be device buffers");
     const int K = d.F->K;
     if (d.n_angles < 1 || K > 16 || (precision == EXT_PREC_BF16X3 && d.n_angles > 128))
@@ -1030,7 +1279,7 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
     EXT_TRY(ensure(plan, kS[b].c_str(), max_S, &dS[b]));
     EXT_TRY(ensure(plan, kGrid[b].c_str(), max_grid, &dgrid[b]));
     EXT_TRY(ensure(plan, kHh[b].c_str(), max_Hh, &dHh[b]));
-    EXT_TRY(ensure(plan, kHf[b].c_str(), plan->tma ? max_Hf : 16, &dHf[b]));
+    EXT_TRY(ensure(plan, kHf[b].c_str(), plan->tma || plan->autotune ? max_Hf : 16, &dHf[b]));
     EXT_TRY(ensure(plan, kZ[b].c_str(), max_Z, &dZ[b]));
     EXT_TRY(ensure(plan, kG[b].c_str(), max_G, &dG[b]));
     EXT_TRY(ensure(plan, kP[b].c_str(), std::max<size_t>(max_polar, 8), &dpolar[b]));
@@ -1062,6 +1311,15 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
   }
   EXT_CUDA(cudaMemcpyAsync(din, plan->batch_host.data(), host_bytes, cudaMemcpyHostToDevice, st));
   EXT_CUDA(cudaStreamSynchronize(st));   // the host staging buffer is reused by the next call
+  // ---- autotuning: every new shape class is tuned on its first image
+  if (plan->autotune) {
+    for (int i = 0; i < n; ++i) {
+      const ext_image_desc& d = imgs[i];
+      if (plan->tuned.count(class_key(d.h, d.w, d.F->K))) continue;
+      PassVariant v;
+      EXT_TRY(tune_components(plan, d.H, d.h, d.w, d.F, (float*)dG[0], st, &v));
+    }
+  }
   // ---- capture the per-image launch sequences once, then replay
   if (plan->batch_exec == nullptr || plan->batch_key != key) {
     if (plan->batch_exec) {
@@ -1089,6 +1347,15 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
       const ext_filter_so2* F = d.F;
       const int K = F->K, h = d.h, w = d.w;
       const size_t P = (size_t)h * w;
+      PassVariant v;
+      v.tma = plan->tma;
+      v.pipelined = plan->pipelined;
+      v.kchunk = plan->kchunk;
+      if (plan->autotune) {
+        auto it = plan->tuned.find(class_key(h, w, K));
+        if (it != plan->tuned.end()) v = parse_variant(it->second);
+      }
+      VariantScope scope(plan, v);
       const double2* coef = (const double2*)((unsigned char*)din + off_in[i]);
       if (F->kind == EXT_FILTER_SAMPLED) {
         double2* table = (double2*)((unsigned char*)dcoef + off_coef[i]);

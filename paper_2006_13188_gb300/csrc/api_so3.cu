@@ -96,7 +96,7 @@ ext_status so3_spectra(ext_plan plan, int ncomp, const int4* dcomp, const double
   SpecEntry e;
   e.key = key;
   e.bytes = sizeof(float2) * per_k * ncomp;
-  EXT_CUDA(cudaMalloc(&e.S, e.bytes));
+  EXT_TRY(plan_malloc(plan, (void**)&e.S, e.bytes));
   ext_status bs = build(e.S);
   if (bs != EXT_OK) {
     cudaFree(e.S);
@@ -274,6 +274,7 @@ ext_status ext_sweep_so3(ext_plan plan, const float* G, int64_t n_vox, int L, co
   if (!plan || !G || !quats || !max_out || !argmax || n_vox < 0 || n_rot < 1)
     return fail(EXT_ERR_INVALID_ARG, "bad arguments");
   if (L < 0 || L > 6) return fail(EXT_ERR_UNSUPPORTED, "L <= 6");
+  precision = resolve_precision(plan, precision);
   if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3) return fail(EXT_ERR_INVALID_ARG, "precision");
   if (n_vox == 0) return EXT_OK;
   EXT_CUDA(cudaSetDevice(plan->device));
@@ -295,6 +296,7 @@ ext_status ext_corr_so3(ext_plan plan, const float* V, int nz, int ny, int nx, c
   if (!plan || !V || !tables || !quats || !max_out || !argmax || n_rot < 1)
     return fail(EXT_ERR_INVALID_ARG, "NULL argument");
   EXT_TRY(check_so3_args(nz, ny, nx, L, n_r, dr, R));
+  precision = resolve_precision(plan, precision);
   if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3) return fail(EXT_ERR_INVALID_ARG, "precision");
   EXT_CUDA(cudaSetDevice(plan->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -1059,6 +1061,7 @@ ext_status ext_so3_propose(ext_plan plan, const float* G, int64_t n_vox, int L, 
                            int64_t* counts, void* stream) {
   if (!plan || !G || !quats || !score || n_vox < 0 || n_rot < 1) return fail(EXT_ERR_INVALID_ARG, "bad arguments");
   if (L < 0 || L > 6) return fail(EXT_ERR_UNSUPPORTED, "L <= 6");
+  precision = resolve_precision(plan, precision);
   if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3) return fail(EXT_ERR_INVALID_ARG, "precision");
   if (n_vox > INT32_MAX) return fail(EXT_ERR_UNSUPPORTED, "at most 2^31 - 1 voxels");
   if (net && net->n_in != so3_layout(L).nchan) return fail(EXT_ERR_INVALID_ARG, "network n_in != channels of L");
@@ -1087,6 +1090,7 @@ ext_status ext_corr_so3_propose(ext_plan plan, const float* V, int nz, int ny, i
                                 void* stream) {
   if (!plan || !V || !tables || !quats || !score || n_rot < 1) return fail(EXT_ERR_INVALID_ARG, "NULL argument");
   EXT_TRY(check_so3_args(nz, ny, nx, L, n_r, dr, R));
+  precision = resolve_precision(plan, precision);
   if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3) return fail(EXT_ERR_INVALID_ARG, "precision");
   if (net && net->n_in != so3_layout(L).nchan) return fail(EXT_ERR_INVALID_ARG, "network n_in != channels of L");
   if (net && net->plan != plan) return fail(EXT_ERR_INVALID_ARG, "network belongs to another plan");
@@ -1107,6 +1111,195 @@ ext_status ext_corr_so3_propose(ext_plan plan, const float* V, int nz, int ny, i
   if (quat) EXT_TRY(stage_out_finish(sQ, st));
   if (grid_idx) EXT_TRY(stage_out_finish(sI, st));
   return finish_host(plan, sV.host || sS.host || sQ.host || sI.host, st);
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------- checkpoints ---
+// The network's whole training state in one file (layout in extconv.h):
+// resuming from it continues Adam exactly where it stopped.
+namespace {
+
+// CRC-32 of IEEE 802.3 (reflected polynomial 0xEDB88320, register preset to
+// all ones, result complemented), one bit at a time from its definition.
+uint32_t crc32_ieee(const unsigned char* p, size_t n) {
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < n; ++i) {
+    c ^= p[i];
+    for (int b = 0; b < 8; ++b) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+  }
+  return ~c;
+}
+
+constexpr char CKPT_MAGIC[9] = "EXTMLP01";
+constexpr uint32_t CKPT_VERSION = 1;
+constexpr size_t CKPT_HEADER = 40;
+
+void put_u32(unsigned char* p, uint32_t v) {
+  for (int i = 0; i < 4; ++i) p[i] = (unsigned char)(v >> (8 * i));
+}
+void put_u64(unsigned char* p, uint64_t v) {
+  for (int i = 0; i < 8; ++i) p[i] = (unsigned char)(v >> (8 * i));
+}
+uint32_t get_u32(const unsigned char* p) {
+  uint32_t v = 0;
+  for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i);
+  return v;
+}
+uint64_t get_u64(const unsigned char* p) {
+  uint64_t v = 0;
+  for (int i = 0; i < 8; ++i) v |= (uint64_t)p[i] << (8 * i);
+  return v;
+}
+
+uint64_t ckpt_floats(uint64_t n_in, uint64_t hidden) { return hidden * (n_in + hidden + 6) + 4; }
+
+struct CkptInfo {
+  int n_in = 0, hidden = 0;
+  uint64_t step = 0, n = 0;
+};
+
+// Reads and checks a checkpoint file; on success the whole file is in `bytes`.
+ext_status ckpt_read(const char* path, std::vector<unsigned char>* bytes, CkptInfo* info) {
+  if (!path) return fail(EXT_ERR_INVALID_ARG, "checkpoint path is NULL");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(EXT_ERR_CHECKPOINT, std::string("cannot open checkpoint ") + path);
+  std::vector<unsigned char>& b = *bytes;
+  b.clear();
+  unsigned char buf[1 << 16];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) b.insert(b.end(), buf, buf + got);
+  const bool bad = std::ferror(f) != 0;
+  std::fclose(f);
+  if (bad) return fail(EXT_ERR_CHECKPOINT, "error reading the checkpoint");
+  if (b.size() < CKPT_HEADER + 4) return fail(EXT_ERR_CHECKPOINT, "checkpoint truncated (shorter than its header)");
+  if (std::memcmp(b.data(), CKPT_MAGIC, 8) != 0) return fail(EXT_ERR_CHECKPOINT, "not a network checkpoint (magic)");
+  if (get_u32(b.data() + 8) != CKPT_VERSION) return fail(EXT_ERR_CHECKPOINT, "unknown checkpoint version");
+  const uint32_t n_in = get_u32(b.data() + 12), hidden = get_u32(b.data() + 16);
+  const uint64_t n = get_u64(b.data() + 32);
+  if (n_in < 1 || n_in > 4096 || hidden < 16 || hidden > 1024 || hidden % 16 || n != ckpt_floats(n_in, hidden))
+    return fail(EXT_ERR_CHECKPOINT, "checkpoint header has impossible shapes");
+  if (b.size() != CKPT_HEADER + 3 * 4 * n + 4) return fail(EXT_ERR_CHECKPOINT, "checkpoint length does not match its header");
+  if (crc32_ieee(b.data(), b.size() - 4) != get_u32(b.data() + b.size() - 4))
+    return fail(EXT_ERR_CHECKPOINT, "checkpoint CRC-32 mismatch (corrupt file)");
+  info->n_in = (int)n_in;
+  info->hidden = (int)hidden;
+  info->step = get_u64(b.data() + 24);
+  info->n = n;
+  return EXT_OK;
+}
+
+// One parameter-sized device buffer (padded layout of the network) <-> the
+// packed layout of ext_mlp_set_params: W1, b1, W2, b2, W3, b3.
+ext_status ckpt_pack(ext_mlp net, const float* base, float* out) {
+  const size_t H = net->H, f = sizeof(float), ni = net->n_in;
+  float* o = out;
+  EXT_CUDA(cudaMemcpy2D(o, f * ni, base + net->oW1, f * net->dp, f * ni, H, cudaMemcpyDeviceToHost));
+  o += H * ni;
+  EXT_CUDA(cudaMemcpy(o, base + net->ob1, f * H, cudaMemcpyDeviceToHost));
+  o += H;
+  EXT_CUDA(cudaMemcpy(o, base + net->oW2, f * H * H, cudaMemcpyDeviceToHost));
+  o += H * H;
+  EXT_CUDA(cudaMemcpy(o, base + net->ob2, f * H, cudaMemcpyDeviceToHost));
+  o += H;
+  EXT_CUDA(cudaMemcpy(o, base + net->oW3, f * 4 * H, cudaMemcpyDeviceToHost));
+  o += 4 * H;
+  EXT_CUDA(cudaMemcpy(o, base + net->ob3, f * 4, cudaMemcpyDeviceToHost));
+  return EXT_OK;
+}
+
+ext_status ckpt_unpack(ext_mlp net, const float* in, float* base) {
+  const size_t H = net->H, f = sizeof(float), ni = net->n_in;
+  EXT_CUDA(cudaMemset(base, 0, f * net->n_par));
+  const float* s = in;
+  EXT_CUDA(cudaMemcpy2D(base + net->oW1, f * net->dp, s, f * ni, f * ni, H, cudaMemcpyHostToDevice));
+  s += H * ni;
+  EXT_CUDA(cudaMemcpy(base + net->ob1, s, f * H, cudaMemcpyHostToDevice));
+  s += H;
+  EXT_CUDA(cudaMemcpy(base + net->oW2, s, f * H * H, cudaMemcpyHostToDevice));
+  s += H * H;
+  EXT_CUDA(cudaMemcpy(base + net->ob2, s, f * H, cudaMemcpyHostToDevice));
+  s += H;
+  EXT_CUDA(cudaMemcpy(base + net->oW3, s, f * 4 * H, cudaMemcpyHostToDevice));
+  s += 4 * H;
+  EXT_CUDA(cudaMemcpy(base + net->ob3, s, f * 4, cudaMemcpyHostToDevice));
+  return EXT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ext_status ext_mlp_save(ext_mlp net, const char* path) {
+  if (!net || !path) return fail(EXT_ERR_INVALID_ARG, "NULL argument");
+  EXT_CUDA(cudaSetDevice(net->device));
+  EXT_CUDA(cudaDeviceSynchronize());
+  const uint64_t n = ckpt_floats(net->n_in, net->H);
+  std::vector<unsigned char> b(CKPT_HEADER + 3 * 4 * n + 4, 0);
+  std::memcpy(b.data(), CKPT_MAGIC, 8);
+  put_u32(b.data() + 8, CKPT_VERSION);
+  put_u32(b.data() + 12, (uint32_t)net->n_in);
+  put_u32(b.data() + 16, (uint32_t)net->H);
+  put_u64(b.data() + 24, (uint64_t)net->step);
+  put_u64(b.data() + 32, n);
+  std::vector<float> blk(n);
+  const float* bases[3] = {net->w, net->m, net->v};
+  for (int i = 0; i < 3; ++i) {
+    EXT_TRY(ckpt_pack(net, bases[i], blk.data()));
+    unsigned char* dst = b.data() + CKPT_HEADER + (size_t)i * 4 * n;
+    for (uint64_t j = 0; j < n; ++j) {
+      uint32_t u;
+      std::memcpy(&u, &blk[j], 4);
+      put_u32(dst + 4 * j, u);
+    }
+  }
+  put_u32(b.data() + b.size() - 4, crc32_ieee(b.data(), b.size() - 4));
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return fail(EXT_ERR_CHECKPOINT, std::string("cannot create ") + tmp);
+  const bool ok = std::fwrite(b.data(), 1, b.size(), f) == b.size();
+  const bool closed = std::fclose(f) == 0;
+  if (!ok || !closed || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return fail(EXT_ERR_CHECKPOINT, std::string("cannot write checkpoint ") + path);
+  }
+  return EXT_OK;
+}
+
+ext_status ext_mlp_load(ext_mlp net, const char* path) {
+  if (!net || !path) return fail(EXT_ERR_INVALID_ARG, "NULL argument");
+  std::vector<unsigned char> b;
+  CkptInfo info;
+  EXT_TRY(ckpt_read(path, &b, &info));
+  if (info.n_in != net->n_in || info.hidden != net->H)
+    return fail(EXT_ERR_CHECKPOINT, "checkpoint shapes differ from the network's");
+  EXT_CUDA(cudaSetDevice(net->device));
+  EXT_CUDA(cudaDeviceSynchronize());
+  std::vector<float> blk(info.n);
+  float* bases[3] = {net->w, net->m, net->v};
+  for (int i = 0; i < 3; ++i) {
+    const unsigned char* src = b.data() + CKPT_HEADER + (size_t)i * 4 * info.n;
+    for (uint64_t j = 0; j < info.n; ++j) {
+      const uint32_t u = get_u32(src + 4 * j);
+      std::memcpy(&blk[j], &u, 4);
+    }
+    EXT_TRY(ckpt_unpack(net, blk.data(), bases[i]));
+  }
+  net->step = (int)info.step;
+  launch(net->plan, "mlp_to_bf16", 0, [&] { launch_f32_to_bf16(net->w, (long long)net->n_par, net->w16, 0); });
+  EXT_CUDA(cudaGetLastError());
+  EXT_CUDA(cudaDeviceSynchronize());
+  return EXT_OK;
+}
+
+ext_status ext_mlp_checkpoint_info(const char* path, int* n_in, int* hidden, int64_t* step) {
+  std::vector<unsigned char> b;
+  CkptInfo info;
+  EXT_TRY(ckpt_read(path, &b, &info));
+  if (n_in) *n_in = info.n_in;
+  if (hidden) *hidden = info.hidden;
+  if (step) *step = (int64_t)info.step;
+  return EXT_OK;
 }
 
 }  // extern "C"

@@ -117,10 +117,18 @@ void launch_gradient_field(const float* I, int h, int w, float* H, float* theta,
 // out[c][p] /= D[p] for c < channels (normalize.cu)
 void launch_divide_channels(float* out, const float* D, long long P, int channels, int sms, cudaStream_t st);
 
+// ----- failure-path self-test (status.cu): one wait that nothing completes, bounded by the status block's budget
+void launch_selftest_timeout(int* err, cudaStream_t st);
+// Opt-in to `bytes` of dynamic shared memory for `func` on the current device
+// (a per-device function attribute; set once per (device, function, size)).
+bool ext_smem_optin(const void* func, int bytes);
+
 // ----- sweep (sweep.cu)
 // B: J rows of cp floats (cp = 2K rounded up to a multiple of 4).
 bool sweep_fp32(const float* G, long long P, int K, int J, const float* B, int cp, float* maxv,
                 int32_t* argmax, cudaStream_t st);
+// whether the J x 2K steering table of the FP32 sweep fits the current device's shared memory
+bool sweep_fp32_fits(int K, int J);
 // tcgen05 split-BF16 sweep (sweep_tc.cu); err receives EXT_ERR_TIMEOUT if a bounded wait expires.
 bool sweep_bf16x3(const float* G, long long P, int K, int J, const float* B, int cp, float* maxv, int32_t* argmax,
                   int* err, int sms, cudaStream_t st);

@@ -112,9 +112,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
 template <int BN>
 static void launch_gemm_bn(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                            const GemmEpilogue& ep, int* err, cudaStream_t st) {
-  static const bool once =
-      (cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM_REQUEST), true);
-  (void)once;
+  ext_smem_optin((const void*)k_gemm_bf16<BN>, G_SMEM_REQUEST);
   dim3 grid((M + GBM - 1) / GBM, (N + BN - 1) / BN);
   k_gemm_bf16<BN><<<grid, 128, G_SMEM_REQUEST, st>>>(A, lda, B, ldb, M, N, K, ep, err);
 }

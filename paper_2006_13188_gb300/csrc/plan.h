@@ -82,7 +82,15 @@ struct ext_plan_s {
   int kchunk = 0;        // components per inverse launch (0 = by L2 budget)
   bool pipelined = true; // persistent prefetching passes where they fit
   bool tma = true;       // tensor-memory-accelerator staged column pass where it fits
-  int* dev_err = nullptr; // device-side status word (bounded waits)
+  int* dev_err = nullptr; // device-side status block: int status word, then (byte 8) the wait budget in ns
+  int precision = EXT_PREC_FP32;        // used where a call passes EXT_PREC_DEFAULT
+  unsigned long long wait_budget_ns = 1000000000ull;
+  int fault_inject = EXT_FAULT_NONE;    // host-side fault injection (tests of the error paths)
+  long long fault_countdown = -1;       // allocations left before the injected failure (-1: none)
+  // autotuner: chosen pass variant per shape class, and where the cache lives
+  bool autotune = false;
+  std::string tune_cache;
+  std::map<std::string, std::string> tuned;   // shape-class key -> "tma pipelined kchunk ms"
   // batched correlation: captured CUDA graph of the last batch and its key
   cudaGraphExec_t batch_exec = nullptr;
   uint64_t batch_key = 0;
@@ -126,13 +134,33 @@ void launch(ext_plan plan, const char* name, cudaStream_t st, F&& f) {
   plan->pending.push_back(p);
 }
 
+// Every device allocation of a plan goes through here, so that an injected
+// allocation failure (ext_options.fault_inject) takes the same error path as
+// a real one.
+ext_status plan_malloc(ext_plan plan, void** p, size_t bytes) {
+  if (plan->fault_inject == EXT_FAULT_ALLOC && plan->fault_countdown >= 0) {
+    if (plan->fault_countdown == 0) {
+      plan->fault_countdown = -1;
+      *p = nullptr;
+      return fail(EXT_ERR_OOM, "device allocation failed (injected by ext_options.fault_inject)");
+    }
+    --plan->fault_countdown;
+  }
+  EXT_CUDA(cudaMalloc(p, bytes));
+  return EXT_OK;
+}
+
+int resolve_precision(ext_plan plan, int precision) {
+  return precision == EXT_PREC_DEFAULT ? plan->precision : precision;
+}
+
 ext_status ensure(ext_plan plan, const char* name, size_t bytes, void** out) {
   DevBuf& b = plan->ws[name];
   if (b.bytes < bytes) {
     if (b.p) EXT_CUDA(cudaFree(b.p));
     b.p = nullptr;
     b.bytes = 0;
-    EXT_CUDA(cudaMalloc(&b.p, bytes));
+    EXT_TRY(plan_malloc(plan, &b.p, bytes));
     b.bytes = bytes;
   }
   *out = b.p;
@@ -143,7 +171,7 @@ ext_status twiddle(ext_plan plan, int n, cudaStream_t st, const float2** out) {
   auto it = plan->twiddles.find(n);
   if (it == plan->twiddles.end()) {
     float2* tw = nullptr;
-    EXT_CUDA(cudaMalloc(&tw, sizeof(float2) * n));
+    EXT_TRY(plan_malloc(plan, (void**)&tw, sizeof(float2) * n));
     launch_twiddle(tw, n, st);
     EXT_CUDA(cudaGetLastError());
     it = plan->twiddles.emplace(n, tw).first;
@@ -168,7 +196,7 @@ ext_status stage_table(ext_plan plan, int n, cudaStream_t st, const float2** out
     const float2* tw = nullptr;
     EXT_TRY(twiddle(plan, n, st, &tw));
     float2* t = nullptr;
-    EXT_CUDA(cudaMalloc(&t, sizeof(float2) * n));
+    EXT_TRY(plan_malloc(plan, (void**)&t, sizeof(float2) * n));
     fft_build_stage_table(n, tw, t, st);
     EXT_CUDA(cudaGetLastError());
     it = plan->twiddles.emplace(-n, t).first;
@@ -177,15 +205,25 @@ ext_status stage_table(ext_plan plan, int n, cudaStream_t st, const float2** out
   return EXT_OK;
 }
 
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
+// 1: device (or managed) memory the kernels of `device` can use; 0: host
+// memory (pageable or page-locked); -1: device memory of another GPU.
+int pointer_kind(const void* p, int device) {
+  if (!p) return 0;
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, p);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return 1;
+  if (at.type == cudaMemoryTypeDevice) return at.device == device ? 1 : -1;
+  return 0;
+}
+
+bool is_device_ptr(const void* p, int device) { return pointer_kind(p, device) == 1; }
+
+ext_status foreign_device(const char* name) {
+  return fail(EXT_ERR_INVALID_ARG, std::string(name) + ": device buffer on another GPU than the plan's");
 }
 
 // Host/device staging of one argument.
@@ -201,7 +239,9 @@ ext_status stage_in(ext_plan plan, const char* name, const void* user, size_t by
                     Staged* s) {
   s->user = user;
   s->bytes = bytes;
-  s->host = user && !is_device_ptr(user);
+  const int kind = pointer_kind(user, plan->device);
+  if (kind < 0) return foreign_device(name);
+  s->host = user && kind == 0;
   if (!s->host) {
     s->dev = const_cast<void*>(user);
     return EXT_OK;
@@ -214,7 +254,9 @@ ext_status stage_in(ext_plan plan, const char* name, const void* user, size_t by
 ext_status stage_out_alloc(ext_plan plan, const char* name, void* user, size_t bytes, Staged* s) {
   s->user = user;
   s->bytes = bytes;
-  s->host = user && !is_device_ptr(user);
+  const int kind = pointer_kind(user, plan->device);
+  if (kind < 0) return foreign_device(name);
+  s->host = user && kind == 0;
   if (!s->host) {
     s->dev = user;
     return EXT_OK;
@@ -227,7 +269,7 @@ ext_status stage_out_alloc(ext_plan plan, const char* name, void* user, size_t b
 // transfer to the host overlaps that kernel instead of following it as a
 // copy; other host memory is staged as usual.
 ext_status stage_out_direct(ext_plan plan, const char* name, void* user, size_t bytes, Staged* s) {
-  if (user && !is_device_ptr(user)) {
+  if (user && !is_device_ptr(user, plan->device)) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, user) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
       s->user = user;

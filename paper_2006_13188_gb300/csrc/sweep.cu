@@ -11,6 +11,7 @@
 
 #include <cfloat>
 #include <mutex>
+#include <string>
 
 // Each thread handles two adjacent pixels so that every B value read from
 // shared memory feeds two FMAs.  B rows are padded to CP floats (multiple of 4).
@@ -65,19 +66,41 @@ __global__ void __launch_bounds__(256) k_sweep_fp32(const float* __restrict__ G,
   }
 }
 
+// Dynamic shared memory of the FP32 sweep: the J x CP steering table.
+static int sweep_fp32_smem(int K, int J) { return J * ((2 * K + 3) / 4 * 4) * 4; }
+
+bool sweep_fp32_fits(int K, int J) {
+  int dev = 0, optin = 48 * 1024;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return sweep_fp32_smem(K, J) <= optin;
+}
+
+// The opt-in to more than 48 KB of dynamic shared memory is a per-device
+// function attribute: set it once per (device, K).
+static std::mutex g_attr_mutex;
+static uint32_t g_attr_set[256] = {};   // bit K set: done on that device ordinal
+
 template <int K>
-static void launch_sweep_fp32(const float* G, long long P, int J, const float* B, float* maxv, int32_t* argmax,
+static bool sweep_fp32_optin(int dev) {
+  if (dev < 0 || dev >= 256) return false;
+  std::lock_guard<std::mutex> lock(g_attr_mutex);
+  if (g_attr_set[dev] & (1u << K)) return true;
+  int optin = 48 * 1024;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (cudaFuncSetAttribute(k_sweep_fp32<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+    return false;
+  g_attr_set[dev] |= 1u << K;
+  return true;
+}
+
+template <int K>
+static bool launch_sweep_fp32(const float* G, long long P, int J, const float* B, float* maxv, int32_t* argmax,
                               cudaStream_t st) {
-  constexpr int CP = (2 * K + 3) / 4 * 4;
-  const int smem = J * CP * 4;
-  static const bool once = (smem > 0 ? cudaFuncSetAttribute(k_sweep_fp32<K>,
-                                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                            227 * 1024)
-                                     : cudaSuccess,
-                            true);
-  (void)once;
+  const int smem = sweep_fp32_smem(K, J);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
+  if (smem > 48 * 1024 && !sweep_fp32_optin<K>(dev)) return false;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long npairs = (P + 1) / 2;
   long long blocks = (npairs + 255) / 256;
@@ -85,13 +108,14 @@ static void launch_sweep_fp32(const float* G, long long P, int J, const float* B
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   k_sweep_fp32<K><<<(unsigned)blocks, 256, smem, st>>>(G, P, J, B, maxv, argmax);
+  return true;
 }
 
 bool sweep_fp32(const float* G, long long P, int K, int J, const float* B, int cp, float* maxv, int32_t* argmax,
                 cudaStream_t st) {
   (void)cp;
   switch (K) {
-#define EXT_SWEEP_CASE(KK) case KK: launch_sweep_fp32<KK>(G, P, J, B, maxv, argmax, st); return true;
+#define EXT_SWEEP_CASE(KK) case KK: return launch_sweep_fp32<KK>(G, P, J, B, maxv, argmax, st);
     EXT_SWEEP_CASE(1) EXT_SWEEP_CASE(2) EXT_SWEEP_CASE(3) EXT_SWEEP_CASE(4)
     EXT_SWEEP_CASE(5) EXT_SWEEP_CASE(6) EXT_SWEEP_CASE(7) EXT_SWEEP_CASE(8)
     EXT_SWEEP_CASE(9) EXT_SWEEP_CASE(10) EXT_SWEEP_CASE(11) EXT_SWEEP_CASE(12)
@@ -141,13 +165,14 @@ ext_status noalloc_table(float** out) {
   return EXT_OK;
 }
 
-bool on_device(const void* p) {
+// Device memory of `dev` (the current device) or managed memory.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
 }
 }  // namespace
 
@@ -162,9 +187,22 @@ extern "C" ext_status ext_sweep_so2_noalloc(const float* G, int64_t n_pix, int K
     return EXT_ERR_UNSUPPORTED;
   }
   if (n_pix == 0) return EXT_OK;
-  if (!G || !max_out || !argmax || !on_device(G) || !on_device(max_out) || !on_device(argmax)) {
-    ext_set_error("ext_sweep_so2_noalloc: G, max_out and argmax must be device buffers");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    ext_set_error("ext_sweep_so2_noalloc: no usable current device");
+    return EXT_ERR_CUDA;
+  }
+  if (!G || !max_out || !argmax || !on_device(G, dev) || !on_device(max_out, dev) || !on_device(argmax, dev)) {
+    ext_set_error("ext_sweep_so2_noalloc: G, max_out and argmax must be device buffers of the current device");
     return EXT_ERR_INVALID_ARG;
+  }
+  // An error left by earlier, unrelated work on this thread would be read
+  // below as this call's own: report it and leave it in place for its owner.
+  cudaError_t prior = cudaPeekAtLastError();
+  if (prior != cudaSuccess) {
+    ext_set_error((std::string("ext_sweep_so2_noalloc: a CUDA error from earlier work is pending on this thread: ") +
+                   cudaGetErrorString(prior)).c_str());
+    return EXT_ERR_CUDA;
   }
   float* table = nullptr;
   ext_status s = noalloc_table(&table);

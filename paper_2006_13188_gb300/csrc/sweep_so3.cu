@@ -285,9 +285,7 @@ void sweep_so3_tc(const float* G, long long P, int C, int cpad, const unsigned c
   const int ntn = (J + TN - 1) / TN, nkc = (cpad + TKC - 1) / TKC;
   // two blocks per SM share the 512 TMEM columns: request shared memory accordingly
   constexpr int request = 100 * 1024;
-  static const bool once =
-      (cudaFuncSetAttribute(k_sweep_so3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, request), true);
-  (void)once;
+  ext_smem_optin((const void*)k_sweep_so3_tc, request);
   const long long ntm = (P + TM - 1) / TM;
   const int nsplit = keys ? sweep_so3_tc_split(P, J, sms) : 1;
   long long grid = ((long long)sms * 2 + nsplit - 1) / nsplit;

@@ -58,7 +58,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t phase) {
 }
 
 // Waits for the mbarrier phase; gives up after `limit_ns` and reports it.
+// The budget comes from the plan's status block (byte 8) when it sets one.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t addr, uint32_t phase, uint64_t limit_ns, int* err) {
+  if (mbar_try_wait(addr, phase)) return true;
+  if (err) {
+    const uint64_t b = *reinterpret_cast<const volatile unsigned long long*>(err + 2);
+    if (b) limit_ns = b;
+  }
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(addr, phase)) {
     if (global_ns() - t0 > limit_ns) {
@@ -249,9 +255,7 @@ bool launch_tc(const float* G, long long P, int K, int J, const float* B, int cp
   constexpr int per_sm = (512 / TCOLS) < 6 ? (512 / TCOLS) : 6;
   constexpr int floor_bytes = (220 * 1024) / per_sm;
   constexpr int request = bytes < floor_bytes ? floor_bytes : bytes;
-  static const bool once =
-      (cudaFuncSetAttribute(k_sweep_tc<KC, JP>, cudaFuncAttributeMaxDynamicSharedMemorySize, request), true);
-  (void)once;
+  if (!ext_smem_optin((const void*)k_sweep_tc<KC, JP>, request)) return false;
   const long long ntiles = (P + TILE_M - 1) / TILE_M;
   long long grid = (long long)sms * per_sm;
   if (grid > ntiles) grid = ntiles;
@@ -478,9 +482,7 @@ bool launch_tc2(const float* G, long long P, int K, int J, const float* B, int c
   if (P % 4 != 0 || !make_tmap_2d_f32(G, (unsigned long long)P, (unsigned long long)(2 * K + 1),
                                       (unsigned long long)P * 4, TILE_M, (unsigned)(2 * K + 1), &tm))
     return false;
-  static const bool once =
-      (cudaFuncSetAttribute(k_sweep_tc2<KC, JP, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM), true);
-  (void)once;
+  if (!ext_smem_optin((const void*)k_sweep_tc2<KC, JP, NST>, CF::SMEM)) return false;
   const long long ntiles = (P + TILE_M - 1) / TILE_M;
   const int per_sm = (227 * 1024) / (CF::SMEM + 1024) < 1 ? 1 : (227 * 1024) / (CF::SMEM + 1024);
   long long grid = (long long)sms * (per_sm < 512 / CF::TCOLS ? per_sm : 512 / CF::TCOLS);

@@ -41,12 +41,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t phase) {
   return done != 0;
 }
 
-// false (and *err = timeout) if the phase did not complete within limit_ns
+// The status block a kernel reports into holds the status word (int, at
+// byte 0) and the plan's wait budget in ns (uint64, at byte 8; 0: none set).
+__device__ __forceinline__ uint64_t wait_budget(const int* err, uint64_t dflt) {
+  if (!err) return dflt;
+  const uint64_t b = *reinterpret_cast<const volatile unsigned long long*>(err + 2);
+  return b ? b : dflt;
+}
+
+// false (and *err = code) if the phase did not complete within the plan's
+// wait budget (limit_ns where the status block sets none); the budget and the
+// start time are read only once the first test has failed
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t addr, uint32_t phase, uint64_t limit_ns, int* err,
                                                   int code) {
+  if (mbar_try_wait(addr, phase)) return true;
+  const uint64_t limit = wait_budget(err, limit_ns);
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(addr, phase)) {
-    if (global_ns() - t0 > limit_ns) {
+    if (global_ns() - t0 > limit) {
       atomicExch(err, code);
       return false;
     }

@@ -4,11 +4,16 @@ allocator, or they cannot afford the synchronisation cudaMalloc implies).
 
 It must give the same maxima and argmax as the planned ext_sweep_so2 (FP32)
 on two calls in a row -- the second with a different bandwidth and angle
-count, so that the shared scratch table really is rewritten per call.  This
-file is collected last on purpose.
+count, so that the shared scratch table really is rewritten per call -- and
+agree with the FP64 oracle's steering sum (maxima within 1e-5 of the score
+scale, argmax identical outside the 1e-6 tie window), so that an error
+shared by the two entry points' table or kernel would not pass.  This file
+is collected last on purpose.
 """
 import numpy as np
 import pytest
+
+from oracle.so2 import sweep_from_components
 
 torch = pytest.importorskip("torch")
 
@@ -39,6 +44,14 @@ def test_noalloc_sweep_matches_planned_sweep_on_two_calls():
         scale = np.abs(r).max()
         assert np.max(np.abs(g - r)) <= 1e-5 * scale, (K, J)
         assert np.array_equal(got_arg.cpu().numpy(), ref_arg.cpu().numpy()), (K, J)
+        G64 = G.cpu().numpy().astype(np.float64)
+        Gc = [G64[0]] + [G64[2 * k - 1] + 1j * G64[2 * k] for k in range(1, K + 1)]
+        S = sweep_from_components(Gc, K, J).real.T
+        oscale = np.abs(S).max()
+        assert np.max(np.abs(g - S.max(axis=1))) <= 1e-5 * oscale, (K, J)
+        srt = np.sort(S, axis=1)
+        clear = (srt[:, -1] - srt[:, -2]) > 1e-6 * oscale
+        assert np.all(got_arg.cpu().numpy()[clear] == S.argmax(axis=1)[clear]), (K, J)
     plan.close()
 
 
