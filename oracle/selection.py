@@ -15,6 +15,12 @@ largest coefficients), test infrastructure only.
   angle-independent mean) is always kept, and the remaining budget - 1
   components are the k >= 1 of largest E_k (ties to the smaller k).
 * Subset sweep: S(p, j) = G_0(p) + 2 sum_{k in S, k >= 1} Re(e^{ik alpha_j} G_k(p)).
+* The alternative the paper compares against (Fig. f:frequency): with a
+  budget of B standard correlations, correlate the image with B rotated
+  copies of the pattern itself (no band limit), alpha_j = 2 pi j / B, and
+  keep per pixel the largest response.  The copies are the sampled pattern
+  rotated by cubic-spline interpolation (a library step), the correlations
+  FFTs (a library step).
 """
 from __future__ import annotations
 
@@ -76,3 +82,42 @@ def sweep_subset_from_components(G, ks, J: int):
     keep = set(ks)
     Gs = [G[k] if k in keep else np.zeros_like(G[k]) for k in range(K + 1)]
     return sweep_from_components(Gs, K, J).real
+
+
+def rotate_pattern(img, alpha):
+    """The sampled pattern rotated by alpha, (T_alpha P)(d) = P(R(-alpha) d) on
+    the same (2R+1)^2 box (d = (column, row) offset from the centre), by cubic
+    spline interpolation (scipy.ndimage.map_coordinates; zero outside)."""
+    from scipy import ndimage
+    img = np.asarray(img, np.float64)
+    n = img.shape[0]
+    R = (n - 1) // 2
+    dy, dx = np.mgrid[-R:R + 1, -R:R + 1].astype(np.float64)
+    c, s = np.cos(alpha), np.sin(alpha)
+    x = c * dx + s * dy                     # R(-alpha) d
+    y = -s * dx + c * dy
+    return ndimage.map_coordinates(img, [y + R, x + R], order=3, mode="constant", cval=0.0)
+
+
+def rotated_copies_sweep(H, pattern, B: int, workers: int = -1):
+    """Max over B rotated copies of the pattern of the plain correlation
+    sum_d H(p + d) (T_{alpha_j} P)(d), alpha_j = 2 pi j / B; returns (max,
+    first argmax j).  Periodic, the box wrapped as in the other operators."""
+    import scipy.fft as sfft
+    H = np.asarray(H, np.float64)
+    h, w = H.shape
+    n = np.shape(pattern)[0]
+    R = (n - 1) // 2
+    dy, dx = np.mgrid[-R:R + 1, -R:R + 1]
+    Hf = sfft.rfft2(H, workers=workers)
+    best = np.full((h, w), -np.inf)
+    arg = np.zeros((h, w), np.int64)
+    for j in range(B):
+        f = rotate_pattern(pattern, 2 * np.pi * j / B)
+        grid = np.zeros((h, w))
+        np.add.at(grid, (dy.ravel() % h, dx.ravel() % w), f.ravel())
+        s = sfft.irfft2(Hf * np.conj(sfft.rfft2(grid, workers=workers)), s=(h, w), workers=workers)
+        upd = s > best
+        arg = np.where(upd, j, arg)
+        best = np.where(upd, s, best)
+    return best, arg

@@ -98,3 +98,57 @@ def test_subset_rejects_bad_lists(ec, plan):
     for ks in ([], [1, 2], [0, 2, 2], [0, 3, 1], [0, 5]):
         with pytest.raises(ec.ExtError):
             ec.ext_corr_so2_subset(plan, H, 32, 32, F, ks, 8, mx, am, ec.EXT_PREC_FP32)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _detected(resp, centres, radius):
+    """Planted centres among the len(centres) strongest local maxima (peaks
+    at least one box apart, periodic), within 2 px."""
+    from scipy import ndimage
+    h, w = resp.shape
+    mx = ndimage.maximum_filter(resp, size=2 * radius + 1, mode="wrap")
+    pk = np.argwhere(resp == mx)
+    top = pk[np.argsort(-resp[pk[:, 0], pk[:, 1]])[:len(centres)]]
+    found = 0
+    for c in centres:
+        d = np.abs(top - np.asarray(c))
+        d = np.minimum(d, np.array([h, w]) - d)
+        found += bool(np.any(d.max(axis=1) <= 2))
+    return found
+
+
+def test_band_limited_budget_beats_rotated_copies(ec, plan):
+    """Fig. f:frequency (Sec. 5 "Band-Limiting Revisited"): with the same
+    number B of standard correlations, steering the B largest-energy angular
+    components (the GPU's subset sweep over 64 angles) approximates exact
+    rotation-independent matching -- the maximum over 128 rotated copies of a
+    pattern that is not band-limited -- better than correlating with B
+    rotated copies, and finds every planted pattern from a smaller budget."""
+    from oracle.selection import rotated_copies_sweep
+    prob = synth.so2_match_problem(seed=77, size=512, n_plant=8, radius=24, K=32, J=64, blur=1.5)
+    H, T, R = prob["H"], prob["template"], prob["radius"]
+    truth, _ = rotated_copies_sweep(H, T, 128)
+    F = ec.FilterSO2.sampled(T, 32, prob["dr"], prob["n_theta"])
+    E = ec.ext_filter_so2_energy(plan, F)
+    mx = torch.empty((512, 512), dtype=torch.float32, device="cuda")
+    am = torch.empty((512, 512), dtype=torch.int32, device="cuda")
+    Hd = dev(H)
+    last = None
+    for B in (2, 3, 5, 9, 13):
+        ks = ec.ext_select_components(E, B)
+        ec.ext_corr_so2_subset(plan, Hd, 512, 512, F, ks, 64, mx, am, ec.EXT_PREC_FP32)
+        plan.sync()
+        bl = mx.cpu().numpy().astype(np.float64)
+        rot, _ = rotated_copies_sweep(H, T, B)
+        e_bl, e_rot = _rel(bl, truth), _rel(rot, truth)
+        d_bl, d_rot = _detected(bl, prob["centres"], R), _detected(rot, prob["centres"], R)
+        print(f"budget {B}: components {ks}: error {e_bl:.3f}, {d_bl}/8 found; "
+              f"{B} rotated copies: error {e_rot:.3f}, {d_rot}/8 found")
+        assert e_bl < e_rot
+        assert d_bl == 8
+        if last is not None:
+            assert e_bl < last
+        last = e_bl

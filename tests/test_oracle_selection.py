@@ -55,3 +55,46 @@ def test_subset_sweep_limits():
                                sweep_from_components(G, K, J).real, atol=1e-12)
     S0 = sweep_subset_from_components(G, [0], J)
     np.testing.assert_allclose(S0, np.broadcast_to(G[0].real, S0.shape), atol=1e-12)
+
+
+def test_rotate_pattern_quarter_turn_and_identity():
+    """Rotating the sampled pattern by 0 returns it and by a quarter turn is
+    the exact lattice rotation d -> R(-pi/2) d (spline interpolation is exact
+    at lattice points); the rotated copy of a pattern sampled from an
+    analytic band-limited filter matches that filter's rotation."""
+    from oracle.selection import rotate_pattern
+    rng = np.random.default_rng(3)
+    P = synth.smooth_random_template(rng, 10, 2.0)
+    np.testing.assert_allclose(rotate_pattern(P, 0.0), P, atol=1e-12)
+    q = rotate_pattern(P, np.pi / 2)
+    R = 10
+    for dy in range(-R, R + 1, 3):
+        for dx in range(-R, R + 1, 4):
+            # R(-pi/2) (dx, dy) = (dy, -dx)
+            assert abs(q[dy + R, dx + R] - P[-dx + R, dy + R]) < 1e-9
+
+
+def test_rotated_copies_sweep_matches_direct_correlation():
+    """B = 1 is the plain correlation with the pattern (brute force), and
+    with B = 4 the maximum is over the four exact quarter turns."""
+    from oracle.selection import rotate_pattern, rotated_copies_sweep
+    rng = np.random.default_rng(4)
+    P = synth.smooth_random_template(rng, 4, 1.0)
+    H = rng.standard_normal((14, 12))
+    R = 4
+    dy, dx = np.mgrid[-R:R + 1, -R:R + 1]
+
+    def corr(f):
+        out = np.zeros_like(H)
+        for a, b, v in zip(dy.ravel(), dx.ravel(), f.ravel()):
+            out += np.roll(H, (-a, -b), axis=(0, 1)) * v
+        return out
+    best1, arg1 = rotated_copies_sweep(H, P, 1)
+    np.testing.assert_allclose(best1, corr(P), atol=1e-10)
+    assert np.all(arg1 == 0)
+    best4, arg4 = rotated_copies_sweep(H, P, 4)
+    ref = np.stack([corr(rotate_pattern(P, np.pi * j / 2)) for j in range(4)])
+    np.testing.assert_allclose(best4, ref.max(axis=0), atol=1e-10)
+    np.testing.assert_array_equal(arg4, ref.argmax(axis=0))
+    quarter = np.stack([corr(np.rot90(P, j)) for j in range(4)])
+    np.testing.assert_allclose(np.sort(ref, axis=0), np.sort(quarter, axis=0), atol=1e-9)
