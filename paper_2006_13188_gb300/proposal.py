@@ -52,6 +52,25 @@ def training_rows(plan, V, shape, tables, dr, radius, grid, vox, precision=b.EXT
     return X, q, mx[vt.long()].clone()
 
 
+def training_set(plan, problems, grid, reach=2, precision=b.EXT_PREC_BF16X3):
+    """Rows, labels and the grid maxima at the planted centres from planted
+    volumes (dicts with V, centres, tables, dr, radius, e.g. from
+    synth.so3_training_volumes): every planted centre and its (2 reach + 1)^3
+    neighbourhood.  Returns (X, q) as device tensors and the centre maxima."""
+    import torch
+    rows, labels, peaks = [], [], []
+    mid = ((2 * reach + 1) ** 3) // 2
+    for prob in problems:
+        shape = prob["V"].shape
+        vox = neighbourhood_voxels(prob["centres"], shape, reach)
+        V = torch.from_numpy(np.ascontiguousarray(prob["V"])).cuda()
+        X, q, mx = training_rows(plan, V, shape, prob["tables"], prob["dr"], prob["radius"], grid, vox, precision)
+        rows.append(X)
+        labels.append(q)
+        peaks.extend(mx.cpu().numpy()[mid::(2 * reach + 1) ** 3].tolist())
+    return torch.cat(rows), torch.cat(labels), np.asarray(peaks)
+
+
 def train(net, X, q, L, rows, Q, steps, batch, lrs=(1e-3, 2.5e-4)):
     """Adam on (X, q) with rotation augmentation, the steps split evenly over
     the learning rates `lrs`; rows (int32 [steps*batch]) and Q (float32

@@ -532,6 +532,14 @@ def so3_match_problem(seed: int | None = None, size: int = 128, n_plant: int = 1
                 centres=np.array(centres), quats=quats)
 
 
+def so3_training_volumes(seed: int, tables, n_volumes: int = 64, size: int = 64, n_plant: int = 6):
+    """The proposal network's training data source: n_volumes planted volumes
+    (so3_match_problem with seeds seed, seed + 1, ...) sharing one filter,
+    generated one at a time."""
+    for i in range(n_volumes):
+        yield so3_match_problem(seed=seed + i, size=size, n_plant=n_plant, L=len(tables) - 1, tables=tables)
+
+
 def aniso_gauss_template(sigma_u: float, sigma_v: float, radius: int):
     """The anisotropic Gaussian exp(-x^2 / 2 sigma_u^2 - y^2 / 2 sigma_v^2)
     sampled on the (2R+1)^2 box (x = column offset, y = row offset): the

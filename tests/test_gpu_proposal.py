@@ -345,30 +345,23 @@ def test_refinement_matches_oracle(ec, plan):
 
 @pytest.fixture(scope="module")
 def trained(ec, plan):
-    """A network trained on two planted 64^3 volumes (same filter as the test
-    volume, other centres and rotations): rows = channels at the planted
-    centres and their 5^3 neighbourhoods; labels = the grid argmax refined
-    on the GPU; rotation augmentation on every step."""
+    """A network trained on 64 method-generated volumes (64^3, 6 planted
+    templates each, the same filter as the held-out 128^3 test volume, other
+    centres and rotations): rows = channels at the planted centres and their
+    5^3 neighbourhoods; labels = the grid argmax refined on the GPU; rotation
+    augmentation on every step."""
     from paper_2006_13188_gb300 import proposal
     tables = synth.so3_filter_tables(1306, L6, 8.0, 0.125)
     grid = synth.so3_rotation_grid()
-    rows, labels, peaks = [], [], []
-    for seed in (401, 402):
-        prob = synth.so3_match_problem(seed=seed, size=64, n_plant=6, L=L6, tables=tables)
-        vox = proposal.neighbourhood_voxels(prob["centres"], (64, 64, 64), reach=2)
-        X, q, mx = proposal.training_rows(plan, dev(prob["V"]), (64, 64, 64), tables, prob["dr"], prob["radius"],
-                                          grid, vox)
-        rows.append(X)
-        labels.append(q)
-        peaks.extend(mx.cpu().numpy()[62::125].tolist())      # the centre is voxel 62 of each 5^3 block
-    X, qt = torch.cat(rows), torch.cat(labels)
+    X, qt, peaks = proposal.training_set(plan, synth.so3_training_volumes(4000, tables, 64), grid)
     net = ec.MLP(plan, NCH, 256)
     net.set_params(synth.mlp_init(11, NCH, 256))
     steps, batch = 6000, 512
     r, Q = synth.training_draws(12, X.shape[0], steps, batch)
     losses = proposal.train(net, X, qt, L6, dev(r), dev(Q), steps, batch)
     bound = 0.5 * float(np.median(peaks))
-    print(f"training: {X.shape[0]} rows, loss {losses[:50].mean():.4f} -> {losses[-50:].mean():.4f}, B = {bound:.4f}")
+    curve = " ".join(f"{losses[i:i + 500].mean():.3f}" for i in range(0, steps, 500))
+    print(f"training: {X.shape[0]} rows from 64 volumes, loss per 500 steps {curve}, B = {bound:.4f}")
     return dict(net=net, bound=bound, tables=tables, grid=grid, losses=losses)
 
 
