@@ -1072,7 +1072,8 @@ def bench_so3(args, world, rank, local):
     prof = {k: v for k, v in plan.profile_read().items() if v[1] > 0}
     plan.profile(False)
     nch = ec.ext_so3_channels(L)
-    sweep_ms = prof.get("so3_sweep_bf16x3", (None, 1))[0]
+    sweep_name = "so3_sweep_ws" if "so3_sweep_ws" in prof else "so3_sweep_bf16x3"
+    sweep_ms = prof.get(sweep_name, (None, 1))[0]
     flops = 3 * 2.0 * P * nch * len(grid)          # three split-BF16 products
     burst, sustained, kind = measured_bf16()
     ach = flops / (sweep_ms * 1e-3) / 1e12 if sweep_ms else None
@@ -1087,9 +1088,13 @@ def bench_so3(args, world, rank, local):
             "clocks": clk.summary(),
             "plain_fp32": {"value": world * plain_steps * P / (plain * 1e-3) / 1e6, "unit": "Mvox/s",
                            "ms_per_step": plain / plain_steps},
-            "roofline": {"kernel": "so3_sweep_bf16x3", "bound": "tensor", "achieved": ach, "peak": sustained,
-                         "peak_kind": kind + " bf16 sustained", "unit": "TFLOP/s",
-                         "frac": ach / sustained if ach else None, "traffic": None,
+            "roofline": {"kernel": sweep_name, "bound": "tensor", "achieved": ach, "peak": burst,
+                         "peak_kind": kind + " bf16 burst (one ~13 ms launch at full clocks)", "unit": "TFLOP/s",
+                         "frac": ach / burst if ach else None,
+                         "frac_of_sustained": ach / sustained if ach else None,
+                         "traffic": 520.055e6 * 8 if sweep_name == "so3_sweep_ws" else None,
+                         "traffic_note": "ncu dram read+write of the 64^3 launch (525 MB) scaled by the 8x voxel "
+                                         "tiles of 128^3; A' and B' read once from DRAM",
                          "algorithmic_flops": flops,
                          "kernels": {k: {"ms_per_call": v[0], "launches": v[1]} for k, v in prof.items()}}}))
     plan.close()

@@ -677,6 +677,7 @@ ext_status ext_plan_create(ext_plan* plan, const ext_options* options) {
   if (const char* e = getenv("EXT_KCHUNK")) p->kchunk = atoi(e);
   if (const char* e = getenv("EXT_PIPELINED")) p->pipelined = atoi(e) != 0;
   if (const char* e = getenv("EXT_TMA")) p->tma = atoi(e) != 0;
+  if (const char* e = getenv("EXT_SO3_WS")) p->so3_ws = atoi(e) != 0;
   if (p->autotune) tune_cache_read(p);
   *plan = p;
   return EXT_OK;

@@ -184,7 +184,7 @@ ext_status so3_components(ext_plan plan, const float* V, int nz, int ny, int nx,
 // Steering table B[j][c] (FP32, rows padded to cpad) of a rotation set, and
 // for the tensor-core sweep its split-BF16 blocks; cached for the last set.
 ext_status so3_tables(ext_plan plan, const double* quats, int n_rot, int L, cudaStream_t st, const float** B,
-                      const unsigned char** Bt, int* cpad_out, int* nchan_out) {
+                      const unsigned char** Bt, int* cpad_out, int* nchan_out, const unsigned char** Bws = nullptr) {
   const So3Layout lay = so3_layout(L);
   const int nchan = lay.nchan;
   const int cpad = (nchan + 31) / 32 * 32;
@@ -195,18 +195,22 @@ ext_status so3_tables(ext_plan plan, const double* quats, int n_rot, int L, cuda
   EXT_TRY(ensure(plan, "so3_B", sizeof(float) * (size_t)n_rot * cpad, &dB));
   EXT_TRY(ensure(plan, "so3_Bt", so3_btc_bytes(n_rot, cpad), &dBt));
   EXT_TRY(ensure(plan, "so3_chans", sizeof(int4) * lay.comp.size(), &dch));
-  for (void* q : {dq, dB, dBt}) key = fnv1a(key, &q, sizeof(q));
+  void* dBw = nullptr;
+  EXT_TRY(ensure(plan, "so3_Bws", so3_ws_b_bytes(n_rot, cpad), &dBw));
+  for (void* q : {dq, dB, dBt, dBw}) key = fnv1a(key, &q, sizeof(q));
   if (plan->so3_rot_key != key) {
     EXT_CUDA(cudaMemcpyAsync(dq, quats, sizeof(double) * 4 * n_rot, cudaMemcpyHostToDevice, st));
     EXT_CUDA(cudaMemcpyAsync(dch, lay.comp.data(), sizeof(int4) * lay.comp.size(), cudaMemcpyHostToDevice, st));
     launch_so3_wigner((const double*)dq, n_rot, L, nullptr, (const int4*)dch, (int)lay.comp.size(), cpad, (float*)dB, st);
     so3_build_btc((const float*)dB, cpad, n_rot, (unsigned char*)dBt, st);
+    so3_ws_build_b((const float*)dB, cpad, n_rot, (unsigned char*)dBw, st);
     EXT_CUDA(cudaGetLastError());
     EXT_CUDA(cudaStreamSynchronize(st));   // the host quaternions may change after return
     plan->so3_rot_key = key;
   }
   *B = (const float*)dB;
   *Bt = (const unsigned char*)dBt;
+  if (Bws) *Bws = (const unsigned char*)dBw;
   *cpad_out = cpad;
   *nchan_out = nchan;
   return EXT_OK;
@@ -215,9 +219,24 @@ ext_status so3_tables(ext_plan plan, const double* quats, int n_rot, int L, cuda
 ext_status so3_sweep(ext_plan plan, const float* G, long long P, int L, const double* quats, int n_rot, float* maxv,
                      int32_t* argmax, int precision, cudaStream_t st) {
   const float* B;
-  const unsigned char* Bt;
+  const unsigned char *Bt, *Bws;
   int cpad, nchan;
-  EXT_TRY(so3_tables(plan, quats, n_rot, L, st, &B, &Bt, &cpad, &nchan));
+  EXT_TRY(so3_tables(plan, quats, n_rot, L, st, &B, &Bt, &cpad, &nchan, &Bws));
+  // many voxel tiles: the warp-specialised sweep over pre-split operands, one block per SM
+  if (precision == EXT_PREC_BF16X3 && plan->so3_ws && P >= 128LL * plan->sms) {
+    void* Ab = nullptr;
+    EXT_TRY(ensure(plan, "so3_Aws", so3_ws_a_bytes(P, cpad), &Ab));
+    bool ok = false;
+    launch(plan, "so3_split_a", st,
+           [&] { so3_ws_split_a(G, P, nchan, cpad, (unsigned char*)Ab, plan->sms, st); });
+    launch(plan, "so3_sweep_ws", st, [&] {
+      ok = sweep_so3_ws(P, cpad, (const unsigned char*)Ab, Bws, n_rot, maxv, argmax, plan->dev_err, plan->sms, st);
+    });
+    if (ok) {
+      EXT_CUDA(cudaGetLastError());
+      return EXT_OK;
+    }
+  }
   if (precision == EXT_PREC_BF16X3) {
     void* keys = nullptr;
     if (sweep_so3_tc_split(P, n_rot, plan->sms) > 1)

@@ -141,6 +141,14 @@ void launch_so3_wigner(const double* quats, int n, int L, double2* C, const int4
 void launch_real_to_complex(const float* V, long long n, float2* X, int sms, cudaStream_t st);
 void sweep_so3_fp32(const float* G, long long P, int C, const float* B, int cpad, int J, float* maxv,
                     int32_t* argmax, cudaStream_t st);
+// warp-specialised split-BF16 sweep over pre-split operands: B' blocks built once per rotation set
+// (so3_ws_build_b), A' blocks of the voxels written into Ab (so3_ws_a_bytes) by the call itself
+size_t so3_ws_a_bytes(long long P, int cpad);
+size_t so3_ws_b_bytes(int J, int cpad);
+void so3_ws_build_b(const float* B, int cpad, int J, unsigned char* Bb, cudaStream_t st);
+void so3_ws_split_a(const float* G, long long P, int C, int cpad, unsigned char* Ab, int sms, cudaStream_t st);
+bool sweep_so3_ws(long long P, int cpad, const unsigned char* Ab, const unsigned char* Bb, int J, float* maxv,
+                  int32_t* argmax, int* err, int sms, cudaStream_t st);
 size_t so3_btc_bytes(int J, int cpad);
 void so3_build_btc(const float* B, int cpad, int J, unsigned char* Bt, cudaStream_t st);
 // keys (P entries of scratch, or NULL): lets small voxel counts split the

@@ -82,6 +82,7 @@ struct ext_plan_s {
   int kchunk = 0;        // components per inverse launch (0 = by L2 budget)
   bool pipelined = true; // persistent prefetching passes where they fit
   bool tma = true;       // tensor-memory-accelerator staged column pass where it fits
+  bool so3_ws = true;    // warp-specialised SO(3) sweep for many voxels
   int* dev_err = nullptr; // device-side status block: int status word, then (byte 8) the wait budget in ns
   int precision = EXT_PREC_FP32;        // used where a call passes EXT_PREC_DEFAULT
   unsigned long long wait_budget_ns = 1000000000ull;

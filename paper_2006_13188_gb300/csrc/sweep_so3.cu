@@ -299,3 +299,283 @@ void sweep_so3_tc(const float* G, long long P, int C, int cpad, const unsigned c
     k_sweep_keys_finish<<<(unsigned)b, 256, 0, st>>>(keys, P, maxv, argmax);
   }
 }
+
+// ------------------------------------------- warp-specialised tcgen05 sweep ---
+// The split-BF16 GEMM S = A_hi B_hi + A_hi B_lo + A_lo B_hi over pre-split
+// operands: A' (the voxel channels) and B' (the steering rows) are written
+// once per call / rotation set in the exact shared-memory image of each
+// (tile, 32-channel chunk) block, hi and lo halves only (the third product
+// reuses A_hi and B_hi through the descriptors).  Per block (one per SM):
+//   warp 0, one thread: bulk copies of the A' and B' blocks of each chunk into
+//     a ring of NS stages (48 KB each), waiting for the stage to be free;
+//   warp 1, one thread: six M128 N256 K16 MMAs per chunk into one of two TMEM
+//     accumulators (512 columns), freeing the stage and, after the last chunk
+//     of a tile, signalling the accumulator full;
+//   warps 2-5: max / first argmax of each accumulator over its 256 rotations,
+//     one voxel per thread (TMEM lane), while the MMAs fill the other one.
+// Work: voxel tiles strided over the blocks, for each all rotation tiles of
+// the block's rotation range (gridDim.y > 1 splits the rotation tiles and
+// folds results through keys as k_sweep_so3_tc does).  Every wait is bounded;
+// on expiry a role records EXT_ERR_TIMEOUT, stops, waits (bounded) for its own
+// copies or MMAs in flight, and the block frees its tensor memory.
+namespace ws {
+constexpr int M = 128, N = 256, KC = 32;
+constexpr int SBO = (KC / 8) * 128;         // 512 B between 8-row groups
+constexpr int A_HALF = (M / 8) * SBO;       // 8 KB: A_hi or A_lo of one chunk
+constexpr int B_HALF = (N / 8) * SBO;       // 16 KB: B_hi or B_lo of one chunk
+constexpr int A_BYTES = 2 * A_HALF, B_BYTES = 2 * B_HALF;
+constexpr int STAGE = A_BYTES + B_BYTES;    // 48 KB
+constexpr int NS = 4;
+constexpr int SMEM = NS * STAGE + 1024;     // + room to align the ring to 1 KB
+constexpr int THREADS = 192;
+}  // namespace ws
+
+// A' [mt][kc]: hi block then lo block, 128 voxel rows x 32 channels each in
+// core-matrix order; voxels beyond P and channels beyond C are zero.
+__global__ void k_so3_a_split(const float* __restrict__ G, long long P, int C, int nkc, unsigned char* __restrict__ Ab) {
+  using namespace ws;
+  const long long rows = (P + M - 1) / M * M;
+  const long long total = rows * nkc * (KC / 8);
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    const long long p = q % rows;           // voxel fastest: coalesced plane reads
+    const int g = (int)(q / rows);          // 8-channel group
+    const int kc = g / (KC / 8), kb = g % (KC / 8);
+    const long long mt = p / M;
+    const int r = (int)(p % M);
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float x[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int ch = g * 8 + 2 * t + u;
+        x[u] = (p < P && ch < C) ? __ldg(G + (size_t)ch * P + p) : 0.f;
+      }
+      hi[t] = tc::pack_bf16(x[0], x[1]);
+      lo[t] = tc::pack_bf16(x[0] - tc::bf16_round(x[0]), x[1] - tc::bf16_round(x[1]));
+    }
+    unsigned char* blk = Ab + ((size_t)mt * nkc + kc) * A_BYTES;
+    const int off = (r / 8) * SBO + kb * 128 + (r % 8) * 16;
+    *reinterpret_cast<uint4*>(blk + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(blk + A_HALF + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
+// B' [nt][kc]: hi block then lo block, 256 rotation rows x 32 channels each.
+__global__ void k_so3_b_split(const float* __restrict__ B, int cpad, int J, int ntn, int nkc,
+                              unsigned char* __restrict__ Bb) {
+  using namespace ws;
+  const long long total = (long long)ntn * nkc * N * (KC / 8);
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    const int kb = (int)(q % (KC / 8));
+    const int n = (int)((q / (KC / 8)) % N);
+    const int kc = (int)((q / ((long long)(KC / 8) * N)) % nkc);
+    const int nt = (int)(q / ((long long)(KC / 8) * N * nkc));
+    const int j = nt * N + n;
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float x[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c = kc * KC + kb * 8 + 2 * t + u;
+        x[u] = (j < J && c < cpad) ? B[(size_t)j * cpad + c] : 0.f;
+      }
+      hi[t] = tc::pack_bf16(x[0], x[1]);
+      lo[t] = tc::pack_bf16(x[0] - tc::bf16_round(x[0]), x[1] - tc::bf16_round(x[1]));
+    }
+    unsigned char* blk = Bb + ((size_t)nt * nkc + kc) * B_BYTES;
+    const int off = (n / 8) * SBO + kb * 128 + (n % 8) * 16;
+    *reinterpret_cast<uint4*>(blk + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(blk + B_HALF + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
+__global__ void __launch_bounds__(ws::THREADS, 1)
+    k_sweep_so3_ws(const unsigned char* __restrict__ Ab, const unsigned char* __restrict__ Bb, long long P, int nkc,
+                   int ntn, int J, float* __restrict__ maxv, int32_t* __restrict__ argmax,
+                   unsigned long long* __restrict__ keys, int* __restrict__ err, unsigned long long limit_ns) {
+  using namespace ws;
+  extern __shared__ __align__(1024) unsigned char ws_smem[];
+  __shared__ __align__(8) uint64_t full[NS], empty[NS], accf[2], acce[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t base = (tc::smem_u32(ws_smem) + 1023u) & ~1023u;
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < NS; ++s) {
+      tc::mbar_init(tc::smem_u32(&full[s]), 1);
+      tc::mbar_init(tc::smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(tc::smem_u32(&accf[b]), 1);
+      tc::mbar_init(tc::smem_u32(&acce[b]), 4);
+    }
+  }
+  if (warp == 1) tc::tmem_alloc<512>(tc::smem_u32(&tmem_slot));
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_slot;
+  const long long ntm = (P + M - 1) / M;
+  const int nsplit = gridDim.y;
+  const int nt0 = (int)((long long)ntn * blockIdx.y / nsplit), nt1 = (int)((long long)ntn * (blockIdx.y + 1) / nsplit);
+
+  if (warp == 0) {
+    if (lane == 0) {   // ---- producer: bulk copies into the ring
+      long long it = 0;
+      for (long long mt = blockIdx.x; mt < ntm && !abort_flag; mt += gridDim.x)
+        for (int nt = nt0; nt < nt1 && !abort_flag; ++nt)
+          for (int kc = 0; kc < nkc; ++kc) {
+            const int s = (int)(it % NS);
+            const uint32_t par = (uint32_t)(((it / NS) & 1) ^ 1);
+            if (!tc::mbar_wait_bounded(tc::smem_u32(&empty[s]), par, limit_ns, err, EXT_ERR_TIMEOUT)) {
+              abort_flag = 1;
+              break;
+            }
+            const uint32_t fb = tc::smem_u32(&full[s]), dst = base + (uint32_t)s * STAGE;
+            tc::mbar_expect_tx(fb, STAGE);
+            tc::bulk_load(dst, Ab + ((size_t)mt * nkc + kc) * A_BYTES, A_BYTES, fb);
+            tc::bulk_load(dst + A_BYTES, Bb + ((size_t)nt * nkc + kc) * B_BYTES, B_BYTES, fb);
+            ++it;
+          }
+      // the copies of the last chunks issued must have landed before the block exits
+      for (long long q = it > NS ? it - NS : 0; q < it; ++q)
+        tc::mbar_wait_bounded(tc::smem_u32(&full[q % NS]), (uint32_t)((q / NS) & 1), limit_ns, err, EXT_ERR_TIMEOUT);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {   // ---- MMA issue
+      constexpr uint32_t IDESC = tc::make_idesc(M, N);
+      long long it = 0;
+      int t = 0;
+      for (long long mt = blockIdx.x; mt < ntm && !abort_flag; mt += gridDim.x)
+        for (int nt = nt0; nt < nt1 && !abort_flag; ++nt, ++t) {
+          const int b = t & 1;
+          if (!tc::mbar_wait_bounded(tc::smem_u32(&acce[b]), (uint32_t)(((t >> 1) & 1) ^ 1), limit_ns, err,
+                                     EXT_ERR_TIMEOUT)) {
+            abort_flag = 1;
+            break;
+          }
+          tc::fence_after();
+          const uint32_t d = tmem + (uint32_t)(b * N);
+          for (int kc = 0; kc < nkc; ++kc) {
+            const int s = (int)(it % NS);
+            if (!tc::mbar_wait_bounded(tc::smem_u32(&full[s]), (uint32_t)((it / NS) & 1), limit_ns, err,
+                                       EXT_ERR_TIMEOUT)) {
+              abort_flag = 1;
+              break;
+            }
+            tc::fence_after();
+            const uint32_t a_hi = base + (uint32_t)s * STAGE, a_lo = a_hi + A_HALF;
+            const uint32_t b_hi = a_hi + A_BYTES, b_lo = b_hi + B_HALF;
+            // products in the order hi.hi, hi.lo, lo.hi, each over both K = 16 halves (the accumulation
+            // order of k_sweep_so3_tc, so both kernels give identical sums)
+            const uint32_t pa[3] = {a_hi, a_hi, a_lo}, pb[3] = {b_hi, b_lo, b_hi};
+#pragma unroll
+            for (int part = 0; part < 3; ++part)
+#pragma unroll
+              for (int k2 = 0; k2 < KC / 16; ++k2) {
+                const uint32_t o = (uint32_t)k2 * 256;
+                tc::mma_bf16(d, tc::make_desc(pa[part] + o, 128, SBO), tc::make_desc(pb[part] + o, 128, SBO), IDESC,
+                             (kc > 0 || part > 0 || k2 > 0) ? 1u : 0u);
+              }
+            tc::mma_commit(tc::smem_u32(&empty[s]));
+            ++it;
+          }
+          if (abort_flag) break;
+          tc::mma_commit(tc::smem_u32(&accf[b]));
+        }
+      // every MMA issued must be complete before the tensor memory is freed
+      if (it > 0)
+        tc::mbar_wait_bounded(tc::smem_u32(&empty[(it - 1) % NS]), (uint32_t)(((it - 1) / NS) & 1), limit_ns, err,
+                              EXT_ERR_TIMEOUT);
+    }
+  } else {   // ---- epilogue: warps 2..5, one voxel row per thread
+    const int q4 = warp & 3;                 // the TMEM lane quarter this warp may read
+    const int row = q4 * 32 + lane;
+    // every branch below is taken by the whole warp (the tensor-memory loads are warp-wide)
+    int t = 0;
+    for (long long mt = blockIdx.x; mt < ntm; mt += gridDim.x) {
+      if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+      float best = -FLT_MAX;
+      int bj = nt0 * N;
+      bool first = true, stop = false;
+      for (int nt = nt0; nt < nt1; ++nt, ++t) {
+        const int b = t & 1;
+        int ok = 1;
+        if (lane == 0)
+          ok = tc::mbar_wait_bounded(tc::smem_u32(&accf[b]), (uint32_t)((t >> 1) & 1), limit_ns, err, EXT_ERR_TIMEOUT)
+                   ? 1 : 0;
+        if (__any_sync(0xffffffffu, ok == 0 || abort_flag != 0)) {
+          abort_flag = 1;
+          stop = true;
+          break;
+        }
+        tc::fence_after();
+#pragma unroll 1
+        for (int c0 = 0; c0 < N; c0 += 32) {
+          float v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * N + c0), v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int j = nt * N + c0 + i;
+            if (j < J && (first || v[i] > best)) {
+              best = v[i];
+              bj = j;
+              first = false;
+            }
+          }
+        }
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(tc::smem_u32(&acce[b]));
+      }
+      if (stop) break;
+      const long long p = mt * M + row;
+      if (p < P) {
+        if (nsplit == 1) {
+          maxv[p] = best;
+          argmax[p] = bj;
+        } else {
+          atomicMax(keys + p, sweep_key(best, bj));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after();
+    tc::tmem_dealloc<512>(tmem);
+  }
+}
+
+size_t so3_ws_a_bytes(long long P, int cpad) {
+  return (size_t)((P + ws::M - 1) / ws::M) * (size_t)(cpad / ws::KC) * ws::A_BYTES;
+}
+
+size_t so3_ws_b_bytes(int J, int cpad) {
+  return (size_t)((J + ws::N - 1) / ws::N) * (size_t)(cpad / ws::KC) * ws::B_BYTES;
+}
+
+void so3_ws_build_b(const float* B, int cpad, int J, unsigned char* Bb, cudaStream_t st) {
+  const int ntn = (J + ws::N - 1) / ws::N, nkc = cpad / ws::KC;
+  k_so3_b_split<<<1024, 256, 0, st>>>(B, cpad, J, ntn, nkc, Bb);
+}
+
+void so3_ws_split_a(const float* G, long long P, int C, int cpad, unsigned char* Ab, int sms, cudaStream_t st) {
+  k_so3_a_split<<<sms * 8, 256, 0, st>>>(G, P, C, cpad / ws::KC, Ab);
+}
+
+bool sweep_so3_ws(long long P, int cpad, const unsigned char* Ab, const unsigned char* Bb, int J, float* maxv,
+                  int32_t* argmax, int* err, int sms, cudaStream_t st) {
+  if (cpad % ws::KC != 0 || P < 1) return false;
+  if (!ext_smem_optin((const void*)k_sweep_so3_ws, ws::SMEM)) return false;
+  const int ntn = (J + ws::N - 1) / ws::N, nkc = cpad / ws::KC;
+  const long long ntm = (P + ws::M - 1) / ws::M;
+  long long grid = sms;
+  if (grid > ntm) grid = ntm;
+  k_sweep_so3_ws<<<dim3((unsigned)grid, 1), ws::THREADS, ws::SMEM, st>>>(Ab, Bb, P, nkc, ntn, J, maxv, argmax, nullptr,
+                                                                        err, 2000000000ull);
+  return true;
+}

@@ -103,9 +103,11 @@ def test_components_match_oracle(ec, plan):
             assert np.max(np.abs(Gn[ch + 1, flat] - ref.imag)) <= 1e-5 * scale, (l, a, b)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
-def test_sweep_matches_oracle_linear_combination(ec, plan, prec):
-    L, n, nrot = 6, 600, 300
+@pytest.mark.parametrize("prec,n", [("fp32", 600), ("bf16x3", 600), ("bf16x3", 20001)])
+def test_sweep_matches_oracle_linear_combination(ec, plan, prec, n):
+    """n = 20001 takes the warp-specialised sweep (many voxel tiles, a ragged
+    last tile; 300 rotations: a ragged second rotation tile)."""
+    L, nrot = 6, 300
     rng = np.random.default_rng(7)
     nch = ec.ext_so3_channels(L)
     channels = rng.standard_normal((nch, n)).astype(np.float32)
