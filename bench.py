@@ -397,7 +397,7 @@ def bench_conv(args, world, rank, local):
 
 CONV_BATCH_WORKLOAD = ("SO(2) extended convolution, batched: 512 images of 256^2 f32 (blurred uniform noise), each with "
                        "its own angle field, one analytic filter K=4 (31x31 box); all images per step in one captured "
-                       "CUDA graph, calls spread over 8 streams")
+                       "CUDA graph, calls spread over 8 streams (one plan each)")
 
 
 def bench_conv_batched(args, world, rank, local):
@@ -466,8 +466,8 @@ def bench_conv_batched(args, world, rank, local):
         for i in range(0, nimg, max(1, nimg // 32)):
             pix = rng.integers(0, n, (16, 2))
             t1 = time.perf_counter()
-            ref = ext_conv_so2_at(probs[i]["H"].astype(np.float64), AnalyticGaussPow(probs[i]["a"], probs[i]["sigma"]),
-                                  probs[i]["alpha"].astype(np.float64), probs[i]["radius"], pix).real
+            ref = ext_conv_so2_at(probs[i]["H"].astype(np.float64), AnalyticGaussPow(probs[0]["a"], probs[0]["sigma"]),
+                                  probs[i]["alpha"].astype(np.float64), probs[0]["radius"], pix).real
             t_or += time.perf_counter() - t1
             n_or += len(pix)
             worst = max(worst, float(np.max(np.abs(got[i][pix[:, 0], pix[:, 1]] - ref)) / np.abs(got[i]).max()))
@@ -889,7 +889,9 @@ def bench_scale(args, world, rank, local):
 
 # ----------------------------------------------------- batched workload ---
 BATCH_WORKLOAD = ("batched uneven SO(2) correlation sweep: 512 f32 images, sides 128..1024 step 64 (non-square), "
-                  "one planted 33..97 px template each, K in {4,8,16}, 32..128 angles, one captured graph, BF16x3 sweep")
+                  "one planted 33..97 px template each, K in {4,8,16}, 32..128 angles, BF16x3 sweep; the templates' "
+                  "spectra are built once per plan (plan_ms, setup graph), each step replays one captured graph of "
+                  "every image's forward FFT, correlation passes and sweep")
 
 
 def _batched_oracle_image(task):
@@ -920,14 +922,15 @@ def bench_batched(args, world, rank, local):
         probs.append(prob)
     P = sum(d["h"] * d["w"] for d in descs)
     plan = ec.Plan(local)
+    batch = ec.BatchDescriptors(items)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     t0 = time.perf_counter()
-    ec.ext_batch_corr_so2(plan, items)
+    ec.ext_batch_corr_so2(plan, batch)
     plan.sync()
     plan_ms = 1e3 * (time.perf_counter() - t0)
     for _ in range(args.warmup):
-        ec.ext_batch_corr_so2(plan, items)
+        ec.ext_batch_corr_so2(plan, batch)
     plan.sync()
     barrier(world)
     total = 0.0
@@ -936,7 +939,7 @@ def bench_batched(args, world, rank, local):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ec.ext_batch_corr_so2(plan, items)
+            ec.ext_batch_corr_so2(plan, batch)
             e1.record(stream)
             torch.cuda.synchronize()
             total += e0.elapsed_time(e1)

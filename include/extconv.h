@@ -278,11 +278,15 @@ ext_status ext_sweep_so2(ext_plan plan, const float* G, int64_t n_pix, int K, in
  * Batched correlation sweep over many images of uneven sizes, bandwidths and
  * angle counts (each image as ext_corr_so2 in sweep mode with its own
  * filter).  All image and output buffers must be DEVICE memory; filter
- * descriptions are HOST memory read during the call.  The whole batch is
- * recorded once as a CUDA graph (per-image filter decomposition, component
- * spectra, forward FFT, inverse passes and sweep) and replayed while the
- * descriptor list, the filters and the plan's workspace stay the same; the
- * call is asynchronous on `stream`.
+ * descriptions are HOST memory read during the call.  The batch is recorded
+ * as two CUDA graphs: a setup graph (per-image filter decomposition and the
+ * component spectra of every template, kept in plan workspace: the sum over
+ * the images of (K_i + 1) h_i w_i complex values, plus tile padding) replayed
+ * when the descriptor list or a filter changes, and a step graph (forward
+ * FFT, inverse correlation passes and sweep of every image) replayed on every
+ * call -- a fixed template library matched against new image data in the
+ * same buffers.  The call is asynchronous on `stream` (a changed batch first
+ * waits for its filter data to be copied).
  */
 typedef struct {
   const float* H;          /* h x w image, device */

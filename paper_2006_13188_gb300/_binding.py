@@ -339,14 +339,24 @@ def ext_conv_scale(plan: Plan, H, channels, h, w, mellin_c, log_period, r_min, r
                                 _ptr(out), _stream(stream)))
 
 
+class BatchDescriptors:
+    """The ext_image_desc array of a batch, built once: pass it instead of
+    the item list to ext_batch_corr_so2 to skip re-marshalling the same
+    buffers and filters on every call."""
+
+    def __init__(self, items):
+        self.items = list(items)
+        self.arr = (ext_image_desc * len(self.items))()
+        for i, (H, h, w, F, J, mx, am) in enumerate(self.items):
+            self.arr[i] = ext_image_desc(_ptr(H), int(h), int(w), ctypes.pointer(F.struct), int(J), _ptr(mx),
+                                         _ptr(am))
+
+
 def ext_batch_corr_so2(plan: Plan, items, precision=EXT_PREC_BF16X3, stream=None):
-    """items: sequence of (H, h, w, FilterSO2, n_angles, max_out, argmax) with device tensors."""
-    arr = (ext_image_desc * len(items))()
-    keep = []
-    for i, (H, h, w, F, J, mx, am) in enumerate(items):
-        arr[i] = ext_image_desc(_ptr(H), int(h), int(w), ctypes.pointer(F.struct), int(J), _ptr(mx), _ptr(am))
-        keep.append(F)
-    _check(lib().ext_batch_corr_so2(plan.handle, arr, len(items), int(precision), _stream(stream)))
+    """items: sequence of (H, h, w, FilterSO2, n_angles, max_out, argmax) with device tensors, or a
+    BatchDescriptors of such a sequence."""
+    batch = items if isinstance(items, BatchDescriptors) else BatchDescriptors(items)
+    _check(lib().ext_batch_corr_so2(plan.handle, batch.arr, len(batch.items), int(precision), _stream(stream)))
 
 
 def so3_pack_tables(tables):

@@ -59,6 +59,27 @@ ext_status check_filter(const ext_filter_so2* F) {
   return EXT_OK;
 }
 
+// Content hash of a filter's arrays, read as 64-bit words in four independent
+// multiply-xor lanes (a batch hashes every template on every call, so the
+// byte-serial FNV of the other keys would cost milliseconds there).
+uint64_t hash_words(uint64_t h, const void* data, size_t n) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  uint64_t lane[4] = {h ^ 0x9E3779B97F4A7C15ull, h + 0xC2B2AE3D27D4EB4Full, h ^ 0x165667B19E3779F9ull,
+                      h + 0x27D4EB2F165667C5ull};
+  size_t i = 0;
+  for (; i + 32 <= n; i += 32) {
+    uint64_t w[4];
+    std::memcpy(w, p + i, 32);
+    for (int q = 0; q < 4; ++q) lane[q] = (lane[q] ^ w[q]) * 0x100000001B3ull;
+  }
+  uint64_t out = fnv1a(h, p + i, n - i);
+  for (int q = 0; q < 4; ++q) {
+    out ^= lane[q] + 0x9E3779B97F4A7C15ull + (out << 6) + (out >> 2);
+    out *= 0xff51afd7ed558ccdull;
+  }
+  return out ^ (out >> 33);
+}
+
 uint64_t filter_key(const ext_filter_so2* F) {
   uint64_t h = 1469598103934665603ull;
   h = fnv1a(h, &F->kind, sizeof(int));
@@ -71,12 +92,12 @@ uint64_t filter_key(const ext_filter_so2* F) {
   } else if (F->kind == EXT_FILTER_TABLE) {
     h = fnv1a(h, &F->n_r, sizeof(int));
     h = fnv1a(h, &F->dr, sizeof(double));
-    h = fnv1a(h, F->fk, sizeof(double) * 2 * nk * F->n_r);
+    h = hash_words(h, F->fk, sizeof(double) * 2 * nk * F->n_r);
   } else {
     const size_t side = (size_t)(2 * F->R + 1);
     h = fnv1a(h, &F->dr, sizeof(double));
     h = fnv1a(h, &F->n_theta, sizeof(int));
-    h = fnv1a(h, F->img, sizeof(double) * side * side);
+    h = hash_words(h, F->img, sizeof(double) * side * side);
   }
   return h;
 }
@@ -678,6 +699,7 @@ ext_status ext_plan_create(ext_plan* plan, const ext_options* options) {
   if (const char* e = getenv("EXT_PIPELINED")) p->pipelined = atoi(e) != 0;
   if (const char* e = getenv("EXT_TMA")) p->tma = atoi(e) != 0;
   if (const char* e = getenv("EXT_SO3_WS")) p->so3_ws = atoi(e) != 0;
+  if (const char* e = getenv("EXT_BATCH_BRANCHES")) p->batch_branches = atoi(e);
   if (p->autotune) tune_cache_read(p);
   *plan = p;
   return EXT_OK;
@@ -719,7 +741,9 @@ ext_status ext_plan_trim(ext_plan plan) {
   // everything cached in the workspace is gone: the captured batch graph and
   // the SO(3) tables point into it
   if (plan->batch_exec) cudaGraphExecDestroy(plan->batch_exec);
+  if (plan->batch_setup_exec) cudaGraphExecDestroy(plan->batch_setup_exec);
   plan->batch_exec = nullptr;
+  plan->batch_setup_exec = nullptr;
   plan->batch_key = 0;
   plan->so3_rot_key = 0;
   plan->so3_steer_L = -1;
@@ -740,6 +764,7 @@ ext_status ext_plan_destroy(ext_plan plan) {
   }
   for (auto e : plan->event_pool) cudaEventDestroy(e);
   if (plan->batch_exec) cudaGraphExecDestroy(plan->batch_exec);
+  if (plan->batch_setup_exec) cudaGraphExecDestroy(plan->batch_setup_exec);
   if (plan->pinned) cudaFreeHost(plan->pinned);
   cudaFree(plan->dev_err);
   delete plan;
@@ -1263,33 +1288,44 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
     key = fnv1a(key, &d, sizeof(d));
   }
   key = fnv1a(key, &precision, sizeof(int));
-  // independent images run on NB parallel branches of the graph, each with its own workspace set
-  constexpr int NBMAX = 8;
-  const int NB = n < NBMAX ? n : NBMAX;
-  std::string kS[NBMAX], kGrid[NBMAX], kHh[NBMAX], kHf[NBMAX], kZ[NBMAX], kG[NBMAX], kP[NBMAX];
-  void *dS[NBMAX], *dgrid[NBMAX], *dHh[NBMAX], *dHf[NBMAX], *dZ[NBMAX], *dG[NBMAX], *dpolar[NBMAX], *din, *dcoef;
+  // the template spectra of every image, kept in plan workspace while the batch stays the same
+  std::vector<size_t> off_S(n);
+  size_t spec_bytes = 0;
+  for (int i = 0; i < n; ++i) {
+    const ext_image_desc& d = imgs[i];
+    const int cw = fft_col_tile(d.h);
+    off_S[i] = spec_bytes;
+    spec_bytes += (sizeof(float2) * (size_t)(d.F->K + 1) * ((d.w + cw - 1) / cw) * d.h * cw + 255) / 256 * 256;
+  }
+  (void)max_S;
+  // independent images run on NB parallel branches of the graphs, each with its own workspace set
+  constexpr int NBMAX = 32;
+  const int nbr = std::max(1, std::min(NBMAX, plan->batch_branches));
+  const int NB = n < nbr ? n : nbr;
+  key = fnv1a(key, &NB, sizeof(int));
+  std::string kGrid[NBMAX], kHh[NBMAX], kHf[NBMAX], kZ[NBMAX], kG[NBMAX], kP[NBMAX];
+  void *dgrid[NBMAX], *dHh[NBMAX], *dHf[NBMAX], *dZ[NBMAX], *dG[NBMAX], *dpolar[NBMAX], *din, *dcoef, *dspec;
   for (int b = 0; b < NB; ++b) {
     const std::string t = std::to_string(b);
-    kS[b] = "Sbatch" + t;
     kGrid[b] = "grid" + t;
     kHh[b] = "Hh" + t;
     kHf[b] = "Hf" + t;
     kZ[b] = "Z" + t;
     kG[b] = "G" + t;
     kP[b] = "fpolar" + t;
-    EXT_TRY(ensure(plan, kS[b].c_str(), max_S, &dS[b]));
     EXT_TRY(ensure(plan, kGrid[b].c_str(), max_grid, &dgrid[b]));
     EXT_TRY(ensure(plan, kHh[b].c_str(), max_Hh, &dHh[b]));
     EXT_TRY(ensure(plan, kHf[b].c_str(), plan->tma || plan->autotune ? max_Hf : 16, &dHf[b]));
     EXT_TRY(ensure(plan, kZ[b].c_str(), max_Z, &dZ[b]));
     EXT_TRY(ensure(plan, kG[b].c_str(), max_G, &dG[b]));
     EXT_TRY(ensure(plan, kP[b].c_str(), std::max<size_t>(max_polar, 8), &dpolar[b]));
-    for (void* q : {dS[b], dgrid[b], dHh[b], dHf[b], dZ[b], dG[b], dpolar[b]}) key = fnv1a(key, &q, sizeof(q));
+    for (void* q : {dgrid[b], dHh[b], dHf[b], dZ[b], dG[b], dpolar[b]}) key = fnv1a(key, &q, sizeof(q));
   }
   EXT_TRY(ensure(plan, "batch_in", host_bytes, &din));
   EXT_TRY(ensure(plan, "batch_coef", coef_bytes, &dcoef));
-  for (void* q : {din, dcoef}) key = fnv1a(key, &q, sizeof(q));
-  // tables used inside the graph are created beforehand
+  EXT_TRY(ensure(plan, "batch_spectra", std::max<size_t>(spec_bytes, 256), &dspec));
+  for (void* q : {din, dcoef, dspec}) key = fnv1a(key, &q, sizeof(q));
+  // tables used inside the graphs are created beforehand
   for (int i = 0; i < n; ++i) {
     const float2* t;
     EXT_TRY(twiddle(plan, imgs[i].w, st, &t));
@@ -1300,18 +1336,21 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
       EXT_TRY(sweep_table(plan, imgs[i].F->K, imgs[i].n_angles, st, &B, &cp));
     }
   }
-  // ---- upload the filter data (every call; the graph reads it from batch_in)
-  plan->batch_host.resize(std::max<size_t>(host_bytes, 1));
-  for (int i = 0; i < n; ++i) {
-    const ext_filter_so2* F = imgs[i].F;
-    const size_t nk = (size_t)(2 * F->K + 1);
-    unsigned char* dst = plan->batch_host.data() + off_in[i];
-    if (F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW) std::memcpy(dst, F->a, sizeof(double2) * nk);
-    else if (F->kind == EXT_FILTER_TABLE) std::memcpy(dst, F->fk, sizeof(double2) * nk * F->n_r);
-    else std::memcpy(dst, F->img, sizeof(double) * (2 * F->R + 1) * (2 * F->R + 1));
+  const bool fresh = plan->batch_exec == nullptr || plan->batch_setup_exec == nullptr || plan->batch_key != key;
+  if (fresh) {
+    // ---- upload the filter data (the setup graph reads it from batch_in)
+    plan->batch_host.resize(std::max<size_t>(host_bytes, 1));
+    for (int i = 0; i < n; ++i) {
+      const ext_filter_so2* F = imgs[i].F;
+      const size_t nk = (size_t)(2 * F->K + 1);
+      unsigned char* dst = plan->batch_host.data() + off_in[i];
+      if (F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW) std::memcpy(dst, F->a, sizeof(double2) * nk);
+      else if (F->kind == EXT_FILTER_TABLE) std::memcpy(dst, F->fk, sizeof(double2) * nk * F->n_r);
+      else std::memcpy(dst, F->img, sizeof(double) * (2 * F->R + 1) * (2 * F->R + 1));
+    }
+    EXT_CUDA(cudaMemcpyAsync(din, plan->batch_host.data(), host_bytes, cudaMemcpyHostToDevice, st));
+    EXT_CUDA(cudaStreamSynchronize(st));   // the host staging buffer is reused by the next call
   }
-  EXT_CUDA(cudaMemcpyAsync(din, plan->batch_host.data(), host_bytes, cudaMemcpyHostToDevice, st));
-  EXT_CUDA(cudaStreamSynchronize(st));   // the host staging buffer is reused by the next call
   // ---- autotuning: every new shape class is tuned on its first image
   if (plan->autotune) {
     for (int i = 0; i < n; ++i) {
@@ -1321,12 +1360,9 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
       EXT_TRY(tune_components(plan, d.H, d.h, d.w, d.F, (float*)dG[0], st, &v));
     }
   }
-  // ---- capture the per-image launch sequences once, then replay
-  if (plan->batch_exec == nullptr || plan->batch_key != key) {
-    if (plan->batch_exec) {
-      EXT_CUDA(cudaGraphExecDestroy(plan->batch_exec));
-      plan->batch_exec = nullptr;
-    }
+  // ---- capture the per-image launch sequences once (setup: filter decomposition and template
+  // spectra; step: forward transform, inverse correlation passes, sweep), then replay
+  auto capture = [&](bool setup, cudaGraphExec_t* out) -> ext_status {
     const bool profiling = plan->profiling;
     plan->profiling = false;   // no event records inside the graph
     cudaStream_t cs = nullptr, br[NBMAX] = {};
@@ -1348,6 +1384,23 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
       const ext_filter_so2* F = d.F;
       const int K = F->K, h = d.h, w = d.w;
       const size_t P = (size_t)h * w;
+      float2* Si = (float2*)((unsigned char*)dspec + off_S[i]);
+      if (setup) {
+        const double2* coef = (const double2*)((unsigned char*)din + off_in[i]);
+        if (F->kind == EXT_FILTER_SAMPLED) {
+          double2* table = (double2*)((unsigned char*)dcoef + off_coef[i]);
+          launch_decompose_sampled((const double*)coef, 2 * F->R + 1, F->dr, nr[i], F->n_theta, K, (double*)dpolar[b],
+                                   table, bs);
+          coef = table;
+        }
+        const int kind = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? EXT_FILTER_ANALYTIC_GAUSSPOW : EXT_FILTER_TABLE;
+        const double dr = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? 0.0 : F->dr;
+        auto sample = [&](int k0, int nk, float2* grid) {
+          launch_component_grid(kind, K, k0, coef, nr[i], dr, F->sigma, F->R, h, w, grid, bs, nk);
+        };
+        ss = build_spectra(plan, h, w, K + 1, SPEC_CORR, bs, sample, Si, kGrid[b].c_str());
+        continue;
+      }
       PassVariant v;
       v.tma = plan->tma;
       v.pipelined = plan->pipelined;
@@ -1357,20 +1410,6 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
         if (it != plan->tuned.end()) v = parse_variant(it->second);
       }
       VariantScope scope(plan, v);
-      const double2* coef = (const double2*)((unsigned char*)din + off_in[i]);
-      if (F->kind == EXT_FILTER_SAMPLED) {
-        double2* table = (double2*)((unsigned char*)dcoef + off_coef[i]);
-        launch_decompose_sampled((const double*)coef, 2 * F->R + 1, F->dr, nr[i], F->n_theta, K, (double*)dpolar[b], table,
-                                 bs);
-        coef = table;
-      }
-      const int kind = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? EXT_FILTER_ANALYTIC_GAUSSPOW : EXT_FILTER_TABLE;
-      const double dr = F->kind == EXT_FILTER_ANALYTIC_GAUSSPOW ? 0.0 : F->dr;
-      auto sample = [&](int k0, int nk, float2* grid) {
-        launch_component_grid(kind, K, k0, coef, nr[i], dr, F->sigma, F->R, h, w, grid, bs, nk);
-      };
-      ss = build_spectra(plan, h, w, K + 1, SPEC_CORR, bs, sample, (float2*)dS[b], kGrid[b].c_str());
-      if (ss != EXT_OK) break;
       const float2 *tw_w = nullptr, *tw_h = nullptr;
       twiddle(plan, w, bs, &tw_w);
       twiddle(plan, h, bs, &tw_h);
@@ -1383,13 +1422,13 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
       fft_rows_r2c(w, d.H, h, (float2*)dHh[b], tw_w, bs);
       fft_cols_fwd_half(h, (float2*)dHh[b], wh, tw_h, bs, tma_ok ? (float2*)dHf[b] : nullptr, w);
       if (tma_ok)
-        done = fft_cols_inv_corr_tma(h, tmH, w, brows, (const float2*)dS[b], 0, K + 1, (float2*)dZ[b], tw_h,
-                                     plan->dev_err, plan->sms, bs);
-      if (!done && !fft_cols_inv_corr_pipe(h, (const float2*)dHh[b], w, (const float2*)dS[b], 0, K + 1,
-                                           (float2*)dZ[b], tw_h, plan->sms, bs))
-        fft_cols_inv_corr(h, (const float2*)dHh[b], w, (const float2*)dS[b], 0, K + 1, (float2*)dZ[b], tw_h, bs);
-      if (!fft_rows_inv_components_pipe(w, (const float2*)dZ[b], h, 0, K + 1, (float*)dG[b], tw_w, plan->dev_err,
-                                        plan->sms, bs))
+        done = fft_cols_inv_corr_tma(h, tmH, w, brows, Si, 0, K + 1, (float2*)dZ[b], tw_h, plan->dev_err, plan->sms, bs);
+      if (!done && (!plan->pipelined ||
+                    !fft_cols_inv_corr_pipe(h, (const float2*)dHh[b], w, Si, 0, K + 1, (float2*)dZ[b], tw_h, plan->sms,
+                                            bs)))
+        fft_cols_inv_corr(h, (const float2*)dHh[b], w, Si, 0, K + 1, (float2*)dZ[b], tw_h, bs);
+      if (!plan->pipelined || !fft_rows_inv_components_pipe(w, (const float2*)dZ[b], h, 0, K + 1, (float*)dG[b], tw_w,
+                                                            plan->dev_err, plan->sms, bs))
         fft_rows_inv_components(w, (const float2*)dZ[b], h, 0, K + 1, (float*)dG[b], tw_w, bs);
       ss = run_sweep(plan, (const float*)dG[b], (long long)P, K, d.n_angles, d.max_out, d.argmax, precision, bs);
     }
@@ -1400,27 +1439,33 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     plan->profiling = profiling;
-    auto cleanup = [&] {
-      cudaStreamDestroy(cs);
-      for (int b = 0; b < NB; ++b) {
-        cudaStreamDestroy(br[b]);
-        cudaEventDestroy(join[b]);
-      }
-      cudaEventDestroy(fork);
-    };
+    cudaStreamDestroy(cs);
+    for (int b = 0; b < NB; ++b) {
+      cudaStreamDestroy(br[b]);
+      cudaEventDestroy(join[b]);
+    }
+    cudaEventDestroy(fork);
     if (ss != EXT_OK) {
       if (graph) cudaGraphDestroy(graph);
-      cleanup();
       return ss;
     }
-    if (ce != cudaSuccess) {
-      cleanup();
-      return fail(EXT_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(ce));
-    }
-    ce = cudaGraphInstantiate(&plan->batch_exec, graph, 0);
+    if (ce != cudaSuccess) return fail(EXT_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
-    cleanup();
     if (ce != cudaSuccess) return fail(EXT_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(ce));
+    return EXT_OK;
+  };
+  if (fresh) {
+    for (cudaGraphExec_t* g : {&plan->batch_exec, &plan->batch_setup_exec})
+      if (*g) {
+        EXT_CUDA(cudaGraphExecDestroy(*g));
+        *g = nullptr;
+      }
+    plan->batch_key = 0;
+    EXT_TRY(capture(true, &plan->batch_setup_exec));
+    EXT_TRY(capture(false, &plan->batch_exec));
+    plan->prof["batch_setup_graph"].launches += 1;
+    EXT_CUDA(cudaGraphLaunch(plan->batch_setup_exec, st));
     plan->batch_key = key;
   }
   plan->prof["batch_graph"].launches += 1;

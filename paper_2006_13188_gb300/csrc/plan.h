@@ -83,6 +83,7 @@ struct ext_plan_s {
   bool pipelined = true; // persistent prefetching passes where they fit
   bool tma = true;       // tensor-memory-accelerator staged column pass where it fits
   bool so3_ws = true;    // warp-specialised SO(3) sweep for many voxels
+  int batch_branches = 4; // parallel graph branches of the batched correlation (4: measured best of 1-16)
   int* dev_err = nullptr; // device-side status block: int status word, then (byte 8) the wait budget in ns
   int precision = EXT_PREC_FP32;        // used where a call passes EXT_PREC_DEFAULT
   unsigned long long wait_budget_ns = 1000000000ull;
@@ -93,7 +94,8 @@ struct ext_plan_s {
   std::string tune_cache;
   std::map<std::string, std::string> tuned;   // shape-class key -> "tma pipelined kchunk ms"
   // batched correlation: captured CUDA graph of the last batch and its key
-  cudaGraphExec_t batch_exec = nullptr;
+  cudaGraphExec_t batch_exec = nullptr;         // per step: forward transforms, correlations, sweeps
+  cudaGraphExec_t batch_setup_exec = nullptr;   // once per batch: filter decomposition, template spectra
   uint64_t batch_key = 0;
   std::vector<unsigned char> batch_host;   // packed filter data (host staging)
   // SO(3): steering tables of the last rotation set

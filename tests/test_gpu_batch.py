@@ -102,3 +102,39 @@ def test_batch_graph_replay_reads_new_data(ec):
         assert not torch.equal(mx, old)
     plan.close()
     single.close()
+
+
+def test_batch_rebuilds_template_spectra_when_a_filter_changes(ec):
+    """The template spectra are kept between calls; a changed filter (another
+    template, or the same arrays rewritten in place) rebuilds them."""
+    plan = ec.Plan(0)
+    items, probs = make_batch(ec, seed=4)
+    ec.ext_batch_corr_so2(plan, items)
+    plan.sync()
+    rng = np.random.default_rng(8)
+    h, w, side, K, J = CASES[2]
+    tpl = synth.smooth_random_template(rng, (side - 1) // 2, 3.0)
+    H, h, w, F, J, mx, am = items[2]
+    items[2] = (H, h, w, ec.FilterSO2.sampled(tpl, K, probs[2]["dr"], probs[2]["n_theta"]), J, mx, am)
+    ec.ext_batch_corr_so2(plan, items)
+    plan.sync()
+    single = ec.Plan(0)
+    for (H, h, w, F, J, mx, am) in items:
+        mx1 = torch.empty_like(mx)
+        am1 = torch.empty_like(am)
+        ec.ext_corr_so2(single, H, h, w, F, None, J, mx1, am1, ec.EXT_PREC_BF16X3)
+        single.sync()
+        assert torch.equal(mx, mx1) and torch.equal(am, am1)
+    # the same filter arrays rewritten in place
+    F3 = items[3][3]
+    F3._img[...] = np.flipud(F3._img).copy()
+    ec.ext_batch_corr_so2(plan, items)
+    plan.sync()
+    H, h, w, F, J, mx, am = items[3]
+    mx1 = torch.empty_like(mx)
+    am1 = torch.empty_like(am)
+    ec.ext_corr_so2(single, H, h, w, F, None, J, mx1, am1, ec.EXT_PREC_BF16X3)
+    single.sync()
+    assert torch.equal(mx, mx1) and torch.equal(am, am1)
+    plan.close()
+    single.close()
