@@ -76,6 +76,8 @@ def parse_args():
                          "so3conv: SO(3) extended convolution of a 128^3 volume, L=6, smooth rotation field; "
                          "similarity: smoothing of a 2048x2048x3 image under joint rotation and scale fields")
     ap.add_argument("--n-images", type=int, default=512)
+    ap.add_argument("--scale-shape", default="4096x4096",
+                    help="scale: image rows x columns (4096x4096 is the workload; smaller only for profiling captures)")
     return ap.parse_args()
 
 
@@ -813,7 +815,8 @@ def bench_scale(args, world, rank, local):
         prob = dict(img=d["img"], s=d["s"], c=synth.mellin_disk_coeffs(), log_period=8.0, r_min=1.0, r_max=16.0,
                     centre_tap=1.0)
     else:
-        prob = synth.scale_smoothing_problem(seed=synth.seed_for(3) + rank)
+        hs, ws_ = (int(v) for v in args.scale_shape.lower().split("x"))
+        prob = synth.scale_smoothing_problem(seed=synth.seed_for(3) + rank, size=(hs, ws_))
     img, s, c = prob["img"], prob["s"], prob["c"]
     h, w = s.shape
     P = h * w

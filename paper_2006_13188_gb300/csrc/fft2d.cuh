@@ -1503,14 +1503,18 @@ struct FftOps {
                                        int* err, int sms, cudaStream_t st);
 };
 
+bool ext_smem_optin(const void* func, int bytes);   // api.cu
+
+// The dynamic shared-memory opt-in is a per-device function attribute: it is
+// requested on every launch path and set once per (device, kernel, size).
 template <typename KernelT>
-static inline void ext_set_smem(KernelT kernel, int bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+static inline bool ext_set_smem(KernelT kernel, int bytes) {
+  return ext_smem_optin((const void*)kernel, bytes);
 }
 
 template <int N>
 void FftOps<N>::rows_r2c(const float* H, int h, float2* Hh, const float2* tw, cudaStream_t st) {
-  static const bool once = (ext_set_smem(k_rows_r2c<N>, C::ROW_SMEM), true);
+  const bool once = (ext_set_smem(k_rows_r2c<N>, C::ROW_SMEM), true);
   (void)once;
   const int pairs = (h + 1) / 2;
   dim3 grid((pairs + C::RL - 1) / C::RL);
@@ -1520,7 +1524,7 @@ void FftOps<N>::rows_r2c(const float* H, int h, float2* Hh, const float2* tw, cu
 template <int N>
 void FftOps<N>::rows_fwd_phase(const float* H, const float* alpha, int h, int k0, int nk, float2* A,
                                const float2* tw, cudaStream_t st) {
-  static const bool once = (ext_set_smem(k_rows_fwd_phase<N>, C::ROW_SMEM), true);
+  const bool once = (ext_set_smem(k_rows_fwd_phase<N>, C::ROW_SMEM), true);
   (void)once;
   dim3 grid(nk, (h + C::RL - 1) / C::RL);
   k_rows_fwd_phase<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, alpha, h, k0, A, tw);
@@ -1529,7 +1533,7 @@ void FftOps<N>::rows_fwd_phase(const float* H, const float* alpha, int h, int k0
 template <int N>
 void FftOps<N>::rows_c2c(const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
                          cudaStream_t st) {
-  static const bool once = (ext_set_smem(k_rows_c2c<N, false>, C::ROW_SMEM),
+  const bool once = (ext_set_smem(k_rows_c2c<N, false>, C::ROW_SMEM),
                             ext_set_smem(k_rows_c2c<N, true>, C::ROW_SMEM), true);
   (void)once;
   dim3 grid((h + C::RL - 1) / C::RL, nplanes);
@@ -1540,7 +1544,7 @@ void FftOps<N>::rows_c2c(const float2* X, int h, int nplanes, float2* Y, bool in
 template <int N>
 void FftOps<N>::rows_inv_components(const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
                                     cudaStream_t st) {
-  static const bool once = (ext_set_smem(k_rows_inv_components<N>, C::ROW_SMEM), true);
+  const bool once = (ext_set_smem(k_rows_inv_components<N>, C::ROW_SMEM), true);
   (void)once;
   dim3 grid((h + C::RL - 1) / C::RL, nk);
   k_rows_inv_components<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(Z, h, k0, G, tw);
@@ -1550,7 +1554,7 @@ template <int N>
 void FftOps<N>::rows_inv_field(const float2* Z, int h, int K, const float* alpha, float* out,
                                const float2* tw, cudaStream_t st) {
   constexpr int smem = C::ROW_SMEM + C::RL * N * 4;
-  static const bool once = (ext_set_smem(k_rows_inv_field<N>, smem), true);
+  const bool once = (ext_set_smem(k_rows_inv_field<N>, smem), true);
   (void)once;
   dim3 grid((h + C::RL - 1) / C::RL);
   k_rows_inv_field<N><<<grid, C::ROW_THREADS, smem, st>>>(Z, h, K, alpha, out, tw);
@@ -1558,7 +1562,7 @@ void FftOps<N>::rows_inv_field(const float2* Z, int h, int K, const float* alpha
 
 template <int N>
 void FftOps<N>::rows_inv_real(const float2* Y, int h, float* out, const float2* tw, cudaStream_t st) {
-  static const bool once = (ext_set_smem(k_rows_inv_real<N>, C::ROW_SMEM), true);
+  const bool once = (ext_set_smem(k_rows_inv_real<N>, C::ROW_SMEM), true);
   (void)once;
   dim3 grid((h + C::RL - 1) / C::RL);
   k_rows_inv_real<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(Y, h, out, tw);
@@ -1566,7 +1570,7 @@ void FftOps<N>::rows_inv_real(const float2* Y, int h, float* out, const float2* 
 
 template <int N>
 void FftOps<N>::cols_fwd_half(float2* Hh, int ncols, const float2* tw, cudaStream_t st, float2* Hf, int w) {
-  static const bool once = (ext_set_smem(k_cols_fwd_half<N>, C::COL_SMEM), true);
+  const bool once = (ext_set_smem(k_cols_fwd_half<N>, C::COL_SMEM), true);
   (void)once;
   dim3 grid((ncols + C::CW - 1) / C::CW);
   k_cols_fwd_half<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(Hh, ncols, tw, Hf, w);
@@ -1575,7 +1579,7 @@ void FftOps<N>::cols_fwd_half(float2* Hh, int ncols, const float2* tw, cudaStrea
 template <int N>
 void FftOps<N>::cols_fwd_spectrum(const float2* X, int w, int conj_out, float scale, float2* S,
                                   const float2* tw, cudaStream_t st, int nplanes, float scale_rest) {
-  static const bool once = (ext_set_smem(k_cols_fwd_spectrum<N>, C::COL_SMEM), true);
+  const bool once = (ext_set_smem(k_cols_fwd_spectrum<N>, C::COL_SMEM), true);
   (void)once;
   dim3 grid((w + C::CW - 1) / C::CW, nplanes);
   k_cols_fwd_spectrum<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(X, w, conj_out, scale, scale_rest, S, tw);
@@ -1584,7 +1588,7 @@ void FftOps<N>::cols_fwd_spectrum(const float2* X, int w, int conj_out, float sc
 template <int N>
 void FftOps<N>::cols_inv_corr(const float2* Hh, int w, const float2* S, int k0, int nk, float2* Z,
                               const float2* tw, cudaStream_t st) {
-  static const bool once = (ext_set_smem(k_cols_inv_corr<N>, C::COL_SMEM), true);
+  const bool once = (ext_set_smem(k_cols_inv_corr<N>, C::COL_SMEM), true);
   (void)once;
   dim3 grid((w + C::CW - 1) / C::CW, nk);
   k_cols_inv_corr<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(Hh, w, S, k0, Z, tw);
@@ -1593,7 +1597,7 @@ void FftOps<N>::cols_inv_corr(const float2* Hh, int w, const float2* S, int k0, 
 template <int N>
 void FftOps<N>::cols_conv(const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
                           cudaStream_t st) {
-  static const bool once = (ext_set_smem(k_cols_conv<N>, C::COL_SMEM), true);
+  const bool once = (ext_set_smem(k_cols_conv<N>, C::COL_SMEM), true);
   (void)once;
   dim3 grid((w + C::CW - 1) / C::CW);
   k_cols_conv<N><<<grid, C::COL_THREADS, C::COL_SMEM, st>>>(A, w, K, S, Y, tw);
@@ -1622,13 +1626,13 @@ bool FftOps<N>::cols_inv_corr_pipe(const float2* Hh, int w, const float2* S, int
     // (4-column tiles) the single-buffered pass is faster (0.45 vs 0.50 ms)
     if constexpr (Pipe2Cfg<N>::OK && C::CW >= 16) {
       constexpr bool REUSE = true;
-      static const bool once2 = (ext_set_smem(k_cols_inv_corr_pipe2<N, true, REUSE>, Pipe2Cfg<N>::SMEM), true);
+      const bool once2 = (ext_set_smem(k_cols_inv_corr_pipe2<N, true, REUSE>, Pipe2Cfg<N>::SMEM), true);
       (void)once2;
       const int grid = pipe_grid<N>(items, sms, Pipe2Cfg<N>::SMEM, C::COL_THREADS);
       k_cols_inv_corr_pipe2<N, true, REUSE><<<grid, C::COL_THREADS, Pipe2Cfg<N>::SMEM, st>>>(Hh, w, S, k0, nk, Z, tw);
       return true;
     }
-    static const bool once = (ext_set_smem(k_cols_inv_corr_pipe<N, true>, PipeCfg<N>::COL_SMEM), true);
+    const bool once = (ext_set_smem(k_cols_inv_corr_pipe<N, true>, PipeCfg<N>::COL_SMEM), true);
     (void)once;
     const int grid = pipe_grid<N>(items, sms, PipeCfg<N>::COL_SMEM, C::COL_THREADS);
     k_cols_inv_corr_pipe<N, true><<<grid, C::COL_THREADS, PipeCfg<N>::COL_SMEM, st>>>(Hh, w, S, k0, nk, Z, tw);
@@ -1642,7 +1646,7 @@ bool FftOps<N>::cols_inv_corr_tma(const CUtensorMap& tmH, int w, int br, const f
   if constexpr (!TmaColCfg<N>::OK) {
     return false;
   } else {
-    static const bool once = (ext_set_smem(k_cols_inv_corr_tma<N>, TmaColCfg<N>::SMEM), true);
+    const bool once = (ext_set_smem(k_cols_inv_corr_tma<N>, TmaColCfg<N>::SMEM), true);
     (void)once;
     const int items = ((w + C::CW - 1) / C::CW) * nk;
     const int grid = pipe_grid<N>(items, sms, TmaColCfg<N>::SMEM, C::COL_THREADS);
@@ -1660,7 +1664,7 @@ bool FftOps<N>::cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, cons
   } else {
     if (!TC::OK && !stw_g) return false;
     constexpr int smem = TC::OK ? TC::SMEM : TC::SMEM_GTW;
-    static const bool once = (ext_set_smem(k_cols_conv_tma<N>, smem), true);
+    const bool once = (ext_set_smem(k_cols_conv_tma<N>, smem), true);
     (void)once;
     const int tiles = (w + C::CW - 1) / C::CW;
     const int grid = pipe_grid<N>(tiles, sms, smem, C::COL_THREADS);
@@ -1680,7 +1684,7 @@ bool FftOps<N>::planes_fwd_c2c(float2* U, int nplanes, const float2* tw, int* er
   if constexpr (!PlaneCfg<N>::OK) {
     return false;
   } else {
-    static const bool once = (ext_set_smem(k_planes_fwd_c2c<N>, PlaneCfg<N>::SMEM), true);
+    const bool once = (ext_set_smem(k_planes_fwd_c2c<N>, PlaneCfg<N>::SMEM), true);
     (void)once;
     int per_sm = (227 * 1024) / (PlaneCfg<N>::SMEM + 1024);
     const int by_threads = 2048 / PlaneCfg<N>::THREADS;
@@ -1698,7 +1702,7 @@ bool FftOps<N>::planes_inv_channels(const float2* Z, int nz, int k0, int nk, con
   if constexpr (!PlaneCfg<N>::OK) {
     return false;
   } else {
-    static const bool once = (ext_set_smem(k_planes_inv_channels<N>, PlaneCfg<N>::SMEM), true);
+    const bool once = (ext_set_smem(k_planes_inv_channels<N>, PlaneCfg<N>::SMEM), true);
     (void)once;
     const int planes = nk * nz;
     int per_sm = (227 * 1024) / (PlaneCfg<N>::SMEM + 1024);
@@ -1720,13 +1724,13 @@ bool FftOps<N>::cols_inv_full_pipe(const float2* H, int w, const float2* S, int 
     const int items = ((w + C::CW - 1) / C::CW) * nk;
     if constexpr (Pipe2Cfg<N>::OK && C::CW >= 16) {
       constexpr bool REUSE = true;
-      static const bool once2 = (ext_set_smem(k_cols_inv_corr_pipe2<N, false, REUSE>, Pipe2Cfg<N>::SMEM), true);
+      const bool once2 = (ext_set_smem(k_cols_inv_corr_pipe2<N, false, REUSE>, Pipe2Cfg<N>::SMEM), true);
       (void)once2;
       const int grid = pipe_grid<N>(items, sms, Pipe2Cfg<N>::SMEM, C::COL_THREADS);
       k_cols_inv_corr_pipe2<N, false, REUSE><<<grid, C::COL_THREADS, Pipe2Cfg<N>::SMEM, st>>>(H, w, S, k0, nk, Z, tw);
       return true;
     }
-    static const bool once = (ext_set_smem(k_cols_inv_corr_pipe<N, false>, PipeCfg<N>::COL_SMEM), true);
+    const bool once = (ext_set_smem(k_cols_inv_corr_pipe<N, false>, PipeCfg<N>::COL_SMEM), true);
     (void)once;
     const int grid = pipe_grid<N>(items, sms, PipeCfg<N>::COL_SMEM, C::COL_THREADS);
     k_cols_inv_corr_pipe<N, false><<<grid, C::COL_THREADS, PipeCfg<N>::COL_SMEM, st>>>(H, w, S, k0, nk, Z, tw);
@@ -1736,7 +1740,7 @@ bool FftOps<N>::cols_inv_full_pipe(const float2* H, int w, const float2* S, int 
 
 template <int N>
 void FftOps<N>::cols_c2c(float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st) {
-  static const bool once = (ext_set_smem(k_cols_c2c<N, false>, C::COL_SMEM),
+  const bool once = (ext_set_smem(k_cols_c2c<N, false>, C::COL_SMEM),
                             ext_set_smem(k_cols_c2c<N, true>, C::COL_SMEM), true);
   (void)once;
   dim3 grid((w + C::CW - 1) / C::CW, planes);
@@ -1747,7 +1751,7 @@ void FftOps<N>::cols_c2c(float2* X, int w, int planes, bool inv, const float2* t
 template <int N>
 void FftOps<N>::rows_inv_channels(const float2* Z, int rows, int k0, int nk, const int2* chan, float* G,
                                   const float2* tw, cudaStream_t st) {
-  static const bool once = (ext_set_smem(k_rows_inv_channels<N>, C::ROW_SMEM), true);
+  const bool once = (ext_set_smem(k_rows_inv_channels<N>, C::ROW_SMEM), true);
   (void)once;
   dim3 grid((rows + C::RL - 1) / C::RL, nk);
   k_rows_inv_channels<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(Z, rows, k0, chan, G, tw);
@@ -1759,7 +1763,7 @@ bool FftOps<N>::rows_inv_components_pipe(const float2* Z, int h, int k0, int nk,
   if constexpr (!PipeCfg<N>::ROW_OK) {
     return false;
   } else {
-    static const bool once = (ext_set_smem(k_rows_inv_components_pipe<N>, PipeCfg<N>::ROW_SMEM), true);
+    const bool once = (ext_set_smem(k_rows_inv_components_pipe<N>, PipeCfg<N>::ROW_SMEM), true);
     (void)once;
     const int items = ((h + C::RL - 1) / C::RL) * nk;
     const int grid = pipe_grid<N>(items, sms, PipeCfg<N>::ROW_SMEM, C::ROW_THREADS);
@@ -1771,7 +1775,7 @@ bool FftOps<N>::rows_inv_components_pipe(const float2* Z, int h, int k0, int nk,
 template <int N>
 void FftOps<N>::rows_fwd_simil(const float* H, const float4* uv, const float* s, int h, const int2* kj, int ncomp,
                                int unit_integral, float2* A, const float2* tw, cudaStream_t st) {
-  static const bool once = (ext_set_smem(k_rows_fwd_simil<N>, C::ROW_SMEM), true);
+  const bool once = (ext_set_smem(k_rows_fwd_simil<N>, C::ROW_SMEM), true);
   (void)once;
   dim3 grid(ncomp, (h + C::RL - 1) / C::RL);
   k_rows_fwd_simil<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, uv, s, h, kj, unit_integral, A, tw);
@@ -1780,7 +1784,7 @@ void FftOps<N>::rows_fwd_simil(const float* H, const float4* uv, const float* s,
 template <int N>
 void FftOps<N>::rows_fwd_scale(const float* H, const float* s, int h, int k0, int nk, float omega_step,
                                int unit_integral, float2* A, const float2* tw, cudaStream_t st) {
-  static const bool once = (ext_set_smem(k_rows_fwd_scale<N>, C::ROW_SMEM), true);
+  const bool once = (ext_set_smem(k_rows_fwd_scale<N>, C::ROW_SMEM), true);
   (void)once;
   dim3 grid((h + C::RL - 1) / C::RL, nk);
   k_rows_fwd_scale<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, s, h, k0, omega_step, unit_integral, A, tw);
