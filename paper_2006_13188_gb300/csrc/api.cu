@@ -699,6 +699,7 @@ ext_status ext_plan_create(ext_plan* plan, const ext_options* options) {
   if (const char* e = getenv("EXT_PIPELINED")) p->pipelined = atoi(e) != 0;
   if (const char* e = getenv("EXT_TMA")) p->tma = atoi(e) != 0;
   if (const char* e = getenv("EXT_SO3_WS")) p->so3_ws = atoi(e) != 0;
+  if (const char* e = getenv("EXT_SCALE_TABLE")) p->scale_table = atoi(e) != 0;
   if (const char* e = getenv("EXT_BATCH_BRANCHES")) p->batch_branches = atoi(e);
   if (p->autotune) tune_cache_read(p);
   *plan = p;
@@ -1137,11 +1138,21 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
   EXT_TRY(ensure(plan, "Dscale", sizeof(float) * P, &Db));
   const float omega_step = (float)(two_pi / log_period);
   const int unit = mode == 2 ? 1 : 0;
+  void* Tb = nullptr;
+  if (plan->scale_table && n_h <= 32) {   // measured: 3 % faster at 24 harmonics, 7 % slower at 64 (longer powering)
+    EXT_TRY(ensure(plan, "scale_phasors", sizeof(float4) * P, &Tb));
+    launch(plan, "scale_phasors", st, [&] {
+      launch_scale_phasors((const float*)sS.dev, (long long)P, omega_step, unit, (float4*)Tb, plan->sms, st);
+    });
+  }
   EXT_TRY(conv_signals(
       plan, h, w, n_h, channels + (mode == 0 ? 0 : 1), S, st, "rows_fwd_scale",
       [&](int sig, float2* A, const float2* tw_w) {
         const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
-        fft_rows_fwd_scale(w, src, (const float*)sS.dev, h, 0, n_h, omega_step, unit, A, tw_w, st);
+        if (Tb)
+          fft_rows_fwd_scale_tab(w, src, (const float4*)Tb, h, 0, n_h, A, tw_w, st);
+        else
+          fft_rows_fwd_scale(w, src, (const float*)sS.dev, h, 0, n_h, omega_step, unit, A, tw_w, st);
       },
       [&](int sig) { return sig < channels ? (float*)Nb + P * sig : (float*)Db; }));
   launch(plan, "scale_finalize", st, [&] {

@@ -410,6 +410,54 @@ k_rows_fwd_scale(const float* __restrict__ H, const float* __restrict__ sfield, 
   });
 }
 
+// The same transform with the per-pixel values formed once per call:
+//   T[p] = (u, wgt, 0), u = e^{-i w_1 ln s(p)} (one logf and sincos per pixel
+//   instead of per pixel and harmonic), A_k = H wgt u^k, u^k by repeated
+// squaring; blockIdx.x = harmonic (fastest) so the row block's H and T come
+// from L2 for all harmonics.
+__device__ __forceinline__ float2 c_pow_u(float2 b, int e) {
+  float2 r = make_float2(1.f, 0.f);
+  while (e) {
+    if (e & 1) r = c_mul(r, b);
+    b = c_mul(b, b);
+    e >>= 1;
+  }
+  return r;
+}
+
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
+k_rows_fwd_scale_tab(const float* __restrict__ H, const float4* __restrict__ T, int h, int k0,
+                     float2* __restrict__ A, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int TH = C::ROW_THREADS;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::RL * C::LS>(sm, tw, C::ROW_THREADS);
+  const int y0 = blockIdx.y * C::RL;
+  const int k = k0 + (int)blockIdx.x;
+  float hv[STAGE_G];
+  float4 tv[STAGE_G];
+  for_elems_staged<C::RL * N, TH, STAGE_G>(
+      [&](int i, int e) {
+        const int y = y0 + e / N;
+        const size_t idx = (size_t)y * N + e % N;
+        hv[i] = (y < h) ? (H ? __ldg(H + idx) : 1.0f) : 0.f;
+        tv[i] = (y < h) ? __ldg(T + idx) : make_float4(1.f, 0.f, 0.f, 0.f);
+      },
+      [&](int i, int e) {
+        const float a = hv[i] * tv[i].z;
+        const float2 z = c_pow_u(make_float2(tv[i].x, tv[i].y), k);
+        sm[(e / N) * C::LS + sidx(e % N)] = make_float2(a * z.x, a * z.y);
+      });
+  __syncthreads();
+  row_fft<N, false>(sm, twl);
+  float2* out = A + (size_t)blockIdx.x * h * N;
+  for_elems<C::RL * N, TH>([&](int i, int e) {
+    const int y = y0 + e / N;
+    if (y < h) out[(size_t)y * N + e % N] = sm[(e / N) * C::LS + sidx(e % N)];
+  });
+}
+
 // Forward transform of the similarity-steered signals (rotation and scale
 // fields together, in log-polar harmonics):
 //   A_c = H wgt exp(-i (k alpha + w_j ln s)) = H wgt u^k v^j,  (k, j) = kj[blockIdx.x],
@@ -1475,6 +1523,8 @@ struct FftOps {
                        cudaStream_t st);
   static void rows_fwd_simil(const float* H, const float4* uv, const float* s, int h, const int2* kj, int ncomp,
                              int unit_integral, float2* A, const float2* tw, cudaStream_t st);
+  static void rows_fwd_scale_tab(const float* H, const float4* T, int h, int k0, int nk, float2* A,
+                                 const float2* tw, cudaStream_t st);
   static void rows_fwd_scale(const float* H, const float* s, int h, int k0, int nk, float omega_step,
                              int unit_integral, float2* A, const float2* tw, cudaStream_t st);
   static void rows_inv_components(const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
@@ -1779,6 +1829,15 @@ void FftOps<N>::rows_fwd_simil(const float* H, const float4* uv, const float* s,
   (void)once;
   dim3 grid(ncomp, (h + C::RL - 1) / C::RL);
   k_rows_fwd_simil<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, uv, s, h, kj, unit_integral, A, tw);
+}
+
+template <int N>
+void FftOps<N>::rows_fwd_scale_tab(const float* H, const float4* T, int h, int k0, int nk, float2* A,
+                                   const float2* tw, cudaStream_t st) {
+  const bool once = (ext_set_smem(k_rows_fwd_scale_tab<N>, C::ROW_SMEM), true);
+  (void)once;
+  dim3 grid(nk, (h + C::RL - 1) / C::RL);
+  k_rows_fwd_scale_tab<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, T, h, k0, A, tw);
 }
 
 template <int N>

@@ -133,6 +133,31 @@ void launch_simil_phasors(const float* alpha, const float* s, long long P, float
   k_simil_phasors<<<blocks, 256, 0, st>>>(alpha, s, P, omega_step, uv);
 }
 
+// Per-pixel values of the scale-steered signals: (e^{-i w_1 ln s}, wgt, 0), wgt = 1/s^2 or 1.
+__global__ void k_scale_phasors(const float* __restrict__ sfield, long long P, float omega_step, int unit_integral,
+                                float4* __restrict__ T) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    const float sv = __ldg(sfield + p);
+    float sn, cs;
+    sincos_wx(omega_step, logf(sv), &sn, &cs);
+    T[p] = make_float4(cs, -sn, unit_integral ? 1.0f / (sv * sv) : 1.0f, 0.f);
+  }
+}
+
+void launch_scale_phasors(const float* s, long long P, float omega_step, int unit_integral, float4* T, int sms,
+                          cudaStream_t st) {
+  if (P <= 0) return;
+  const int blocks = (int)std::min<long long>((P + 255) / 256, (long long)sms * 8);
+  k_scale_phasors<<<blocks, 256, 0, st>>>(s, P, omega_step, unit_integral, T);
+}
+
+#define EXT_C1(N) case N: FftOps<N>::rows_fwd_scale_tab(H, T, h, k0, nk, A, tw, st); return;
+void fft_rows_fwd_scale_tab(int w, const float* H, const float4* T, int h, int k0, int nk, float2* A,
+                            const float2* tw, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
 #define EXT_C1(N) case N: FftOps<N>::rows_fwd_scale(H, s, h, k0, nk, omega_step, unit_integral, A, tw, st); return;
 void fft_rows_fwd_scale(int w, const float* H, const float* s, int h, int k0, int nk, float omega_step,
                         int unit_integral, float2* A, const float2* tw, cudaStream_t st) {

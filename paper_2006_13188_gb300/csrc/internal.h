@@ -33,6 +33,11 @@ void fft_rows_fwd_simil(int w, const float* H, const float4* uv, const float* s,
                         int unit_integral, float2* A, const float2* tw, cudaStream_t st);
 void launch_simil_phasors(const float* alpha, const float* s, long long P, float omega_step, float4* uv, int sms,
                           cudaStream_t st);
+// the same from a per-call table T = (e^{-i w_1 ln s}, wgt, 0) of launch_scale_phasors (harmonic-fastest grid)
+void launch_scale_phasors(const float* s, long long P, float omega_step, int unit_integral, float4* T, int sms,
+                          cudaStream_t st);
+void fft_rows_fwd_scale_tab(int w, const float* H, const float4* T, int h, int k0, int nk, float2* A,
+                            const float2* tw, cudaStream_t st);
 void fft_rows_fwd_scale(int w, const float* H, const float* s, int h, int k0, int nk, float omega_step,
                         int unit_integral, float2* A, const float2* tw, cudaStream_t st);
 void fft_rows_c2c(int w, const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
