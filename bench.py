@@ -76,6 +76,8 @@ def parse_args():
                          "so3conv: SO(3) extended convolution of a 128^3 volume, L=6, smooth rotation field; "
                          "similarity: smoothing of a 2048x2048x3 image under joint rotation and scale fields")
     ap.add_argument("--n-images", type=int, default=512)
+    ap.add_argument("--simil-shape", default="2048x2048",
+                    help="similarity: image rows x columns (2048x2048 is the workload; smaller only for profiling)")
     ap.add_argument("--scale-shape", default="4096x4096",
                     help="scale: image rows x columns (4096x4096 is the workload; smaller only for profiling captures)")
     return ap.parse_args()
@@ -1379,7 +1381,8 @@ def bench_similarity(args, world, rank, local):
     import synth
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    p = synth.similarity_problem(seed=synth.seed_for(10) + rank)
+    hs, ws_ = (int(v) for v in args.simil_shape.lower().split("x"))
+    p = synth.similarity_problem(seed=synth.seed_for(10) + rank, size=(hs, ws_))
     C, h, w = p["img"].shape
     P = h * w
     K, nj = p["c"].shape[0] - 1, p["c"].shape[1]
