@@ -238,17 +238,37 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // r * NS - 1 + k, contiguous in k so that adjacent butterflies read adjacent
 // words.  The stage blocks telescope to N - 1 entries in total.  Values are
 // copied from the FP64-derived table W_N^m = exp(-2 pi i m / N).
+// Product of the radices before stage S.
+__host__ __device__ constexpr int radix_prefix(int n, int S) {
+  int p = 1;
+  const RadixList L = factor_radices(n);
+  for (int i = 0; i < S; ++i) p *= L.r[i];
+  return p;
+}
+
+// Stage table of the Stockham passes: for stage s (NS = product of the
+// earlier radices, radix R), entry NS - 1 + (r - 1) NS + k = w^(r k N / (NS R)),
+// 1 <= r < R, 0 <= k < NS; N - 1 entries.  Filled stage by stage so every
+// division is by a compile-time constant.
+template <int N, int S>
+__device__ __forceinline__ void stage_twiddles_fill(float2* t, const float2* __restrict__ tw, int threads) {
+  constexpr RadixList L = factor_radices(N);
+  if constexpr (S < L.cnt) {
+    constexpr int NS = radix_prefix(N, S);
+    constexpr int R = L.r[S];
+    constexpr int STEP = N / (NS * R);
+    for (int e = threadIdx.x; e < (R - 1) * NS; e += threads) {
+      const int r = e / NS + 1, k = e % NS;
+      t[NS - 1 + e] = __ldg(tw + r * k * STEP);
+    }
+    stage_twiddles_fill<N, S + 1>(t, tw, threads);
+  }
+}
+
 template <int N, int DATA_ELEMS>
 __device__ __forceinline__ const float2* stage_twiddles(float2* sm, const float2* __restrict__ tw, int threads) {
   float2* t = sm + DATA_ELEMS;
-  constexpr RadixList L = factor_radices(N);
-  for (int i = threadIdx.x; i < N - 1; i += threads) {
-    int ns = 1, s = 0;
-    while (s + 1 < L.cnt && ns * L.r[s] <= i + 1) { ns *= L.r[s]; ++s; }
-    const int rel = i + 1 - ns;
-    const int r = rel / ns + 1, k = rel % ns;
-    t[i] = __ldg(tw + r * k * (N / (ns * L.r[s])));
-  }
+  stage_twiddles_fill<N, 0>(t, tw, threads);
   return t;
 }
 
