@@ -1382,6 +1382,20 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
   }
   // ---- capture the per-image launch sequences once (setup: filter decomposition and template
   // spectra; step: forward transform, inverse correlation passes, sweep), then replay
+  // branch of each image: largest images first, each to the least-loaded branch (work ~ (K+1) h w)
+  std::vector<int> branch(n, 0);
+  {
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto cost = [&](int i) { return (double)(imgs[i].F->K + 1) * imgs[i].h * imgs[i].w; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<double> load(NB, 0.0);
+    for (int i : order) {
+      const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      branch[i] = b;
+      load[b] += cost(i);
+    }
+  }
   auto capture = [&](bool setup, cudaGraphExec_t* out) -> ext_status {
     const bool profiling = plan->profiling;
     plan->profiling = false;   // no event records inside the graph
@@ -1398,7 +1412,7 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
     for (int b = 0; b < NB; ++b) EXT_CUDA(cudaStreamWaitEvent(br[b], fork, 0));
     ext_status ss = EXT_OK;
     for (int i = 0; i < n && ss == EXT_OK; ++i) {
-      const int b = i % NB;
+      const int b = branch[i];
       cudaStream_t bs = br[b];
       const ext_image_desc& d = imgs[i];
       const ext_filter_so2* F = d.F;
