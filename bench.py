@@ -1046,16 +1046,24 @@ def bench_so3(args, world, rank, local):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
 
-    def call(prec):
-        ec.ext_corr_so3(plan, V, n, n, n, prob["tables"], prob["dr"], prob["radius"], grid, mx, am, prec)
+    dirs, n_psi = synth.so3_rotation_grid_factors()
+
+    def call(prec, factored=True):
+        # the 4608-rotation grid is 192 directions x 24 in-plane angles: the factored sweep steers the
+        # in-plane angle in the GEMM's epilogue; the plain one sweeps the expanded list
+        if factored:
+            ec.ext_corr_so3_grid(plan, V, n, n, n, prob["tables"], prob["dr"], prob["radius"], dirs, n_psi, mx, am,
+                                 prec)
+        else:
+            ec.ext_corr_so3(plan, V, n, n, n, prob["tables"], prob["dr"], prob["radius"], grid, mx, am, prec)
     t0 = time.perf_counter()
     call(ec.EXT_PREC_BF16X3)
     plan.sync()
     plan_ms = 1e3 * (time.perf_counter() - t0)
 
-    def timed(prec, steps):
+    def timed(prec, steps, factored=True):
         for _ in range(args.warmup):
-            call(prec)
+            call(prec, factored)
         plan.sync()
         barrier(world)
         tot = 0.0
@@ -1063,28 +1071,38 @@ def bench_so3(args, world, rank, local):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            call(prec)
+            call(prec, factored)
             e1.record(stream)
             torch.cuda.synchronize()
             tot += e0.elapsed_time(e1)
         return reduce_max(tot, world, device)
     with ClockSampler(local) as clk:
         total = timed(ec.EXT_PREC_BF16X3, args.steps)
+    list_steps = max(1, min(args.steps, 5))
+    list_total = timed(ec.EXT_PREC_BF16X3, list_steps, factored=False)
     plain = timed(ec.EXT_PREC_FP32, max(1, min(args.steps, 3)))
     plain_steps = max(1, min(args.steps, 3))
     value = world * args.steps * P / (total * 1e-3) / 1e6
-    plan.profile_read()
-    plan.profile(True)
-    call(ec.EXT_PREC_BF16X3)
-    plan.sync()
-    prof = {k: v for k, v in plan.profile_read().items() if v[1] > 0}
-    plan.profile(False)
     nch = ec.ext_so3_channels(L)
-    sweep_name = "so3_sweep_ws" if "so3_sweep_ws" in prof else "so3_sweep_bf16x3"
-    sweep_ms = prof.get(sweep_name, (None, 1))[0]
-    flops = 3 * 2.0 * P * nch * len(grid)          # three split-BF16 products
     burst, sustained, kind = measured_bf16()
+
+    def profile(factored):
+        plan.profile_read()
+        plan.profile(True)
+        call(ec.EXT_PREC_BF16X3, factored)
+        plan.sync()
+        out = {k: v for k, v in plan.profile_read().items() if v[1] > 0}
+        plan.profile(False)
+        return out
+    prof_list = profile(False)
+    prof = profile(True)
+    sweep_name = "so3_sweep_ws" if "so3_sweep_ws" in prof_list else "so3_sweep_bf16x3"
+    sweep_ms = prof_list.get(sweep_name, (None, 1))[0]
+    flops = 3 * 2.0 * P * nch * len(grid)          # three split-BF16 products over the expanded list
     ach = flops / (sweep_ms * 1e-3) / 1e12 if sweep_ms else None
+    gms = prof.get("so3_sweep_grid", (None, 1))[0]
+    gflops = 3 * 2.0 * P * nch * 16 * len(dirs)    # the factored GEMM: 16 rows per direction
+    gach = gflops / (gms * 1e-3) / 1e12 if gms else None
     if rank == 0:
         print(json.dumps({
             "metric": "SO(3) extended-correlation Mvox/s (4608-rotation sweep)", "value": value, "unit": "Mvox/s",
@@ -1096,15 +1114,28 @@ def bench_so3(args, world, rank, local):
             "clocks": clk.summary(),
             "plain_fp32": {"value": world * plain_steps * P / (plain * 1e-3) / 1e6, "unit": "Mvox/s",
                            "ms_per_step": plain / plain_steps},
-            "roofline": {"kernel": sweep_name, "bound": "tensor", "achieved": ach, "peak": burst,
-                         "peak_kind": kind + " bf16 burst (one ~13 ms launch at full clocks)", "unit": "TFLOP/s",
-                         "frac": ach / burst if ach else None,
-                         "frac_of_sustained": ach / sustained if ach else None,
-                         "traffic": 520.055e6 * 8 if sweep_name == "so3_sweep_ws" else None,
-                         "traffic_note": "ncu dram read+write of the 64^3 launch (525 MB) scaled by the 8x voxel "
-                                         "tiles of 128^3; A' and B' read once from DRAM",
-                         "algorithmic_flops": flops,
-                         "kernels": {k: {"ms_per_call": v[0], "launches": v[1]} for k, v in prof.items()}}}))
+            "list_sweep": {"value": world * list_steps * P / (list_total * 1e-3) / 1e6, "unit": "Mvox/s",
+                           "ms_per_step": list_total / list_steps,
+                           "note": "the same grid swept as the expanded list of 4608 rotations"},
+            "roofline": {"kernel": "so3_sweep_grid", "bound": "tensor", "achieved": gach, "peak": burst,
+                         "peak_kind": kind + " bf16 burst (one launch of a few ms at full clocks)", "unit": "TFLOP/s",
+                         "frac": gach / burst if gach else None,
+                         "frac_of_sustained": gach / sustained if gach else None, "traffic": None,
+                         "algorithmic_flops": gflops,
+                         "note": "the factored GEMM's own work: 3 split products x 2 x 455 channels x 16 rows per "
+                                 "direction x 192 directions per voxel; equivalent_tflops counts the expanded "
+                                 "4608-rotation GEMM's work in the same time",
+                         "equivalent_tflops": flops / (gms * 1e-3) / 1e12 if gms else None,
+                         "kernels": {k: {"ms_per_call": v[0], "launches": v[1]} for k, v in prof.items()}},
+            "list_sweep_roofline": {"kernel": sweep_name, "bound": "tensor", "achieved": ach, "peak": burst,
+                                    "unit": "TFLOP/s", "frac": ach / burst if ach else None,
+                                    "frac_of_sustained": ach / sustained if ach else None,
+                                    "traffic": (520.055e6 + 4.978e6) * 8 if sweep_name == "so3_sweep_ws" else None,
+                                    "traffic_note": "ncu dram read+write of the 64^3 launch (525 MB) scaled by the 8x "
+                                                    "voxel tiles of 128^3; A' and B' read once from DRAM",
+                                    "algorithmic_flops": flops,
+                                    "kernels": {k: {"ms_per_call": v[0], "launches": v[1]}
+                                                for k, v in prof_list.items()}}}))
     plan.close()
     return 0
 
@@ -1161,8 +1192,11 @@ def bench_so3p(args, world, rank, local):
         counts["c"] = ec.ext_corr_so3_propose(plan, V, n, n, n, tables, prob["dr"], prob["radius"], net, grid, bound,
                                               sc, qq, gi, ec.EXT_PREC_BF16X3)
 
-    def exhaustive():
-        ec.ext_corr_so3(plan, V, n, n, n, tables, prob["dr"], prob["radius"], grid, mx, am, ec.EXT_PREC_BF16X3)
+    dirs, n_psi = synth.so3_rotation_grid_factors()
+
+    def exhaustive():   # the same 4608-rotation grid, factored as 192 directions x 24 in-plane angles
+        ec.ext_corr_so3_grid(plan, V, n, n, n, tables, prob["dr"], prob["radius"], dirs, n_psi, mx, am,
+                             ec.EXT_PREC_BF16X3)
     t0 = time.perf_counter()
     call()
     plan.sync()

@@ -395,6 +395,27 @@ ext_status ext_conv_so3(ext_plan plan, const float* V, int nz, int ny, int nx, c
 ext_status ext_corr_so3(ext_plan plan, const float* V, int nz, int ny, int nx, const double* tables, int L, int n_r,
                         double dr, int R, const double* quats, int n_rot, float* max_out, int32_t* argmax,
                         int precision, void* stream);
+/*
+ * The sweep over a product grid of rotations R_{d,t} = R_d R_z(2 pi t / n_psi)
+ * (n_dirs direction rotations R_d, HOST quaternions [n_dirs][4], each followed
+ * on the right by n_psi uniformly spaced rotations about z; rotation index
+ * d * n_psi + t), e.g. a Hopf-fibration grid.  Sec. 9's score factors over
+ * the in-plane angle: C(R_d R_z(psi)) = C(R_z(psi)) C(R_d) with
+ * C^l_ab(R_z(psi)) = delta_ab e^{-i a psi}, so
+ *   S(p, R_{d,t}) = H_0 + 2 sum_{a=1..L} Re(e^{i a psi_t} H_a),
+ *   H_a(p, d) = sum_{l >= a, b} conj(C^l_ab(R_d)) G_l^{ab}(p)
+ * (H_{-a} = conj(H_a) for a real score).  With EXT_PREC_BF16X3 the 2L+1 real
+ * H values of every direction come from a split-BF16 tensor-core GEMM and the
+ * n_psi angles are steered in its epilogue; EXT_PREC_FP32 sweeps the
+ * expanded rotation list as ext_sweep_so3.  Outputs as ext_sweep_so3 (max and
+ * the first maximising index).  n_psi <= 64; L <= 6.
+ */
+ext_status ext_sweep_so3_grid(ext_plan plan, const float* G, int64_t n_vox, int L, const double* dir_quats,
+                              int n_dirs, int n_psi, float* max_out, int32_t* argmax, int precision, void* stream);
+/* Components then the product-grid sweep. */
+ext_status ext_corr_so3_grid(ext_plan plan, const float* V, int nz, int ny, int nx, const double* tables, int L,
+                             int n_r, double dr, int R, const double* dir_quats, int n_dirs, int n_psi,
+                             float* max_out, int32_t* argmax, int precision, void* stream);
 
 /*
  * Learned SO(3) proposal (Sec. 9 matching, with a network proposing the

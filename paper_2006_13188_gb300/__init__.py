@@ -13,5 +13,5 @@ from ._binding import (  # noqa: F401
     ext_so3_refine, ext_so3_propose, ext_corr_so3_propose, ext_gradient_field, ext_consensus_radius,
     ext_consensus_filter, ext_ght_detect, ext_conv_so2_normalized, ext_filter_so2_energy, ext_corr_so2_subset,
     EXT_PREC_DEFAULT, EXT_FAULT_ALLOC, EXT_FAULT_NONE, EXT_TUNE_OFF, EXT_TUNE_ON, ext_mlp_checkpoint_info,
-    ext_select_components, BatchDescriptors,
+    ext_select_components, BatchDescriptors, ext_sweep_so3_grid, ext_corr_so3_grid,
 )

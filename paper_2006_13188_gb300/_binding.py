@@ -48,7 +48,8 @@ EXPORTED = (
     "ext_so3_propose", "ext_corr_so3_propose", "ext_gradient_field", "ext_consensus_radius",
     "ext_consensus_filter", "ext_ght_detect", "ext_conv_so2_normalized", "ext_filter_so2_energy",
     "ext_corr_so2_subset", "ext_conv_so3", "ext_conv_similarity", "ext_options_init", "ext_plan_selftest_timeout",
-    "ext_select_components", "ext_mlp_save", "ext_mlp_load", "ext_mlp_checkpoint_info",
+    "ext_select_components", "ext_mlp_save", "ext_mlp_load", "ext_mlp_checkpoint_info", "ext_sweep_so3_grid",
+    "ext_corr_so3_grid",
 )
 
 
@@ -126,6 +127,9 @@ def lib():
         L.ext_corr_so3_components.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, vp]
         L.ext_sweep_so3.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp, i32, vp]
         L.ext_corr_so3.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, i32, vp, vp, i32, vp]
+        L.ext_sweep_so3_grid.argtypes = [vp, vp, i64, i32, vp, i32, i32, vp, vp, i32, vp]
+        L.ext_corr_so3_grid.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, i32, i32, vp,
+                                        vp, i32, vp]
         L.ext_conv_so3.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, i32, vp, vp, vp]
         L.ext_conv_similarity.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, vp, vp, i32, vp, vp]
@@ -397,6 +401,23 @@ def ext_corr_so3(plan: Plan, V, nz, ny, nx, tables, dr, R, quats, max_out, argma
     _check(lib().ext_corr_so3(plan.handle, _ptr(V), int(nz), int(ny), int(nx), _ptr(t.view(np.float64)), L, t.shape[1],
                               float(dr), int(R), _ptr(q), q.shape[0], _ptr(max_out), _ptr(argmax), int(precision),
                               _stream(stream)))
+
+
+def ext_sweep_so3_grid(plan: Plan, G, n_vox, L, dir_quats, n_psi, max_out, argmax, precision=EXT_PREC_BF16X3,
+                       stream=None):
+    q = np.ascontiguousarray(np.asarray(dir_quats, np.float64).reshape(-1, 4))
+    _check(lib().ext_sweep_so3_grid(plan.handle, _ptr(G), int(n_vox), int(L), _ptr(q), q.shape[0], int(n_psi),
+                                    _ptr(max_out), _ptr(argmax), int(precision), _stream(stream)))
+
+
+def ext_corr_so3_grid(plan: Plan, V, nz, ny, nx, tables, dr, R, dir_quats, n_psi, max_out, argmax,
+                      precision=EXT_PREC_BF16X3, stream=None):
+    t = so3_pack_tables(tables)
+    L = len(tables) - 1
+    q = np.ascontiguousarray(np.asarray(dir_quats, np.float64).reshape(-1, 4))
+    _check(lib().ext_corr_so3_grid(plan.handle, _ptr(V), int(nz), int(ny), int(nx), _ptr(t.view(np.float64)), L,
+                                   t.shape[1], float(dr), int(R), _ptr(q), q.shape[0], int(n_psi), _ptr(max_out),
+                                   _ptr(argmax), int(precision), _stream(stream)))
 
 
 def ext_conv_similarity(plan: Plan, H, channels, h, w, coef, log_period, r_min, r_max, centre_tap, alpha, s, mode,

@@ -756,6 +756,7 @@ ext_status ext_plan_trim(ext_plan plan) {
   plan->batch_setup_exec = nullptr;
   plan->batch_key = 0;
   plan->so3_rot_key = 0;
+  plan->so3_grid_key = 0;
   plan->so3_steer_L = -1;
   return EXT_OK;
 }

@@ -2,6 +2,8 @@
 // learned proposal.
 #include "plan.h"
 
+#include <cmath>
+
 // ------------------------------------------------------------------ SO(3) ---
 namespace {
 
@@ -252,9 +254,135 @@ ext_status so3_sweep(ext_plan plan, const float* G, long long P, int L, const do
   return EXT_OK;
 }
 
+// The grid R_d R_z(2 pi t / n_psi): full quaternion list (for the FP32 sweep)
+// q_d q_z(psi_t), and the split B' blocks of the 16 in-plane-harmonic rows of
+// every direction (cached for the last direction set).
+void grid_quats(const double* dirs, int n_dirs, int n_psi, std::vector<double>* out) {
+  out->resize((size_t)4 * n_dirs * n_psi);
+  for (int d = 0; d < n_dirs; ++d)
+    for (int t = 0; t < n_psi; ++t) {
+      const double h = 3.141592653589793238462643383279502884 * t / n_psi;   // half angle
+      const double w1 = dirs[4 * d], x1 = dirs[4 * d + 1], y1 = dirs[4 * d + 2], z1 = dirs[4 * d + 3];
+      const double w2 = std::cos(h), z2 = std::sin(h);
+      double* q = out->data() + (size_t)4 * (d * n_psi + t);
+      q[0] = w1 * w2 - z1 * z2;
+      q[1] = x1 * w2 + y1 * z2;
+      q[2] = y1 * w2 - x1 * z2;
+      q[3] = w1 * z2 + z1 * w2;
+    }
+}
+
+ext_status so3_grid_tables(ext_plan plan, const double* dirs, int n_dirs, int L, cudaStream_t st,
+                           const unsigned char** Bb, int* cpad_out) {
+  const So3Layout lay = so3_layout(L);
+  const int cpad = (lay.nchan + 31) / 32 * 32;
+  const size_t per = (size_t)(L + 1) * (2 * L + 1) * (2 * L + 3) / 3;
+  uint64_t key = fnv1a(0x9a1d5ull, dirs, sizeof(double) * 4 * n_dirs);
+  key = fnv1a(key, &L, sizeof(int));
+  void *dq, *dC, *dB, *dBb, *dch;
+  EXT_TRY(ensure(plan, "grid_quats", sizeof(double) * 4 * n_dirs, &dq));
+  EXT_TRY(ensure(plan, "grid_C", sizeof(double2) * per * n_dirs, &dC));
+  EXT_TRY(ensure(plan, "grid_rows", sizeof(float) * (size_t)16 * n_dirs * cpad, &dB));
+  EXT_TRY(ensure(plan, "grid_Bws", so3_ws_b_bytes(16 * n_dirs, cpad), &dBb));
+  EXT_TRY(ensure(plan, "grid_chans", sizeof(int4) * lay.comp.size(), &dch));
+  for (void* q : {dq, dC, dB, dBb, dch}) key = fnv1a(key, &q, sizeof(q));
+  if (plan->so3_grid_key != key) {
+    EXT_CUDA(cudaMemcpyAsync(dq, dirs, sizeof(double) * 4 * n_dirs, cudaMemcpyHostToDevice, st));
+    EXT_CUDA(cudaMemcpyAsync(dch, lay.comp.data(), sizeof(int4) * lay.comp.size(), cudaMemcpyHostToDevice, st));
+    launch_so3_wigner((const double*)dq, n_dirs, L, (double2*)dC, nullptr, 0, 0, nullptr, st);
+    launch_so3_grid_rows((const double2*)dC, n_dirs, L, (const int4*)dch, (int)lay.comp.size(), cpad, (float*)dB, st);
+    so3_ws_build_b((const float*)dB, cpad, 16 * n_dirs, (unsigned char*)dBb, st);
+    EXT_CUDA(cudaGetLastError());
+    EXT_CUDA(cudaStreamSynchronize(st));   // the host directions may change after return
+    plan->so3_grid_key = key;
+  }
+  *Bb = (const unsigned char*)dBb;
+  *cpad_out = cpad;
+  return EXT_OK;
+}
+
+ext_status so3_sweep_grid(ext_plan plan, const float* G, long long P, int L, const double* dirs, int n_dirs, int n_psi,
+                          float* maxv, int32_t* argmax, int precision, cudaStream_t st) {
+  if (precision == EXT_PREC_BF16X3) {
+    const unsigned char* Bb;
+    int cpad;
+    EXT_TRY(so3_grid_tables(plan, dirs, n_dirs, L, st, &Bb, &cpad));
+    void* Ab = nullptr;
+    EXT_TRY(ensure(plan, "so3_Aws", so3_ws_a_bytes(P, cpad), &Ab));
+    void* keys = nullptr;
+    EXT_TRY(ensure(plan, "so3_keys", sizeof(unsigned long long) * P, &keys));
+    const int nchan = so3_layout(L).nchan;
+    bool ok = false;
+    launch(plan, "so3_split_a", st, [&] { so3_ws_split_a(G, P, nchan, cpad, (unsigned char*)Ab, plan->sms, st); });
+    launch(plan, "so3_sweep_grid", st, [&] {
+      ok = sweep_so3_ws_grid(P, cpad, (const unsigned char*)Ab, Bb, n_dirs, n_psi, maxv, argmax,
+                             (unsigned long long*)keys, plan->dev_err, plan->sms, st);
+    });
+    if (!ok) return fail(EXT_ERR_UNSUPPORTED, "grid sweep: unsupported shape");
+    EXT_CUDA(cudaGetLastError());
+    return EXT_OK;
+  }
+  std::vector<double> q;
+  grid_quats(dirs, n_dirs, n_psi, &q);
+  return so3_sweep(plan, G, P, L, q.data(), n_dirs * n_psi, maxv, argmax, precision, st);
+}
+
+ext_status check_grid_args(const double* dirs, int n_dirs, int n_psi) {
+  if (!dirs || n_dirs < 1 || n_psi < 1) return fail(EXT_ERR_INVALID_ARG, "need directions and n_psi >= 1");
+  if (n_psi > 64) return fail(EXT_ERR_UNSUPPORTED, "n_psi must be <= 64");
+  if ((long long)n_dirs * n_psi > (1LL << 30)) return fail(EXT_ERR_UNSUPPORTED, "too many grid rotations");
+  return EXT_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+ext_status ext_sweep_so3_grid(ext_plan plan, const float* G, int64_t n_vox, int L, const double* dir_quats,
+                              int n_dirs, int n_psi, float* max_out, int32_t* argmax, int precision, void* stream) {
+  if (!plan || !G || !max_out || !argmax || n_vox < 0) return fail(EXT_ERR_INVALID_ARG, "bad arguments");
+  EXT_TRY(check_grid_args(dir_quats, n_dirs, n_psi));
+  if (L < 0 || L > 6) return fail(EXT_ERR_UNSUPPORTED, "L <= 6");
+  precision = resolve_precision(plan, precision);
+  if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3) return fail(EXT_ERR_INVALID_ARG, "precision");
+  if (n_vox == 0) return EXT_OK;
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  Staged sG, sM, sA;
+  EXT_TRY(stage_in(plan, "in_G", G, sizeof(float) * n_vox * so3_layout(L).nchan, st, &sG));
+  EXT_TRY(stage_out_alloc(plan, "out_max", max_out, sizeof(float) * n_vox, &sM));
+  EXT_TRY(stage_out_alloc(plan, "out_arg", argmax, sizeof(int32_t) * n_vox, &sA));
+  EXT_TRY(so3_sweep_grid(plan, (const float*)sG.dev, n_vox, L, dir_quats, n_dirs, n_psi, (float*)sM.dev,
+                         (int32_t*)sA.dev, precision, st));
+  EXT_TRY(stage_out_finish(sM, st));
+  EXT_TRY(stage_out_finish(sA, st));
+  return finish_host(plan, sG.host || sM.host || sA.host, st);
+}
+
+ext_status ext_corr_so3_grid(ext_plan plan, const float* V, int nz, int ny, int nx, const double* tables, int L,
+                             int n_r, double dr, int R, const double* dir_quats, int n_dirs, int n_psi,
+                             float* max_out, int32_t* argmax, int precision, void* stream) {
+  if (!plan || !V || !tables || !max_out || !argmax) return fail(EXT_ERR_INVALID_ARG, "NULL argument");
+  EXT_TRY(check_so3_args(nz, ny, nx, L, n_r, dr, R));
+  EXT_TRY(check_grid_args(dir_quats, n_dirs, n_psi));
+  precision = resolve_precision(plan, precision);
+  if (precision != EXT_PREC_FP32 && precision != EXT_PREC_BF16X3) return fail(EXT_ERR_INVALID_ARG, "precision");
+  EXT_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)nz * ny * nx;
+  Staged sV, sM, sA;
+  EXT_TRY(stage_in(plan, "in_V", V, sizeof(float) * P, st, &sV));
+  EXT_TRY(stage_out_alloc(plan, "out_max", max_out, sizeof(float) * P, &sM));
+  EXT_TRY(stage_out_alloc(plan, "out_arg", argmax, sizeof(int32_t) * P, &sA));
+  void* G;
+  EXT_TRY(ensure(plan, "so3_G", sizeof(float) * P * so3_layout(L).nchan, &G));
+  EXT_TRY(so3_components(plan, (const float*)sV.dev, nz, ny, nx, tables, L, n_r, dr, R, (float*)G, st));
+  EXT_TRY(so3_sweep_grid(plan, (const float*)G, (long long)P, L, dir_quats, n_dirs, n_psi, (float*)sM.dev,
+                         (int32_t*)sA.dev, precision, st));
+  EXT_TRY(stage_out_finish(sM, st));
+  EXT_TRY(stage_out_finish(sA, st));
+  return finish_host(plan, sV.host || sM.host || sA.host, st);
+}
 
 int ext_so3_channels(int L) { return (L < 0 || L > 6) ? -1 : so3_layout(L).nchan; }
 

@@ -154,6 +154,13 @@ void so3_ws_build_b(const float* B, int cpad, int J, unsigned char* Bb, cudaStre
 void so3_ws_split_a(const float* G, long long P, int C, int cpad, unsigned char* Ab, int sms, cudaStream_t st);
 bool sweep_so3_ws(long long P, int cpad, const unsigned char* Ab, const unsigned char* Bb, int J, float* maxv,
                   int32_t* argmax, int* err, int sms, cudaStream_t st);
+// the grid sweep over R_d R_z(2 pi t / n_psi): B' = 16 in-plane-harmonic rows per direction (launch_so3_grid_rows),
+// hi/lo split as so3_ws_build_b with J = 16 n_dirs rows; index dir * n_psi + t
+bool sweep_so3_ws_grid(long long P, int cpad, const unsigned char* Ab, const unsigned char* Bb, int n_dirs,
+                       int n_psi, float* maxv, int32_t* argmax, unsigned long long* keys, int* err, int sms,
+                       cudaStream_t st);
+void launch_so3_grid_rows(const double2* C, int n_dirs, int L, const int4* comps, int ncomp, int cpad, float* Brow,
+                          cudaStream_t st);
 size_t so3_btc_bytes(int J, int cpad);
 void so3_build_btc(const float* B, int cpad, int J, unsigned char* Bt, cudaStream_t st);
 // keys (P entries of scratch, or NULL): lets small voxel counts split the

@@ -101,6 +101,7 @@ struct ext_plan_s {
   std::vector<unsigned char> batch_host;   // packed filter data (host staging)
   // SO(3): steering tables of the last rotation set
   uint64_t so3_rot_key = 0;
+  uint64_t so3_grid_key = 0;       // direction set of the grid sweep's cached rows
   int so3_rot_n = 0, so3_rot_L = -1;
   int so3_steer_L = -1;            // degree of the steering-entry table in workspace "so3_steer"
   int* pinned = nullptr;           // small pinned host buffer for counts read back mid-call

@@ -219,3 +219,49 @@ void launch_real_to_complex(const float* V, long long n, float2* X, int sms, cud
   if (b > (long long)sms * 8) b = (long long)sms * 8;
   k_real_to_complex<<<(unsigned)b, 256, 0, st>>>(V, n, X);
 }
+
+// Steering rows of a direction set for the grid sweep over R = R_d R_z(psi)
+// (rotation about z applied first).  C(R_d R_z(psi)) = C(R_z(psi)) C(R_d) and
+// C(R_z(psi)) = diag(e^{-i a psi}), so
+//   S(p, R) = sum_{l,a,b} conj(C^l_ab(R)) G_l^{ab}(p) = sum_a e^{i a psi} H_a(p),
+//   H_a = sum_{l >= |a|, b} conj(C^l_ab(R_d)) G_l^{ab},
+// and since S is real, H_{-a} = conj(H_a): S = H_0 + 2 sum_{a >= 1} Re(e^{i a psi} H_a).
+// Per direction 16 rows over the real channels: row 0 = H_0 (real), rows 2a-1
+// and 2a = Re H_a and Im H_a (a = 1..L), the rest zero.  C: the Wigner blocks of
+// every direction as k_so3_wigner writes them; comps: (l, a, b, first channel)
+// of the stored components (G^{-a,-b} = (-1)^{a+b} conj G^{ab}).
+__global__ void k_so3_grid_rows(const double2* __restrict__ C, int n_dirs, int L, const int4* __restrict__ comps,
+                                int ncomp, int cpad, float* __restrict__ Brow) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_dirs) return;
+  const size_t per = (size_t)(L + 1) * (2 * L + 1) * (2 * L + 3) / 3;
+  const double2* Cd = C + (size_t)d * per;
+  float* rows = Brow + (size_t)d * 16 * cpad;
+  for (int i = 0; i < 16 * cpad; ++i) rows[i] = 0.f;
+  for (int q = 0; q < ncomp; ++q) {
+    const int4 cp = comps[q];
+    const int l = cp.x, a = cp.y, b = cp.z, ch = cp.w;
+    const size_t off = (size_t)l * (2 * l - 1) * (2 * l + 1) / 3;
+    const double2 c = Cd[off + (size_t)(a + l) * (2 * l + 1) + (b + l)];
+    if (a == 0 && b == 0) {
+      rows[ch] += (float)c.x;                                    // H_0 += Re C_00 G (G real)
+    } else if (a == 0) {                                         // (0, b) and its partner (0, -b)
+      const double2 cm = Cd[off + (size_t)l * (2 * l + 1) + (-b + l)];
+      const double sg = (b & 1) ? -1.0 : 1.0;
+      rows[ch] += (float)(c.x + sg * cm.x);
+      rows[ch + 1] += (float)(c.y - sg * cm.y);
+    } else {                                                     // a > 0: H_a += conj(C_ab) G^{ab}
+      float* re = rows + (size_t)(2 * a - 1) * cpad;
+      float* im = rows + (size_t)(2 * a) * cpad;
+      re[ch] += (float)c.x;
+      re[ch + 1] += (float)c.y;
+      im[ch] += (float)(-c.y);
+      im[ch + 1] += (float)c.x;
+    }
+  }
+}
+
+void launch_so3_grid_rows(const double2* C, int n_dirs, int L, const int4* comps, int ncomp, int cpad, float* Brow,
+                          cudaStream_t st) {
+  k_so3_grid_rows<<<(n_dirs + 63) / 64, 64, 0, st>>>(C, n_dirs, L, comps, ncomp, cpad, Brow);
+}

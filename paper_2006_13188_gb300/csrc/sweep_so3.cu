@@ -328,6 +328,7 @@ constexpr int STAGE = A_BYTES + B_BYTES;    // 48 KB
 constexpr int NS = 4;
 constexpr int SMEM = NS * STAGE + 1024;     // + room to align the ring to 1 KB
 constexpr int THREADS = 192;
+constexpr int THREADS_GRID = 320;          // the grid variant: eight epilogue warps, two per lane quarter
 }  // namespace ws
 
 // A' [mt][kc]: hi block then lo block, 128 voxel rows x 32 channels each in
@@ -391,17 +392,31 @@ __global__ void k_so3_b_split(const float* __restrict__ B, int cpad, int J, int 
   }
 }
 
-__global__ void __launch_bounds__(ws::THREADS, 1)
+// GRID: the B' rows are 16 per direction (in-plane harmonics H_0, Re/Im H_a of
+// k_so3_grid_rows) and the epilogue forms S(psi_t) = H_0 + sum_a (2 cos(a psi_t)
+// Re H_a - 2 sin(a psi_t) Im H_a) for t < n_psi, rotation index dir * n_psi + t;
+// J is then the number of directions.
+template <bool GRID>
+__global__ void __launch_bounds__(GRID ? ws::THREADS_GRID : ws::THREADS, 1)
     k_sweep_so3_ws(const unsigned char* __restrict__ Ab, const unsigned char* __restrict__ Bb, long long P, int nkc,
-                   int ntn, int J, float* __restrict__ maxv, int32_t* __restrict__ argmax,
+                   int ntn, int J, int n_psi, float* __restrict__ maxv, int32_t* __restrict__ argmax,
                    unsigned long long* __restrict__ keys, int* __restrict__ err, unsigned long long limit_ns) {
   using namespace ws;
   extern __shared__ __align__(1024) unsigned char ws_smem[];
   __shared__ __align__(8) uint64_t full[NS], empty[NS], accf[2], acce[2];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
+  __shared__ __align__(16) float psi_tab[GRID ? 64 * 12 : 4];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t base = (tc::smem_u32(ws_smem) + 1023u) & ~1023u;
+  if constexpr (GRID) {   // [q][t]: 2 cos(a psi_t) (q = 2a - 2), -2 sin(a psi_t) (q = 2a - 1), a = 1..6, t < n_psi
+    for (int e = tid; e < 64 * 12; e += (GRID ? THREADS_GRID : THREADS)) {
+      const int q = e / 64, t = e % 64, a = q / 2 + 1;
+      double sv, cv;
+      sincospi(2.0 * a * t / (double)(n_psi > 0 ? n_psi : 1), &sv, &cv);
+      psi_tab[e] = t < n_psi ? (float)((q & 1) ? -2.0 * sv : 2.0 * cv) : 0.f;
+    }
+  }
   if (tid == 0) {
     abort_flag = 0;
     for (int s = 0; s < NS; ++s) {
@@ -410,7 +425,7 @@ __global__ void __launch_bounds__(ws::THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(tc::smem_u32(&accf[b]), 1);
-      tc::mbar_init(tc::smem_u32(&acce[b]), 4);
+      tc::mbar_init(tc::smem_u32(&acce[b]), GRID ? 8 : 4);
     }
   }
   if (warp == 1) tc::tmem_alloc<512>(tc::smem_u32(&tmem_slot));
@@ -491,9 +506,13 @@ __global__ void __launch_bounds__(ws::THREADS, 1)
         tc::mbar_wait_bounded(tc::smem_u32(&empty[(it - 1) % NS]), (uint32_t)(((it - 1) / NS) & 1), limit_ns, err,
                               EXT_ERR_TIMEOUT);
     }
-  } else {   // ---- epilogue: warps 2..5, one voxel row per thread
+  } else {   // ---- epilogue: warps 2..5 (grid variant: 2..9), one voxel row per thread
     const int q4 = warp & 3;                 // the TMEM lane quarter this warp may read
     const int row = q4 * 32 + lane;
+    // grid variant: the two warps of a lane quarter take half of each tile's columns each and fold
+    // their results through keys (the larger score, then the smaller index)
+    const int part = GRID ? (warp - 2) / 4 : 0;
+    constexpr int C_SPAN = GRID ? N / 2 : N;
     // every branch below is taken by the whole warp (the tensor-memory loads are warp-wide)
     int t = 0;
     for (long long mt = blockIdx.x; mt < ntm; mt += gridDim.x) {
@@ -514,16 +533,99 @@ __global__ void __launch_bounds__(ws::THREADS, 1)
         }
         tc::fence_after();
 #pragma unroll 1
-        for (int c0 = 0; c0 < N; c0 += 32) {
+        for (int c0 = part * C_SPAN; c0 < part * C_SPAN + C_SPAN; c0 += 32) {
           float v[32];
           tc::tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * N + c0), v);
+          if constexpr (GRID) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int j = nt * N + c0 + i;
-            if (j < J && (first || v[i] > best)) {
-              best = v[i];
-              bj = j;
-              first = false;
+            for (int half = 0; half < 2; ++half) {
+              const int dir = nt * (N / 16) + c0 / 16 + half;   // the same for the whole warp
+              if (dir >= J) continue;
+              const float* hv = v + 16 * half;
+              const float4* tab = reinterpret_cast<const float4*>(psi_tab);
+              if (n_psi == 24) {
+                // psi + pi flips the odd harmonics: S_t = E_t + O_t, S_{t+12} = E_t - O_t (t < 12), even-a
+                // and odd-a partial sums E, O; then the 24 scores compared in index order
+                float sc[24];
+#pragma unroll
+                for (int g = 0; g < 3; ++g) {
+                  float e[4], o[4];
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    e[u] = hv[0];
+                    o[u] = 0.f;
+                  }
+#pragma unroll
+                  for (int q = 0; q < 12; ++q) {
+                    const float4 c = tab[q * 16 + g];
+                    const float hq = hv[q + 1];
+                    if ((q / 2) % 2 == 1) {   // a = q / 2 + 1 even
+                      e[0] = fmaf(c.x, hq, e[0]);
+                      e[1] = fmaf(c.y, hq, e[1]);
+                      e[2] = fmaf(c.z, hq, e[2]);
+                      e[3] = fmaf(c.w, hq, e[3]);
+                    } else {
+                      o[0] = fmaf(c.x, hq, o[0]);
+                      o[1] = fmaf(c.y, hq, o[1]);
+                      o[2] = fmaf(c.z, hq, o[2]);
+                      o[3] = fmaf(c.w, hq, o[3]);
+                    }
+                  }
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    sc[4 * g + u] = e[u] + o[u];
+                    sc[12 + 4 * g + u] = e[u] - o[u];
+                  }
+                }
+#pragma unroll
+                for (int t = 0; t < 24; ++t) {
+                  if (first || sc[t] > best) {
+                    best = sc[t];
+                    bj = dir * 24 + t;
+                    first = false;
+                  }
+                }
+                continue;
+              }
+              // eight angles at a time: independent accumulators, one coefficient row per harmonic term
+#pragma unroll 1
+              for (int t0 = 0; t0 < n_psi; t0 += 8) {
+                float sc[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sc[u] = hv[0];
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                  const float4 c0 = tab[q * 16 + t0 / 4], c1 = tab[q * 16 + t0 / 4 + 1];
+                  const float hq = hv[q + 1];
+                  sc[0] = fmaf(c0.x, hq, sc[0]);
+                  sc[1] = fmaf(c0.y, hq, sc[1]);
+                  sc[2] = fmaf(c0.z, hq, sc[2]);
+                  sc[3] = fmaf(c0.w, hq, sc[3]);
+                  sc[4] = fmaf(c1.x, hq, sc[4]);
+                  sc[5] = fmaf(c1.y, hq, sc[5]);
+                  sc[6] = fmaf(c1.z, hq, sc[6]);
+                  sc[7] = fmaf(c1.w, hq, sc[7]);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                  const int t = t0 + u;
+                  if (t < n_psi && (first || sc[u] > best)) {
+                    best = sc[u];
+                    bj = dir * n_psi + t;
+                    first = false;
+                  }
+                }
+              }
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int j = nt * N + c0 + i;
+              if (j < J && (first || v[i] > best)) {
+                best = v[i];
+                bj = j;
+                first = false;
+              }
             }
           }
         }
@@ -534,7 +636,9 @@ __global__ void __launch_bounds__(ws::THREADS, 1)
       if (stop) break;
       const long long p = mt * M + row;
       if (p < P) {
-        if (nsplit == 1) {
+        if (GRID) {
+          if (!first) atomicMax(keys + p, sweep_key(best, bj));
+        } else if (nsplit == 1) {
           maxv[p] = best;
           argmax[p] = bj;
         } else {
@@ -570,12 +674,30 @@ void so3_ws_split_a(const float* G, long long P, int C, int cpad, unsigned char*
 bool sweep_so3_ws(long long P, int cpad, const unsigned char* Ab, const unsigned char* Bb, int J, float* maxv,
                   int32_t* argmax, int* err, int sms, cudaStream_t st) {
   if (cpad % ws::KC != 0 || P < 1) return false;
-  if (!ext_smem_optin((const void*)k_sweep_so3_ws, ws::SMEM)) return false;
+  if (!ext_smem_optin((const void*)k_sweep_so3_ws<false>, ws::SMEM)) return false;
   const int ntn = (J + ws::N - 1) / ws::N, nkc = cpad / ws::KC;
   const long long ntm = (P + ws::M - 1) / ws::M;
   long long grid = sms;
   if (grid > ntm) grid = ntm;
-  k_sweep_so3_ws<<<dim3((unsigned)grid, 1), ws::THREADS, ws::SMEM, st>>>(Ab, Bb, P, nkc, ntn, J, maxv, argmax, nullptr,
-                                                                        err, 2000000000ull);
+  k_sweep_so3_ws<false><<<dim3((unsigned)grid, 1), ws::THREADS, ws::SMEM, st>>>(Ab, Bb, P, nkc, ntn, J, 0, maxv,
+                                                                               argmax, nullptr, err, 2000000000ull);
+  return true;
+}
+
+bool sweep_so3_ws_grid(long long P, int cpad, const unsigned char* Ab, const unsigned char* Bb, int n_dirs,
+                       int n_psi, float* maxv, int32_t* argmax, unsigned long long* keys, int* err, int sms,
+                       cudaStream_t st) {
+  if (cpad % ws::KC != 0 || P < 1 || n_psi < 1 || n_psi > 64 || !keys) return false;
+  if (!ext_smem_optin((const void*)k_sweep_so3_ws<true>, ws::SMEM)) return false;
+  const int ntn = (16 * n_dirs + ws::N - 1) / ws::N, nkc = cpad / ws::KC;
+  const long long ntm = (P + ws::M - 1) / ws::M;
+  long long grid = sms;
+  if (grid > ntm) grid = ntm;
+  cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * P, st);
+  k_sweep_so3_ws<true><<<dim3((unsigned)grid, 1), ws::THREADS_GRID, ws::SMEM, st>>>(
+      Ab, Bb, P, nkc, ntn, n_dirs, n_psi, maxv, argmax, keys, err, 2000000000ull);
+  long long b = (P + 255) / 256;
+  if (b > 4096) b = 4096;
+  k_sweep_keys_finish<<<(unsigned)b, 256, 0, st>>>(keys, P, maxv, argmax);
   return true;
 }

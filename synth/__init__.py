@@ -476,6 +476,18 @@ def so3_rotation_grid(n_dirs: int = 192, n_psi: int = 24):
     return np.array(out)
 
 
+def so3_rotation_grid_factors(n_dirs: int = 192, n_psi: int = 24):
+    """The factors of so3_rotation_grid: the n_dirs direction rotations
+    R_z(phi) R_y(theta) as quaternions [n_dirs][4] and n_psi, so that rotation
+    d * n_psi + j of the grid is R_dir(d) R_z(2 pi j / n_psi)."""
+    golden = math.pi * (3.0 - math.sqrt(5.0))
+    out = []
+    for i in range(n_dirs):
+        zc = 1.0 - (2.0 * i + 1.0) / n_dirs
+        out.append(_quat_from_zyz((golden * i) % (2 * math.pi), math.acos(zc), 0.0))
+    return np.array(out), n_psi
+
+
 def _sample_template(tables, dr, radius, Rm=None):
     """Samples sum_{l,a} f_l^a(|x|) Y_l^a(x^) at x = R^-1 d on the (2R+1)^3 box
     (data generation for planting; linear interpolation of the radial

@@ -258,3 +258,70 @@ def test_full_size_sweep_against_oracle_sampled_voxels(ec, plan, oracle_128, pre
     assert err <= tol
     assert np.all(ok[gap > window])
     assert ok.mean() >= 0.99
+
+
+def _qmul(p, q):
+    w1, x1, y1, z1 = p
+    w2, x2, y2, z2 = q
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+
+
+def _expanded_grid(dirs, n_psi):
+    return np.array([_qmul(d, np.array([math.cos(math.pi * t / n_psi), 0.0, 0.0, math.sin(math.pi * t / n_psi)]))
+                     for d in dirs for t in range(n_psi)])
+
+
+@pytest.mark.parametrize("prec,n,n_dirs,n_psi", [("bf16x3", 20001, 40, 24), ("bf16x3", 600, 17, 7),
+                                                 ("fp32", 600, 17, 7)])
+def test_grid_sweep_matches_oracle_over_the_expanded_rotations(ec, plan, prec, n, n_dirs, n_psi):
+    """ext_sweep_so3_grid over R_d R_z(2 pi t / n_psi) (Haar-random directions,
+    ragged direction tiles) against the oracle's scores of the expanded list of
+    n_dirs * n_psi rotations, index d * n_psi + t."""
+    L = 6
+    rng = np.random.default_rng(n + n_dirs)
+    nch = ec.ext_so3_channels(L)
+    channels = rng.standard_normal((nch, n)).astype(np.float32)
+    dirs = np.array([synth.haar_quaternion(rng) for _ in range(n_dirs)])
+    precision = ec.EXT_PREC_FP32 if prec == "fp32" else ec.EXT_PREC_BF16X3
+    mx = torch.empty(n, dtype=torch.float32, device="cuda")
+    am = torch.empty(n, dtype=torch.int32, device="cuda")
+    ec.ext_sweep_so3_grid(plan, dev(channels), n, L, dirs, n_psi, mx, am, precision)
+    plan.sync()
+    S = _scores_from_channels(channels, L, [quat_to_matrix(q) for q in _expanded_grid(dirs, n_psi)])
+    scale = np.abs(S).max()
+    err = np.max(np.abs(mx.cpu().numpy() - S.max(axis=1))) / scale
+    srt = np.sort(S, axis=1)
+    gap = (srt[:, -1] - srt[:, -2]) / scale
+    ok = am.cpu().numpy() == S.argmax(axis=1)
+    tol, window = (1e-5, 1e-6) if prec == "fp32" else (1e-4, 2e-4)
+    print(f"so3 grid sweep {prec} n={n} dirs={n_dirs} psi={n_psi}: score error {err:.2e}, argmax agreement "
+          f"{ok.mean():.4f}")
+    assert err <= tol
+    assert np.all(ok[gap > window])
+    assert ok.mean() >= 0.99
+
+
+def test_full_size_grid_sweep_against_oracle_sampled_voxels(ec, plan, oracle_128):
+    """ext_corr_so3_grid on the whole 128^3 volume with the factors of the
+    4608-rotation grid (192 directions x 24 in-plane angles) against the
+    oracle's scores at the 944 sampled voxels, as the plain sweep."""
+    prob, grid, vox, S = oracle_128
+    n = prob["V"].shape[0]
+    dirs, n_psi = synth.so3_rotation_grid_factors()
+    mx = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    am = torch.empty((n, n, n), dtype=torch.int32, device="cuda")
+    ec.ext_corr_so3_grid(plan, dev(prob["V"]), n, n, n, prob["tables"], prob["dr"], prob["radius"], dirs, n_psi, mx,
+                         am, ec.EXT_PREC_BF16X3)
+    plan.sync()
+    got = mx.cpu().numpy()[vox[:, 0], vox[:, 1], vox[:, 2]].astype(np.float64)
+    arg = am.cpu().numpy()[vox[:, 0], vox[:, 1], vox[:, 2]]
+    scale = np.abs(S).max()
+    err = np.max(np.abs(got - S.max(axis=1))) / scale
+    srt = np.sort(S, axis=1)
+    gap = (srt[:, -1] - srt[:, -2]) / scale
+    ok = arg == S.argmax(axis=1)
+    print(f"so3 128^3 grid sweep: score error {err:.2e} of scale, argmax agreement {ok.mean():.4f}")
+    assert err <= 1e-4
+    assert np.all(ok[gap > 2e-4])
+    assert ok.mean() >= 0.99

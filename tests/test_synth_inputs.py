@@ -81,3 +81,22 @@ def test_rotation_grid_covering_radius():
     radius = float(cur.max())
     print(f"rotation grid covering radius >= {radius:.2f} degrees")
     assert 12.0 <= radius <= 13.0
+
+
+def test_rotation_grid_is_directions_times_in_plane_angles():
+    """Rotation d * n_psi + j of the 4608-rotation grid is the direction
+    rotation d followed (on the right) by the rotation about z by 2 pi j / n_psi."""
+    grid = synth.so3_rotation_grid()
+    dirs, n_psi = synth.so3_rotation_grid_factors()
+    assert len(dirs) * n_psi == len(grid)
+
+    def qmul(p, q):
+        w1, x1, y1, z1 = p
+        w2, x2, y2, z2 = q
+        return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                         w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+    for d in (0, 5, 100, 191):
+        for j in (0, 7, 23):
+            t = 2 * math.pi * j / n_psi
+            q = qmul(dirs[d], np.array([math.cos(t / 2), 0.0, 0.0, math.sin(t / 2)]))
+            np.testing.assert_allclose(q, grid[d * n_psi + j], atol=1e-13)
