@@ -173,8 +173,9 @@ def dist_setup(n_gpus):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
+        backend = "nccl" if torch.cuda.is_available() else "gloo"   # gloo: the host-side tests on CPU
         dist.init_process_group(backend)
     return world, rank, local
 
@@ -183,6 +184,12 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def job_throughput(world, steps, units_per_rank_step, max_ms):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (in millions of units per second)."""
+    return world * steps * units_per_rank_step / (max_ms * 1e-3) / 1e6
 
 
 def reduce_max(x, world, device):
@@ -1616,7 +1623,7 @@ def main():
     launches = sum(c for _, c in plan.profile_read().values())
     clocks = clk.summary()
     total_ms = reduce_max(total_ms, world, device)
-    value = world * args.steps * P / (total_ms * 1e-3) / 1e6
+    value = job_throughput(world, args.steps, P, total_ms)
     if args.only_timed:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "Mpx/s", "steps": args.steps,
