@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>   // header-only NVTX v3: ranges cost nothing unless a profiler is attached
+
 #include "internal.h"
 
 namespace {
@@ -124,6 +126,10 @@ cudaEvent_t take_event(ext_plan plan) {
 // kernel name and, when profiling is on, bracketed by events on its stream.
 template <typename F>
 void launch(ext_plan plan, const char* name, cudaStream_t st, F&& f) {
+  struct Range {   // an NVTX range named after the kernel around its launch (tracing tools)
+    explicit Range(const char* n) { nvtxRangePushA(n); }
+    ~Range() { nvtxRangePop(); }
+  } range(name);
   if (!plan->profiling) {
     plan->prof[name].launches += 1;
     f();
