@@ -66,7 +66,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with ThreadPoolExecutor(workers) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"]
+    # --no-undefined: a declared but never defined host function fails here, not at load time
+    cmd = [nvcc, "-shared", *ARCH, "-Xlinker", "--no-undefined", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -607,7 +607,11 @@ ext_status run_conv_so2(ext_plan plan, const float* H, const float* alpha, int h
   EXT_TRY(spectra(plan, F, h, w, SPEC_CONV, st, &S));
   return conv_signals(
       plan, h, w, K + 1, 1, S, st, "rows_fwd_phase",
-      [&](int, float2* A, const float2* tw_w) { fft_rows_fwd_phase(w, H, alpha, h, 0, K + 1, A, tw_w, st); },
+      [&](int, float2* A, const float2* tw_w) {
+        if (plan->steer_mode == 2 && fft_rows_fwd_hloop_phase(w, H, alpha, h, 0, K + 1, A, tw_w, plan->sms, st)) return;
+        if (plan->steer_mode == 1) fft_rows_fwd_phase_io(w, H, alpha, h, 0, K + 1, A, tw_w, st);
+        else fft_rows_fwd_phase(w, H, alpha, h, 0, K + 1, A, tw_w, st);
+      },
       [&](int) { return out; });
 }
 
@@ -708,7 +712,7 @@ ext_status ext_plan_create(ext_plan* plan, const ext_options* options) {
   if (const char* e = getenv("EXT_PIPELINED")) p->pipelined = atoi(e) != 0;
   if (const char* e = getenv("EXT_TMA")) p->tma = atoi(e) != 0;
   if (const char* e = getenv("EXT_SO3_WS")) p->so3_ws = atoi(e) != 0;
-  if (const char* e = getenv("EXT_SCALE_TABLE")) p->scale_table = atoi(e) != 0;
+  if (const char* e = getenv("EXT_STEER_MODE")) p->steer_mode = atoi(e);
   if (const char* e = getenv("EXT_BATCH_BRANCHES")) p->batch_branches = atoi(e);
   if (p->autotune) tune_cache_read(p);
   *plan = p;
@@ -1148,19 +1152,23 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
   EXT_TRY(ensure(plan, "Dscale", sizeof(float) * P, &Db));
   const float omega_step = (float)(two_pi / log_period);
   const int unit = mode == 2 ? 1 : 0;
-  void* Tb = nullptr;
-  if (plan->scale_table && n_h <= 32) {   // measured: 3 % faster at 24 harmonics, 7 % slower at 64 (longer powering)
-    EXT_TRY(ensure(plan, "scale_phasors", sizeof(float4) * P, &Tb));
-    launch(plan, "scale_phasors", st, [&] {
-      launch_scale_phasors((const float*)sS.dev, (long long)P, omega_step, unit, (float4*)Tb, plan->sms, st);
+  void* Tt = nullptr;
+  if (plan->steer_mode >= 1) {
+    EXT_TRY(ensure(plan, "scale_turns", sizeof(float2) * P, &Tt));
+    launch(plan, "scale_turns", st, [&] {
+      launch_scale_turns((const float*)sS.dev, (long long)P, (float)(1.0 / log_period), unit, (float2*)Tt,
+                         plan->sms, st);
     });
   }
   EXT_TRY(conv_signals(
       plan, h, w, n_h, channels + (mode == 0 ? 0 : 1), S, st, "rows_fwd_scale",
       [&](int sig, float2* A, const float2* tw_w) {
         const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
-        if (Tb)
-          fft_rows_fwd_scale_tab(w, src, (const float4*)Tb, h, 0, n_h, A, tw_w, st);
+        if (Tt && plan->steer_mode == 2 &&
+            fft_rows_fwd_hloop_scale(w, src, (const float2*)Tt, h, 0, n_h, A, tw_w, plan->sms, st))
+          return;
+        if (Tt)
+          fft_rows_fwd_scale_turns(w, src, (const float2*)Tt, h, 0, n_h, A, tw_w, st);
         else
           fft_rows_fwd_scale(w, src, (const float*)sS.dev, h, 0, n_h, omega_step, unit, A, tw_w, st);
       },
@@ -1235,16 +1243,28 @@ ext_status ext_conv_similarity(ext_plan plan, const float* H, int channels, int 
   EXT_TRY(ensure(plan, "simil_uv", sizeof(float4) * P, &UV));
   const float omega_step = (float)(two_pi / log_period);
   const int unit = mode == 2 ? 1 : 0;
-  launch(plan, "simil_phasors", st, [&] {
-    launch_simil_phasors((const float*)sA.dev, (const float*)sS.dev, (long long)P, omega_step, (float4*)UV,
-                         plan->sms, st);
-  });
+  if (plan->steer_mode >= 1)
+    launch(plan, "simil_turns", st, [&] {
+      launch_simil_turns((const float*)sA.dev, (const float*)sS.dev, (long long)P, (float)(1.0 / log_period), unit,
+                         (float4*)UV, plan->sms, st);
+    });
+  else
+    launch(plan, "simil_phasors", st, [&] {
+      launch_simil_phasors((const float*)sA.dev, (const float*)sS.dev, (long long)P, omega_step, (float4*)UV,
+                           plan->sms, st);
+    });
   EXT_TRY(conv_signals(
       plan, h, w, ncomp, channels + (mode == 0 ? 0 : 1), S, st, "rows_fwd_simil",
       [&](int sig, float2* A, const float2* tw_w) {
         const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
-        fft_rows_fwd_simil(w, src, (const float4*)UV, (const float*)sS.dev, h, (const int2*)dkj, ncomp, unit, A,
-                           tw_w, st);
+        if (plan->steer_mode == 2 &&
+            fft_rows_fwd_hloop_simil(w, src, (const float4*)UV, h, (const int2*)dkj, ncomp, A, tw_w, plan->sms, st))
+          return;
+        if (plan->steer_mode >= 1)
+          fft_rows_fwd_simil_turns(w, src, (const float4*)UV, h, (const int2*)dkj, ncomp, A, tw_w, st);
+        else
+          fft_rows_fwd_simil(w, src, (const float4*)UV, (const float*)sS.dev, h, (const int2*)dkj, ncomp, unit, A,
+                             tw_w, st);
       },
       [&](int sig) { return sig < channels ? (float*)Nb + P * sig : (float*)Db; }));
   launch(plan, "scale_finalize", st, [&] {

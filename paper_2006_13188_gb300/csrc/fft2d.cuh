@@ -300,6 +300,21 @@ __device__ __forceinline__ void sincos_kalpha(int k, float alpha, float* s, floa
   sincosf(r, s, c);
 }
 
+// The same reduction with the remainder (|r| <= pi + |e|) passed to
+// sincospif as r / pi: branch-free, so loads ahead of it can be hoisted; the
+// extra rounding of r / pi adds at most about 3e-7 rad.
+__device__ __forceinline__ void sincos_kalpha_pi(int k, float alpha, float* s, float* c) {
+  const float kf = (float)k;
+  const float p = kf * alpha;
+  const float e = fmaf(kf, alpha, -p);
+  const float n = rintf(p * 0.15915494309189535f);
+  float r = fmaf(-n, 6.28125f, p);
+  r = fmaf(-n, 0.0019353071693331003f, r);
+  r = fmaf(-n, 1.0253131677018246e-11f, r);
+  r += e;
+  sincospif(r * 0.31830988618379067f, s, c);
+}
+
 // exp(i w x) for FP32 w, x: the product is formed exactly as p + e and
 // reduced like sincos_kalpha.
 __device__ __forceinline__ void sincos_wx(float wk, float x, float* s, float* c) {
@@ -430,54 +445,6 @@ k_rows_fwd_scale(const float* __restrict__ H, const float* __restrict__ sfield, 
   });
 }
 
-// The same transform with the per-pixel values formed once per call:
-//   T[p] = (u, wgt, 0), u = e^{-i w_1 ln s(p)} (one logf and sincos per pixel
-//   instead of per pixel and harmonic), A_k = H wgt u^k, u^k by repeated
-// squaring; blockIdx.x = harmonic (fastest) so the row block's H and T come
-// from L2 for all harmonics.
-__device__ __forceinline__ float2 c_pow_u(float2 b, int e) {
-  float2 r = make_float2(1.f, 0.f);
-  while (e) {
-    if (e & 1) r = c_mul(r, b);
-    b = c_mul(b, b);
-    e >>= 1;
-  }
-  return r;
-}
-
-template <int N>
-__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
-k_rows_fwd_scale_tab(const float* __restrict__ H, const float4* __restrict__ T, int h, int k0,
-                     float2* __restrict__ A, const float2* __restrict__ tw) {
-  using C = LineCfg<N>;
-  constexpr int TH = C::ROW_THREADS;
-  extern __shared__ float2 sm[];
-  const float2* twl = stage_twiddles<N, C::RL * C::LS>(sm, tw, C::ROW_THREADS);
-  const int y0 = blockIdx.y * C::RL;
-  const int k = k0 + (int)blockIdx.x;
-  float hv[STAGE_G];
-  float4 tv[STAGE_G];
-  for_elems_staged<C::RL * N, TH, STAGE_G>(
-      [&](int i, int e) {
-        const int y = y0 + e / N;
-        const size_t idx = (size_t)y * N + e % N;
-        hv[i] = (y < h) ? (H ? __ldg(H + idx) : 1.0f) : 0.f;
-        tv[i] = (y < h) ? __ldg(T + idx) : make_float4(1.f, 0.f, 0.f, 0.f);
-      },
-      [&](int i, int e) {
-        const float a = hv[i] * tv[i].z;
-        const float2 z = c_pow_u(make_float2(tv[i].x, tv[i].y), k);
-        sm[(e / N) * C::LS + sidx(e % N)] = make_float2(a * z.x, a * z.y);
-      });
-  __syncthreads();
-  row_fft<N, false>(sm, twl);
-  float2* out = A + (size_t)blockIdx.x * h * N;
-  for_elems<C::RL * N, TH>([&](int i, int e) {
-    const int y = y0 + e / N;
-    if (y < h) out[(size_t)y * N + e % N] = sm[(e / N) * C::LS + sidx(e % N)];
-  });
-}
-
 // Forward transform of the similarity-steered signals (rotation and scale
 // fields together, in log-polar harmonics):
 //   A_c = H wgt exp(-i (k alpha + w_j ln s)) = H wgt u^k v^j,  (k, j) = kj[blockIdx.x],
@@ -536,6 +503,244 @@ k_rows_fwd_simil(const float* __restrict__ H, const float4* __restrict__ uv, con
     const int y = y0 + e / N;
     if (y < h) out[(size_t)y * N + e % N] = sm[(e / N) * C::LS + sidx(e % N)];
   });
+}
+
+// ------------------------------------------ steered forward row passes ---
+// e^{-2 pi i q} for q = m t (t a fraction of a turn, m an integer held in a
+// float): the product is formed exactly as p + e (two-product with an FMA),
+// its integer part is dropped (p - rint(p) is exact), and the remainder,
+// |r| <= 1/2 + |e|, goes to sincospif.  No range reduction by 2 pi is needed.
+__device__ __forceinline__ float2 turn_phasor(float m, float t) {
+  const float p = m * t;
+  const float e = fmaf(m, t, -p);
+  const float r = (p - rintf(p)) + e;
+  float sn, cs;
+  sincospif(2.f * r, &sn, &cs);
+  return make_float2(cs, -sn);
+}
+
+// Steering policies of k_rows_fwd_steered: comp(c) gives the constants of
+// component c, at(cc, p) the steered signal of that component at pixel p.
+// H == nullptr stands for the constant signal 1 (the denominator of Eq.
+// normalization).
+struct SteerPhase {   // A_k = H e^{-i k alpha} (Sec. 4.1, extended convolution)
+  const float* H;
+  const float* alpha;
+  int k0;
+  __device__ __forceinline__ int comp(int c) const { return k0 + c; }
+  __device__ __forceinline__ float2 at(int k, size_t p) const {
+    const float hv = H ? __ldg(H + p) : 1.0f;
+    float sn, cs;
+    sincos_kalpha_pi(k, __ldg(alpha + p), &sn, &cs);
+    return make_float2(hv * cs, -hv * sn);
+  }
+};
+
+struct SteerScale {   // A_k = H wgt e^{-i w_k ln s} = H wgt e^{-2 pi i k t}, (t, wgt) = T[p] (Sec. 8)
+  const float* H;
+  const float2* T;
+  int k0;
+  __device__ __forceinline__ float comp(int c) const { return (float)(k0 + c); }
+  __device__ __forceinline__ float2 at(float k, size_t p) const {
+    const float2 tv = __ldg(T + p);
+    const float a = (H ? __ldg(H + p) : 1.0f) * tv.y;
+    const float2 z = turn_phasor(k, tv.x);
+    return make_float2(a * z.x, a * z.y);
+  }
+};
+
+struct SteerSimil {   // A_(k,j) = H wgt e^{-i (k alpha + w_j ln s)}, (a, b, wgt) = T[p], turns a = alpha / 2 pi, b = ln s / log_period
+  const float* H;
+  const float4* T;
+  const int2* kj;
+  __device__ __forceinline__ float2 comp(int c) const {
+    const int2 v = kj[c];
+    return make_float2((float)v.x, (float)v.y);
+  }
+  __device__ __forceinline__ float2 at(float2 c, size_t p) const {
+    const float4 tv = __ldg(T + p);
+    const float a = (H ? __ldg(H + p) : 1.0f) * tv.z;
+    const float p1 = c.x * tv.x, e1 = fmaf(c.x, tv.x, -p1);
+    const float p2 = c.y * tv.y, e2 = fmaf(c.y, tv.y, -p2);
+    const float r = ((p1 - rintf(p1)) + (p2 - rintf(p2))) + (e1 + e2);
+    float sn, cs;
+    sincospif(2.f * r, &sn, &cs);
+    return make_float2(a * cs, -a * sn);
+  }
+};
+
+// Forward row transform of steered signals: the steering is evaluated in the
+// first butterfly stage's loads (straight from global memory, coalesced) and
+// the last stage writes its outputs straight to global memory, so each
+// element passes through shared memory twice fewer than when the lines are
+// staged first.  blockIdx.x = component (fastest: the blocks of all
+// components of a row block run together and read its inputs from L2),
+// blockIdx.y = row block; component c's plane is A + c h N.
+template <int N, class Steer>
+__global__ void __launch_bounds__(LineCfg<N>::ROW_THREADS, LineCfg<N>::ROW_MINB)
+k_rows_fwd_steered(const Steer sp, int h, float2* __restrict__ A, const float2* __restrict__ tw) {
+  using C = LineCfg<N>;
+  constexpr int T = C::ROW_THREADS;
+  extern __shared__ float2 sm[];
+  const float2* twl = stage_twiddles<N, C::RL * C::LS>(sm, tw, T);
+  const int y0 = blockIdx.y * C::RL;
+  const auto cc = sp.comp((int)blockIdx.x);
+  float2* out = A + (size_t)blockIdx.x * h * N;
+  auto load = [&](int l, int x) -> float2 {
+    const int y = y0 + l;
+    return y < h ? sp.at(cc, (size_t)y * N + x) : make_float2(0.f, 0.f);
+  };
+  auto store = [&](int l, int x, float2 v) {
+    const int y = y0 + l;
+    if (y < h) out[(size_t)y * N + x] = v;
+  };
+  ct_fft_io<N, false, false, C::RL, T>(sm, C::LS, 1, twl, load, store);
+}
+
+// --------------------------- steered forward row passes, component loop ---
+// One row per block, N / 16 threads, 16 elements per thread: the per-pixel
+// inputs of the row are read once into registers and every component of the
+// block's group is then steered from them and transformed (first radix-16
+// stage in registers, the other two stages ping-ponging between two
+// shared-memory rows, the last one writing straight to global memory), so the
+// loads and the stage-twiddle staging are paid once per row instead of once
+// per row and component, and each component needs two barriers.
+template <int N>
+struct HloopCfg {
+  static constexpr RadixList L = factor_radices(N);
+  static constexpr int THREADS = N / 16;
+  static constexpr int LS = ct_sidx_len(N);
+  static constexpr int SMEM = 2 * LS * 8 + N * 8;   // two padded rows + the stage twiddles
+  static constexpr int MINB = THREADS > 0 && 512 / THREADS > 0 ? 512 / THREADS : 1;
+  static constexpr bool OK = L.cnt == 3 && L.r[0] == 16 && THREADS >= 64 && THREADS % 32 == 0 &&
+                             SMEM * MINB <= 220 * 1024;
+};
+
+// Ping-pong Stockham stage: reads `in`, writes `out` (or, LAST, hands each
+// output to store(x, value)); no barrier inside.
+template <int N, int R, int NS, int THREADS, bool LAST, class Store>
+__device__ __forceinline__ void pp_stage(const float2* in, float2* out, const float2* __restrict__ tw,
+                                         Store&& store) {
+  constexpr int NB = N / R;
+  constexpr int S = (NB + THREADS - 1) / THREADS;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int j = threadIdx.x + s * THREADS;
+    if (NB % THREADS == 0 || j < NB) {
+      const int k = j % NS;
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float2 a = in[sidx(j + r * NB)];
+        if (r > 0) a = c_mul(a, tw[r * NS - 1 + k]);
+        v[r] = a;
+      }
+      dft<R, false>(v);
+      const int dst = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (LAST) store(dst + r * NS, v[r]);
+        else out[sidx(dst + r * NS)] = v[r];
+      }
+    }
+  }
+}
+
+// Steering policies of k_rows_fwd_hloop: load(p) gives the per-pixel state q
+// held across components, comp(c) the constants of component c, at(cc, q)
+// the steered signal.  H == nullptr stands for the constant signal 1.
+struct HloopScale {   // A_k = H wgt e^{-2 pi i k t}; q = (H wgt, t)
+  const float* H;
+  const float2* T;
+  int k0;
+  using Q = float2;
+  __device__ __forceinline__ Q load(size_t p) const {
+    const float2 tv = __ldg(T + p);
+    return make_float2((H ? __ldg(H + p) : 1.0f) * tv.y, tv.x);
+  }
+  __device__ __forceinline__ float comp(int c) const { return (float)(k0 + c); }
+  __device__ __forceinline__ float2 at(float k, const Q& q) const {
+    const float2 z = turn_phasor(k, q.y);
+    return make_float2(q.x * z.x, q.x * z.y);
+  }
+};
+
+struct HloopSimil {   // A_(k,j) = H wgt e^{-2 pi i (k a + j b)}; q = (H wgt, a, b)
+  const float* H;
+  const float4* T;
+  const int2* kj;
+  using Q = float3;
+  __device__ __forceinline__ Q load(size_t p) const {
+    const float4 tv = __ldg(T + p);
+    return make_float3((H ? __ldg(H + p) : 1.0f) * tv.z, tv.x, tv.y);
+  }
+  __device__ __forceinline__ float2 comp(int c) const {
+    const int2 v = kj[c];
+    return make_float2((float)v.x, (float)v.y);
+  }
+  __device__ __forceinline__ float2 at(float2 c, const Q& q) const {
+    const float p1 = c.x * q.y, e1 = fmaf(c.x, q.y, -p1);
+    const float p2 = c.y * q.z, e2 = fmaf(c.y, q.z, -p2);
+    const float r = ((p1 - rintf(p1)) + (p2 - rintf(p2))) + (e1 + e2);
+    float sn, cs;
+    sincospif(2.f * r, &sn, &cs);
+    return make_float2(q.x * cs, -q.x * sn);
+  }
+};
+
+struct HloopPhase {   // A_k = H e^{-i k alpha}; q = (H, alpha)
+  const float* H;
+  const float* alpha;
+  int k0;
+  using Q = float2;
+  __device__ __forceinline__ Q load(size_t p) const {
+    return make_float2(H ? __ldg(H + p) : 1.0f, __ldg(alpha + p));
+  }
+  __device__ __forceinline__ int comp(int c) const { return k0 + c; }
+  __device__ __forceinline__ float2 at(int k, const Q& q) const {
+    float sn, cs;
+    sincos_kalpha_pi(k, q.y, &sn, &cs);
+    return make_float2(q.x * cs, -q.x * sn);
+  }
+};
+
+// blockIdx.x = row, blockIdx.y = component group [c0, c1), c0 = blockIdx.y *
+// cpb; component c's plane is A + c h N.
+template <int N, class Steer>
+__global__ void __launch_bounds__(HloopCfg<N>::THREADS, HloopCfg<N>::MINB)
+k_rows_fwd_hloop(const Steer sp, int h, int ncomp, int cpb, float2* __restrict__ A, const float2* __restrict__ tw) {
+  using HC = HloopCfg<N>;
+  constexpr int T = HC::THREADS;
+  constexpr int LS = HC::LS;
+  constexpr int R1 = HC::L.r[1], R2 = HC::L.r[2];
+  extern __shared__ float2 sm[];
+  float2* X = sm;
+  float2* Y = sm + LS;
+  const float2* twl = stage_twiddles<N, 2 * LS>(sm, tw, T);
+  const int y = blockIdx.x;
+  const int c0 = blockIdx.y * cpb;
+  const int c1 = min(ncomp, c0 + cpb);
+  const int j = threadIdx.x;
+  typename Steer::Q q[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) q[r] = sp.load((size_t)y * N + j + r * T);
+  auto nostore = [](int, float2) {};
+  for (int c = c0; c < c1; ++c) {
+    const auto cc = sp.comp(c);
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = sp.at(cc, q[r]);
+    dft<16, false>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) X[sidx(j * 16 + r)] = v[r];
+    __syncthreads();   // X complete (and, on the first pass, the stage twiddles)
+    pp_stage<N, R1, 16, T, false>(X, Y, twl, nostore);
+    __syncthreads();   // Y complete; X free for the next component
+    float2* out = A + (size_t)c * h * N + (size_t)y * N;
+    pp_stage<N, R2, 16 * R1, T, true>(Y, nullptr, twl, [&](int x, float2 v2) { out[x] = v2; });
+    // the next component writes X (read before the barrier above) and then Y
+    // (after its own first barrier, when every thread has finished this read)
+  }
 }
 
 template <int N>
@@ -1543,8 +1748,19 @@ struct FftOps {
                        cudaStream_t st);
   static void rows_fwd_simil(const float* H, const float4* uv, const float* s, int h, const int2* kj, int ncomp,
                              int unit_integral, float2* A, const float2* tw, cudaStream_t st);
-  static void rows_fwd_scale_tab(const float* H, const float4* T, int h, int k0, int nk, float2* A,
-                                 const float2* tw, cudaStream_t st);
+  static void rows_fwd_scale_turns(const float* H, const float2* T, int h, int k0, int nk, float2* A,
+                                   const float2* tw, cudaStream_t st);
+  static void rows_fwd_simil_turns(const float* H, const float4* T, int h, const int2* kj, int ncomp, float2* A,
+                                   const float2* tw, cudaStream_t st);
+  static void rows_fwd_phase_io(const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                                const float2* tw, cudaStream_t st);
+  // component-loop variants (false where the line length has no 16 x R1 x R2 plan)
+  static bool rows_fwd_hloop_scale(const float* H, const float2* T, int h, int k0, int nk, float2* A,
+                                   const float2* tw, int sms, cudaStream_t st);
+  static bool rows_fwd_hloop_simil(const float* H, const float4* T, int h, const int2* kj, int ncomp, float2* A,
+                                   const float2* tw, int sms, cudaStream_t st);
+  static bool rows_fwd_hloop_phase(const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                                   const float2* tw, int sms, cudaStream_t st);
   static void rows_fwd_scale(const float* H, const float* s, int h, int k0, int nk, float omega_step,
                              int unit_integral, float2* A, const float2* tw, cudaStream_t st);
   static void rows_inv_components(const float2* Z, int h, int k0, int nk, float* G, const float2* tw,
@@ -1851,13 +2067,84 @@ void FftOps<N>::rows_fwd_simil(const float* H, const float4* uv, const float* s,
   k_rows_fwd_simil<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, uv, s, h, kj, unit_integral, A, tw);
 }
 
-template <int N>
-void FftOps<N>::rows_fwd_scale_tab(const float* H, const float4* T, int h, int k0, int nk, float2* A,
-                                   const float2* tw, cudaStream_t st) {
-  const bool once = (ext_set_smem(k_rows_fwd_scale_tab<N>, C::ROW_SMEM), true);
+template <int N, class Steer>
+static void launch_rows_fwd_steered(const Steer& sp, int h, int ncomp, float2* A, const float2* tw, cudaStream_t st) {
+  using C = LineCfg<N>;
+  const bool once = (ext_set_smem(k_rows_fwd_steered<N, Steer>, C::ROW_SMEM), true);
   (void)once;
-  dim3 grid(nk, (h + C::RL - 1) / C::RL);
-  k_rows_fwd_scale_tab<N><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(H, T, h, k0, A, tw);
+  dim3 grid(ncomp, (h + C::RL - 1) / C::RL);
+  k_rows_fwd_steered<N, Steer><<<grid, C::ROW_THREADS, C::ROW_SMEM, st>>>(sp, h, A, tw);
+}
+
+// Component groups of the component-loop pass: the group count G minimises
+// waves(h G blocks) x (ceil(ncomp / G) + 1), a block taking about one
+// component's time for its loads and twiddle staging plus one per component.
+inline int hloop_groups(int h, int ncomp, int slots) {
+  long long best = -1;
+  int bg = 1;
+  for (int g = 1; g <= ncomp; ++g) {
+    const int cpb = (ncomp + g - 1) / g;
+    if (g > 1 && (ncomp + cpb - 1) / cpb < g) continue;   // same split as a smaller g
+    const long long waves = ((long long)h * g + slots - 1) / slots;
+    const long long cost = waves * (cpb + 1);
+    if (best < 0 || cost < best) {
+      best = cost;
+      bg = g;
+    }
+  }
+  return bg;
+}
+
+template <int N, class Steer>
+static bool launch_rows_fwd_hloop(const Steer& sp, int h, int ncomp, float2* A, const float2* tw, int sms,
+                                  cudaStream_t st) {
+  using HC = HloopCfg<N>;
+  if constexpr (!HC::OK) {
+    return false;
+  } else {
+    if (!ext_set_smem(k_rows_fwd_hloop<N, Steer>, HC::SMEM)) return false;
+    const int g = hloop_groups(h, ncomp, sms * HC::MINB);
+    const int cpb = (ncomp + g - 1) / g;
+    dim3 grid(h, (ncomp + cpb - 1) / cpb);
+    k_rows_fwd_hloop<N, Steer><<<grid, HC::THREADS, HC::SMEM, st>>>(sp, h, ncomp, cpb, A, tw);
+    return true;
+  }
+}
+
+template <int N>
+bool FftOps<N>::rows_fwd_hloop_scale(const float* H, const float2* T, int h, int k0, int nk, float2* A,
+                                     const float2* tw, int sms, cudaStream_t st) {
+  return launch_rows_fwd_hloop<N>(HloopScale{H, T, k0}, h, nk, A, tw, sms, st);
+}
+
+template <int N>
+bool FftOps<N>::rows_fwd_hloop_simil(const float* H, const float4* T, int h, const int2* kj, int ncomp, float2* A,
+                                     const float2* tw, int sms, cudaStream_t st) {
+  return launch_rows_fwd_hloop<N>(HloopSimil{H, T, kj}, h, ncomp, A, tw, sms, st);
+}
+
+template <int N>
+bool FftOps<N>::rows_fwd_hloop_phase(const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                                     const float2* tw, int sms, cudaStream_t st) {
+  return launch_rows_fwd_hloop<N>(HloopPhase{H, alpha, k0}, h, nk, A, tw, sms, st);
+}
+
+template <int N>
+void FftOps<N>::rows_fwd_scale_turns(const float* H, const float2* T, int h, int k0, int nk, float2* A,
+                                     const float2* tw, cudaStream_t st) {
+  launch_rows_fwd_steered<N>(SteerScale{H, T, k0}, h, nk, A, tw, st);
+}
+
+template <int N>
+void FftOps<N>::rows_fwd_simil_turns(const float* H, const float4* T, int h, const int2* kj, int ncomp, float2* A,
+                                     const float2* tw, cudaStream_t st) {
+  launch_rows_fwd_steered<N>(SteerSimil{H, T, kj}, h, ncomp, A, tw, st);
+}
+
+template <int N>
+void FftOps<N>::rows_fwd_phase_io(const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                                  const float2* tw, cudaStream_t st) {
+  launch_rows_fwd_steered<N>(SteerPhase{H, alpha, k0}, h, nk, A, tw, st);
 }
 
 template <int N>

@@ -133,30 +133,85 @@ void launch_simil_phasors(const float* alpha, const float* s, long long P, float
   k_simil_phasors<<<blocks, 256, 0, st>>>(alpha, s, P, omega_step, uv);
 }
 
-// Per-pixel values of the scale-steered signals: (e^{-i w_1 ln s}, wgt, 0), wgt = 1/s^2 or 1.
-__global__ void k_scale_phasors(const float* __restrict__ sfield, long long P, float omega_step, int unit_integral,
-                                float4* __restrict__ T) {
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
-    const float sv = __ldg(sfield + p);
-    float sn, cs;
-    sincos_wx(omega_step, logf(sv), &sn, &cs);
-    T[p] = make_float4(cs, -sn, unit_integral ? 1.0f / (sv * sv) : 1.0f, 0.f);
-  }
-}
-
-void launch_scale_phasors(const float* s, long long P, float omega_step, int unit_integral, float4* T, int sms,
-                          cudaStream_t st) {
-  if (P <= 0) return;
-  const int blocks = (int)std::min<long long>((P + 255) / 256, (long long)sms * 8);
-  k_scale_phasors<<<blocks, 256, 0, st>>>(s, P, omega_step, unit_integral, T);
-}
-
-#define EXT_C1(N) case N: FftOps<N>::rows_fwd_scale_tab(H, T, h, k0, nk, A, tw, st); return;
-void fft_rows_fwd_scale_tab(int w, const float* H, const float4* T, int h, int k0, int nk, float2* A,
-                            const float2* tw, cudaStream_t st) {
+#define EXT_C1(N) case N: FftOps<N>::rows_fwd_scale_turns(H, T, h, k0, nk, A, tw, st); return;
+void fft_rows_fwd_scale_turns(int w, const float* H, const float2* T, int h, int k0, int nk, float2* A,
+                              const float2* tw, cudaStream_t st) {
   switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
 }
 #undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::rows_fwd_simil_turns(H, T, h, kj, ncomp, A, tw, st); return;
+void fft_rows_fwd_simil_turns(int w, const float* H, const float4* T, int h, const int2* kj, int ncomp, float2* A,
+                              const float2* tw, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: FftOps<N>::rows_fwd_phase_io(H, alpha, h, k0, nk, A, tw, st); return;
+void fft_rows_fwd_phase_io(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                           const float2* tw, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: return FftOps<N>::rows_fwd_hloop_scale(H, T, h, k0, nk, A, tw, sms, st);
+bool fft_rows_fwd_hloop_scale(int w, const float* H, const float2* T, int h, int k0, int nk, float2* A,
+                              const float2* tw, int sms, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return false; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: return FftOps<N>::rows_fwd_hloop_simil(H, T, h, kj, ncomp, A, tw, sms, st);
+bool fft_rows_fwd_hloop_simil(int w, const float* H, const float4* T, int h, const int2* kj, int ncomp, float2* A,
+                              const float2* tw, int sms, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return false; }
+}
+#undef EXT_C1
+
+#define EXT_C1(N) case N: return FftOps<N>::rows_fwd_hloop_phase(H, alpha, h, k0, nk, A, tw, sms, st);
+bool fft_rows_fwd_hloop_phase(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                              const float2* tw, int sms, cudaStream_t st) {
+  switch (w) { EXT_FFT_SIZES(EXT_C1) default: return false; }
+}
+#undef EXT_C1
+
+// Per-pixel turns of the scale steering: t = ln s / log_period reduced to
+// [-1/2, 1/2] (the phase of harmonic k is 2 pi k t, since w_k = 2 pi k /
+// log_period) and the weight 1/s^2 (unit_integral) or 1.
+__global__ void k_scale_turns(const float* __restrict__ sfield, long long P, float inv_log_period, int unit_integral,
+                              float2* __restrict__ T) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    const float sv = __ldg(sfield + p);
+    const float t = logf(sv) * inv_log_period;
+    T[p] = make_float2(t - rintf(t), unit_integral ? 1.0f / (sv * sv) : 1.0f);
+  }
+}
+
+void launch_scale_turns(const float* s, long long P, float inv_log_period, int unit_integral, float2* T, int sms,
+                        cudaStream_t st) {
+  if (P <= 0) return;
+  const int blocks = (int)std::min<long long>((P + 255) / 256, (long long)sms * 8);
+  k_scale_turns<<<blocks, 256, 0, st>>>(s, P, inv_log_period, unit_integral, T);
+}
+
+// Per-pixel turns of the similarity steering: (alpha / 2 pi, ln s / log_period),
+// each reduced to [-1/2, 1/2], and the weight 1/s^2 (unit_integral) or 1.
+__global__ void k_simil_turns(const float* __restrict__ alpha, const float* __restrict__ sfield, long long P,
+                              float inv_log_period, int unit_integral, float4* __restrict__ T) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    const float sv = __ldg(sfield + p);
+    const float a = __ldg(alpha + p) * 0.15915494309189535f;
+    const float b = logf(sv) * inv_log_period;
+    T[p] = make_float4(a - rintf(a), b - rintf(b), unit_integral ? 1.0f / (sv * sv) : 1.0f, 0.f);
+  }
+}
+
+void launch_simil_turns(const float* alpha, const float* s, long long P, float inv_log_period, int unit_integral,
+                        float4* T, int sms, cudaStream_t st) {
+  if (P <= 0) return;
+  const int blocks = (int)std::min<long long>((P + 255) / 256, (long long)sms * 8);
+  k_simil_turns<<<blocks, 256, 0, st>>>(alpha, s, P, inv_log_period, unit_integral, T);
+}
 
 #define EXT_C1(N) case N: FftOps<N>::rows_fwd_scale(H, s, h, k0, nk, omega_step, unit_integral, A, tw, st); return;
 void fft_rows_fwd_scale(int w, const float* H, const float* s, int h, int k0, int nk, float omega_step,

@@ -31,13 +31,26 @@ void fft_rows_fwd_phase(int w, const float* H, const float* alpha, int h, int k0
 // per-pixel phasors (e^{-i alpha}, e^{-i w_1 ln s}) of launch_simil_phasors
 void fft_rows_fwd_simil(int w, const float* H, const float4* uv, const float* s, int h, const int2* kj, int ncomp,
                         int unit_integral, float2* A, const float2* tw, cudaStream_t st);
+void fft_rows_fwd_scale_turns(int w, const float* H, const float2* T, int h, int k0, int nk, float2* A,
+                              const float2* tw, cudaStream_t st);
+void fft_rows_fwd_simil_turns(int w, const float* H, const float4* T, int h, const int2* kj, int ncomp, float2* A,
+                              const float2* tw, cudaStream_t st);
+void fft_rows_fwd_phase_io(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                           const float2* tw, cudaStream_t st);
+// component-loop steered row passes (false: no plan for this line length; use the others)
+bool fft_rows_fwd_hloop_scale(int w, const float* H, const float2* T, int h, int k0, int nk, float2* A,
+                              const float2* tw, int sms, cudaStream_t st);
+bool fft_rows_fwd_hloop_simil(int w, const float* H, const float4* T, int h, const int2* kj, int ncomp, float2* A,
+                              const float2* tw, int sms, cudaStream_t st);
+bool fft_rows_fwd_hloop_phase(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
+                              const float2* tw, int sms, cudaStream_t st);
+// per-pixel turns (t, wgt) / (alpha / 2 pi, ln s / log_period, wgt) of the steered row passes
+void launch_scale_turns(const float* s, long long P, float inv_log_period, int unit_integral, float2* T, int sms,
+                        cudaStream_t st);
+void launch_simil_turns(const float* alpha, const float* s, long long P, float inv_log_period, int unit_integral,
+                        float4* T, int sms, cudaStream_t st);
 void launch_simil_phasors(const float* alpha, const float* s, long long P, float omega_step, float4* uv, int sms,
                           cudaStream_t st);
-// the same from a per-call table T = (e^{-i w_1 ln s}, wgt, 0) of launch_scale_phasors (harmonic-fastest grid)
-void launch_scale_phasors(const float* s, long long P, float omega_step, int unit_integral, float4* T, int sms,
-                          cudaStream_t st);
-void fft_rows_fwd_scale_tab(int w, const float* H, const float4* T, int h, int k0, int nk, float2* A,
-                            const float2* tw, cudaStream_t st);
 void fft_rows_fwd_scale(int w, const float* H, const float* s, int h, int k0, int nk, float omega_step,
                         int unit_integral, float2* A, const float2* tw, cudaStream_t st);
 void fft_rows_c2c(int w, const float2* X, int h, int nplanes, float2* Y, bool inv, const float2* tw,
