@@ -587,7 +587,8 @@ ext_status conv_signals(ext_plan plan, int h, int w, int ncomp, int nsig, const 
     bool done = false;
     if (tma_A)
       launch(plan, "cols_conv_tma", st, [&] {
-        done = fft_cols_conv_tma(h, tmA, w, br, ncomp - 1, S, (float2*)Y, tw_h, stw, plan->dev_err, plan->sms, st);
+        done = fft_cols_conv_tma(h, tmA, w, br, ncomp - 1, S, (float2*)Y, tw_h, stw, plan->dev_err, plan->sms, st,
+                                 plan->colconv_form == 2);
       });
     if (!done)
       launch(plan, "cols_conv", st,
@@ -713,6 +714,7 @@ ext_status ext_plan_create(ext_plan* plan, const ext_options* options) {
   if (const char* e = getenv("EXT_TMA")) p->tma = atoi(e) != 0;
   if (const char* e = getenv("EXT_SO3_WS")) p->so3_ws = atoi(e) != 0;
   if (const char* e = getenv("EXT_STEER_MODE")) p->steer_mode = atoi(e);
+  if (const char* e = getenv("EXT_COLCONV")) p->colconv_form = atoi(e);
   if (const char* e = getenv("EXT_BATCH_BRANCHES")) p->batch_branches = atoi(e);
   if (p->autotune) tune_cache_read(p);
   *plan = p;

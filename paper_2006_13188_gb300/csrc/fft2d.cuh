@@ -150,6 +150,63 @@ __device__ __forceinline__ void ct_fft(float2* buf, int ls, int es, const float2
   }
 }
 
+// Stages ST .. END-1 of the transform (in place, as ct_fft).
+template <int N, bool INV, bool LINE_FAST, int NLINES, int THREADS, int ST, int END, int NS>
+__device__ __forceinline__ void ct_fft_range(float2* buf, int ls, int es, const float2* tw) {
+  constexpr RadixList L = factor_radices(N);
+  if constexpr (ST < END) {
+    constexpr int R = L.r[ST];
+    ct_stage<N, R, NS, INV, LINE_FAST, NLINES, THREADS>(buf, ls, es, tw);
+    ct_fft_range<N, INV, LINE_FAST, NLINES, THREADS, ST + 1, END, NS * R>(buf, ls, es, tw);
+  }
+}
+
+// Output (line, x) of butterfly s, value r of the last forward stage of a
+// column transform (LINE_FAST: line = it mod NLINES); valid() is false for
+// butterflies past the end.
+template <int N, int NLINES, int THREADS>
+struct LastColStage {
+  static constexpr RadixList L = factor_radices(N);
+  static constexpr int R = L.r[L.cnt - 1];
+  static constexpr int NS = N / R;
+  static constexpr int NB = N / R;
+  static constexpr int TOTAL = NB * NLINES;
+  static constexpr int S = (TOTAL + THREADS - 1) / THREADS;
+  __device__ static __forceinline__ bool valid(int s) {
+    return TOTAL % THREADS == 0 || (int)threadIdx.x + s * THREADS < TOTAL;
+  }
+  __device__ static __forceinline__ int line(int s) { return ((int)threadIdx.x + s * THREADS) % NLINES; }
+  // NS R = N, so the butterfly's first output is j itself
+  __device__ static __forceinline__ int x(int s, int r) { return ((int)threadIdx.x + s * THREADS) / NLINES + r * NS; }
+};
+
+// The last forward stage of a column transform (buf in the column layout,
+// line stride 1, element stride es), its outputs handed to fn(s, r, value)
+// instead of being stored; s and r are compile-time after unrolling.
+template <int N, int NLINES, int THREADS, class Fn>
+__device__ __forceinline__ void ct_last_stage_cols(const float2* buf, int es, const float2* __restrict__ tw, Fn&& fn) {
+  using LS_ = LastColStage<N, NLINES, THREADS>;
+  constexpr int R = LS_::R, NS = LS_::NS, NB = LS_::NB;
+#pragma unroll
+  for (int s = 0; s < LS_::S; ++s) {
+    if (LS_::valid(s)) {
+      const int it = threadIdx.x + s * THREADS;
+      const int line = it % NLINES, j = it / NLINES;
+      const int k = j % NS;
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float2 a = buf[line + sidx(j + r * NB) * es];
+        if (NS > 1 && r > 0) a = c_mul(a, tw[r * NS - 1 + k]);
+        v[r] = a;
+      }
+      dft<R, false>(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r) fn(s, r, v[r]);
+    }
+  }
+}
+
 // Stage with functor I/O: load(line, idx) supplies the inputs (FIRST: from
 // anywhere, e.g. a staging buffer with a product fused in; INPLACE_FIRST: the
 // first stage's loads read buf itself, so all reads finish before any write)
@@ -1554,19 +1611,21 @@ k_cols_inv_corr_tma(const __grid_constant__ CUtensorMap tmH, int w, int br, cons
 // the products have been accumulated (in registers).  Column tiles are
 // strided over the blocks; waits are bounded (err = EXT_ERR_TIMEOUT, the
 // block stops).
-template <int N>
+template <int N, bool FUSED>
 __global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, 1)
 k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, const float2* __restrict__ S,
                 float2* __restrict__ Y, const float2* __restrict__ tw, const float2* __restrict__ stw_g,
                 int* __restrict__ err) {
   using C = LineCfg<N>;
   using TC = TmaColCfg<N>;
+  using LC = LastColStage<N, C::CW, C::COL_THREADS>;
   constexpr int T = C::COL_THREADS;
   constexpr int CW = C::CW;
   constexpr int TILE = TC::TILE;
+  constexpr int NACC = FUSED ? LC::S * LC::R : C::COL_EPT;
   extern __shared__ float2 sm_raw[];
   __shared__ __align__(8) uint64_t bar_a, bar_s;
-  __shared__ int abort_flag;
+  __shared__ int abort_a, abort_s;   // separate flags: each is read only after a barrier that follows its writes
   float2* sm = reinterpret_cast<float2*>(sm_raw) + ((128 - (tc::smem_u32(sm_raw) & 127)) & 127) / 8;
   float2* W = sm;
   float2* SS = sm + TC::OFF_S;
@@ -1577,7 +1636,8 @@ k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, c
   const int ntiles = (w + CW - 1) / CW;
   const uint32_t ma = tc::smem_u32(&bar_a), ms = tc::smem_u32(&bar_s);
   if (threadIdx.x == 0) {
-    abort_flag = 0;
+    abort_a = 0;
+    abort_s = 0;
     tc::mbar_init(ma, 1);
     tc::mbar_init(ms, 1);
   }
@@ -1607,43 +1667,75 @@ k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, c
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int u0 = tile * CW;
     const int next_tile = tile + gridDim.x;
-    float2 acc[C::COL_EPT];
-    for_elems<C::CW * N, T>([&](int i, int e) { acc[i] = make_float2(0.f, 0.f); });
+    float2 acc[NACC];
+#pragma unroll
+    for (int i = 0; i < NACC; ++i) acc[i] = make_float2(0.f, 0.f);
     for (int k = 0; k <= K; ++k) {
       const bool more = k < K || next_tile < ntiles;
       const int nt = k < K ? tile : next_tile, nk = k < K ? k + 1 : 0;
-      if (!tc::mbar_wait_bounded(ma, pa, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_flag = 1;
-      __syncthreads();
-      if (abort_flag) break;
+      if (!tc::mbar_wait_bounded(ma, pa, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_a = 1;
+      if constexpr (!FUSED) {
+        __syncthreads();
+        if (abort_a) break;
+      }
       pa ^= 1u;
       pend_a = false;
       auto load = [&](int c, int v) -> float2 { return AS[v * CW + c]; };
       auto nostore = [](int, int, float2) {};
-      ct_stage_io<N, R0, 1, false, true, CW, T, true, false>(W, 1, CW, TWs, load, nostore);
+      ct_stage_io<N, R0, 1, false, true, CW, T, true, false>(W, 1, CW, TWs, load, nostore);   // ends with a barrier
+      if constexpr (FUSED) {
+        if (abort_a) break;
+      }
       if (more) {   // the first stage has read the A tile
         if (threadIdx.x == 0) issue_a(nt, nk);
         pend_a = true;
       }
-      ct_fft<N, false, true, CW, T, 1, R0>(W, 1, CW, TWs);
-      if (!tc::mbar_wait_bounded(ms, ps, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_flag = 1;
-      __syncthreads();
-      if (abort_flag) break;
-      ps ^= 1u;
-      pend_s = false;
-      for_elems<C::CW * N, T>([&](int i, int e) {
-        const float2 sp = SS[e];
-        const float2 x = W[e % CW + sidx(e / CW) * CW];
-        acc[i].x = fmaf(x.x, sp.x, fmaf(-x.y, sp.y, acc[i].x));
-        acc[i].y = fmaf(x.x, sp.y, fmaf(x.y, sp.x, acc[i].y));
-      });
-      __syncthreads();   // products read W and the spectrum tile
+      if constexpr (FUSED) {
+        // middle stages in place, then the last stage multiplies its outputs
+        // with the staged spectrum tile (laid out in the order of the
+        // outputs) and accumulates them in registers
+        ct_fft_range<N, false, true, CW, T, 1, L.cnt - 1, R0>(W, 1, CW, TWs);
+        if (!tc::mbar_wait_bounded(ms, ps, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_s = 1;
+        ps ^= 1u;
+        pend_s = false;
+        ct_last_stage_cols<N, CW, T>(W, CW, TWs, [&](int s2, int r, float2 v) {
+          const float2 sp = SS[LC::x(s2, r) * CW + LC::line(s2)];
+          float2& a = acc[s2 * LC::R + r];
+          a.x = fmaf(v.x, sp.x, fmaf(-v.y, sp.y, a.x));
+          a.y = fmaf(v.x, sp.y, fmaf(v.y, sp.x, a.y));
+        });
+        __syncthreads();   // W and the spectrum tile read
+        if (abort_s) break;
+      } else {
+        ct_fft<N, false, true, CW, T, 1, R0>(W, 1, CW, TWs);
+        if (!tc::mbar_wait_bounded(ms, ps, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_s = 1;
+        __syncthreads();
+        if (abort_s) break;
+        ps ^= 1u;
+        pend_s = false;
+        for_elems<C::CW * N, T>([&](int i, int e) {
+          const float2 sp = SS[e];
+          const float2 x = W[e % CW + sidx(e / CW) * CW];
+          acc[i].x = fmaf(x.x, sp.x, fmaf(-x.y, sp.y, acc[i].x));
+          acc[i].y = fmaf(x.x, sp.y, fmaf(x.y, sp.x, acc[i].y));
+        });
+        __syncthreads();   // products read W and the spectrum tile
+      }
       if (more) {
         if (threadIdx.x == 0) issue_s(nt, nk);
         pend_s = true;
       }
     }
-    if (abort_flag) break;
-    cols_store_sm<N>(W, acc);
+    if (abort_a || abort_s) break;
+    if constexpr (FUSED) {
+#pragma unroll
+      for (int s2 = 0; s2 < LC::S; ++s2)
+#pragma unroll
+        for (int r = 0; r < LC::R; ++r)
+          if (LC::valid(s2)) W[LC::line(s2) + sidx(LC::x(s2, r)) * CW] = acc[s2 * LC::R + r];
+    } else {
+      cols_store_sm<N>(W, acc);
+    }
     __syncthreads();
     col_fft<N, true>(W, TWs);
     for_elems<C::CW * N, T>([&](int i, int e) {
@@ -1776,7 +1868,7 @@ struct FftOps {
   static void cols_conv(const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
                         cudaStream_t st);
   static bool cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
-                            const float2* tw, const float2* stw_g, int* err, int sms, cudaStream_t st);
+                            const float2* tw, const float2* stw_g, int* err, int sms, bool fused, cudaStream_t st);
   static void cols_c2c(float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st);
   static void rows_inv_channels(const float2* Z, int rows, int k0, int nk, const int2* chan, float* G,
                                 const float2* tw, cudaStream_t st);
@@ -1943,18 +2035,23 @@ bool FftOps<N>::cols_inv_corr_tma(const CUtensorMap& tmH, int w, int br, const f
 
 template <int N>
 bool FftOps<N>::cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
-                              const float2* tw, const float2* stw_g, int* err, int sms, cudaStream_t st) {
+                              const float2* tw, const float2* stw_g, int* err, int sms, bool fused,
+                              cudaStream_t st) {
   using TC = TmaColCfg<N>;
   if constexpr (!(TC::OK || TC::OK_GTW) || factor_radices(N).cnt < 2) {
     return false;
   } else {
     if (!TC::OK && !stw_g) return false;
     constexpr int smem = TC::OK ? TC::SMEM : TC::SMEM_GTW;
-    const bool once = (ext_set_smem(k_cols_conv_tma<N>, smem), true);
-    (void)once;
     const int tiles = (w + C::CW - 1) / C::CW;
     const int grid = pipe_grid<N>(tiles, sms, smem, C::COL_THREADS);
-    k_cols_conv_tma<N><<<grid, C::COL_THREADS, smem, st>>>(tmA, w, br, K, S, Y, tw, stw_g, err);
+    if (fused) {
+      if (!ext_set_smem(k_cols_conv_tma<N, true>, smem)) return false;
+      k_cols_conv_tma<N, true><<<grid, C::COL_THREADS, smem, st>>>(tmA, w, br, K, S, Y, tw, stw_g, err);
+    } else {
+      if (!ext_set_smem(k_cols_conv_tma<N, false>, smem)) return false;
+      k_cols_conv_tma<N, false><<<grid, C::COL_THREADS, smem, st>>>(tmA, w, br, K, S, Y, tw, stw_g, err);
+    }
     return true;
   }
 }

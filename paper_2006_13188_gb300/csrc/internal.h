@@ -98,9 +98,12 @@ void fft_cols_conv(int h, const float2* A, int w, int K, const float2* S, float2
                    cudaStream_t st);
 // The same pass with the A_k and spectrum tiles staged by the tensor memory
 // accelerator: tmA maps A as (K+1) h rows of 2w floats, boxes of 2 * col_tile
-// floats x br rows; false if this length has no such variant.
+// floats x br rows; false if this length has no such variant.  fused: the
+// last butterfly stage multiplies and accumulates its outputs in registers
+// (no shared-memory pass of the products).
 bool fft_cols_conv_tma(int h, const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
-                       const float2* tw, const float2* stw_g, int* err, int sms, cudaStream_t st);
+                       const float2* tw, const float2* stw_g, int* err, int sms, cudaStream_t st,
+                       bool fused = true);
 // whether the staged convolution pass exists for column length h, and whether it
 // reads its stage twiddles from a global table (fft_build_stage_table) instead of
 // a shared-memory copy
