@@ -868,7 +868,10 @@ def bench_scale(args, world, rank, local):
     plan.profile(False)
     dom, (dms, dn) = max(prof.items(), key=lambda kv: kv[1][0])
     n_h = len(c)
-    alg = {"cols_conv": n_h * 8 * P * 2 + 8 * P, "rows_fwd_scale": 8 * P + n_h * 8 * P}.get(dom)
+    # per launch (one signal): the column pass reads the n_h steered row transforms and the n_h
+    # spectra and writes the sum; the row pass reads H and the (t, wgt) table and writes n_h planes
+    alg = {"cols_conv": n_h * 8 * P * 2 + 8 * P, "cols_conv_tma": n_h * 8 * P * 2 + 8 * P,
+           "rows_fwd_scale": 12 * P + n_h * 8 * P}.get(dom)
     peak, kind = measured_peaks()
     ach = alg / (dms / dn * 1e-3) / 1e9 if alg else None
     cpu = None
