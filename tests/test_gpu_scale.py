@@ -133,3 +133,32 @@ def test_depth_defocus_disk_filter_matches_oracle(ec, plan):
     err = float(np.abs(got - ref).max() / np.abs(ref).max())
     print(f"depth defocus (64 frequencies): max error {err:.2e} of the output scale")
     assert err < REL_L2
+
+
+def test_failure_modes_of_sec8_on_a_step_mask(ec, plan):
+    """The failure modes discussed in Sec. 8, through the CUDA path on a step
+    image 0 | 1 and a step mask s = 1 | 3: un-normalised smoothing (mode 0)
+    darkens the narrow-filter side of a constant image; dividing by {1, T} * F
+    without H / |T|^2 (mode 1) bleeds the wide side across the boundary more
+    than the unit-integral form (mode 2).  Every mode also matches the oracle
+    on the whole image."""
+    h, w = 32, 64
+    left = np.arange(w)[None, :] < w // 2
+    s = (np.where(left, 1.0, 3.0) * np.ones((h, 1))).astype(np.float32)
+    step = (np.where(left, 0.0, 1.0) * np.ones((h, 1))).astype(np.float32)
+    ones = np.ones((h, w), np.float32)
+    img = np.stack([step, ones])
+    c = synth.mellin_gaussian_coeffs()
+    filt = MellinFilter(c, 8.0, 1.0, 10.0, 1.0)
+    got = {}
+    for mode in (0, 1, 2):
+        out = torch.empty((2, h, w), dtype=torch.float32, device="cuda")
+        ec.ext_conv_scale(plan, dev(img), 2, h, w, c, 8.0, 1.0, 10.0, 1.0, dev(s), mode, out)
+        got[mode] = out.cpu().numpy()
+        ref = smooth(img, s, filt, mode=mode)
+        assert rel_l2(got[mode], ref) < REL_L2
+    raw = got[0][1]
+    assert raw[:, 6:18].mean() < raw[:, 38:50].mean()          # narrow filters accumulate less
+    near = [w // 2 - 2, w // 2 - 1]
+    assert got[1][0][:, near].mean() > got[2][0][:, near].mean() + 1e-3
+    np.testing.assert_allclose(got[2][1], 1.0, atol=1e-5)        # constant image reproduced

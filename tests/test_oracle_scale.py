@@ -92,6 +92,32 @@ def test_unnormalised_smoothing_darkens_small_scales():
     assert raw[:, 3:9].mean() < raw[:, 15:21].mean()
 
 
+def test_unit_integral_normalisation_stops_bleeding_across_the_mask():
+    """Sec. 8 discussion of the failure modes: dividing by {1, T} * F restores
+    the luminance but, with H not divided by |T|^2, the wide filters of the
+    large-scale side carry s^2 times the mass of the narrow ones and bleed
+    across the mask boundary; with H / |T|^2 every source spreads unit mass.
+    Step image 0 | 1 on a step mask s = 1 | 3 (periodic, so two boundaries):
+    the sharp side next to the boundary picks up more of the other side in
+    mode 1 than in mode 2, both stay in [0, 1], and far from the boundaries
+    (beyond the filter reach) both reproduce the image."""
+    h, w = 8, 48
+    left = np.arange(w)[None, :] < w // 2
+    s = np.where(left, 1.0, 3.0) * np.ones((h, 1))
+    img = np.where(left, 0.0, 1.0)[None] * np.ones((1, h, 1))
+    f = small_filter(r_max=10.0)
+    m1 = smooth(img, s, f, mode=1)[0]
+    m2 = smooth(img, s, f, mode=2)[0]
+    near = [w // 2 - 2, w // 2 - 1]               # sharp side, next to the boundary at w / 2
+    assert m1[:, near].mean() > m2[:, near].mean() + 1e-3
+    for m in (m1, m2):   # a normalised average; the fitted profile's lobes (< 5e-7) may overshoot slightly
+        assert m.min() > -1e-6 and m.max() < 1 + 1e-6
+    # columns farther than the widest filter's reach (10 px) from both boundaries (w/2 and 0 = w)
+    far_left = [11, 12]
+    np.testing.assert_allclose(m1[:, far_left], 0.0, atol=1e-9)
+    np.testing.assert_allclose(m2[:, far_left], 0.0, atol=1e-9)
+
+
 def test_disk_profile_matches_the_smoothed_disk():
     """Depth-defocus filter (Sec. 8): 64 Mellin frequencies reproduce the
     radially smoothed disk indicator 1 / (1 + e^{(ln r - ln s) / tau}) to 1e-6."""
