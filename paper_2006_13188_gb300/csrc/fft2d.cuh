@@ -92,8 +92,26 @@ __device__ __forceinline__ void for_elems_staged(Load&& load, Store&& store) {
 
 constexpr int STAGE_G = 8;
 
-template <int N, int R, int NS, bool INV, bool LINE_FAST, int NLINES, int THREADS>
-__device__ __forceinline__ void ct_stage(float2* buf, int ls, int es, const float2* __restrict__ tw) {
+// Twiddle sources of the stages: the stage table (see stage_twiddles), or a
+// split table W_N^m = lo[m mod 64] hi[m / 64] (64 + N / 64 entries, one
+// extra complex product per twiddle) for passes whose shared memory has no
+// room for the N - 1 entries of the stage table.
+struct SplitTw {
+  const float2* lo;
+  const float2* hi;
+};
+template <int NS, int STEP>
+__device__ __forceinline__ float2 tw_get(const float2* __restrict__ t, int r, int k) {
+  return t[r * NS - 1 + k];
+}
+template <int NS, int STEP>
+__device__ __forceinline__ float2 tw_get(const SplitTw& t, int r, int k) {
+  const int m = r * k * STEP;
+  return c_mul(t.lo[m & 63], t.hi[m >> 6]);
+}
+
+template <int N, int R, int NS, bool INV, bool LINE_FAST, int NLINES, int THREADS, class TWT>
+__device__ __forceinline__ void ct_stage(float2* buf, int ls, int es, TWT tw) {
   constexpr int NB = N / R;
   constexpr int TSTEP = N / (NS * R);
   constexpr int total = NB * NLINES;
@@ -117,7 +135,7 @@ __device__ __forceinline__ void ct_stage(float2* buf, int ls, int es, const floa
       for (int r = 0; r < R; ++r) {
         float2 a = base[sidx(j + r * NB) * es];
         if (NS > 1 && r > 0) {
-          float2 w = tw[r * NS - 1 + k];   // stage table, see stage_twiddles
+          float2 w = tw_get<NS, TSTEP>(tw, r, k);
           if (INV) w.y = -w.y;
           a = c_mul(a, w);
         }
@@ -140,8 +158,8 @@ __device__ __forceinline__ void ct_stage(float2* buf, int ls, int es, const floa
   __syncthreads();
 }
 
-template <int N, bool INV, bool LINE_FAST, int NLINES, int THREADS, int ST = 0, int NS = 1>
-__device__ __forceinline__ void ct_fft(float2* buf, int ls, int es, const float2* tw) {
+template <int N, bool INV, bool LINE_FAST, int NLINES, int THREADS, int ST = 0, int NS = 1, class TWT>
+__device__ __forceinline__ void ct_fft(float2* buf, int ls, int es, TWT tw) {
   constexpr RadixList L = factor_radices(N);
   if constexpr (ST < L.cnt) {
     constexpr int R = L.r[ST];
@@ -151,8 +169,8 @@ __device__ __forceinline__ void ct_fft(float2* buf, int ls, int es, const float2
 }
 
 // Stages ST .. END-1 of the transform (in place, as ct_fft).
-template <int N, bool INV, bool LINE_FAST, int NLINES, int THREADS, int ST, int END, int NS>
-__device__ __forceinline__ void ct_fft_range(float2* buf, int ls, int es, const float2* tw) {
+template <int N, bool INV, bool LINE_FAST, int NLINES, int THREADS, int ST, int END, int NS, class TWT>
+__device__ __forceinline__ void ct_fft_range(float2* buf, int ls, int es, TWT tw) {
   constexpr RadixList L = factor_radices(N);
   if constexpr (ST < END) {
     constexpr int R = L.r[ST];
@@ -183,8 +201,8 @@ struct LastColStage {
 // The last forward stage of a column transform (buf in the column layout,
 // line stride 1, element stride es), its outputs handed to fn(s, r, value)
 // instead of being stored; s and r are compile-time after unrolling.
-template <int N, int NLINES, int THREADS, class Fn>
-__device__ __forceinline__ void ct_last_stage_cols(const float2* buf, int es, const float2* __restrict__ tw, Fn&& fn) {
+template <int N, int NLINES, int THREADS, class TWT, class Fn>
+__device__ __forceinline__ void ct_last_stage_cols(const float2* buf, int es, TWT tw, Fn&& fn) {
   using LS_ = LastColStage<N, NLINES, THREADS>;
   constexpr int R = LS_::R, NS = LS_::NS, NB = LS_::NB;
 #pragma unroll
@@ -197,7 +215,7 @@ __device__ __forceinline__ void ct_last_stage_cols(const float2* buf, int es, co
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         float2 a = buf[line + sidx(j + r * NB) * es];
-        if (NS > 1 && r > 0) a = c_mul(a, tw[r * NS - 1 + k]);
+        if (NS > 1 && r > 0) a = c_mul(a, tw_get<NS, 1>(tw, r, k));
         v[r] = a;
       }
       dft<R, false>(v);
@@ -213,8 +231,8 @@ __device__ __forceinline__ void ct_last_stage_cols(const float2* buf, int es, co
 // and store(line, idx, value) consumes the outputs (LAST: e.g. straight to
 // global memory); otherwise both use the padded shared-memory layout of buf.
 template <int N, int R, int NS, bool INV, bool LINE_FAST, int NLINES, int THREADS, bool FIRST, bool LAST,
-          bool INPLACE_FIRST = false, class Load, class Store>
-__device__ __forceinline__ void ct_stage_io(float2* buf, int ls, int es, const float2* __restrict__ tw, Load&& load,
+          bool INPLACE_FIRST = false, class TWT, class Load, class Store>
+__device__ __forceinline__ void ct_stage_io(float2* buf, int ls, int es, TWT tw, Load&& load,
                                             Store&& store) {
   constexpr int NB = N / R;
   constexpr int TSTEP = N / (NS * R);
@@ -237,7 +255,7 @@ __device__ __forceinline__ void ct_stage_io(float2* buf, int ls, int es, const f
       for (int r = 0; r < R; ++r) {
         float2 a = FIRST ? load(line, j + r * NB) : buf[line * ls + sidx(j + r * NB) * es];
         if (NS > 1 && r > 0) {
-          float2 w = tw[r * NS - 1 + k];   // stage table, see stage_twiddles
+          float2 w = tw_get<NS, TSTEP>(tw, r, k);
           if (INV) w.y = -w.y;
           a = c_mul(a, w);
         }
@@ -264,8 +282,9 @@ __device__ __forceinline__ void ct_stage_io(float2* buf, int ls, int es, const f
 
 // Whole transform with functor input (first stage) and output (last stage).
 // The caller must __syncthreads() before re-using buf or the load source.
-template <int N, bool INV, bool LINE_FAST, int NLINES, int THREADS, int ST = 0, int NS = 1, class Load, class Store>
-__device__ __forceinline__ void ct_fft_io(float2* buf, int ls, int es, const float2* tw, Load&& load, Store&& store) {
+template <int N, bool INV, bool LINE_FAST, int NLINES, int THREADS, int ST = 0, int NS = 1, class TWT, class Load,
+          class Store>
+__device__ __forceinline__ void ct_fft_io(float2* buf, int ls, int es, TWT tw, Load&& load, Store&& store) {
   constexpr RadixList L = factor_radices(N);
   if constexpr (ST < L.cnt) {
     constexpr int R = L.r[ST];
@@ -336,8 +355,8 @@ __device__ __forceinline__ void row_fft(float2* sm, const float2* tw) {
   ct_fft<N, INV, false, C::RL, C::ROW_THREADS>(sm, C::LS, 1, tw);
 }
 // Column layout: column c, element v at sm[c + sidx(v) * CW].
-template <int N, bool INV>
-__device__ __forceinline__ void col_fft(float2* sm, const float2* tw) {
+template <int N, bool INV, class TWT>
+__device__ __forceinline__ void col_fft(float2* sm, TWT tw) {
   using C = LineCfg<N>;
   ct_fft<N, INV, true, C::CW, C::COL_THREADS>(sm, 1, C::CW, tw);
 }
@@ -1527,7 +1546,24 @@ struct TmaColCfg {
   // without the twiddle copy (the stage table read from global memory through L1)
   static constexpr int SMEM_GTW = OFF_TW * 8 + 128;
   static constexpr bool OK_GTW = !OK && SMEM_GTW <= 227 * 1024 && C::CW % 2 == 0;
+  // with the split twiddle table (64 + N / 64 entries) instead of the stage table
+  static constexpr int SMEM_SPLIT = (OFF_TW + 64 + N / 64) * 8 + 128;
+  static constexpr bool OK_SPLIT = !OK && N % 64 == 0 && SMEM_SPLIT <= 227 * 1024 && C::CW % 2 == 0;
 };
+
+// Builds the split twiddle table (lo[b] = W_N^b, b < 64; hi[a] = W_N^{64 a},
+// a < N / 64, copied from the FP64-derived table W_N^m) in shared memory at
+// float2 offset OFF; visible after the caller's next barrier.
+template <int N, int OFF>
+__device__ __forceinline__ SplitTw split_twiddles(float2* sm, const float2* __restrict__ tw, int threads) {
+  float2* lo = sm + OFF;
+  float2* hi = lo + 64;
+  for (int e = threadIdx.x; e < 64 + N / 64; e += threads) {
+    if (e < 64) lo[e] = __ldg(tw + e);
+    else hi[e - 64] = __ldg(tw + (size_t)(e - 64) * 64);
+  }
+  return SplitTw{lo, hi};
+}
 
 template <int N>
 __global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, 1)
@@ -1630,9 +1666,13 @@ k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, c
   float2* W = sm;
   float2* SS = sm + TC::OFF_S;
   float2* AS = sm + TC::OFF_H;
-  // stage twiddles: copied into shared memory where they fit, else the global stage table (stw_g)
-  const float2* TWs = stw_g;
-  if constexpr (TC::OK) TWs = stage_twiddles<N, TC::OFF_TW>(sm, tw, T);
+  // stage twiddles: copied into shared memory where they fit, else the split
+  // table in shared memory, else the global stage table (stw_g)
+  const auto TWs = [&]() {
+    if constexpr (TC::OK) return stage_twiddles<N, TC::OFF_TW>(sm, tw, T);
+    else if constexpr (TC::OK_SPLIT) return split_twiddles<N, TC::OFF_TW>(sm, tw, T);
+    else return stw_g;
+  }();
   const int ntiles = (w + CW - 1) / CW;
   const uint32_t ma = tc::smem_u32(&bar_a), ms = tc::smem_u32(&bar_s);
   if (threadIdx.x == 0) {
@@ -2041,8 +2081,8 @@ bool FftOps<N>::cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, cons
   if constexpr (!(TC::OK || TC::OK_GTW) || factor_radices(N).cnt < 2) {
     return false;
   } else {
-    if (!TC::OK && !stw_g) return false;
-    constexpr int smem = TC::OK ? TC::SMEM : TC::SMEM_GTW;
+    if (!TC::OK && !TC::OK_SPLIT && !stw_g) return false;
+    constexpr int smem = TC::OK ? TC::SMEM : (TC::OK_SPLIT ? TC::SMEM_SPLIT : TC::SMEM_GTW);
     const int tiles = (w + C::CW - 1) / C::CW;
     const int grid = pipe_grid<N>(tiles, sms, smem, C::COL_THREADS);
     if (fused) {

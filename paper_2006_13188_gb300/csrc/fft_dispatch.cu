@@ -251,7 +251,7 @@ bool fft_cols_conv_tma_ok(int h, bool* needs_stage_table) {
   switch (h) {
 #define EXT_CASE(N)                                         \
   case N:                                                   \
-    *needs_stage_table = !TmaColCfg<N>::OK;                 \
+    *needs_stage_table = !TmaColCfg<N>::OK && !TmaColCfg<N>::OK_SPLIT; \
     return TmaColCfg<N>::OK || TmaColCfg<N>::OK_GTW;
     EXT_FFT_SIZES(EXT_CASE)
 #undef EXT_CASE
