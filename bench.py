@@ -812,6 +812,14 @@ SCALE_WORKLOAD = ("scale-adaptive smoothing: 4096x4096x3 f32 Voronoi image, scal
                   "24 Mellin harmonics, radii 1-64, normalised (unit-integral) mode")
 
 
+def conv_column_bytes(n_comp, P, n_sig, launches):
+    """Algorithmic bytes of one launch of the convolution column pass: the
+    steered row transforms (n_comp complex planes of P pixels) of the launch's
+    signals, the n_comp filter spectra once, and one complex sum per signal."""
+    per = n_sig / max(launches, 1)
+    return per * (n_comp * 8 * P + 8 * P) + n_comp * 8 * P
+
+
 def bench_scale(args, world, rank, local):
     import numpy as np
     import torch
@@ -868,10 +876,11 @@ def bench_scale(args, world, rank, local):
     plan.profile(False)
     dom, (dms, dn) = max(prof.items(), key=lambda kv: kv[1][0])
     n_h = len(c)
-    # per launch (one signal): the column pass reads the n_h steered row transforms and the n_h
-    # spectra and writes the sum; the row pass reads H and the (t, wgt) table and writes n_h planes
-    alg = {"cols_conv": n_h * 8 * P * 2 + 8 * P, "cols_conv_tma": n_h * 8 * P * 2 + 8 * P,
-           "rows_fwd_scale": 12 * P + n_h * 8 * P}.get(dom)
+    # per launch: the column pass reads the n_h steered row transforms of each of its signals and
+    # the n_h spectra (once per launch) and writes each signal's sum; the row pass reads H and the
+    # (t, wgt) table and writes n_h planes
+    col = conv_column_bytes(n_h, P, 4, dn)
+    alg = {"cols_conv": col, "cols_conv_tma": col, "rows_fwd_scale": 12 * P + n_h * 8 * P}.get(dom)
     peak, kind = measured_peaks()
     ach = alg / (dms / dn * 1e-3) / 1e9 if alg else None
     cpu = None
@@ -1486,8 +1495,8 @@ def bench_similarity(args, world, rank, local):
     e2e_s = reduce_max(time.perf_counter() - t1, world, device)
     dom_name, (dom_ms, dom_n) = max(prof.items(), key=lambda kv: kv[1][0])
     avg_ms = dom_ms / dom_n
-    alg = {"cols_conv_tma": nc * 16 * P + 8 * P, "cols_conv": nc * 16 * P + 8 * P,
-           "rows_fwd_simil": 12 * P + nc * 8 * P}.get(dom_name)
+    col = conv_column_bytes(nc, P, C + 1, dom_n / prof_steps)
+    alg = {"cols_conv_tma": col, "cols_conv": col, "rows_fwd_simil": 12 * P + nc * 8 * P}.get(dom_name)
     peak, peak_kind = measured_peaks()
     achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
     roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,

@@ -570,18 +570,41 @@ ext_status conv_signals(ext_plan plan, int h, int w, int ncomp, int nsig, const 
   const float2 *tw_w = nullptr, *tw_h = nullptr;
   EXT_TRY(twiddle(plan, w, st, &tw_w));
   EXT_TRY(twiddle(plan, h, st, &tw_h));
-  void *A = nullptr, *Y = nullptr;
-  EXT_TRY(ensure(plan, "Aall", sizeof(float2) * P * ncomp, &A));
-  EXT_TRY(ensure(plan, "Y", sizeof(float2) * P, &Y));
   const int cw = fft_col_tile(h);
   bool gtw = false;
   const int br = plan->tma && fft_cols_conv_tma_ok(h, &gtw) ? tma_rows(h, cw) : 0;
   const float2* stw = nullptr;
   if (br > 0 && gtw) EXT_TRY(stage_table(plan, h, st, &stw));
+  // All signals through one column-pass launch where their steered row
+  // transforms fit the workspace budget: the launch interleaves the signals
+  // tile by tile, so each spectrum tile comes from HBM once instead of once
+  // per signal.
+  const size_t all_bytes = sizeof(float2) * P * ncomp * (size_t)nsig;
+  const bool together = br > 0 && nsig > 1 && plan->colconv_form == 2 && plan->conv_together &&
+                        all_bytes <= ((size_t)16 << 30) && (size_t)ncomp * nsig * h < (1ull << 31);
+  void *A = nullptr, *Y = nullptr;
+  EXT_TRY(ensure(plan, "Aall", together ? all_bytes : sizeof(float2) * P * ncomp, &A));
+  EXT_TRY(ensure(plan, "Y", sizeof(float2) * P * (together ? nsig : 1), &Y));
   CUtensorMap tmA;
-  const bool tma_A = br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w, (unsigned long long)ncomp * h,
+  const bool tma_A = br > 0 && make_tmap_2d_f32(A, (unsigned long long)2 * w,
+                                                (unsigned long long)ncomp * h * (together ? nsig : 1),
                                                 (unsigned long long)2 * w * sizeof(float), (unsigned)(2 * cw),
                                                 (unsigned)br, &tmA);
+  if (together && tma_A) {
+    for (int sig = 0; sig < nsig; ++sig)
+      launch(plan, row_name, st, [&] { rows(sig, (float2*)A + P * ncomp * sig, tw_w); });
+    bool done = false;
+    launch(plan, "cols_conv_tma", st, [&] {
+      done = fft_cols_conv_tma(h, tmA, w, br, ncomp - 1, S, (float2*)Y, tw_h, stw, plan->dev_err, plan->sms, st,
+                               true, nsig);
+    });
+    if (!done) return fail(EXT_ERR_CUDA, "the multi-signal convolution column pass could not be launched");
+    for (int sig = 0; sig < nsig; ++sig)
+      launch(plan, "rows_inv_real", st,
+             [&] { fft_rows_inv_real(w, (const float2*)Y + P * sig, h, dst(sig), tw_w, st); });
+    EXT_CUDA(cudaGetLastError());
+    return EXT_OK;
+  }
   for (int sig = 0; sig < nsig; ++sig) {
     launch(plan, row_name, st, [&] { rows(sig, (float2*)A, tw_w); });
     bool done = false;
@@ -715,6 +738,7 @@ ext_status ext_plan_create(ext_plan* plan, const ext_options* options) {
   if (const char* e = getenv("EXT_SO3_WS")) p->so3_ws = atoi(e) != 0;
   if (const char* e = getenv("EXT_STEER_MODE")) p->steer_mode = atoi(e);
   if (const char* e = getenv("EXT_COLCONV")) p->colconv_form = atoi(e);
+  if (const char* e = getenv("EXT_CONV_TOGETHER")) p->conv_together = atoi(e) != 0;
   if (const char* e = getenv("EXT_BATCH_BRANCHES")) p->batch_branches = atoi(e);
   if (p->autotune) tune_cache_read(p);
   *plan = p;

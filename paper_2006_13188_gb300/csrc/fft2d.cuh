@@ -1649,7 +1649,7 @@ k_cols_inv_corr_tma(const __grid_constant__ CUtensorMap tmH, int w, int br, cons
 // block stops).
 template <int N, bool FUSED>
 __global__ void __launch_bounds__(LineCfg<N>::COL_THREADS, 1)
-k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, const float2* __restrict__ S,
+k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, int nsig, const float2* __restrict__ S,
                 float2* __restrict__ Y, const float2* __restrict__ tw, const float2* __restrict__ stw_g,
                 int* __restrict__ err) {
   using C = LineCfg<N>;
@@ -1682,12 +1682,18 @@ k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, c
     tc::mbar_init(ms, 1);
   }
   __syncthreads();
-  auto issue_a = [&](int tile, int k) {   // thread 0
+  // items: (column tile, signal), signal fastest, so the blocks of all signals of a tile run
+  // together and read each spectrum tile from HBM once and from L2 for the other signals
+  const int nitems = ntiles * nsig;
+  auto issue_a = [&](int item, int k) {   // thread 0; signal sig's component k is A row block sig (K+1) + k
+    const int tile = item / nsig, sig = item % nsig;
     tc::fence_proxy_async();
     tc::mbar_expect_tx(ma, TILE * 8u);
-    for (int y = 0; y < N; y += br) tc::tma_load_2d(tc::smem_u32(AS + y * CW), &tmA, 2 * tile * CW, k * N + y, ma);
+    for (int y = 0; y < N; y += br)
+      tc::tma_load_2d(tc::smem_u32(AS + y * CW), &tmA, 2 * tile * CW, (sig * (K + 1) + k) * N + y, ma);
   };
-  auto issue_s = [&](int tile, int k) {   // thread 0
+  auto issue_s = [&](int item, int k) {   // thread 0
+    const int tile = item / nsig;
     tc::fence_proxy_async();
     tc::mbar_expect_tx(ms, TILE * 8u);
     tc::bulk_load(tc::smem_u32(SS), S + ((size_t)k * ntiles + tile) * TILE, TILE * 8u, ms);
@@ -1697,22 +1703,24 @@ k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, c
   static_assert(L.cnt > 1, "at least two radix stages");
   uint32_t pa = 0, ps = 0;
   bool pend_a = false, pend_s = false;
-  if ((int)blockIdx.x < ntiles) {
+  if ((int)blockIdx.x < nitems) {
     if (threadIdx.x == 0) {
       issue_a(blockIdx.x, 0);
       issue_s(blockIdx.x, 0);
     }
     pend_a = pend_s = true;
   }
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int tile = item / nsig;
     const int u0 = tile * CW;
-    const int next_tile = tile + gridDim.x;
+    float2* const Ysig = Y + (size_t)(item % nsig) * N * w;
+    const int next_item = item + gridDim.x;
     float2 acc[NACC];
 #pragma unroll
     for (int i = 0; i < NACC; ++i) acc[i] = make_float2(0.f, 0.f);
     for (int k = 0; k <= K; ++k) {
-      const bool more = k < K || next_tile < ntiles;
-      const int nt = k < K ? tile : next_tile, nk = k < K ? k + 1 : 0;
+      const bool more = k < K || next_item < nitems;
+      const int nt = k < K ? item : next_item, nk = k < K ? k + 1 : 0;
       if (!tc::mbar_wait_bounded(ma, pa, 1000000000ull, err, EXT_ERR_TIMEOUT)) abort_a = 1;
       if constexpr (!FUSED) {
         __syncthreads();
@@ -1780,7 +1788,7 @@ k_cols_conv_tma(const __grid_constant__ CUtensorMap tmA, int w, int br, int K, c
     col_fft<N, true>(W, TWs);
     for_elems<C::CW * N, T>([&](int i, int e) {
       const int u = u0 + e % CW;
-      if (u < w) Y[(size_t)(e / CW) * w + u] = W[e % CW + sidx(e / CW) * CW];
+      if (u < w) Ysig[(size_t)(e / CW) * w + u] = W[e % CW + sidx(e / CW) * CW];
     });
     __syncthreads();
   }
@@ -1907,7 +1915,7 @@ struct FftOps {
                             const float2* tw, cudaStream_t st);
   static void cols_conv(const float2* A, int w, int K, const float2* S, float2* Y, const float2* tw,
                         cudaStream_t st);
-  static bool cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
+  static bool cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, int nsig, const float2* S, float2* Y,
                             const float2* tw, const float2* stw_g, int* err, int sms, bool fused, cudaStream_t st);
   static void cols_c2c(float2* X, int w, int planes, bool inv, const float2* tw, cudaStream_t st);
   static void rows_inv_channels(const float2* Z, int rows, int k0, int nk, const int2* chan, float* G,
@@ -2074,7 +2082,7 @@ bool FftOps<N>::cols_inv_corr_tma(const CUtensorMap& tmH, int w, int br, const f
 }
 
 template <int N>
-bool FftOps<N>::cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
+bool FftOps<N>::cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, int nsig, const float2* S, float2* Y,
                               const float2* tw, const float2* stw_g, int* err, int sms, bool fused,
                               cudaStream_t st) {
   using TC = TmaColCfg<N>;
@@ -2083,14 +2091,14 @@ bool FftOps<N>::cols_conv_tma(const CUtensorMap& tmA, int w, int br, int K, cons
   } else {
     if (!TC::OK && !TC::OK_SPLIT && !stw_g) return false;
     constexpr int smem = TC::OK ? TC::SMEM : (TC::OK_SPLIT ? TC::SMEM_SPLIT : TC::SMEM_GTW);
-    const int tiles = (w + C::CW - 1) / C::CW;
-    const int grid = pipe_grid<N>(tiles, sms, smem, C::COL_THREADS);
+    const int items = (w + C::CW - 1) / C::CW * nsig;
+    const int grid = pipe_grid<N>(items, sms, smem, C::COL_THREADS);
     if (fused) {
       if (!ext_set_smem(k_cols_conv_tma<N, true>, smem)) return false;
-      k_cols_conv_tma<N, true><<<grid, C::COL_THREADS, smem, st>>>(tmA, w, br, K, S, Y, tw, stw_g, err);
+      k_cols_conv_tma<N, true><<<grid, C::COL_THREADS, smem, st>>>(tmA, w, br, K, nsig, S, Y, tw, stw_g, err);
     } else {
       if (!ext_set_smem(k_cols_conv_tma<N, false>, smem)) return false;
-      k_cols_conv_tma<N, false><<<grid, C::COL_THREADS, smem, st>>>(tmA, w, br, K, S, Y, tw, stw_g, err);
+      k_cols_conv_tma<N, false><<<grid, C::COL_THREADS, smem, st>>>(tmA, w, br, K, nsig, S, Y, tw, stw_g, err);
     }
     return true;
   }

@@ -240,9 +240,10 @@ bool fft_cols_inv_full_pipe(int h, const float2* H, int w, const float2* S, int 
 }
 #undef EXT_C1
 
-#define EXT_C1(N) case N: return FftOps<N>::cols_conv_tma(tmA, w, br, K, S, Y, tw, stw_g, err, sms, fused, st);
+#define EXT_C1(N) case N: return FftOps<N>::cols_conv_tma(tmA, w, br, K, nsig, S, Y, tw, stw_g, err, sms, fused, st);
 bool fft_cols_conv_tma(int h, const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
-                       const float2* tw, const float2* stw_g, int* err, int sms, cudaStream_t st, bool fused) {
+                       const float2* tw, const float2* stw_g, int* err, int sms, cudaStream_t st, bool fused,
+                       int nsig) {
   switch (h) { EXT_FFT_SIZES(EXT_C1) default: return false; }
 }
 #undef EXT_C1

@@ -100,10 +100,12 @@ void fft_cols_conv(int h, const float2* A, int w, int K, const float2* S, float2
 // accelerator: tmA maps A as (K+1) h rows of 2w floats, boxes of 2 * col_tile
 // floats x br rows; false if this length has no such variant.  fused: the
 // last butterfly stage multiplies and accumulates its outputs in registers
-// (no shared-memory pass of the products).
+// (no shared-memory pass of the products).  nsig > 1: nsig signals in one
+// launch, signal s's components at A rows (s (K+1) + k) h, its sum at
+// Y + s h w; they share each spectrum tile.
 bool fft_cols_conv_tma(int h, const CUtensorMap& tmA, int w, int br, int K, const float2* S, float2* Y,
                        const float2* tw, const float2* stw_g, int* err, int sms, cudaStream_t st,
-                       bool fused = true);
+                       bool fused = true, int nsig = 1);
 // whether the staged convolution pass exists for column length h, and whether it
 // reads its stage twiddles from a global table (fft_build_stage_table) instead of
 // a shared-memory copy

@@ -85,6 +85,7 @@ struct ext_plan_s {
   bool pipelined = true; // persistent prefetching passes where they fit
   bool tma = true;       // tensor-memory-accelerator staged column pass where it fits
   bool so3_ws = true;    // warp-specialised SO(3) sweep for many voxels
+  bool conv_together = true; // all signals of a convolution through one column-pass launch (workspace permitting)
   int colconv_form = 2;    // convolution column pass: 1 products through shared memory, 2 fused into the last stage
   int steer_mode = 2;      // steered row passes: 0 staged lines, 1 steering in the first stage's loads, 2 component loop
   int batch_branches = 4; // parallel graph branches of the batched correlation (4: measured best of 1-16)
