@@ -690,8 +690,8 @@ def bench_lic(args, world, rank, local):
     dom_name, (dom_ms, dom_n) = max(prof.items(), key=lambda kv: kv[1][0])
     avg_ms = dom_ms / dom_n
     kc = K + 1
-    alg = {"cols_conv_tma": kc * 8 * P * 2 + 8 * P, "cols_conv": kc * 8 * P * 2 + 8 * P,
-           "rows_fwd_phase": 8 * P + kc * 8 * P}.get(dom_name)
+    col = conv_column_bytes(kc, P, 2, dom_n / prof_steps)   # the channel and the denominator
+    alg = {"cols_conv_tma": col, "cols_conv": col, "rows_fwd_phase": 8 * P + kc * 8 * P}.get(dom_name)
     peak, peak_kind = measured_peaks()
     achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
     roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,

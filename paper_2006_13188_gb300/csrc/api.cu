@@ -624,19 +624,26 @@ ext_status conv_signals(ext_plan plan, int h, int w, int ncomp, int nsig, const 
 
 // Extended convolution of device buffers (Sec. 2.2 Eq. Def-EConv, the algorithm
 // of Sec. 4.1): out = Re sum_k (H e^{-ik alpha}) * F_k.
-ext_status run_conv_so2(ext_plan plan, const float* H, const float* alpha, int h, int w, const ext_filter_so2* F,
-                        float* out, cudaStream_t st) {
+// Several signals with one angle field: Hs[i] (nullptr: the constant signal 1) -> outs[i].
+ext_status run_conv_so2_signals(ext_plan plan, const float* const* Hs, float* const* outs, int nsig, const float* alpha,
+                                int h, int w, const ext_filter_so2* F, cudaStream_t st) {
   const int K = F->K;
   const float2* S = nullptr;
   EXT_TRY(spectra(plan, F, h, w, SPEC_CONV, st, &S));
   return conv_signals(
-      plan, h, w, K + 1, 1, S, st, "rows_fwd_phase",
-      [&](int, float2* A, const float2* tw_w) {
+      plan, h, w, K + 1, nsig, S, st, "rows_fwd_phase",
+      [&](int sig, float2* A, const float2* tw_w) {
+        const float* H = Hs[sig];
         if (plan->steer_mode == 2 && fft_rows_fwd_hloop_phase(w, H, alpha, h, 0, K + 1, A, tw_w, plan->sms, st)) return;
         if (plan->steer_mode == 1) fft_rows_fwd_phase_io(w, H, alpha, h, 0, K + 1, A, tw_w, st);
         else fft_rows_fwd_phase(w, H, alpha, h, 0, K + 1, A, tw_w, st);
       },
-      [&](int) { return out; });
+      [&](int sig) { return outs[sig]; });
+}
+
+ext_status run_conv_so2(ext_plan plan, const float* H, const float* alpha, int h, int w, const ext_filter_so2* F,
+                        float* out, cudaStream_t st) {
+  return run_conv_so2_signals(plan, &H, &out, 1, alpha, h, w, F, st);
 }
 
 ext_status run_sweep(ext_plan plan, const float* G, long long P, int K, int J, float* maxv, int32_t* argmax,
@@ -1101,11 +1108,17 @@ ext_status ext_conv_so2_normalized(ext_plan plan, const float* H, int channels, 
   EXT_TRY(stage_out_alloc(plan, "out_0", out, sizeof(float) * P * channels, &sO));
   void* D = nullptr;
   EXT_TRY(ensure(plan, "norm_D", sizeof(float) * P, &D));
-  // denominator: the response to the constant signal 1 (the phase row pass's H = NULL)
-  EXT_TRY(run_conv_so2(plan, nullptr, (const float*)sAl.dev, h, w, F, (float*)D, st));
-  for (int c = 0; c < channels; ++c)
-    EXT_TRY(run_conv_so2(plan, (const float*)sH.dev + P * c, (const float*)sAl.dev, h, w, F, (float*)sO.dev + P * c,
-                         st));
+  // the channels and the denominator (the response to the constant signal 1,
+  // the phase row pass's H = NULL) in one call, sharing the column pass
+  std::vector<const float*> srcs;
+  std::vector<float*> dsts;
+  for (int c = 0; c < channels; ++c) {
+    srcs.push_back((const float*)sH.dev + P * c);
+    dsts.push_back((float*)sO.dev + P * c);
+  }
+  srcs.push_back(nullptr);
+  dsts.push_back((float*)D);
+  EXT_TRY(run_conv_so2_signals(plan, srcs.data(), dsts.data(), channels + 1, (const float*)sAl.dev, h, w, F, st));
   launch(plan, "divide_channels", st, [&] {
     launch_divide_channels((float*)sO.dev, (const float*)D, (long long)P, channels, plan->sms, st);
   });
