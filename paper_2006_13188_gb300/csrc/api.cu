@@ -634,7 +634,9 @@ ext_status run_conv_so2_signals(ext_plan plan, const float* const* Hs, float* co
       plan, h, w, K + 1, nsig, S, st, "rows_fwd_phase",
       [&](int sig, float2* A, const float2* tw_w) {
         const float* H = Hs[sig];
-        if (plan->steer_mode == 2 && fft_rows_fwd_hloop_phase(w, H, alpha, h, 0, K + 1, A, tw_w, plan->sms, st)) return;
+        if (plan->steer_mode >= 2 &&
+            fft_rows_fwd_hloop_phase(w, H, alpha, h, 0, K + 1, A, tw_w, plan->sms, st, plan->steer_mode == 2))
+          return;
         if (plan->steer_mode == 1) fft_rows_fwd_phase_io(w, H, alpha, h, 0, K + 1, A, tw_w, st);
         else fft_rows_fwd_phase(w, H, alpha, h, 0, K + 1, A, tw_w, st);
       },
@@ -1203,8 +1205,9 @@ ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, in
       plan, h, w, n_h, channels + (mode == 0 ? 0 : 1), S, st, "rows_fwd_scale",
       [&](int sig, float2* A, const float2* tw_w) {
         const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
-        if (Tt && plan->steer_mode == 2 &&
-            fft_rows_fwd_hloop_scale(w, src, (const float2*)Tt, h, 0, n_h, A, tw_w, plan->sms, st))
+        if (Tt && plan->steer_mode >= 2 &&
+            fft_rows_fwd_hloop_scale(w, src, (const float2*)Tt, h, 0, n_h, A, tw_w, plan->sms, st,
+                                     plan->steer_mode == 2))
           return;
         if (Tt)
           fft_rows_fwd_scale_turns(w, src, (const float2*)Tt, h, 0, n_h, A, tw_w, st);
@@ -1296,8 +1299,9 @@ ext_status ext_conv_similarity(ext_plan plan, const float* H, int channels, int 
       plan, h, w, ncomp, channels + (mode == 0 ? 0 : 1), S, st, "rows_fwd_simil",
       [&](int sig, float2* A, const float2* tw_w) {
         const float* src = sig < channels ? (const float*)sH.dev + P * sig : nullptr;   // nullptr: the signal 1
-        if (plan->steer_mode == 2 &&
-            fft_rows_fwd_hloop_simil(w, src, (const float4*)UV, h, (const int2*)dkj, ncomp, A, tw_w, plan->sms, st))
+        if (plan->steer_mode >= 2 &&
+            fft_rows_fwd_hloop_simil(w, src, (const float4*)UV, h, (const int2*)dkj, ncomp, A, tw_w, plan->sms, st,
+                                     plan->steer_mode == 2))
           return;
         if (plan->steer_mode >= 1)
           fft_rows_fwd_simil_turns(w, src, (const float4*)UV, h, (const int2*)dkj, ncomp, A, tw_w, st);

@@ -154,23 +154,23 @@ void fft_rows_fwd_phase_io(int w, const float* H, const float* alpha, int h, int
 }
 #undef EXT_C1
 
-#define EXT_C1(N) case N: return FftOps<N>::rows_fwd_hloop_scale(H, T, h, k0, nk, A, tw, sms, st);
+#define EXT_C1(N) case N: return FftOps<N>::rows_fwd_hloop_scale(H, T, h, k0, nk, A, tw, sms, fast, st);
 bool fft_rows_fwd_hloop_scale(int w, const float* H, const float2* T, int h, int k0, int nk, float2* A,
-                              const float2* tw, int sms, cudaStream_t st) {
+                              const float2* tw, int sms, cudaStream_t st, bool fast) {
   switch (w) { EXT_FFT_SIZES(EXT_C1) default: return false; }
 }
 #undef EXT_C1
 
-#define EXT_C1(N) case N: return FftOps<N>::rows_fwd_hloop_simil(H, T, h, kj, ncomp, A, tw, sms, st);
+#define EXT_C1(N) case N: return FftOps<N>::rows_fwd_hloop_simil(H, T, h, kj, ncomp, A, tw, sms, fast, st);
 bool fft_rows_fwd_hloop_simil(int w, const float* H, const float4* T, int h, const int2* kj, int ncomp, float2* A,
-                              const float2* tw, int sms, cudaStream_t st) {
+                              const float2* tw, int sms, cudaStream_t st, bool fast) {
   switch (w) { EXT_FFT_SIZES(EXT_C1) default: return false; }
 }
 #undef EXT_C1
 
-#define EXT_C1(N) case N: return FftOps<N>::rows_fwd_hloop_phase(H, alpha, h, k0, nk, A, tw, sms, st);
+#define EXT_C1(N) case N: return FftOps<N>::rows_fwd_hloop_phase(H, alpha, h, k0, nk, A, tw, sms, fast, st);
 bool fft_rows_fwd_hloop_phase(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
-                              const float2* tw, int sms, cudaStream_t st) {
+                              const float2* tw, int sms, cudaStream_t st, bool fast) {
   switch (w) { EXT_FFT_SIZES(EXT_C1) default: return false; }
 }
 #undef EXT_C1

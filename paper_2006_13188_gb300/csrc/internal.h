@@ -37,13 +37,14 @@ void fft_rows_fwd_simil_turns(int w, const float* H, const float4* T, int h, con
                               const float2* tw, cudaStream_t st);
 void fft_rows_fwd_phase_io(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
                            const float2* tw, cudaStream_t st);
-// component-loop steered row passes (false: no plan for this line length; use the others)
+// component-loop steered row passes (false: no plan for this line length; use the others);
+// fast: phasors from the hardware sine and cosine after the exact reduction
 bool fft_rows_fwd_hloop_scale(int w, const float* H, const float2* T, int h, int k0, int nk, float2* A,
-                              const float2* tw, int sms, cudaStream_t st);
+                              const float2* tw, int sms, cudaStream_t st, bool fast);
 bool fft_rows_fwd_hloop_simil(int w, const float* H, const float4* T, int h, const int2* kj, int ncomp, float2* A,
-                              const float2* tw, int sms, cudaStream_t st);
+                              const float2* tw, int sms, cudaStream_t st, bool fast);
 bool fft_rows_fwd_hloop_phase(int w, const float* H, const float* alpha, int h, int k0, int nk, float2* A,
-                              const float2* tw, int sms, cudaStream_t st);
+                              const float2* tw, int sms, cudaStream_t st, bool fast);
 // per-pixel turns (t, wgt) / (alpha / 2 pi, ln s / log_period, wgt) of the steered row passes
 void launch_scale_turns(const float* s, long long P, float inv_log_period, int unit_integral, float2* T, int sms,
                         cudaStream_t st);

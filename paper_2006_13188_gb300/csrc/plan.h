@@ -87,7 +87,8 @@ struct ext_plan_s {
   bool so3_ws = true;    // warp-specialised SO(3) sweep for many voxels
   bool conv_together = true; // all signals of a convolution through one column-pass launch (workspace permitting)
   int colconv_form = 2;    // convolution column pass: 1 products through shared memory, 2 fused into the last stage
-  int steer_mode = 2;      // steered row passes: 0 staged lines, 1 steering in the first stage's loads, 2 component loop
+  int steer_mode = 2;      // steered row passes: 0 staged lines, 1 steering in the first stage's loads,
+                           // 2 component loop (hardware sine/cosine), 3 component loop (sincospif)
   int batch_branches = 4; // parallel graph branches of the batched correlation (4: measured best of 1-16)
   int* dev_err = nullptr; // device-side status block: int status word, then (byte 8) the wait budget in ns
   int precision = EXT_PREC_FP32;        // used where a call passes EXT_PREC_DEFAULT

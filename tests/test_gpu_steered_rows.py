@@ -2,12 +2,13 @@
 the component-loop kernel (1024, 2048: one row per block, the per-pixel
 inputs held in registers across the block's components), against the
 oracles at sampled pixels (every row, corners included), plus agreement of
-the three row-pass forms (staged lines, steering in the first stage's loads,
-component loop) with one another.
+the row-pass forms (staged lines, steering in the first stage's loads,
+component loop with hardware or sincospif phasors) with one another.
 
-Tolerances: the oracles' 1e-5 of the output scale.  The three row-pass forms
-compute the same FFT in FP32 with differently rounded phases; each lies
-within about 1.5e-6 of the oracle, so two of them agree within 5e-6 rel-L2."""
+Tolerances: the oracles' 1e-5 of the output scale.  The row-pass forms
+compute the same FFT in FP32 with differently rounded phases (the hardware
+sine and cosine within about 4e-7 absolute); each lies within about 1.5e-6
+of the oracle, so two of them agree within 5e-6 rel-L2."""
 import math
 
 import numpy as np
@@ -46,7 +47,8 @@ def rel_l2(a, b):
 
 def plan_with_form(ec, monkeypatch, form):
     """A plan whose steered row passes use form 0 (staged lines), 1 (steering
-    in the first stage's loads) or 2 (component loop, the default)."""
+    in the first stage's loads), 2 (component loop with the hardware sine and
+    cosine, the default) or 3 (component loop with sincospif)."""
     monkeypatch.setenv("EXT_STEER_MODE", str(form))
     p = ec.Plan(0)
     monkeypatch.delenv("EXT_STEER_MODE")
@@ -145,7 +147,7 @@ def test_row_pass_forms_agree(ec, monkeypatch):
     alpha = rng.uniform(0, 2 * math.pi, (h, w)).astype(np.float32)
     prob = synth.so2_conv_problem(seed=6, size=2048)
     results = []
-    for form in (0, 1, 2):
+    for form in (0, 1, 2, 3):
         plan = plan_with_form(ec, monkeypatch, form)
         r = {"scale": run_scale(ec, plan, img, s, c_scale, 24.0, 2)}
         out = torch.empty((3, h, w), dtype=torch.float32, device="cuda")
@@ -160,7 +162,7 @@ def test_row_pass_forms_agree(ec, monkeypatch):
         plan.close()
         results.append(r)
     for key in results[0]:
-        for form in (0, 1):
+        for form in (0, 1, 3):
             err = rel_l2(results[form][key], results[2][key])
             print(f"{key}: form {form} vs component loop rel-L2 {err:.2e}")
             assert err < FORMS_REL_L2
