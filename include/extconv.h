@@ -312,6 +312,13 @@ ext_status ext_batch_corr_so2(ext_plan plan, const ext_image_desc* imgs, int n, 
  *   mode 1: out_c = {H_c, s} * F / {1, s} * F                 (Eq. normalization)
  *   mode 2: out_c = {H_c / s^2, s} * F / {1 / s^2, s} * F     (unit-integral signal)
  * H, out: channels planes of h x w float32; s: h x w float32 scale field, > 0.
+ * Accuracy: FP32 transforms; each harmonic's phasor e^{-i w_k ln s} comes from
+ * an exact reduction of k ln s / log_period and the hardware sine and cosine
+ * (absolute error about 4e-7; the environment variable EXT_STEER_MODE=3 at
+ * plan creation selects sincospif, about 1e-7).  Against the FP64 definition
+ * the results stay within 1e-5 of the output scale (rel-L2 about 4e-6 on the
+ * 4096 x 4096 x 3, 24-harmonic workload).  The same holds for ext_conv_so2,
+ * ext_conv_so2_normalized and ext_conv_similarity.
  */
 ext_status ext_conv_scale(ext_plan plan, const float* H, int channels, int h, int w, const double* mellin_c, int n_h,
                           double log_period, double r_min, double r_max, double centre_tap, const float* s, int mode,
