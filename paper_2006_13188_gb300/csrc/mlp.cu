@@ -49,19 +49,41 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
   constexpr uint32_t IDESC = tc::make_idesc(GBM, BN);
   uint32_t phase = 0;
   const int nk = (K + GBK - 1) / GBK;
-  for (int kc = 0; kc < nk; ++kc) {
-    const int k0 = kc * GBK;
-    for (int q = tid; q < GBM * 8; q += 128) {
-      const int m = q >> 3, kp = q & 7, k = k0 + kp * 8;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (m0 + m < M && k < K) v = __ldg(reinterpret_cast<const uint4*>(A + (size_t)(m0 + m) * lda + k));
-      *reinterpret_cast<uint4*>(As + (m >> 3) * G_SBO + kp * 128 + (m & 7) * 16) = v;
+  // The K chunk's operand rows are loaded into registers all at once (every
+  // thread's loads in flight together), and the next chunk's while the
+  // tensor cores work on the current one.
+  constexpr int NA = GBM * 8 / 128, NB = (BN * 8 + 127) / 128;
+  uint4 va[NA], vb[NB];
+  auto load_chunk = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const int q = tid + i * 128;
+      const int m = q >> 3, k = k0 + (q & 7) * 8;
+      va[i] = (m0 + m < M && k < K) ? __ldg(reinterpret_cast<const uint4*>(A + (size_t)(m0 + m) * lda + k))
+                                    : make_uint4(0, 0, 0, 0);
     }
-    for (int q = tid; q < BN * 8; q += 128) {
-      const int n = q >> 3, kp = q & 7, k = k0 + kp * 8;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (n0 + n < N && k < K) v = __ldg(reinterpret_cast<const uint4*>(B + (size_t)(n0 + n) * ldb + k));
-      *reinterpret_cast<uint4*>(Bs + (n >> 3) * G_SBO + kp * 128 + (n & 7) * 16) = v;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int q = tid + i * 128;
+      const int n = q >> 3, k = k0 + (q & 7) * 8;
+      vb[i] = (q < BN * 8 && n0 + n < N && k < K)
+                  ? __ldg(reinterpret_cast<const uint4*>(B + (size_t)(n0 + n) * ldb + k))
+                  : make_uint4(0, 0, 0, 0);
+    }
+  };
+  if (nk > 0) load_chunk(0);
+  for (int kc = 0; kc < nk; ++kc) {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const int q = tid + i * 128;
+      const int m = q >> 3, kp = q & 7;
+      *reinterpret_cast<uint4*>(As + (m >> 3) * G_SBO + kp * 128 + (m & 7) * 16) = va[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int q = tid + i * 128;
+      const int n = q >> 3, kp = q & 7;
+      if (q < BN * 8) *reinterpret_cast<uint4*>(Bs + (n >> 3) * G_SBO + kp * 128 + (n & 7) * 16) = vb[i];
     }
     tc::fence_proxy_async();
     __syncthreads();
@@ -73,6 +95,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
                      tc::make_desc(tc::smem_u32(Bs) + s * 256, 128, G_SBO), IDESC, (kc > 0 || s > 0) ? 1u : 0u);
       tc::mma_commit(mbar_addr);
     }
+    if (kc + 1 < nk) load_chunk((kc + 1) * GBK);
     if (!tc::mbar_wait_bounded(mbar_addr, phase, G_WAIT_NS, err, EXT_ERR_TIMEOUT)) abort_flag = 1;
     phase ^= 1u;
     __syncthreads();
@@ -80,24 +103,45 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
   }
   if (!abort_flag) {
     tc::fence_after();
-    const int m = m0 + warp * 32 + (tid & 31);
+    const int lane = tid & 31;
+    const int mw = m0 + warp * 32;   // first row of this warp's TMEM lanes
+    // one output element: bias, ReLU, ReLU mask, FP32 and/or BF16 stores
+    auto emit = [&](int m, int n, float x) {
+      if (ep.bias) x += ep.bias[n];
+      if (ep.relu) x = fmaxf(x, 0.f);
+      if (ep.mask && !(__bfloat162float(ep.mask[(size_t)m * ep.ldm + n]) > 0.f)) x = 0.f;
+      if (ep.out_f32) ep.out_f32[ep.trans ? (size_t)n * ep.ldo + m : (size_t)m * ep.ldo + n] = x;
+      if (ep.out_bf16)
+        ep.out_bf16[ep.trans ? (size_t)n * ep.ldo16 + m : (size_t)m * ep.ldo16 + n] = __float2bfloat16_rn(x);
+    };
+    // row-major outputs go through a per-warp 32 x 32 transpose in shared
+    // memory, so that the lanes of a warp read the mask and store along a row
+    // (coalesced); transposed outputs are already coalesced with one lane per row
+    float* scratch = reinterpret_cast<float*>(Bs + BN * GBK * 2) + warp * 32 * 33;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
       float v[32];
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (m < M) {
+      if (ep.trans) {
+        const int m = mw + lane;
+        if (m < M) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int n = n0 + c0 + i;
-          if (c0 + i >= BN || n >= N) continue;
-          float x = v[i];
-          if (ep.bias) x += ep.bias[n];
-          if (ep.relu) x = fmaxf(x, 0.f);
-          if (ep.mask && !(__bfloat162float(ep.mask[(size_t)m * ep.ldm + n]) > 0.f)) x = 0.f;
-          if (ep.out_f32) ep.out_f32[ep.trans ? (size_t)n * ep.ldo + m : (size_t)m * ep.ldo + n] = x;
-          if (ep.out_bf16)
-            ep.out_bf16[ep.trans ? (size_t)n * ep.ldo16 + m : (size_t)m * ep.ldo16 + n] = __float2bfloat16_rn(x);
+          for (int i = 0; i < 32; ++i) {
+            const int n = n0 + c0 + i;
+            if (c0 + i < BN && n < N) emit(m, n, v[i]);
+          }
         }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) scratch[lane * 33 + i] = v[i];
+        __syncwarp();
+        const int n = n0 + c0 + lane;
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+          const int m = mw + r;
+          if (m < M && c0 + lane < BN && n < N) emit(m, n, scratch[r * 33 + lane]);
+        }
+        __syncwarp();
       }
     }
   }
