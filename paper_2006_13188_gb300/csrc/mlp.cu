@@ -136,12 +136,30 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
         for (int i = 0; i < 32; ++i) scratch[lane * 33 + i] = v[i];
         __syncwarp();
         const int n = n0 + c0 + lane;
-#pragma unroll 4
+        const bool col_ok = c0 + lane < BN && n < N;
+        // this lane's column of the warp's 32 rows: the bias once, the 32 mask
+        // entries all in flight together, then the stores
+        const float bn = (ep.bias && col_ok) ? ep.bias[n] : 0.f;
+        float xs[32];
+        __nv_bfloat16 mk[32];
+#pragma unroll
         for (int r = 0; r < 32; ++r) {
-          const int m = mw + r;
-          if (m < M && c0 + lane < BN && n < N) emit(m, n, scratch[r * 33 + lane]);
+          xs[r] = scratch[r * 33 + lane];
+          mk[r] = (ep.mask && col_ok && mw + r < M) ? ep.mask[(size_t)(mw + r) * ep.ldm + n] : __float2bfloat16_rn(1.f);
         }
         __syncwarp();
+        if (col_ok) {
+#pragma unroll
+          for (int r = 0; r < 32; ++r) {
+            const int m = mw + r;
+            if (m >= M) break;
+            float x = ep.bias ? xs[r] + bn : xs[r];
+            if (ep.relu) x = fmaxf(x, 0.f);
+            if (ep.mask && !(__bfloat162float(mk[r]) > 0.f)) x = 0.f;
+            if (ep.out_f32) ep.out_f32[(size_t)m * ep.ldo + n] = x;
+            if (ep.out_bf16) ep.out_bf16[(size_t)m * ep.ldo16 + n] = __float2bfloat16_rn(x);
+          }
+        }
       }
     }
   }
