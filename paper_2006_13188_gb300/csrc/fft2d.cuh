@@ -1657,7 +1657,9 @@ k_cols_inv_corr_tma(const __grid_constant__ CUtensorMap tmH, int w, int br, cons
       return c_mul(HS[e], SS[e]);
     };
     auto store = [&](int c, int v, float2 val) {
-      if (u0 + c < w) __stcs(dst + (size_t)v * w + u0 + c, val);   // streamed: not re-read by this kernel
+      // plain stores: the last components written are still in L2 when the
+      // inverse row pass, which takes the components in reverse, starts
+      if (u0 + c < w) dst[(size_t)v * w + u0 + c] = val;
     };
     constexpr RadixList L = factor_radices(N);
     constexpr int R0 = L.r[0];
@@ -1863,7 +1865,7 @@ k_rows_inv_components_pipe(const float2* __restrict__ Z, int h, int k0, int nk, 
   }
   __syncthreads();
   auto prefetch = [&](int item) {   // thread 0
-    const int kk = item / nblk, y0 = (item % nblk) * RL;
+    const int kk = nk - 1 - item / nblk, y0 = (item % nblk) * RL;   // last-written components first
     const int rows = (h - y0) < RL ? (h - y0) : RL;
     const uint32_t bytes = (uint32_t)rows * N * 8u;
     tc::fence_proxy_async();
@@ -1881,7 +1883,7 @@ k_rows_inv_components_pipe(const float2* __restrict__ Z, int h, int k0, int nk, 
     if (abort_flag) break;
     phase ^= 1u;
     pending = false;
-    const int kk = item / nblk, y0 = (item % nblk) * RL;
+    const int kk = nk - 1 - item / nblk, y0 = (item % nblk) * RL;   // last-written components first
     const int k = k0 + kk;
     float* re = G + (k == 0 ? 0 : (size_t)(2 * k - 1) * P);
     float* im = G + (size_t)(2 * k) * P;
