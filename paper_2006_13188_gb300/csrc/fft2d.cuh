@@ -701,40 +701,49 @@ k_rows_fwd_steered(const Steer sp, int h, float2* __restrict__ A, const float2* 
 }
 
 // --------------------------- steered forward row passes, component loop ---
-// One row per block, N / 16 threads, 16 elements per thread: the per-pixel
-// inputs of the row are read once into registers and every component of the
-// block's group is then steered from them and transformed (first radix-16
-// stage in registers, the other two stages ping-ponging between two
-// shared-memory rows, the last one writing straight to global memory), so the
-// loads and the stage-twiddle staging are paid once per row instead of once
-// per row and component, and each component needs two barriers.
+// RB rows per block (one for 1024 points and more, enough to make 128
+// threads for shorter rows), N / 16 threads per row, 16 elements per thread:
+// the per-pixel inputs of the rows are read once into registers and every
+// component of the block's group is then steered from them and transformed
+// (first radix-16 stage in registers, the other stages between two
+// shared-memory row buffers, the last one writing straight to global
+// memory), so the loads and the stage-twiddle staging are paid once per row
+// block instead of once per row block and component.  Three-stage lengths
+// take two barriers per component, two-stage lengths one (the two buffers
+// alternate between components).
 template <int N>
 struct HloopCfg {
   static constexpr RadixList L = factor_radices(N);
-  static constexpr int THREADS = N / 16;
+  static constexpr int TPL = N / 16;                                     // threads per row
+  static constexpr int RB = TPL >= 64 ? 1 : (TPL > 0 ? 128 / TPL : 1);   // rows per block
+  static constexpr int THREADS = RB * TPL;
   static constexpr int LS = ct_sidx_len(N);
-  static constexpr int SMEM = 2 * LS * 8 + N * 8;   // two padded rows + the stage twiddles
+  static constexpr int SMEM = 2 * RB * LS * 8 + N * 8;   // two buffers of RB padded rows + the stage twiddles
   static constexpr int MINB = THREADS > 0 && 512 / THREADS > 0 ? 512 / THREADS : 1;
-  static constexpr bool OK = L.cnt == 3 && L.r[0] == 16 && THREADS >= 64 && THREADS % 32 == 0 &&
-                             SMEM * MINB <= 220 * 1024;
+  static constexpr bool OK = (L.cnt == 3 || L.cnt == 2) && L.r[0] == 16 && N % 16 == 0 && THREADS >= 64 &&
+                             THREADS % 32 == 0 && SMEM * MINB <= 220 * 1024;
 };
 
-// Ping-pong Stockham stage: reads `in`, writes `out` (or, LAST, hands each
-// output to store(x, value)); no barrier inside.
-template <int N, int R, int NS, int THREADS, bool LAST, class Store>
-__device__ __forceinline__ void pp_stage(const float2* in, float2* out, const float2* __restrict__ tw,
+// Ping-pong Stockham stage over NL lines of pitch ls: reads `in`, writes
+// `out` (or, LAST, hands each output to store(line, x, value)); no barrier
+// inside.
+template <int N, int R, int NS, int NL, int THREADS, bool LAST, class Store>
+__device__ __forceinline__ void pp_stage(const float2* in, float2* out, int ls, const float2* __restrict__ tw,
                                          Store&& store) {
   constexpr int NB = N / R;
-  constexpr int S = (NB + THREADS - 1) / THREADS;
+  constexpr int TOTAL = NB * NL;
+  constexpr int S = (TOTAL + THREADS - 1) / THREADS;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    const int j = threadIdx.x + s * THREADS;
-    if (NB % THREADS == 0 || j < NB) {
+    const int it = threadIdx.x + s * THREADS;
+    if (TOTAL % THREADS == 0 || it < TOTAL) {
+      const int line = it / NB, j = it % NB;
       const int k = j % NS;
+      const float2* src = in + line * ls;
       float2 v[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float2 a = in[sidx(j + r * NB)];
+        float2 a = src[sidx(j + r * NB)];
         if (r > 0) a = c_mul(a, tw[r * NS - 1 + k]);
         v[r] = a;
       }
@@ -742,8 +751,8 @@ __device__ __forceinline__ void pp_stage(const float2* in, float2* out, const fl
       const int dst = (j / NS) * NS * R + k;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        if (LAST) store(dst + r * NS, v[r]);
-        else out[sidx(dst + r * NS)] = v[r];
+        if (LAST) store(line, dst + r * NS, v[r]);
+        else out[line * ls + sidx(dst + r * NS)] = v[r];
       }
     }
   }
@@ -815,42 +824,57 @@ struct HloopPhase {   // A_k = H e^{-i k alpha}; q = (H, alpha)
   }
 };
 
-// blockIdx.x = row, blockIdx.y = component group [c0, c1), c0 = blockIdx.y *
-// cpb; component c's plane is A + c h N.
+// blockIdx.x = row block (rows blockIdx.x RB ..), blockIdx.y = component
+// group [c0, c1), c0 = blockIdx.y * cpb; component c's plane is A + c h N.
 template <int N, class Steer>
 __global__ void __launch_bounds__(HloopCfg<N>::THREADS, HloopCfg<N>::MINB)
 k_rows_fwd_hloop(const Steer sp, int h, int ncomp, int cpb, float2* __restrict__ A, const float2* __restrict__ tw) {
   using HC = HloopCfg<N>;
   constexpr int T = HC::THREADS;
   constexpr int LS = HC::LS;
-  constexpr int R1 = HC::L.r[1], R2 = HC::L.r[2];
+  constexpr int RB = HC::RB;
+  constexpr int TPL = HC::TPL;
+  constexpr int NST = HC::L.cnt;
+  constexpr int R1 = HC::L.r[1];
   extern __shared__ float2 sm[];
   float2* X = sm;
-  float2* Y = sm + LS;
-  const float2* twl = stage_twiddles<N, 2 * LS>(sm, tw, T);
-  const int y = blockIdx.x;
+  float2* Y = sm + RB * LS;
+  const float2* twl = stage_twiddles<N, 2 * RB * LS>(sm, tw, T);
+  const int l = threadIdx.x / TPL, j = threadIdx.x % TPL;
+  const int yb = blockIdx.x * RB;
   const int c0 = blockIdx.y * cpb;
   const int c1 = min(ncomp, c0 + cpb);
-  const int j = threadIdx.x;
   typename Steer::Q q[16];
 #pragma unroll
-  for (int r = 0; r < 16; ++r) q[r] = sp.load((size_t)y * N + j + r * T);
-  auto nostore = [](int, float2) {};
+  for (int r = 0; r < 16; ++r) q[r] = yb + l < h ? sp.load((size_t)(yb + l) * N + j + r * TPL) : typename Steer::Q{};
+  auto nostore = [](int, int, float2) {};
   for (int c = c0; c < c1; ++c) {
     const auto cc = sp.comp(c);
     float2 v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = sp.at(cc, q[r]);
     dft<16, false>(v);
+    // two-stage lengths alternate the buffers between components
+    float2* B0 = (NST == 2 && ((c - c0) & 1)) ? Y : X;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) X[sidx(j * 16 + r)] = v[r];
-    __syncthreads();   // X complete (and, on the first pass, the stage twiddles)
-    pp_stage<N, R1, 16, T, false>(X, Y, twl, nostore);
-    __syncthreads();   // Y complete; X free for the next component
-    float2* out = A + (size_t)c * h * N + (size_t)y * N;
-    pp_stage<N, R2, 16 * R1, T, true>(Y, nullptr, twl, [&](int x, float2 v2) { out[x] = v2; });
-    // the next component writes X (read before the barrier above) and then Y
-    // (after its own first barrier, when every thread has finished this read)
+    for (int r = 0; r < 16; ++r) B0[l * LS + sidx(j * 16 + r)] = v[r];
+    __syncthreads();   // B0 complete (and, on the first pass, the stage twiddles)
+    float2* out = A + (size_t)c * h * N;
+    auto store = [&](int line, int x, float2 v2) {
+      if (yb + line < h) out[(size_t)(yb + line) * N + x] = v2;
+    };
+    if constexpr (NST == 3) {
+      constexpr int R2 = HC::L.r[2];
+      pp_stage<N, R1, 16, RB, T, false>(X, Y, LS, twl, nostore);
+      __syncthreads();   // Y complete; X free for the next component
+      pp_stage<N, R2, 16 * R1, RB, T, true>(Y, nullptr, LS, twl, store);
+      // the next component writes X (read before the barrier above) and then Y
+      // (after its own first barrier, when every thread has finished this read)
+    } else {
+      pp_stage<N, R1, 16, RB, T, true>(B0, nullptr, LS, twl, store);
+      // the next component writes the other buffer; this one is rewritten two
+      // components on, after a barrier that follows this read
+    }
   }
 }
 
@@ -2261,13 +2285,13 @@ static void launch_rows_fwd_steered(const Steer& sp, int h, int ncomp, float2* A
 // Component groups of the component-loop pass: the group count G minimises
 // waves(h G blocks) x (ceil(ncomp / G) + 1), a block taking about one
 // component's time for its loads and twiddle staging plus one per component.
-inline int hloop_groups(int h, int ncomp, int slots) {
+inline int hloop_groups(int nrb, int ncomp, int slots) {
   long long best = -1;
   int bg = 1;
   for (int g = 1; g <= ncomp; ++g) {
     const int cpb = (ncomp + g - 1) / g;
     if (g > 1 && (ncomp + cpb - 1) / cpb < g) continue;   // same split as a smaller g
-    const long long waves = ((long long)h * g + slots - 1) / slots;
+    const long long waves = ((long long)nrb * g + slots - 1) / slots;
     const long long cost = waves * (cpb + 1);
     if (best < 0 || cost < best) {
       best = cost;
@@ -2285,9 +2309,10 @@ static bool launch_rows_fwd_hloop(const Steer& sp, int h, int ncomp, float2* A, 
     return false;
   } else {
     if (!ext_set_smem(k_rows_fwd_hloop<N, Steer>, HC::SMEM)) return false;
-    const int g = hloop_groups(h, ncomp, sms * HC::MINB);
+    const int nrb = (h + HC::RB - 1) / HC::RB;
+    const int g = hloop_groups(nrb, ncomp, sms * HC::MINB);
     const int cpb = (ncomp + g - 1) / g;
-    dim3 grid(h, (ncomp + cpb - 1) / cpb);
+    dim3 grid(nrb, (ncomp + cpb - 1) / cpb);
     k_rows_fwd_hloop<N, Steer><<<grid, HC::THREADS, HC::SMEM, st>>>(sp, h, ncomp, cpb, A, tw);
     return true;
   }
