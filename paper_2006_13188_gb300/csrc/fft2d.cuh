@@ -983,13 +983,15 @@ k_rows_inv_real(const float2* __restrict__ Y, int h, float* __restrict__ out, co
   extern __shared__ float2 sm[];
   const float2* twl = stage_twiddles<N, C::CW * C::LS>(sm, tw, C::COL_THREADS);
   const int y0 = blockIdx.x * C::RL;
-  rows_load_complex<N>(sm, Y, y0, h);
-  __syncthreads();
-  row_fft<N, true>(sm, twl);
-  for_elems<C::RL * N, C::ROW_THREADS>([&](int i, int e) {
-    const int y = y0 + e / N;
-    if (y < h) out[(size_t)y * N + e % N] = sm[(e / N) * C::LS + sidx(e % N)].x;
-  });
+  // the first butterfly stage reads the rows straight from global memory and
+  // the last one writes the real parts straight back
+  auto load = [&](int l, int x) -> float2 {
+    return y0 + l < h ? Y[(size_t)(y0 + l) * N + x] : make_float2(0.f, 0.f);
+  };
+  auto store = [&](int l, int x, float2 v) {
+    if (y0 + l < h) out[(size_t)(y0 + l) * N + x] = v.x;
+  };
+  ct_fft_io<N, true, false, C::RL, C::ROW_THREADS>(sm, C::LS, 1, twl, load, store);
 }
 
 // --------------------------------------------------------- column passes ---
